@@ -1,0 +1,106 @@
+/*
+ * tde.h -- C ABI of the B300 (sm_103a) boundary-row divide-and-conquer solver for
+ * all eigenvalues of real symmetric tridiagonal matrices T = tridiag(e, d, e),
+ * in IEEE double precision.
+ *
+ * Method: the eigenvalue-only boundary-row D&C of arxiv 2605.26599 ("Reducing
+ * Internal State in Eigenvalue-Only Divide-and-Conquer Tridiagonal
+ * Eigensolvers").  T is torn at balanced cut points into a rank-one modification
+ * of two children (Eq. 1 / Eq. dc-split); each child keeps only its eigenvalues
+ * and the first and last rows of its eigenvector matrix (the boundary-row state,
+ * Eq. boundary-state); a merge forms diag(D) + rho z z^T from the child spectra and
+ * boundary rows (Eq. merge-problem), deflates it, solves the secular equation
+ * for every root, and propagates only the two boundary rows to the parent
+ * (Algorithm 1; Sec. 4.1).  The root merge solves roots only.
+ *
+ * Conventions shared by every entry point
+ *  - All array pointers are DEVICE pointers to float64 data unless a name ends
+ *    in _host.  Arrays are dense and contiguous, 8-byte aligned.  The caller owns
+ *    every buffer; no entry point allocates device memory.
+ *  - ws is caller-provided device workspace, 256-byte aligned, of at least the
+ *    size returned by the matching *_workspace query.  Its contents need no
+ *    initialisation and are clobbered.  Two calls that run concurrently must not
+ *    share a workspace.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Every compute entry point only enqueues work on that stream and returns
+ *    without synchronising; it performs no host<->device copy, so a call can be
+ *    captured into a CUDA graph.
+ *  - leaf is the largest leaf order of the split tree (1..64; 0 selects 32).
+ *  - Return value: TDE_OK, or a negative code for invalid arguments, a too-small
+ *    workspace or a failed launch (nothing has been enqueued for EINVAL/EWORKSPACE).
+ *    Numerical failures found on the device (no convergence, non-finite input)
+ *    are recorded in a status word inside ws and read with tde_get_info().
+ *  - d, e and offsets are read-only; outputs are written once per call.
+ */
+#ifndef TDE_H_
+#define TDE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TDE_OK = 0,
+  TDE_EINVAL = -1,      /* invalid argument (null pointer, negative size, bad leaf) */
+  TDE_ECUDA = -2,       /* a CUDA launch or API call failed */
+  TDE_EWORKSPACE = -3,  /* ws_bytes smaller than the workspace query */
+  TDE_ENOCONV = 1,      /* device: a leaf QL or secular iteration hit its cap */
+  TDE_ENONFINITE = 2,   /* device: d or e holds a NaN or an infinity */
+  TDE_ETIMEOUT = 3      /* device: a bounded wait gave up (reserved) */
+} tde_status;
+
+/* Bytes of workspace tde_eigvals needs for order n with the given leaf order.
+ * Host-only; O(n) (about 200 n bytes).  Defined by the O(n) boundary-row state
+ * contract of Sec. 3.3 / Sec. 4.2. */
+int tde_eigvals_workspace(int64_t n, int32_t leaf, size_t* bytes);
+
+/* All eigenvalues of one tridiagonal (Sec. 3.1 problem setting).
+ *   n       order, n >= 0 (n = 0 is a no-op)
+ *   d       [n]   diagonal
+ *   e       [n-1] off-diagonal (e[i] couples rows i and i+1); may be NULL if n <= 1
+ *   lambda  [n]   output, eigenvalues in ascending order
+ * Internally scales T by 1 / max|T|, sets negligible off-diagonals
+ * (|e_i| <= eps sqrt|d_i| sqrt|d_{i+1}|) to zero (Sec. 4.2 driver), solves the
+ * leaves by implicit QL keeping two eigenvector rows, and merges level by level. */
+int tde_eigvals(int64_t n, const double* d, const double* e, double* lambda, int32_t leaf,
+                void* ws, size_t ws_bytes, void* stream);
+
+/* Workspace for tde_eigvals_batched with the given packing (host offsets). */
+int tde_eigvals_batched_workspace(int64_t batch, const int64_t* offsets_host, int32_t leaf,
+                                  size_t* bytes);
+
+/* Eigenvalues of `batch` independent tridiagonals packed back to back (the
+ * level-synchronous schedule of Sec. 4.1 applied to a forest: every level of
+ * every tree runs in the same launches).
+ *   offsets_host [batch+1] host copy of the packing, offsets[0] = 0,
+ *                non-decreasing; matrix k owns rows offsets[k] .. offsets[k+1]-1
+ *   offsets_dev  [batch+1] the same values in device memory (int64)
+ *   d, e, lambda [offsets[batch]] packed; e[offsets[k+1]-1] is ignored
+ * The plan (tree shapes and launch sizes) is derived from offsets_host on the
+ * host; a CUDA graph captured from this call stays valid while the packing is
+ * unchanged. */
+int tde_eigvals_batched(int64_t batch, const int64_t* offsets_host, const int64_t* offsets_dev,
+                        const double* d, const double* e, double* lambda, int32_t leaf,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* Reads the device status word of a workspace used by a previous call on
+ * `stream` (synchronises that stream).  *info receives 0 or a positive
+ * tde_status code.  The word is reset at the start of every compute call. */
+int tde_get_info(const void* ws, void* stream, int32_t* info);
+
+/* Measured FP64 fused multiply-add throughput of the current device, in FMA
+ * instructions per second (every lane of every warp issuing independent
+ * chains); the denominator of the solver's FP64 roofline.  Blocks the host for
+ * about 50 ms.  Returns TDE_OK and writes *fma_per_s. */
+int tde_measure_fp64_peak(double* fma_per_s);
+
+/* Number of kernel launches the last compute call on this thread enqueued. */
+int64_t tde_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDE_H_ */

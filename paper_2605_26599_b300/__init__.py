@@ -1,0 +1,163 @@
+"""paper_2605_26599_b300 -- a B300 (sm_103a) boundary-row divide-and-conquer solver
+for all eigenvalues of real symmetric tridiagonal matrices, in FP64.
+
+The computation lives in ``libtde.so`` (hand-written CUDA kernels behind the C ABI
+declared in ``include/tde.h``).  This module only marshals arguments: PyTorch
+supplies device memory and the current CUDA stream.  There is no CPU fallback --
+a missing library or a CPU tensor raises.
+
+    import torch, paper_2605_26599_b300 as tde
+    lam = tde.eigvals(d, e)                    # one tridiagonal, d[n], e[n-1]
+    lam = tde.eigvals_batched(d, e, offsets)   # packed forest
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import TdeError  # noqa: F401
+
+__all__ = ["eigvals", "eigvals_batched", "workspace_bytes", "batched_workspace_bytes",
+           "get_info", "measure_fp64_peak", "last_launch_count", "TdeError", "Workspace"]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def workspace_bytes(n: int, leaf: int = 0) -> int:
+    """Device workspace bytes for one tridiagonal of order n."""
+    out = ctypes.c_size_t()
+    _lib.check("tde_eigvals_workspace", _lib.load().tde_eigvals_workspace(int(n), int(leaf),
+                                                                          ctypes.byref(out)))
+    return int(out.value)
+
+
+def _host_offsets(offsets) -> np.ndarray:
+    if hasattr(offsets, "detach"):
+        offsets = offsets.detach().cpu().numpy()
+    return np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+
+
+def batched_workspace_bytes(offsets, leaf: int = 0) -> int:
+    """Device workspace bytes for a packed batch (offsets: B+1 non-decreasing ints)."""
+    off = _host_offsets(offsets)
+    out = ctypes.c_size_t()
+    _lib.check("tde_eigvals_batched_workspace",
+               _lib.load().tde_eigvals_batched_workspace(off.shape[0] - 1, off.ctypes.data, int(leaf),
+                                                         ctypes.byref(out)))
+    return int(out.value)
+
+
+class Workspace:
+    """A reusable device workspace (a uint8 torch tensor, 256-byte aligned)."""
+
+    def __init__(self, nbytes: int, device="cuda"):
+        torch = _torch()
+        self.nbytes = int(nbytes)
+        self._buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device)
+        base = self._buf.data_ptr()
+        self.ptr = (base + 255) & ~255
+
+    def ensure(self, nbytes: int) -> "Workspace":
+        return self if nbytes <= self.nbytes else Workspace(nbytes, self._buf.device)
+
+
+def _check_tensor(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (the solver has no CPU path)")
+    if t.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def get_info(ws: Workspace, stream=None) -> int:
+    """Device status word of the last call that used ``ws`` (synchronises)."""
+    info = ctypes.c_int32()
+    _lib.check("tde_get_info", _lib.load().tde_get_info(ctypes.c_void_p(ws.ptr), _stream_ptr(stream),
+                                                        ctypes.byref(info)))
+    return int(info.value)
+
+
+def eigvals(d, e, leaf: int = 0, out=None, ws: Workspace | None = None, stream=None,
+            check: bool = True):
+    """All eigenvalues (ascending) of tridiag(e, d, e); d: [n], e: [n-1] (or [n], the
+    last entry ignored), float64 CUDA tensors.  With check=True the device status is
+    read back (one synchronisation) and a numerical failure raises TdeError."""
+    torch = _torch()
+    _check_tensor(d, "d")
+    n = d.shape[0]
+    if n > 1:
+        _check_tensor(e, "e")
+        if e.shape[0] < n - 1:
+            raise ValueError("e must hold at least n-1 entries")
+    lam = out if out is not None else torch.empty(n, dtype=torch.float64, device=d.device)
+    if n == 0:
+        return lam
+    need = workspace_bytes(n, leaf)
+    ws = Workspace(need, d.device) if ws is None else ws.ensure(need)
+    rc = _lib.load().tde_eigvals(n, ctypes.c_void_p(d.data_ptr()),
+                                 ctypes.c_void_p(e.data_ptr() if n > 1 else 0),
+                                 ctypes.c_void_p(lam.data_ptr()), int(leaf), ctypes.c_void_p(ws.ptr),
+                                 ws.nbytes, _stream_ptr(stream))
+    _lib.check("tde_eigvals", rc)
+    if check:
+        info = get_info(ws, stream)
+        if info != 0:
+            raise TdeError("tde_eigvals (device status)", info)
+    return lam
+
+
+def eigvals_batched(d, e, offsets, leaf: int = 0, out=None, ws: Workspace | None = None,
+                    stream=None, check: bool = True, offsets_dev=None):
+    """Eigenvalues of a packed batch: matrix k owns rows offsets[k]:offsets[k+1] of d,
+    e and of the result (each matrix's eigenvalues ascending).  ``offsets`` is a host
+    sequence (B+1); ``offsets_dev`` optionally the same values as a CUDA int64 tensor."""
+    torch = _torch()
+    off = _host_offsets(offsets)
+    _check_tensor(d, "d")
+    _check_tensor(e, "e")
+    total = int(off[-1])
+    if d.shape[0] < total or e.shape[0] < total - 1:
+        raise ValueError("d / e shorter than offsets[-1]")
+    lam = out if out is not None else torch.empty(total, dtype=torch.float64, device=d.device)
+    if total == 0:
+        return lam
+    if offsets_dev is None:
+        offsets_dev = torch.from_numpy(off).to(d.device)
+    need = batched_workspace_bytes(off, leaf)
+    ws = Workspace(need, d.device) if ws is None else ws.ensure(need)
+    rc = _lib.load().tde_eigvals_batched(
+        off.shape[0] - 1, off.ctypes.data, ctypes.c_void_p(offsets_dev.data_ptr()),
+        ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(e.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+        int(leaf), ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream))
+    _lib.check("tde_eigvals_batched", rc)
+    if check:
+        info = get_info(ws, stream)
+        if info != 0:
+            raise TdeError("tde_eigvals_batched (device status)", info)
+    return lam
+
+
+def measure_fp64_peak() -> float:
+    """Measured FP64 FMA instructions per second of the current device (all lanes)."""
+    out = ctypes.c_double()
+    _lib.check("tde_measure_fp64_peak", _lib.load().tde_measure_fp64_peak(ctypes.byref(out)))
+    return float(out.value)
+
+
+def last_launch_count() -> int:
+    """Kernel launches the last compute call on this thread enqueued."""
+    return int(_lib.load().tde_last_launch_count())

@@ -1,0 +1,194 @@
+// Internal declarations of the boundary-row D&C solver (sm_103a).
+//
+// Data layout in device memory (one workspace, sections 256-byte aligned; N = the
+// packed number of rows of all matrices):
+//   scaled inputs         ds, es                     2N doubles
+//   boundary-row state    LAM, BLO, BHI              3N doubles (Eq. boundary-state:
+//                         per node, eigenvalues ascending with the first / last
+//                         eigenvector row entry of each column)
+//   merge problem         D, Z, RLO, RHI             4N doubles (Eq. merge-problem,
+//                         sorted by D; RLO / RHI are the rows of diag(Q_L, Q_R))
+//   deflated problem      AD, AZ, ALO, AHI           4N doubles (active poles first,
+//                         then the deflated eigenvalues of the merge, both sorted)
+//   compact roots         TAU (N doubles) + ORG (N int32): lambda_j = AD[ORG] + TAU
+//                         (Sec. 4.1 compact root representation)
+//   maps                  SEG, ROOTMAP, SURV (N int32), PFLAG, RFLAG (N bytes)
+//   sort scratch          KEYA, KEYB (N uint64), IDXA, IDXB (N int32)
+//   plan                  merge and leaf descriptors, per-step merge state
+// Aliases once a buffer is dead within a level: LAMA (roots) -> D, ZHAT -> Z,
+// parent rows of active columns -> RLO / RHI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tde.h"
+
+namespace tde {
+
+constexpr int kMaxLeaf = 64;
+constexpr int kMaxSteps = 40;
+constexpr double kEps = 2.220446049250313e-16;  // DBL_EPSILON = 2^-52
+
+// One merge of the split tree: children [lo, mid) and [mid, hi) (global rows).
+struct Merge {
+  int32_t lo, mid, hi;
+  int32_t info;  // bits 0..30: matrix index; bit 31: root merge (roots only)
+};
+// One leaf [lo, hi) of matrix `mat`.  flags: 1 = torn at lo (d[lo] -= |e[lo-1]|),
+// 2 = torn at hi (d[hi-1] -= |e[hi-1]|), 4 = the leaf is the whole matrix.
+struct Leaf {
+  int32_t lo, hi, mat, flags;
+};
+// Per-merge state of the current step.
+struct MState {
+  int32_t K;     // active rank after deflation
+  int32_t base;  // first index of this merge's roots in ROOTMAP
+  double rho;    // rho' = 2 |beta|
+  double zsq;    // sum of active z^2
+  double pad;
+};
+
+constexpr uint32_t kRootBit = 0x80000000u;
+
+struct Status {
+  int32_t info;
+  int32_t pad[31];
+  uint32_t root_count[kMaxSteps];  // roots allocated per step
+};
+
+struct Workspace {
+  Status* status;
+  unsigned long long* sigma_bits;  // per matrix, max |T| as non-negative double bits
+  int64_t* offsets;                // device offsets (single-matrix calls write here)
+  double *ds, *es;
+  double *LAM, *BLO, *BHI;
+  double *D, *Z, *RLO, *RHI;
+  double *AD, *AZ, *ALO, *AHI;
+  double* TAU;
+  int32_t *ORG, *SEG, *ROOTMAP, *SURV;
+  uint8_t *PFLAG, *RFLAG;
+  unsigned long long *KEYA, *KEYB;
+  int32_t *IDXA, *IDXB;
+  Merge* merges;   // all steps back to back
+  Leaf* leaves;
+  MState* mstate;  // cmax entries, reused every step
+  int32_t* pfx;    // (steps + 1) x (batch + 1) plan prefix counts
+  size_t bytes;
+};
+
+// Host-side plan: depends only on the packing and the leaf order.
+struct Plan {
+  int64_t batch = 0;
+  int64_t nrows = 0;
+  int32_t leaf = 32;
+  int32_t steps = 0;
+  int64_t nleaves = 0;
+  int64_t nmerges = 0;
+  int64_t cmax = 0;
+  int64_t step_count[kMaxSteps] = {0};
+  int64_t step_base[kMaxSteps] = {0};
+  bool step_has_nonroot[kMaxSteps] = {false};
+};
+
+int build_plan(int64_t batch, const int64_t* offsets_host, int32_t leaf, Plan* plan);
+size_t carve_workspace(const Plan& plan, void* base, Workspace* ws);
+int run_solver(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev,
+               const double* d, const double* e, double* lambda, cudaStream_t stream);
+
+// ---- device helpers -------------------------------------------------------
+
+__device__ __forceinline__ void set_status(Status* st, int code) {
+  atomicCAS(&st->info, 0, code);
+}
+
+// Levels of a matrix of order n with leaves of order <= leaf: the smallest L with
+// ceil(n / 2^L) <= leaf (node (h, i) covers [floor(i n / 2^h), floor((i+1) n / 2^h))),
+// but never so deep that a leaf would be empty (2^L <= n); with leaf = 1 and n not
+// a power of two some leaves therefore hold two rows.
+__host__ __device__ inline int levels_of(int64_t n, int leaf) {
+  int L = 0;
+  while (((n + (int64_t(1) << L) - 1) >> L) > leaf && (int64_t(2) << L) <= n) ++L;
+  return L;
+}
+
+// Order-preserving map of a double to an unsigned key.
+__device__ __forceinline__ unsigned long long order_key(double x) {
+  unsigned long long b = __double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+  unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7fffffffffffffffull) : ~k;
+  return __longlong_as_double(b);
+}
+
+__device__ __forceinline__ double shfl_up_d(double v, int o) {
+  return __shfl_up_sync(0xffffffffu, v, o);
+}
+
+// Block-wide exclusive prefix sum of one int per thread; returns the total in
+// *total.  All threads of the block must call it.  sm: NT/32 ints.
+template <int NT>
+__device__ __forceinline__ int block_excl_scan(int v, int* sm, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < NT / 32) ? sm[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) sm[lane] = w;
+  }
+  __syncthreads();
+  int before = (warp > 0) ? sm[warp - 1] : 0;
+  *total = sm[NT / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  double r = sm[0];
+  for (int w = 1; w < NT / 32; ++w) r = fmax(r, sm[w]);
+  __syncthreads();
+  return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  double r = sm[0];
+  for (int w = 1; w < NT / 32; ++w) r += sm[w];
+  __syncthreads();
+  return r;
+}
+
+// ---- launchers (defined in the .cu files) -----------------------------------
+void launch_plan(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev,
+                 cudaStream_t s);
+void launch_scale(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev,
+                  const double* d, const double* e, cudaStream_t s);
+void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s);
+void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda,
+                 cudaStream_t s);
+
+extern thread_local int64_t g_launches;
+
+}  // namespace tde

@@ -1,0 +1,139 @@
+// Leaf solver (Algorithm 1, leaf branch; Sec. 4.1 "solves leaf subproblems,
+// extracts only the first and last eigenvector rows"; Sec. 4.2 leaf DSTEQR('I')
+// keeping two rows).
+//
+// Each leaf is a torn diagonal block (Eq. dc-split: the diagonal entries next to
+// a cut are reduced by |beta|) of order m <= 64.  It is diagonalised by implicit
+// symmetric tridiagonal QR with a Wilkinson shift: every step chases a bulge from
+// the top of the unreduced block to its bottom with plane rotations G_i acting on
+// rows/columns (i, i+1) as T <- G_i^T T G_i.  The eigenvector matrix is
+// Q = G_1 G_2 ..., and by the selected-row lemma (Lemma "selected-row
+// multiplication") its first and last rows are obtained by applying the same
+// rotations to e_1^T and e_m^T only -- the leaf never forms Q.
+// One thread owns one leaf; the outputs are the eigenvalues in ascending order
+// with the matching first-row (blo) and last-row (bhi) entries.
+#include "tde_internal.cuh"
+
+namespace tde {
+
+// Implicit QR on a[0..m), b[0..m-1) (b[i] couples i and i+1), tracking the
+// first row r0 and last row r1 of the accumulated rotation product.
+// Returns false if an unreduced block needed more than 40 steps per row.
+__device__ bool leaf_qr_two_rows(int m, double* a, double* b, double* r0, double* r1) {
+  int hi = m - 1;
+  int steps = 0;
+  const int max_steps = 40 * m;
+  while (hi > 0) {
+    // unreduced block [lo, hi]: walk up while the coupling is not negligible
+    int lo = hi;
+    while (lo > 0) {
+      double c = b[lo - 1];
+      if (fabs(c) <= kEps * (fabs(a[lo - 1]) + fabs(a[lo]))) {
+        b[lo - 1] = 0.0;
+        break;
+      }
+      --lo;
+    }
+    if (lo == hi) {  // a[hi] has converged
+      --hi;
+      continue;
+    }
+    if (++steps > max_steps) return false;
+    // Wilkinson shift: eigenvalue of the trailing 2x2 closer to a[hi]
+    double bh = b[hi - 1];
+    double half = 0.5 * (a[hi - 1] - a[hi]);
+    double root = sqrt(half * half + bh * bh);
+    double mu = a[hi] - bh * bh / (half + (half >= 0.0 ? root : -root));
+    if (!isfinite(mu)) mu = a[hi];
+    // first rotation from the first column of T - mu I, then chase the bulge
+    double x = a[lo] - mu, y = b[lo];
+    for (int i = lo; i < hi; ++i) {
+      double r = sqrt(x * x + y * y);
+      double c = 1.0, s = 0.0;
+      if (r > 0.0) {
+        double inv = 1.0 / r;
+        c = x * inv;
+        s = y * inv;
+      }
+      if (i > lo) b[i - 1] = r;  // the bulge is annihilated into the coupling
+      double ai = a[i], aj = a[i + 1], bi = b[i];
+      double cc = c * c, ss = s * s, cs = c * s;
+      a[i] = cc * ai + 2.0 * cs * bi + ss * aj;
+      a[i + 1] = ss * ai - 2.0 * cs * bi + cc * aj;
+      b[i] = cs * (aj - ai) + (cc - ss) * bi;
+      if (i + 1 < hi) {
+        double bn = b[i + 1];
+        y = s * bn;  // new bulge at (i, i+2)
+        b[i + 1] = c * bn;
+        x = b[i];
+      }
+      // Q <- Q G_i on columns (i, i+1) for the two tracked rows
+      double p0 = r0[i], q0 = r0[i + 1];
+      r0[i] = c * p0 + s * q0;
+      r0[i + 1] = c * q0 - s * p0;
+      double p1 = r1[i], q1 = r1[i + 1];
+      r1[i] = c * p1 + s * q1;
+      r1[i + 1] = c * q1 - s * p1;
+    }
+  }
+  return true;
+}
+
+__global__ void k_leaves(const Leaf* __restrict__ leaves, int64_t nleaves,
+                         const double* __restrict__ ds, const double* __restrict__ es,
+                         const unsigned long long* __restrict__ sigma_bits, double* LAM,
+                         double* BLO, double* BHI, double* out, Status* st) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < nleaves;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const Leaf lf = leaves[t];
+    const int m = lf.hi - lf.lo;
+    double a[kMaxLeaf], b[kMaxLeaf], r0[kMaxLeaf], r1[kMaxLeaf];
+    for (int j = 0; j < m; ++j) {
+      a[j] = ds[lf.lo + j];
+      b[j] = (j + 1 < m) ? es[lf.lo + j] : 0.0;
+      r0[j] = (j == 0) ? 1.0 : 0.0;
+      r1[j] = (j == m - 1) ? 1.0 : 0.0;
+    }
+    // Cuppen tearing (Eq. 1): T = diag(T_L, T_R) + |beta| u u^T, u = e_last + sgn(beta) e_first
+    if (lf.flags & 1) a[0] -= fabs(es[lf.lo - 1]);
+    if (lf.flags & 2) a[m - 1] -= fabs(es[lf.hi - 1]);
+    if (!leaf_qr_two_rows(m, a, b, r0, r1)) set_status(st, TDE_ENOCONV);
+    // ascending order, rows follow their eigenvalue (insertion sort, m <= 64)
+    for (int j = 1; j < m; ++j) {
+      double v = a[j], p = r0[j], q = r1[j];
+      int i = j - 1;
+      while (i >= 0 && a[i] > v) {
+        a[i + 1] = a[i];
+        r0[i + 1] = r0[i];
+        r1[i + 1] = r1[i];
+        --i;
+      }
+      a[i + 1] = v;
+      r0[i + 1] = p;
+      r1[i + 1] = q;
+    }
+    if (lf.flags & 4) {
+      double s = __longlong_as_double((long long)sigma_bits[lf.mat]);
+      int ex = (s > 0.0 && isfinite(s)) ? ilogb(s) : 0;
+      for (int j = 0; j < m; ++j) out[lf.lo + j] = ldexp(a[j], ex);
+    } else {
+      for (int j = 0; j < m; ++j) {
+        LAM[lf.lo + j] = a[j];
+        BLO[lf.lo + j] = r0[j];
+        BHI[lf.lo + j] = r1[j];
+      }
+    }
+  }
+}
+
+void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s) {
+  if (plan.nleaves == 0) return;
+  int block = 64;
+  int64_t grid = (plan.nleaves + block - 1) / block;
+  if (grid > 148 * 32) grid = 148 * 32;
+  k_leaves<<<int(grid), block, 0, s>>>(ws.leaves, plan.nleaves, ws.ds, ws.es, ws.sigma_bits,
+                                       ws.LAM, ws.BLO, ws.BHI, lambda, ws.status);
+  g_launches += 1;
+}
+
+}  // namespace tde

@@ -1,0 +1,827 @@
+// One merge level of the boundary-row D&C (Algorithm 1, internal-node branch;
+// Sec. 4.1 GPU implementation).  Every kernel covers all merges of one step.
+//
+//   k_form     D = Lambda_L (+) Lambda_R by a merge of the two sorted child
+//              spectra; z = concat(bhi(Q_L), s blo(Q_R)) / sqrt(2), rho' = 2|beta|
+//              (Eq. merge-problem, Lemma "boundary sufficiency"); the rows of
+//              diag(Q_L, Q_R) that feed the parent's boundary rows are
+//              RLO = [blo(Q_L), 0] and RHI = [0, bhi(Q_R)].
+//   k_deflate  deflation (Sec. 4.1: negligible z, close poles, Givens rotations on
+//              z and on the two rows, compaction, active / deflated maps; the
+//              rotations and permutations commute with row selection by the
+//              appendix lemmas on column permutations and local rotations).
+//   k_secular  the K roots of 1 + rho' sum z_i^2 / (D_i - lambda) (Sec. 4.1 root
+//              solve), each stored compactly as lambda_j = D_org + tau_j
+//              (Sec. 4.1 compact root representation; appendix "compact delta
+//              reconstruction": Delta_i = (D_i - D_org) - tau).
+//   k_lowner   z-hat from the computed roots (appendix "WPROD product chains"):
+//              zhat_i^2 = prod_j (lambda_j - D_i) / (rho' prod_{j!=i} (D_j - D_i)),
+//              evaluated as a product of positive ratios.
+//   k_rows     parent boundary rows of each active column j (Sec. 4.1,
+//              R_parent(:, j) = R_child y_j with y_j(i) = zhat_i / Delta_ij
+//              normalised): two streamed dot products per root, no Y formed.
+//   k_place    the parent's eigenvalues in ascending order (active roots merged
+//              with the deflated eigenvalues), with their boundary rows; at a
+//              root merge only the eigenvalues, unscaled, into the output.
+#include <algorithm>
+
+#include "tde_internal.cuh"
+
+namespace tde {
+
+constexpr int kNT = 256;  // threads of the per-merge deflation block
+
+__device__ __forceinline__ int64_t find_merge(const Merge* M, int64_t cnt, int64_t p) {
+  int64_t lo = 0, hi = cnt;  // M[lo].lo <= p
+  while (hi - lo > 1) {
+    int64_t m = (lo + hi) >> 1;
+    if (M[m].lo <= p)
+      lo = m;
+    else
+      hi = m;
+  }
+  return lo;
+}
+
+// number of entries of the ascending array a[0..n) strictly below x
+__device__ __forceinline__ int count_less(const double* a, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (a[m] < x)
+      lo = m + 1;
+    else
+      hi = m;
+  }
+  return lo;
+}
+// number of entries of the ascending array a[0..n) less than or equal to x
+__device__ __forceinline__ int count_leq(const double* a, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (a[m] <= x)
+      lo = m + 1;
+    else
+      hi = m;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_form(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
+                       const double* __restrict__ LAM, const double* __restrict__ BLO,
+                       const double* __restrict__ BHI, const double* __restrict__ es, double* D,
+                       double* Z, double* RLO, double* RHI) {
+  const double inv_sqrt2 = 0.70710678118654752440;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < nrows;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const Merge m = M[find_merge(M, cnt, p)];
+    if (p < m.lo || p >= m.hi) continue;
+    const double beta = es[m.mid - 1];
+    const double sgn = beta >= 0.0 ? 1.0 : -1.0;
+    const double x = LAM[p];
+    if (p < m.mid) {
+      int out = m.lo + int(p - m.lo) + count_less(LAM + m.mid, m.hi - m.mid, x);
+      D[out] = x;
+      Z[out] = BHI[p] * inv_sqrt2;
+      RLO[out] = BLO[p];
+      RHI[out] = 0.0;
+    } else {
+      int out = m.lo + int(p - m.mid) + count_leq(LAM + m.lo, m.mid - m.lo, x);
+      D[out] = x;
+      Z[out] = sgn * BLO[p] * inv_sqrt2;
+      RLO[out] = 0.0;
+      RHI[out] = BHI[p];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Close-pole rotations as prefix sums.  Rotating a pole (D_p, z_p) against
+// (D_j, z_j) so that the z-direction keeps all of z leaves a kept pole
+// (w_p D_p + w_j D_j) / (w_p + w_j) with z = sqrt(w_p + w_j), w = z^2, and a
+// deflated pole (w_j D_p + w_p D_j) / (w_p + w_j); the dropped coupling is
+// z_p z_j (D_p - D_j) / (w_p + w_j).  Chaining rotations along a run a..k of
+// consecutive survivors therefore keeps the run's z^2-weighted mean and total
+// weight W, and the kept column of the rows is U / sqrt(W) with U = sum z R.
+// A survivor j continues the run (is rotated into it) iff the dropped coupling
+// is at most tol:  |sqrt(W) z_j (D_j - c)| <= tol (W + w_j), c = DW / W, which
+// is tested squared: w_j (W D_j - DW)^2 <= tol^2 W (W + w_j)^2.
+__device__ __forceinline__ bool continues_run(double W, double DW, double Dj, double wj,
+                                              double tol2) {
+  double a = fma(W, Dj, -DW);
+  double s = W + wj;
+  return wj * a * a <= tol2 * W * s * s;
+}
+
+struct T4 {
+  double w, dw, ulo, uhi;
+};
+__device__ __forceinline__ T4 t4_add(const T4& a, const T4& b) {
+  return T4{a.w + b.w, a.dw + b.dw, a.ulo + b.ulo, a.uhi + b.uhi};
+}
+__device__ __forceinline__ T4 t4_shfl_up(const T4& v, int o) {
+  return T4{shfl_up_d(v.w, o), shfl_up_d(v.dw, o), shfl_up_d(v.ulo, o), shfl_up_d(v.uhi, o)};
+}
+
+// Run boundaries of the survivor list (one warp).  The sequential rule -- walk the
+// survivors in ascending order and let each one join the current run if the test
+// passes -- is evaluated 32 survivors at a time: every lane first assumes the
+// run of its predecessor is that predecessor alone, the assumed runs are summed
+// with a segmented scan, the test is re-evaluated against them, and the first
+// lane whose decision changes is fixed; lanes before it are already exact.
+// RFLAG[k] = 1 iff survivor k starts a run.
+__device__ void run_boundaries(int S, const int32_t* surv, const double* D, const double* Z,
+                               double tol2, uint8_t* rflag) {
+  const int lane = threadIdx.x & 31;
+  double cW = 0.0, cDW = 0.0;
+  for (int base = 0; base < S; base += 32) {
+    const int k = base + lane;
+    const bool valid = k < S;
+    double Dk = 0.0, wk = 0.0;
+    if (valid) {
+      int pos = surv[k];
+      Dk = D[pos];
+      double zk = Z[pos];
+      wk = zk * zk;
+    }
+    const double Dp = shfl_up_d(Dk, 1), wp = shfl_up_d(wk, 1);
+    bool guess;
+    if (lane == 0)
+      guess = valid && base > 0 && continues_run(cW, cDW, Dk, wk, tol2);
+    else
+      guess = valid && continues_run(wp, Dp * wp, Dk, wk, tol2);
+    int start = 0;
+    double W = 0.0, DWv = 0.0;
+    for (int iter = 0; iter <= 32; ++iter) {
+      W = wk;
+      DWv = Dk * wk;
+      if (lane == 0 && guess) {
+        W += cW;
+        DWv += cDW;
+      }
+      bool h = !guess;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        double Wo = shfl_up_d(W, o), DWo = shfl_up_d(DWv, o);
+        bool ho = __shfl_up_sync(0xffffffffu, h, o);
+        if (lane >= o) {
+          if (!h) {
+            W += Wo;
+            DWv += DWo;
+          }
+          h = h || ho;
+        }
+      }
+      const double Wpre = shfl_up_d(W, 1), DWpre = shfl_up_d(DWv, 1);
+      bool truth = guess;
+      if (lane > 0) truth = valid && continues_run(Wpre, DWpre, Dk, wk, tol2);
+      unsigned mis = __ballot_sync(0xffffffffu, valid && lane >= start && truth != guess);
+      if (mis == 0) break;
+      int f = __ffs(mis) - 1;
+      if (lane == f) guess = truth;
+      start = f + 1;
+    }
+    if (valid) rflag[k] = guess ? 0 : 1;
+    int last = min(31, S - 1 - base);
+    cW = __shfl_sync(0xffffffffu, W, last);
+    cDW = __shfl_sync(0xffffffffu, DWv, last);
+  }
+}
+
+// Block merge sort of keys (with int payload) in global scratch; n entries.
+// Tiles of kTile are sorted in shared memory (bitonic), then merged pairwise.
+// Returns a pointer to the buffer (A or B) holding the result.
+constexpr int kTile = 2048;
+__device__ int block_sort(int n, unsigned long long* KA, int32_t* IA, unsigned long long* KB,
+                          int32_t* IB, unsigned long long* skey, int32_t* sidx) {
+  for (int t0 = 0; t0 < n; t0 += kTile) {
+    int len = min(kTile, n - t0);
+    int p2 = 1;
+    while (p2 < len) p2 <<= 1;
+    for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+      skey[i] = (i < len) ? KA[t0 + i] : ~0ull;
+      sidx[i] = (i < len) ? IA[t0 + i] : -1;
+    }
+    __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+          int j = i ^ stride;
+          if (j > i) {
+            bool up = (i & size) == 0;
+            unsigned long long ki = skey[i], kj = skey[j];
+            if ((ki > kj) == up) {
+              skey[i] = kj;
+              skey[j] = ki;
+              int32_t x = sidx[i];
+              sidx[i] = sidx[j];
+              sidx[j] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      KA[t0 + i] = skey[i];
+      IA[t0 + i] = sidx[i];
+    }
+    __syncthreads();
+  }
+  int which = 0;
+  unsigned long long *src_k = KA, *dst_k = KB;
+  int32_t *src_i = IA, *dst_i = IB;
+  for (int width = kTile; width < n; width <<= 1) {
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+      int run = e / width;
+      int run_lo = run * width;
+      int pair_lo = (run & ~1) * width;
+      int partner_lo = (run & 1) ? pair_lo : pair_lo + width;
+      int partner_len = max(0, min(width, n - partner_lo));
+      unsigned long long key = src_k[e];
+      int lo = 0, hi = partner_len;
+      if (run & 1) {  // right run: partner entries <= key come first
+        while (lo < hi) {
+          int m = (lo + hi) >> 1;
+          if (src_k[partner_lo + m] <= key) lo = m + 1; else hi = m;
+        }
+      } else {  // left run: partner entries < key come first
+        while (lo < hi) {
+          int m = (lo + hi) >> 1;
+          if (src_k[partner_lo + m] < key) lo = m + 1; else hi = m;
+        }
+      }
+      int dst = pair_lo + (e - run_lo) + lo;
+      dst_k[dst] = key;
+      dst_i[dst] = src_i[e];
+    }
+    __syncthreads();
+    unsigned long long* tk = src_k;
+    src_k = dst_k;
+    dst_k = tk;
+    int32_t* ti = src_i;
+    src_i = dst_i;
+    dst_i = ti;
+    which ^= 1;
+  }
+  return which;
+}
+
+struct DeflateArgs {
+  const Merge* M;
+  int64_t cnt;
+  int step;
+  const double* es;
+  double *D, *Z, *RLO, *RHI;
+  double *AD, *AZ, *ALO, *AHI;
+  int32_t *SURV, *ROOTMAP, *IDXA, *IDXB;
+  uint8_t *PFLAG, *RFLAG;
+  unsigned long long *KEYA, *KEYB;
+  MState* ms;
+  Status* st;
+};
+
+__global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
+  __shared__ int sm_int[kNT / 32];
+  __shared__ double sm_dbl[kNT / 32];
+  __shared__ T4 s_agg[kNT / 32];
+  __shared__ int s_aggh[kNT / 32];
+  __shared__ T4 s_pre[kNT / 32];
+  __shared__ T4 s_incl[kNT];
+  __shared__ unsigned long long s_key[kTile];
+  __shared__ int32_t s_idx[kTile];
+  __shared__ int s_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  for (int64_t g = blockIdx.x; g < a.cnt; g += gridDim.x) {
+    const Merge m = a.M[g];
+    const int lo = m.lo, n0 = m.hi - m.lo;
+    const double rho = 2.0 * fabs(a.es[m.mid - 1]);
+    double* D = a.D + lo;
+    double* Z = a.Z + lo;
+    double* RLO = a.RLO + lo;
+    double* RHI = a.RHI + lo;
+    uint8_t* PFLAG = a.PFLAG + lo;
+    int32_t* SURV = a.SURV + lo;
+    uint8_t* RFLAG = a.RFLAG + lo;
+
+    // 1. tol = 8 eps max(max|D|, max|z|)   (D is sorted)
+    double zm = 0.0;
+    for (int i = tid; i < n0; i += kNT) zm = fmax(zm, fabs(Z[i]));
+    zm = block_max<kNT>(zm, sm_dbl);
+    const double dmax = fmax(fabs(D[0]), fabs(D[n0 - 1]));
+    const double tol = 8.0 * kEps * fmax(dmax, zm);
+    const double tol2 = tol * tol;
+
+    // 2. negligible z: rho' |z_i| <= tol deflates pole i with its rows unchanged
+    int S = 0;
+    for (int c0 = 0; c0 < n0; c0 += kNT) {
+      int i = c0 + tid;
+      int keep = 0;
+      if (i < n0) {
+        keep = rho * fabs(Z[i]) > tol ? 1 : 0;
+        PFLAG[i] = keep ? 0 : 1;
+      }
+      int total;
+      int ex = block_excl_scan<kNT>(keep, sm_int, &total);
+      if (keep) SURV[S + ex] = lo + i;
+      S += total;
+    }
+    __syncthreads();
+
+    // 3. close poles: run boundaries over the survivors (warp 0)
+    if (warp == 0) run_boundaries(S, SURV, a.D, a.Z, tol2, RFLAG);
+    __syncthreads();
+
+    // 4. emit: continuing survivors deflate in place, run ends become active poles
+    T4 carry{0.0, 0.0, 0.0, 0.0};
+    int K = 0;
+    double zsq = 0.0;
+    for (int c0 = 0; c0 < S; c0 += kNT) {
+      const int k = c0 + tid;
+      const bool valid = k < S;
+      int pos = 0;
+      bool head = true;
+      double Dk = 0.0, zk = 0.0, rl = 0.0, rh = 0.0;
+      T4 own{0.0, 0.0, 0.0, 0.0};
+      if (valid) {
+        pos = SURV[k] - lo;
+        head = RFLAG[k] != 0;
+        Dk = D[pos];
+        zk = Z[pos];
+        rl = RLO[pos];
+        rh = RHI[pos];
+        double wk = zk * zk;
+        own = T4{wk, Dk * wk, zk * rl, zk * rh};
+      }
+      // block segmented inclusive scan with carry-in
+      T4 v = own;
+      bool h = head;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        T4 vo = t4_shfl_up(v, o);
+        bool ho = __shfl_up_sync(0xffffffffu, h, o);
+        if (lane >= o) {
+          if (!h) v = t4_add(v, vo);
+          h = h || ho;
+        }
+      }
+      if (lane == 31) {
+        s_agg[warp] = v;
+        s_aggh[warp] = h ? 1 : 0;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        T4 run = carry;
+        for (int w = 0; w < kNT / 32; ++w) {
+          s_pre[w] = run;
+          run = s_aggh[w] ? s_agg[w] : t4_add(run, s_agg[w]);
+        }
+      }
+      __syncthreads();
+      if (!h) v = t4_add(v, s_pre[warp]);
+      s_incl[tid] = v;
+      __syncthreads();
+      const T4 prev = (tid > 0) ? s_incl[tid - 1] : carry;
+      bool runend = false;
+      if (valid) runend = (k == S - 1) || RFLAG[k + 1] != 0;
+      int ex_total;
+      int act = block_excl_scan<kNT>(runend ? 1 : 0, sm_int, &ex_total);
+      double zact2 = 0.0;
+      if (valid && !head) {
+        // deflated by rotation against the run prefix `prev`
+        double Wp = prev.w, wk = own.w;
+        double c = prev.dw / Wp;
+        double val = (wk * c + Wp * Dk) / (Wp + wk);
+        double sc = 1.0 / sqrt(Wp * (Wp + wk));
+        D[pos] = val;
+        RLO[pos] = (zk * prev.ulo - Wp * rl) * sc;
+        RHI[pos] = (zk * prev.uhi - Wp * rh) * sc;
+        PFLAG[pos] = 1;
+      }
+      if (valid && runend) {
+        double ad, az, al, ah;
+        if (head) {
+          ad = Dk;
+          az = zk;
+          al = rl;
+          ah = rh;
+        } else {
+          double W = v.w;
+          az = sqrt(W);
+          ad = v.dw / W;
+          double inv = 1.0 / az;
+          al = v.ulo * inv;
+          ah = v.uhi * inv;
+        }
+        int idx = lo + K + act;
+        a.AD[idx] = ad;
+        a.AZ[idx] = az;
+        a.ALO[idx] = al;
+        a.AHI[idx] = ah;
+        zact2 = az * az;
+      }
+      zsq += block_sum<kNT>(zact2, sm_dbl);
+      K += ex_total;
+      // carry: inclusive value of the last survivor of this chunk
+      int last = min(kNT - 1, S - 1 - c0);
+      carry = s_incl[last];
+      __syncthreads();
+    }
+
+    // 5. deflated eigenvalues in position order after the active poles
+    const int F = n0 - K;
+    int f = 0;
+    for (int c0 = 0; c0 < n0; c0 += kNT) {
+      int i = c0 + tid;
+      int is = (i < n0 && PFLAG[i]) ? 1 : 0;
+      int total;
+      int ex = block_excl_scan<kNT>(is, sm_int, &total);
+      if (is) {
+        int dst = lo + K + f + ex;
+        a.AD[dst] = D[i];
+        a.ALO[dst] = RLO[i];
+        a.AHI[dst] = RHI[i];
+      }
+      f += total;
+    }
+    if (tid == 0) s_flag = 0;
+    __syncthreads();
+    // 6. rotations can leave the deflated list out of order: sort it if so
+    for (int i = tid; i + 1 < F; i += kNT)
+      if (a.AD[lo + K + i] > a.AD[lo + K + i + 1]) s_flag = 1;
+    __syncthreads();
+    if (s_flag) {
+      double* FD = a.AD + lo + K;
+      double* FL = a.ALO + lo + K;
+      double* FH = a.AHI + lo + K;
+      for (int i = tid; i < F; i += kNT) {
+        a.KEYA[lo + i] = order_key(FD[i]);
+        a.IDXA[lo + i] = i;
+      }
+      __syncthreads();
+      int which = block_sort(F, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);
+      const int32_t* I = which ? a.IDXB + lo : a.IDXA + lo;
+      for (int i = tid; i < F; i += kNT) {  // gather into dead scratch, copy back
+        int s = I[i];
+        D[i] = FD[s];
+        RLO[i] = FL[s];
+        RHI[i] = FH[s];
+      }
+      __syncthreads();
+      for (int i = tid; i < F; i += kNT) {
+        FD[i] = D[i];
+        FL[i] = RLO[i];
+        FH[i] = RHI[i];
+      }
+    }
+    __syncthreads();
+    // 7. roots of this merge get a contiguous range of the step's root list
+    __shared__ int s_base;
+    if (tid == 0) {
+      s_base = K > 0 ? int(atomicAdd(&a.st->root_count[a.step], unsigned(K))) : 0;
+      MState st;
+      st.K = K;
+      st.base = s_base;
+      st.rho = rho;
+      st.zsq = zsq;
+      st.pad = 0.0;
+      a.ms[g] = st;
+    }
+    __syncthreads();
+    for (int j = tid; j < K; j += kNT) a.ROOTMAP[s_base + j] = int32_t(g);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Secular equation.  For root j (0-based) of the active problem with sorted
+// distinct poles D and nonzero z, w(lambda) = 1/rho' + sum_i z_i^2 / (D_i - lambda)
+// has one root in (D_j, D_{j+1}) for j < K-1 and one in (D_{K-1}, D_{K-1} + rho' zsq)
+// for the last root.  In shifted coordinates lambda = D_org + tau with
+// Delta_i = (D_i - D_org) - tau the two poles that bracket the root keep full
+// relative accuracy.
+//
+// Iteration: evaluate w and its derivative split into the poles on the left of
+// the root (psi: i <= jl) and on the right (phi: i > jl), then take the root of the
+// two-pole rational model C + S1 / (Delta_jl - eta) + S2 / (Delta_jr - eta) that
+// matches w and w' (S1 = Delta_jl^2 psi', S2 = Delta_jr^2 phi'), kept inside a
+// bisection bracket.  The start is the midpoint of the interval, whose sign of w
+// also chooses the origin (the nearer pole).  Convergence: |w| below eps times a
+// running bound on the rounding error of its evaluation,
+// 8 (|psi| + |phi|) + 1/rho' + |tau| (psi' + phi').
+struct SecSums {
+  double psi, dpsi, phi, dphi;
+};
+
+__device__ __forceinline__ SecSums sec_sweep(const double* __restrict__ D,
+                                             const double* __restrict__ Z, int K, double dorg,
+                                             double tau, int jl) {
+  SecSums s{0.0, 0.0, 0.0, 0.0};
+  for (int i = 0; i < K; ++i) {
+    double zi = Z[i];
+    double delta = (D[i] - dorg) - tau;
+    double t = zi / delta;
+    double term = zi * t;
+    double dterm = t * t;
+    if (i <= jl) {
+      s.psi += term;
+      s.dpsi += dterm;
+    } else {
+      s.phi += term;
+      s.dphi += dterm;
+    }
+  }
+  return s;
+}
+
+// returns iterations used (negative if the cap was hit)
+__device__ int secular_root(const double* __restrict__ D, const double* __restrict__ Z, int K,
+                            int j, double rho, double zsq, int* org_out, double* tau_out) {
+  const double rhoinv = 1.0 / rho;
+  if (K == 1) {
+    *org_out = 0;
+    *tau_out = rho * Z[0] * Z[0];
+    return 0;
+  }
+  int org, jl, jr;
+  double tau, tlo, thi;
+  SecSums s;
+  double w;
+  if (j < K - 1) {
+    jl = j;
+    jr = j + 1;
+    const double gap = D[j + 1] - D[j];
+    const double half = 0.5 * gap;
+    s = sec_sweep(D, Z, K, D[j], half, jl);
+    w = rhoinv + s.psi + s.phi;
+    if (w >= 0.0) {
+      org = j;
+      tau = half;
+      tlo = 0.0;
+      thi = half;
+    } else {
+      org = j + 1;
+      tau = -half;
+      tlo = -half;
+      thi = 0.0;
+    }
+  } else {
+    jl = K - 2;
+    jr = K - 1;
+    org = K - 1;
+    const double upper = rho * zsq;
+    tau = 0.5 * upper;
+    s = sec_sweep(D, Z, K, D[org], tau, jl);
+    w = rhoinv + s.psi + s.phi;
+    if (w >= 0.0) {
+      tlo = 0.0;
+      thi = tau;
+    } else {
+      tlo = tau;
+      thi = upper;
+    }
+  }
+  const double dorg = D[org];
+  const double ol = D[jl] - dorg, orr = D[jr] - dorg;  // pole offsets from the origin
+  int it = 0;
+  const int max_it = 64;
+  for (; it < max_it; ++it) {
+    const double erretm = 8.0 * (fabs(s.psi) + fabs(s.phi)) + rhoinv + fabs(tau) * (s.dpsi + s.dphi);
+    if (fabs(w) <= kEps * erretm) break;
+    if (w > 0.0)
+      thi = fmin(thi, tau);
+    else
+      tlo = fmax(tlo, tau);
+    const double a = ol - tau, b = orr - tau;  // Delta of the two model poles
+    const double S1 = a * a * s.dpsi, S2 = b * b * s.dphi;
+    const double C = w - S1 / a - S2 / b;
+    const double A = C * (a + b) + S1 + S2;
+    const double Bq = a * b * w;
+    double eta = 0.0;
+    bool have = false;
+    if (C == 0.0) {
+      if (A != 0.0) {
+        eta = Bq / A;
+        have = true;
+      }
+    } else {
+      double disc = fmax(A * A - 4.0 * Bq * C, 0.0);
+      double sq = sqrt(disc);
+      double q = 0.5 * (A >= 0.0 ? A + sq : A - sq);
+      double r1 = q / C;
+      double r2 = (q != 0.0) ? Bq / q : r1;
+      bool ok1 = (tau + r1 > tlo) && (tau + r1 < thi);
+      bool ok2 = (tau + r2 > tlo) && (tau + r2 < thi);
+      if (ok1 && ok2) {
+        eta = fabs(r1) < fabs(r2) ? r1 : r2;
+        have = true;
+      } else if (ok1) {
+        eta = r1;
+        have = true;
+      } else if (ok2) {
+        eta = r2;
+        have = true;
+      }
+    }
+    double ntau = tau + eta;
+    if (!have || !(ntau > tlo && ntau < thi)) ntau = 0.5 * (tlo + thi);
+    if (ntau == tau) break;
+    tau = ntau;
+    s = sec_sweep(D, Z, K, dorg, tau, jl);
+    w = rhoinv + s.psi + s.phi;
+    if (thi - tlo <= 2.0 * kEps * fmax(fabs(tlo), fabs(thi))) break;
+  }
+  *org_out = org;
+  *tau_out = tau;
+  return it < max_it ? it + 1 : -1;
+}
+
+struct RootArgs {
+  const Merge* M;
+  const MState* ms;
+  const int32_t* ROOTMAP;
+  const uint32_t* count;
+  const double *AD, *AZ, *ALO, *AHI;
+  double* TAU;
+  int32_t* ORG;
+  double* LAMA;  // aliases D
+  double* ZHAT;  // aliases Z
+  double *ROWLO, *ROWHI;  // alias RLO, RHI
+  Status* st;
+};
+
+__global__ void k_secular(RootArgs a) {
+  const uint32_t total = *a.count;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
+    const int g = a.ROOTMAP[r];
+    const MState ms = a.ms[g];
+    const int j = int(r) - ms.base;
+    const int lo = a.M[g].lo;
+    int org;
+    double tau;
+    int it = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, &org, &tau);
+    if (it < 0) set_status(a.st, TDE_ENOCONV);
+    a.TAU[lo + j] = tau;
+    a.ORG[lo + j] = org;
+    a.LAMA[lo + j] = a.AD[lo + org] + tau;
+  }
+}
+
+__global__ void k_lowner(RootArgs a) {
+  const uint32_t total = *a.count;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
+    const int g = a.ROOTMAP[r];
+    const Merge m = a.M[g];
+    if (uint32_t(m.info) & kRootBit) continue;
+    const MState ms = a.ms[g];
+    const int K = ms.K, i = int(r) - ms.base, lo = m.lo;
+    const double* AD = a.AD + lo;
+    const int32_t* ORG = a.ORG + lo;
+    const double* TAU = a.TAU + lo;
+    const double Di = AD[i];
+    double prod = ((AD[ORG[K - 1]] - Di) + TAU[K - 1]) / ms.rho;
+    for (int j = 0; j < K - 1; ++j) {
+      double num = (AD[ORG[j]] - Di) + TAU[j];
+      double den = (j < i ? AD[j] : AD[j + 1]) - Di;
+      prod *= num / den;
+    }
+    a.ZHAT[lo + i] = copysign(sqrt(fmax(prod, 0.0)), a.AZ[lo + i]);
+  }
+}
+
+__global__ void k_rows(RootArgs a) {
+  const uint32_t total = *a.count;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
+    const int g = a.ROOTMAP[r];
+    const Merge m = a.M[g];
+    if (uint32_t(m.info) & kRootBit) continue;
+    const MState ms = a.ms[g];
+    const int K = ms.K, j = int(r) - ms.base, lo = m.lo;
+    const double* AD = a.AD + lo;
+    const double* ZH = a.ZHAT + lo;
+    const double* AL = a.ALO + lo;
+    const double* AH = a.AHI + lo;
+    const double dorg = AD[a.ORG[lo + j]];
+    const double tau = a.TAU[lo + j];
+    double s2 = 0.0, sl = 0.0, sh = 0.0;
+    for (int i = 0; i < K; ++i) {
+      double delta = (AD[i] - dorg) - tau;
+      double t = ZH[i] / delta;
+      s2 += t * t;
+      sl += AL[i] * t;
+      sh += AH[i] * t;
+    }
+    double inv = 1.0 / sqrt(s2);
+    a.ROWLO[lo + j] = sl * inv;
+    a.ROWHI[lo + j] = sh * inv;
+  }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_place(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
+                        const MState* __restrict__ ms, const double* __restrict__ LAMA,
+                        const double* __restrict__ ROWLO, const double* __restrict__ ROWHI,
+                        const double* __restrict__ AD, const double* __restrict__ ALO,
+                        const double* __restrict__ AHI,
+                        const unsigned long long* __restrict__ sigma_bits, double* LAM,
+                        double* BLO, double* BHI, double* out) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < nrows;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = find_merge(M, cnt, p);
+    const Merge m = M[g];
+    if (p < m.lo || p >= m.hi) continue;
+    const int K = ms[g].K, lo = m.lo, F = (m.hi - m.lo) - K;
+    const int local = int(p - lo);
+    double x, rl, rh;
+    int rank;
+    if (local < K) {
+      x = LAMA[p];
+      rank = local + count_less(AD + lo + K, F, x);
+      rl = ROWLO[p];
+      rh = ROWHI[p];
+    } else {
+      x = AD[p];
+      rank = (local - K) + count_leq(LAMA + lo, K, x);
+      rl = ALO[p];
+      rh = AHI[p];
+    }
+    const int dst = lo + rank;
+    if (uint32_t(m.info) & kRootBit) {
+      double s = __longlong_as_double((long long)sigma_bits[m.info & 0x7fffffff]);
+      int ex = (s > 0.0 && isfinite(s)) ? ilogb(s) : 0;
+      out[dst] = ldexp(x, ex);
+    } else {
+      LAM[dst] = x;
+      BLO[dst] = rl;
+      BHI[dst] = rh;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s) {
+  const Merge* M = ws.merges + plan.step_base[step];
+  const int64_t cnt = plan.step_count[step];
+  const int64_t nrows = plan.nrows;
+  const int flat_grid = int(std::min<int64_t>((nrows + 255) / 256, 148 * 8));
+  k_form<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.LAM, ws.BLO, ws.BHI, ws.es, ws.D, ws.Z,
+                                   ws.RLO, ws.RHI);
+  DeflateArgs da;
+  da.M = M;
+  da.cnt = cnt;
+  da.step = step;
+  da.es = ws.es;
+  da.D = ws.D;
+  da.Z = ws.Z;
+  da.RLO = ws.RLO;
+  da.RHI = ws.RHI;
+  da.AD = ws.AD;
+  da.AZ = ws.AZ;
+  da.ALO = ws.ALO;
+  da.AHI = ws.AHI;
+  da.SURV = ws.SURV;
+  da.ROOTMAP = ws.ROOTMAP;
+  da.IDXA = ws.IDXA;
+  da.IDXB = ws.IDXB;
+  da.PFLAG = ws.PFLAG;
+  da.RFLAG = ws.RFLAG;
+  da.KEYA = ws.KEYA;
+  da.KEYB = ws.KEYB;
+  da.ms = ws.mstate;
+  da.st = ws.status;
+  const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
+  k_deflate<<<def_grid, kNT, 0, s>>>(da);
+  RootArgs ra;
+  ra.M = M;
+  ra.ms = ws.mstate;
+  ra.ROOTMAP = ws.ROOTMAP;
+  ra.count = &ws.status->root_count[step];
+  ra.AD = ws.AD;
+  ra.AZ = ws.AZ;
+  ra.ALO = ws.ALO;
+  ra.AHI = ws.AHI;
+  ra.TAU = ws.TAU;
+  ra.ORG = ws.ORG;
+  ra.LAMA = ws.D;
+  ra.ZHAT = ws.Z;
+  ra.ROWLO = ws.RLO;
+  ra.ROWHI = ws.RHI;
+  ra.st = ws.status;
+  const int root_grid = int(std::min<int64_t>((nrows + 127) / 128, 148 * 8));
+  k_secular<<<root_grid, 128, 0, s>>>(ra);
+  int launches = 4;
+  if (plan.step_has_nonroot[step]) {
+    k_lowner<<<root_grid, 128, 0, s>>>(ra);
+    k_rows<<<root_grid, 128, 0, s>>>(ra);
+    launches += 2;
+  }
+  k_place<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.mstate, ws.D, ws.RLO, ws.RHI, ws.AD,
+                                    ws.ALO, ws.AHI, ws.sigma_bits, ws.LAM, ws.BLO, ws.BHI,
+                                    lambda);
+  g_launches += launches;
+}
+
+}  // namespace tde
