@@ -1,0 +1,419 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 boundary-row D&C tridiagonal eigensolver.
+
+Metric: FP64 tridiagonal eigenvalues per second at n = 65536.  One step solves the
+four single-matrix families of the n = 65536 workload back to back on one stream:
+(a) d, e iid Uniform(-1, 1) (seed 0), (b) Toeplitz d = 2, e = -1, (c) Wilkinson W+,
+(d) W+_21 blocks glued by 1e-8.  value = 4 n / step time (inputs resident in HBM).
+
+Printed as one JSON line (rank 0).  Besides the base keys it carries:
+  roofline      dominant kernel's algorithmic FP64 rate (per-kernel CUDA events
+                inside the timed region, work from the device counters) against the
+                FP64 FMA peak measured in the same run (x2 flops / FMA)
+  cpu_baseline  the CPU oracle (Sturm bisection) on a bounded sample, host cores
+  e2e           the same metric through the public API with pinned host inputs,
+                host->device copies and the device->host read of the eigenvalues
+                inside the timed region
+  clocks        nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the oracle (the only reference this method has) on the
+host cores instead.  Under torchrun (N > 1) every rank solves its own copy of the
+workload (weak scaling, no data-path collective) and the slowest rank's time is
+used; the reference arm runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2605_26599_b300 import inputs  # noqa: E402
+
+METRIC = "FP64 tridiag eigvals/s (n=64K)"
+UNIT = "eigvals/s"
+FAMILIES = ("a_uniform11", "b_toeplitz", "c_wilkinson", "d_glued_wilkinson")
+
+# Algorithmic FP64 operations per unit of device work (add, mul, division each one
+# flop, a fused multiply-add two):
+#   secular, per pole per sweep:  Delta = (D_i - D_org) - tau (2), t = z / Delta (1),
+#                                 z t (1), accumulate (1), t t (1), accumulate (1)
+#   Lowner, per pair:             numerator (2), denominator (1), ratio (1), product (1)
+#   rows, per pair:               Delta (2), zhat / Delta (1), t^2 + acc (2), two row FMAs (4)
+FLOPS_PER_UNIT = {"secular": 7, "lowner": 5, "rows": 9}
+WORK_OF = {"secular": "secular_pairs", "lowner": "lowner_pairs", "rows": "rows_pairs"}
+
+
+def family_inputs(n: int):
+    return {
+        "a_uniform11": inputs.uniform11(n, seed=0),
+        "b_toeplitz": inputs.toeplitz(n, 2.0, -1.0),
+        "c_wilkinson": inputs.wilkinson_plus(n),
+        "d_glued_wilkinson": inputs.glued_wilkinson(n),
+    }
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2605_26599_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sms, maxs, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sms:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sms)), "sm_max_mhz": float(max(maxs)),
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(n: int, per_family: int, fams) -> tuple[float, int]:
+    """Time the bisection oracle on `per_family` evenly spaced eigenvalue indices of
+    each family; returns (seconds, threads used)."""
+    import oracle
+
+    ks = np.linspace(0, n - 1, per_family).astype(np.int64)
+    t0 = time.perf_counter()
+    for name in FAMILIES:
+        d, e = fams[name]
+        oracle.eigvals_select(d, e, ks)
+    return time.perf_counter() - t0, oracle.last_threads
+
+
+def cpu_baseline(n: int, fams, target_s: float = 12.0) -> dict:
+    probe = 8
+    t, _ = oracle_sample(n, probe, fams)
+    per = int(max(probe, min(n, probe * target_s / max(t, 1e-3))))
+    t, threads = oracle_sample(n, per, fams)
+    return {"value": 4 * per / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"Sturm bisection of {per} evenly spaced eigenvalue indices of each of the "
+                      f"4 families at n={n} ({4 * per} eigenvalues, {t:.1f} s)"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    n = args.n
+    fams = family_inputs(n)
+    import oracle
+
+    oracle.build()
+    per = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_sample(n, per, fams)
+    times = []
+    threads = 0
+    for _ in range(args.steps):
+        t, threads = oracle_sample(n, per, fams)
+        times.append(t)
+    step = float(np.mean(times))
+    value = 4 * per / step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"single tridiagonals n={n}, families a-d (uniform(-1,1) seed 0, "
+                               "Toeplitz 2/-1, Wilkinson W+, glued W+_21)", "n": n,
+                   "families": list(FAMILIES),
+                   "step": f"oracle bisection of {per} eigenvalue indices per family"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{per} evenly spaced eigenvalue indices per family, n={n}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank: int, world: int, dist) -> None:
+    import torch
+
+    import paper_2605_26599_b300 as tde
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    fams = family_inputs(n)
+    host = {}
+    devt = {}
+    outs = {}
+    wss = {}
+    for name in FAMILIES:
+        d, e = fams[name]
+        hd = torch.from_numpy(d).pin_memory()
+        he = torch.from_numpy(e).pin_memory()
+        host[name] = (hd, he)
+        devt[name] = (hd.to(dev), he.to(dev))
+        outs[name] = torch.empty(n, dtype=torch.float64, device=dev)
+        wss[name] = tde.Workspace(tde.workspace_bytes(n, args.leaf), dev)
+    host_out = {name: torch.empty(n, dtype=torch.float64).pin_memory() for name in FAMILIES}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+
+    def one_step():
+        launches = 0
+        for name in FAMILIES:
+            d, e = devt[name]
+            tde.eigvals(d, e, leaf=args.leaf, out=outs[name], ws=wss[name], check=False)
+            launches += tde.last_launch_count()
+        return launches
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # correctness of the status words once, before timing
+    one_step()
+    for name in FAMILIES:
+        info = tde.get_info(wss[name])
+        if info != 0:
+            raise RuntimeError(f"device status {info} on family {name}")
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    tde.profile_enable(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    fam_ev = {name: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                     for _ in range(args.steps)] for name in FAMILIES}
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    launches = 0
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between steps, outside the event-timed region
+        starts[i].record(stream)
+        for name in FAMILIES:
+            d, e = devt[name]
+            fam_ev[name][i][0].record(stream)
+            tde.eigvals(d, e, leaf=args.leaf, out=outs[name], ws=wss[name], check=False)
+            fam_ev[name][i][1].record(stream)
+            launches += tde.last_launch_count()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    tde.profile_enable(False)
+    kprof = tde.profile_collect()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    fam_ms = {name: float(np.mean([a.elapsed_time(b) for a, b in fam_ev[name]])) for name in FAMILIES}
+    ms = float(np.mean(step_ms))
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 4 * n / (ms * 1e-3)
+
+    # device work of one step (identical every step)
+    work = {k: 0 for k in ("secular_pairs", "lowner_pairs", "rows_pairs", "secular_sweeps", "roots",
+                           "deflated", "rotations", "leaf_rotations")}
+    per_family_work = {}
+    for name in FAMILIES:
+        w = tde.read_work(wss[name])
+        per_family_work[name] = w
+        for k in work:
+            work[k] += w[k]
+
+    # end to end through the public API, pinned host buffers
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for name in FAMILIES:
+            hd, he = host[name]
+            d, e = devt[name]
+            d.copy_(hd, non_blocking=True)
+            e.copy_(he, non_blocking=True)
+            tde.eigvals(d, e, leaf=args.leaf, out=outs[name], ws=wss[name], check=False)
+            host_out[name].copy_(outs[name], non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(ev0.elapsed_time(ev1))
+    e2e_step = float(np.mean(e2e_ms))
+    h2d = sum(host[nm][0].numel() * 8 + host[nm][1].numel() * 8 for nm in FAMILIES)
+    d2h = 4 * n * 8
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel
+    fma_per_s = tde.measure_fp64_peak()
+    peak_tflops = 2.0 * fma_per_s / 1e12
+    ktimes = {k: v[0] / args.steps for k, v in kprof.items()}
+    klaunch = {k: v[1] / args.steps for k, v in kprof.items()}
+    total_k = sum(ktimes.values())
+    dominant = max(ktimes, key=ktimes.get)
+    roof = {"bound": "alu", "kernel": dominant, "unit": "TFLOP/s", "peak": peak_tflops,
+            "peak_source": "FP64 FMA-chain microbenchmark run in this process (x2 flops/FMA); "
+                           "MEASURED_PEAKS.json carries no FP64 figure"}
+    if dominant in FLOPS_PER_UNIT:
+        flops = FLOPS_PER_UNIT[dominant] * work[WORK_OF[dominant]]
+        achieved = flops / (ktimes[dominant] * 1e-3) / 1e12
+        roof.update({"achieved": achieved, "frac": achieved / peak_tflops,
+                     "algorithmic_flops_per_step": flops,
+                     "launches_per_step": klaunch[dominant],
+                     "avg_launch_ms": ktimes[dominant] / max(klaunch[dominant], 1)})
+    else:
+        roof.update({"achieved": None, "frac": None,
+                     "note": f"dominant kernel {dominant} is not an FP64 pair kernel"})
+    roof["traffic"] = load_traffic(dominant)
+    kernel_rates = {}
+    for k in FLOPS_PER_UNIT:
+        if ktimes.get(k, 0) > 0:
+            fl = FLOPS_PER_UNIT[k] * work[WORK_OF[k]]
+            kernel_rates[k] = {"ms_per_step": ktimes[k], "tflops": fl / (ktimes[k] * 1e-3) / 1e12,
+                               "frac_of_peak": fl / (ktimes[k] * 1e-3) / 1e12 / peak_tflops}
+
+    cpu = cpu_baseline(n, fams) if (world == 1 and not args.no_cpu_baseline) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"single tridiagonals n={n}, families a-d (uniform(-1,1) seed 0, "
+                               "Toeplitz 2/-1, Wilkinson W+, glued W+_21)",
+                   "n": n, "families": list(FAMILIES), "leaf": args.leaf or 32,
+                   "l2": "flushed between steps (256 MB write outside the event-timed region); "
+                         "inputs are smaller than L2",
+                   "per_family_ms": fam_ms, "step_ms_min": float(min(step_ms)),
+                   "kernel_ms_per_step": ktimes, "kernel_events_in_timed_region": True,
+                   "wall_s_timed_region": wall, "work_per_step": work},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "kernel_fp64_rates": kernel_rates,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * 4 * n / (e2e_step * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
+        "clocks": clocks,
+        "source_hash": source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    entry = rec.get(kernel)
+    if not entry or entry.get("source_hash") != source_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--leaf", type=int, default=0)
+    ap.add_argument("--ref-sample", type=int, default=96,
+                    help="eigenvalue indices per family per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        backend = "nccl" if torch.cuda.is_available() and args.impl == "ours" else "gloo"
+        tdist.init_process_group(backend=backend)
+        dist = tdist
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -100,6 +100,23 @@ int tde_measure_fp64_peak(double* fma_per_s);
 /* Number of kernel launches the last compute call on this thread enqueued. */
 int64_t tde_last_launch_count(void);
 
+/* Per-kernel timing for measurement.  With profiling enabled, every compute call
+ * on this thread records a CUDA event pair around each kernel launch; collect
+ * synchronises on those events, writes per-kernel-class milliseconds and launch
+ * counts into ms[0..nids) / launches[0..nids) (classes: 0 plan, 1 scale, 2 leaves,
+ * 3 form, 4 deflate, 5 secular, 6 lowner, 7 rows, 8 place) and clears the record.
+ * Do not enable it while the stream is being captured into a CUDA graph. */
+int tde_profile_enable(int on);
+int tde_profile_collect(int nids, double* ms, int64_t* launches);
+
+/* Copies the workspace's device work counters (synchronises `stream`):
+ * out[0] secular pole sweeps x K summed over roots (pair-evaluations),
+ * out[1] secular sweeps, out[2] Lowner pairs, out[3] boundary-row pairs,
+ * out[4] roots solved, out[5] deflated eigenvalues, out[6] close-pole rotations,
+ * out[7] leaf plane rotations.  n <= 16 entries are copied.  The counters are
+ * reset at the start of every compute call that uses the workspace. */
+int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,7 +20,8 @@ from . import _lib
 from ._lib import TdeError  # noqa: F401
 
 __all__ = ["eigvals", "eigvals_batched", "workspace_bytes", "batched_workspace_bytes",
-           "get_info", "measure_fp64_peak", "last_launch_count", "TdeError", "Workspace"]
+           "get_info", "measure_fp64_peak", "last_launch_count", "TdeError", "Workspace",
+           "profile_enable", "profile_collect", "read_work"]
 
 
 def _torch():
@@ -161,3 +162,26 @@ def measure_fp64_peak() -> float:
 def last_launch_count() -> int:
     """Kernel launches the last compute call on this thread enqueued."""
     return int(_lib.load().tde_last_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    """Record a CUDA event pair around every kernel of subsequent calls on this thread."""
+    _lib.check("tde_profile_enable", _lib.load().tde_profile_enable(1 if on else 0))
+
+
+def profile_collect() -> dict:
+    """{kernel class: (milliseconds, launches)} since the last collect (synchronises)."""
+    n = len(_lib.KERNEL_NAMES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_int64 * n)()
+    _lib.check("tde_profile_collect", _lib.load().tde_profile_collect(n, ms, cnt))
+    return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(_lib.KERNEL_NAMES)}
+
+
+def read_work(ws: Workspace, stream=None) -> dict:
+    """Device work counters of the last call that used ``ws`` (synchronises)."""
+    n = len(_lib.WORK_NAMES)
+    out = (ctypes.c_ulonglong * n)()
+    _lib.check("tde_read_work", _lib.load().tde_read_work(ctypes.c_void_p(ws.ptr), _stream_ptr(stream),
+                                                          out, n))
+    return {name: int(out[i]) for i, name in enumerate(_lib.WORK_NAMES)}

@@ -1,10 +1,45 @@
 // C ABI of the solver (declarations and contracts in include/tde.h).
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "tde_internal.cuh"
 
 namespace tde {
+
+// Optional per-launch timing: an event pair around every kernel of a call, summed
+// per kernel class by tde_profile_collect.  Off by default; never enable it while
+// a stream is being captured into a graph.
+struct ProfRec {
+  int id;
+  cudaEvent_t a, b;
+};
+static thread_local bool g_prof_on = false;
+static thread_local std::vector<cudaEvent_t> g_pool;
+static thread_local size_t g_pool_next = 0;
+static thread_local std::vector<ProfRec> g_recs;
+static thread_local cudaEvent_t g_open[kNumKernelIds];
+
+static cudaEvent_t next_event() {
+  if (g_pool_next == g_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    g_pool.push_back(e);
+  }
+  return g_pool[g_pool_next++];
+}
+void prof_begin(int id, cudaStream_t s) {
+  if (!g_prof_on) return;
+  cudaEvent_t e = next_event();
+  cudaEventRecord(e, s);
+  g_open[id] = e;
+}
+void prof_end(int id, cudaStream_t s) {
+  if (!g_prof_on) return;
+  cudaEvent_t e = next_event();
+  cudaEventRecord(e, s);
+  g_recs.push_back(ProfRec{id, g_open[id], e});
+}
 
 __global__ void k_set_offsets(int64_t* off, int64_t n) {
   off[0] = 0;
@@ -99,5 +134,45 @@ int tde_get_info(const void* ws, void* stream, int32_t* info) {
 }
 
 int64_t tde_last_launch_count(void) { return g_launches; }
+
+int tde_profile_enable(int on) {
+  g_prof_on = on != 0;
+  return TDE_OK;
+}
+
+int tde_profile_collect(int nids, double* ms, int64_t* launches) {
+  if (nids < 0 || (nids > 0 && (ms == nullptr || launches == nullptr))) return TDE_EINVAL;
+  for (int i = 0; i < nids; ++i) {
+    ms[i] = 0.0;
+    launches[i] = 0;
+  }
+  int rc = TDE_OK;
+  for (const ProfRec& r : g_recs) {
+    if (cudaEventSynchronize(r.b) != cudaSuccess) {
+      rc = TDE_ECUDA;
+      continue;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    if (r.id < nids) {
+      ms[r.id] += t;
+      launches[r.id] += 1;
+    }
+  }
+  g_recs.clear();
+  g_pool_next = 0;
+  return rc;
+}
+
+int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n) {
+  if (ws == nullptr || out == nullptr || n < 0 || n > 16) return TDE_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Status* st = static_cast<const Status*>(ws);
+  if (cudaMemcpyAsync(out, st->work, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s) !=
+      cudaSuccess)
+    return TDE_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TDE_ECUDA;
+  return TDE_OK;
+}
 
 }  // extern "C"

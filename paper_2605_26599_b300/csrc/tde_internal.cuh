@@ -50,11 +50,39 @@ struct MState {
 
 constexpr uint32_t kRootBit = 0x80000000u;
 
+// Work counters accumulated on the device by every call (reset per call):
+enum WorkCounter {
+  kWorkSecularPairs = 0,  // sum over roots of K x (number of pole sweeps)
+  kWorkSecularSweeps,     // sum over roots of the number of pole sweeps
+  kWorkLownerPairs,       // sum over non-root merges of K^2
+  kWorkRowsPairs,         // sum over non-root merges of K^2
+  kWorkRoots,             // roots solved
+  kWorkDeflated,          // eigenvalues deflated (small z or rotation)
+  kWorkRotations,         // close-pole rotations
+  kWorkLeafRotations,     // plane rotations in the leaf QR sweeps
+  kNumWork
+};
+
 struct Status {
   int32_t info;
   int32_t pad[31];
   uint32_t root_count[kMaxSteps];  // roots allocated per step
+  unsigned long long work[16];
 };
+
+// Kernel classes timed by the optional per-launch event profiler.
+enum KernelId { kKPlan = 0, kKScale, kKLeaves, kKForm, kKDeflate, kKSecular, kKLowner, kKRows,
+                kKPlace, kNumKernelIds };
+void prof_begin(int id, cudaStream_t s);
+void prof_end(int id, cudaStream_t s);
+
+// Warp-aggregated add to a device work counter (safe under a partial warp).
+__device__ __forceinline__ void work_add(Status* st, int which, unsigned v) {
+  const unsigned mask = __activemask();
+  const unsigned x = __reduce_add_sync(mask, v);
+  if ((threadIdx.x & 31) == unsigned(__ffs(mask) - 1) && x)
+    atomicAdd(&st->work[which], (unsigned long long)x);
+}
 
 struct Workspace {
   Status* status;

@@ -18,8 +18,10 @@ namespace tde {
 
 // Implicit QR on a[0..m), b[0..m-1) (b[i] couples i and i+1), tracking the
 // first row r0 and last row r1 of the accumulated rotation product.
-// Returns false if an unreduced block needed more than 40 steps per row.
-__device__ bool leaf_qr_two_rows(int m, double* a, double* b, double* r0, double* r1) {
+// Returns false if an unreduced block needed more than 40 steps per row; adds the
+// number of plane rotations applied to *rot.
+__device__ bool leaf_qr_two_rows(int m, double* a, double* b, double* r0, double* r1,
+                                 unsigned* rot) {
   int hi = m - 1;
   int steps = 0;
   const int max_steps = 40 * m;
@@ -47,6 +49,7 @@ __device__ bool leaf_qr_two_rows(int m, double* a, double* b, double* r0, double
     if (!isfinite(mu)) mu = a[hi];
     // first rotation from the first column of T - mu I, then chase the bulge
     double x = a[lo] - mu, y = b[lo];
+    *rot += unsigned(hi - lo);
     for (int i = lo; i < hi; ++i) {
       double r = sqrt(x * x + y * y);
       double c = 1.0, s = 0.0;
@@ -97,7 +100,9 @@ __global__ void k_leaves(const Leaf* __restrict__ leaves, int64_t nleaves,
     // Cuppen tearing (Eq. 1): T = diag(T_L, T_R) + |beta| u u^T, u = e_last + sgn(beta) e_first
     if (lf.flags & 1) a[0] -= fabs(es[lf.lo - 1]);
     if (lf.flags & 2) a[m - 1] -= fabs(es[lf.hi - 1]);
-    if (!leaf_qr_two_rows(m, a, b, r0, r1)) set_status(st, TDE_ENOCONV);
+    unsigned rot = 0;
+    if (!leaf_qr_two_rows(m, a, b, r0, r1, &rot)) set_status(st, TDE_ENOCONV);
+    work_add(st, kWorkLeafRotations, rot);
     // ascending order, rows follow their eigenvalue (insertion sort, m <= 64)
     for (int j = 1; j < m; ++j) {
       double v = a[j], p = r0[j], q = r1[j];
@@ -131,8 +136,10 @@ void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaSt
   int block = 64;
   int64_t grid = (plan.nleaves + block - 1) / block;
   if (grid > 148 * 32) grid = 148 * 32;
+  prof_begin(kKLeaves, s);
   k_leaves<<<int(grid), block, 0, s>>>(ws.leaves, plan.nleaves, ws.ds, ws.es, ws.sigma_bits,
                                        ws.LAM, ws.BLO, ws.BHI, lambda, ws.status);
+  prof_end(kKLeaves, s);
   g_launches += 1;
 }
 

@@ -489,6 +489,8 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       st.zsq = zsq;
       st.pad = 0.0;
       a.ms[g] = st;
+      atomicAdd(&a.st->work[kWorkDeflated], (unsigned long long)(n0 - K));
+      atomicAdd(&a.st->work[kWorkRotations], (unsigned long long)(S - K));
     }
     __syncthreads();
     for (int j = tid; j < K; j += kNT) a.ROOTMAP[s_base + j] = int32_t(g);
@@ -537,15 +539,18 @@ __device__ __forceinline__ SecSums sec_sweep(const double* __restrict__ D,
   return s;
 }
 
-// returns iterations used (negative if the cap was hit)
+// returns the number of pole sweeps; *ok = false if the iteration cap was hit
 __device__ int secular_root(const double* __restrict__ D, const double* __restrict__ Z, int K,
-                            int j, double rho, double zsq, int* org_out, double* tau_out) {
+                            int j, double rho, double zsq, int* org_out, double* tau_out,
+                            bool* ok) {
   const double rhoinv = 1.0 / rho;
+  *ok = true;
   if (K == 1) {
     *org_out = 0;
     *tau_out = rho * Z[0] * Z[0];
     return 0;
   }
+  int sweeps = 1;
   int org, jl, jr;
   double tau, tlo, thi;
   SecSums s;
@@ -631,12 +636,14 @@ __device__ int secular_root(const double* __restrict__ D, const double* __restri
     if (ntau == tau) break;
     tau = ntau;
     s = sec_sweep(D, Z, K, dorg, tau, jl);
+    ++sweeps;
     w = rhoinv + s.psi + s.phi;
     if (thi - tlo <= 2.0 * kEps * fmax(fabs(tlo), fabs(thi))) break;
   }
   *org_out = org;
   *tau_out = tau;
-  return it < max_it ? it + 1 : -1;
+  *ok = it < max_it;
+  return sweeps;
 }
 
 struct RootArgs {
@@ -662,8 +669,12 @@ __global__ void k_secular(RootArgs a) {
     const int lo = a.M[g].lo;
     int org;
     double tau;
-    int it = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, &org, &tau);
-    if (it < 0) set_status(a.st, TDE_ENOCONV);
+    bool ok;
+    int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, &org, &tau, &ok);
+    if (!ok) set_status(a.st, TDE_ENOCONV);
+    work_add(a.st, kWorkSecularPairs, unsigned(sweeps) * unsigned(ms.K));
+    work_add(a.st, kWorkSecularSweeps, unsigned(sweeps));
+    work_add(a.st, kWorkRoots, 1u);
     a.TAU[lo + j] = tau;
     a.ORG[lo + j] = org;
     a.LAMA[lo + j] = a.AD[lo + org] + tau;
@@ -689,6 +700,7 @@ __global__ void k_lowner(RootArgs a) {
       prod *= num / den;
     }
     a.ZHAT[lo + i] = copysign(sqrt(fmax(prod, 0.0)), a.AZ[lo + i]);
+    work_add(a.st, kWorkLownerPairs, unsigned(K));
   }
 }
 
@@ -717,6 +729,7 @@ __global__ void k_rows(RootArgs a) {
     double inv = 1.0 / sqrt(s2);
     a.ROWLO[lo + j] = sl * inv;
     a.ROWHI[lo + j] = sh * inv;
+    work_add(a.st, kWorkRowsPairs, unsigned(K));
   }
 }
 
@@ -767,8 +780,10 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   const int64_t cnt = plan.step_count[step];
   const int64_t nrows = plan.nrows;
   const int flat_grid = int(std::min<int64_t>((nrows + 255) / 256, 148 * 8));
+  prof_begin(kKForm, s);
   k_form<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.LAM, ws.BLO, ws.BHI, ws.es, ws.D, ws.Z,
                                    ws.RLO, ws.RHI);
+  prof_end(kKForm, s);
   DeflateArgs da;
   da.M = M;
   da.cnt = cnt;
@@ -793,7 +808,9 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   da.ms = ws.mstate;
   da.st = ws.status;
   const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
+  prof_begin(kKDeflate, s);
   k_deflate<<<def_grid, kNT, 0, s>>>(da);
+  prof_end(kKDeflate, s);
   RootArgs ra;
   ra.M = M;
   ra.ms = ws.mstate;
@@ -811,16 +828,24 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   ra.ROWHI = ws.RHI;
   ra.st = ws.status;
   const int root_grid = int(std::min<int64_t>((nrows + 127) / 128, 148 * 8));
+  prof_begin(kKSecular, s);
   k_secular<<<root_grid, 128, 0, s>>>(ra);
+  prof_end(kKSecular, s);
   int launches = 4;
   if (plan.step_has_nonroot[step]) {
+    prof_begin(kKLowner, s);
     k_lowner<<<root_grid, 128, 0, s>>>(ra);
+    prof_end(kKLowner, s);
+    prof_begin(kKRows, s);
     k_rows<<<root_grid, 128, 0, s>>>(ra);
+    prof_end(kKRows, s);
     launches += 2;
   }
+  prof_begin(kKPlace, s);
   k_place<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.mstate, ws.D, ws.RLO, ws.RHI, ws.AD,
                                     ws.ALO, ws.AHI, ws.sigma_bits, ws.LAM, ws.BLO, ws.BHI,
                                     lambda);
+  prof_end(kKPlace, s);
   g_launches += launches;
 }
 

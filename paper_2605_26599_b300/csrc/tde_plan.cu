@@ -192,10 +192,12 @@ void launch_plan(const Plan& plan, const Workspace& ws, const int64_t* off, cuda
   a.nmerges = plan.nmerges;
   a.nleaves = plan.nleaves;
   for (int i = 0; i < kMaxSteps; ++i) a.step_base[i] = plan.step_base[i];
+  prof_begin(kKPlan, s);
   k_plan_prefix<<<plan.steps + 1, 256, 0, s>>>(off, a, ws.pfx);
   int64_t total = plan.nmerges + plan.nleaves;
   int grid = int(std::min<int64_t>((total + 255) / 256, 148 * 16));
   k_plan_fill<<<std::max(grid, 1), 256, 0, s>>>(off, a, ws.pfx, ws.merges, ws.leaves);
+  prof_end(kKPlan, s);
   g_launches += 2;
 }
 
@@ -282,8 +284,10 @@ void launch_scale(const Plan& plan, const Workspace& ws, const int64_t* off, con
                   const double* e, cudaStream_t s) {
   if (plan.nrows == 0) return;
   int grid = int(std::min<int64_t>((plan.nrows + 255) / 256, 148 * 8));
+  prof_begin(kKScale, s);
   k_sigma<<<grid, 256, 0, s>>>(off, plan.batch, plan.nrows, d, e, ws.sigma_bits, ws.status);
   k_scale<<<grid, 256, 0, s>>>(off, plan.batch, plan.nrows, d, e, ws.sigma_bits, ws.ds, ws.es);
+  prof_end(kKScale, s);
   g_launches += 2;
 }
 

@@ -1,0 +1,81 @@
+"""GPU parity at the full single-matrix workload sizes (n = 32768 ... 262144).
+
+The oracle computes sampled eigenvalue indices one by one (Sturm bisection); the
+rest of the spectrum is checked through properties that hold at any size: the
+trace and Frobenius invariants, the closed-form Toeplitz spectrum, ascending
+order and the O(n) workspace bound."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_26599_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def tde():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_26599_b300 as tde_mod
+
+    return tde_mod
+
+
+def solve(tde, d, e, leaf=0):
+    import torch
+
+    return tde.eigvals(torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda(), leaf=leaf).cpu().numpy()
+
+
+def sample_indices(n, count=192):
+    ks = np.linspace(0, n - 1, count).astype(np.int64)
+    return np.unique(np.concatenate([ks, [0, 1, 2, n // 2, n - 3, n - 2, n - 1]]))
+
+
+def check_full(d, e, lam, sample=192):
+    n = len(d)
+    tn = oracle.norm1(d, e)
+    gate = 8 * n * EPS * tn
+    assert np.all(np.diff(lam) >= 0)
+    ks = sample_indices(n, sample)
+    ref = oracle.eigvals_select(d, e, ks)
+    err = float(np.max(np.abs(lam[ks] - ref)))
+    assert err <= gate, f"sampled max |dlambda| {err:.3e} > gate {gate:.3e}"
+    # trace and Frobenius invariants (every eigenvalue within the gate)
+    assert abs(lam.sum() - d.sum()) <= n * gate
+    assert abs((lam * lam).sum() - (d * d).sum() - 2 * (e * e).sum()) <= 2 * n * tn * gate
+    return err
+
+
+@pytest.mark.parametrize("n", [32768, 49152, 65536])
+@pytest.mark.parametrize("fam", ["uniform11", "toeplitz", "wilkinson", "glued_wilkinson"])
+def test_single_matrix_families(tde, fam, n):
+    d, e = inputs.family(fam, n, seed=0)
+    lam = solve(tde, d, e)
+    check_full(d, e, lam)
+    if fam == "toeplitz":  # closed form, every eigenvalue
+        k = np.arange(1, n + 1)
+        ref = np.sort(2.0 - 2.0 * np.cos(k * np.pi / (n + 1)))
+        assert np.max(np.abs(lam - ref)) <= 8 * n * EPS * 4.0
+
+
+def test_glued_wilkinson_literal_32_blocks(tde):
+    # the literal reading of "32 glued W+_21 blocks": n = 672
+    d, e = inputs.glued_wilkinson(32 * 21)
+    lam = solve(tde, d, e)
+    ref = oracle.eigvals_bisect(d, e)
+    assert np.max(np.abs(lam - ref)) <= 8 * len(d) * EPS * oracle.norm1(d, e)
+
+
+@pytest.mark.parametrize("n", [131072, 262144])
+@pytest.mark.parametrize("fam", ["normal", "graded"])
+def test_large_o_n_workspace(tde, fam, n):
+    d, e = inputs.family(fam, n, seed=0)
+    assert tde.workspace_bytes(n) <= 256 * n
+    lam = solve(tde, d, e)
+    check_full(d, e, lam, sample=96)
