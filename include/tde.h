@@ -117,6 +117,23 @@ int tde_profile_collect(int nids, double* ms, int64_t* launches);
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 
+/* Largest order tde_eigvals_noalloc accepts. */
+#define TDE_NOALLOC_MAX_N 16384
+
+/* tde_eigvals without a caller workspace, for callers that cannot allocate
+ * device memory (for instance code handed device pointers by a framework that
+ * owns every allocation).  The paper has no counterpart; it is a convenience of
+ * this library.  The workspace is a 4 MiB array compiled into the library, kept
+ * on every GPU that loads it until the process exits.  d, e, lambda, leaf and
+ * stream mean what they mean for tde_eigvals; n must not exceed
+ * TDE_NOALLOC_MAX_N (TDE_EWORKSPACE otherwise, nothing enqueued).  No memory is
+ * allocated.  The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  All calls share the one
+ * array: calls that overlap on the GPU race and must be serialised by the
+ * caller.  The device status word is not readable for this entry point. */
+int tde_eigvals_noalloc(int64_t n, const double* d, const double* e, double* lambda,
+                        int32_t leaf, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
