@@ -133,6 +133,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
+def slowest_rank_ms(ms: float, dist, device="cpu") -> float:
+    """Max over ranks of a per-rank step time (identity on one rank)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms: float, world: int, eigvals_per_rank: int) -> float:
+    """Whole-job eigenvalues per second: every rank solves its own copy (weak scaling)."""
+    return world * eigvals_per_rank / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 def oracle_sample(n: int, per_family: int, fams) -> tuple[float, int]:
     """Time the bisection oracle on `per_family` evenly spaced eigenvalue indices of
@@ -160,7 +176,7 @@ def cpu_baseline(n: int, fams, target_s: float = 12.0) -> dict:
 def run_reference(args, rank: int, world: int) -> None:
     if rank != 0:
         return
-    n = args.n
+    n = args.size
     fams = family_inputs(n)
     import oracle
 
@@ -200,7 +216,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    n = args.n
+    n = args.size
     fams = family_inputs(n)
     host = {}
     devt = {}
@@ -271,12 +287,8 @@ def run_ours(args, rank: int, world: int, dist) -> None:
     clocks = sampler.stop() if sampler else None
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     fam_ms = {name: float(np.mean([a.elapsed_time(b) for a, b in fam_ev[name]])) for name in FAMILIES}
-    ms = float(np.mean(step_ms))
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 4 * n / (ms * 1e-3)
+    ms = slowest_rank_ms(float(np.mean(step_ms)), dist, dev)
+    value = job_value(ms, world, 4 * n)
 
     # device work of one step (identical every step)
     work = {k: 0 for k in ("secular_pairs", "lowner_pairs", "rows_pairs", "secular_sweeps", "roots",
@@ -306,7 +318,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(ev0.elapsed_time(ev1))
-    e2e_step = float(np.mean(e2e_ms))
+    e2e_step = slowest_rank_ms(float(np.mean(e2e_ms)), dist, dev)
     h2d = sum(host[nm][0].numel() * 8 + host[nm][1].numel() * 8 for nm in FAMILIES)
     d2h = 4 * n * 8
 
@@ -357,7 +369,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         "roofline": roof,
         "kernel_fp64_rates": kernel_rates,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * 4 * n / (e2e_step * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(e2e_step, world, 4 * n), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "clocks": clocks,
         "source_hash": source_hash(),
@@ -386,7 +398,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=65536)
+    ap.add_argument("--size", type=int, default=65536, help="matrix order n")
     ap.add_argument("--leaf", type=int, default=0)
     ap.add_argument("--ref-sample", type=int, default=96,
                     help="eigenvalue indices per family per reference step")

@@ -97,6 +97,14 @@ int tde_get_info(const void* ws, void* stream, int32_t* info);
  * about 50 ms.  Returns TDE_OK and writes *fma_per_s. */
 int tde_measure_fp64_peak(double* fma_per_s);
 
+/* Host-only description of the split-tree plan for a packing (no device work):
+ * out[0] merge steps (tree levels), out[1] leaves, out[2] merges, out[3] the
+ * largest number of merges in one step.  Node (h, i) of a matrix of order n covers
+ * rows [floor(i n / 2^h), floor((i+1) n / 2^h)); leaves sit at depth L, the
+ * smallest L with ceil(n / 2^L) <= leaf, capped so that 2^L <= n (Sec. 3.3
+ * balanced tree). */
+int tde_plan_query(int64_t batch, const int64_t* offsets_host, int32_t leaf, int64_t* out);
+
 /* Number of kernel launches the last compute call on this thread enqueued. */
 int64_t tde_last_launch_count(void);
 

@@ -152,6 +152,15 @@ def eigvals_batched(d, e, offsets, leaf: int = 0, out=None, ws: Workspace | None
     return lam
 
 
+def plan_query(offsets, leaf: int = 0) -> dict:
+    """Host-only split-tree plan of a packing: steps, leaves, merges, max merges/step."""
+    off = _host_offsets(offsets)
+    out = (ctypes.c_int64 * 4)()
+    _lib.check("tde_plan_query", _lib.load().tde_plan_query(off.shape[0] - 1, off.ctypes.data,
+                                                            int(leaf), out))
+    return {"steps": int(out[0]), "leaves": int(out[1]), "merges": int(out[2]), "cmax": int(out[3])}
+
+
 def measure_fp64_peak() -> float:
     """Measured FP64 FMA instructions per second of the current device (all lanes)."""
     out = ctypes.c_double()

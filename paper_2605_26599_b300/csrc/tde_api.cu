@@ -135,6 +135,18 @@ int tde_get_info(const void* ws, void* stream, int32_t* info) {
 
 int64_t tde_last_launch_count(void) { return g_launches; }
 
+int tde_plan_query(int64_t batch, const int64_t* offsets_host, int32_t leaf, int64_t* out) {
+  if (out == nullptr) return TDE_EINVAL;
+  Plan p;
+  int rc = build_plan(batch, offsets_host, leaf, &p);
+  if (rc != TDE_OK) return rc;
+  out[0] = p.steps;
+  out[1] = p.nleaves;
+  out[2] = p.nmerges;
+  out[3] = p.cmax;
+  return TDE_OK;
+}
+
 int tde_profile_enable(int on) {
   g_prof_on = on != 0;
   return TDE_OK;
