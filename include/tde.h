@@ -105,6 +105,11 @@ int tde_measure_fp64_peak(double* fma_per_s);
  * balanced tree). */
 int tde_plan_query(int64_t batch, const int64_t* offsets_host, int32_t leaf, int64_t* out);
 
+/* Applies the solver's device reciprocal (a hardware approximation refined by the
+ * third-order step r (1 + e + e^2), e = 1 - x r) to x[0..n) -> out[0..n), device
+ * arrays, on `stream`.  Exposed so tests can compare it with IEEE 1/x. */
+int tde_check_reciprocal(int64_t n, const double* x, double* out, void* stream);
+
 /* Number of kernel launches the last compute call on this thread enqueued. */
 int64_t tde_last_launch_count(void);
 

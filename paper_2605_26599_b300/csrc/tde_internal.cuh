@@ -114,6 +114,7 @@ struct Plan {
   int64_t nmerges = 0;
   int64_t cmax = 0;
   int64_t step_count[kMaxSteps] = {0};
+  int64_t step_maxsize[kMaxSteps] = {0};  // largest merge order (K0) of the step
   int64_t step_base[kMaxSteps] = {0};
   bool step_has_nonroot[kMaxSteps] = {false};
 };
@@ -216,6 +217,21 @@ void launch_scale(const Plan& plan, const Workspace& ws, const int64_t* offsets_
 void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s);
 void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda,
                  cudaStream_t s);
+// secular, Lowner and boundary-row kernels of one step; returns the launch count
+int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s);
+
+// Reciprocal in about three FP64 fused multiply-adds: a hardware approximation r0
+// of 1/x refined by the third-order (Householder) step for 1/x,
+// r = r0 (1 + e + e^2) with e = 1 - x r0, i.e. the geometric series of
+// 1 / (1 - e) truncated after the quadratic term; the relative error drops from
+// |e| to about |e|^3 plus the final rounding.
+__device__ __forceinline__ double rcp_refined(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
+  const double ee = fma(e, e, e);
+  return fma(r, ee, r);
+}
 
 extern thread_local int64_t g_launches;
 

@@ -499,241 +499,6 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Secular equation.  For root j (0-based) of the active problem with sorted
-// distinct poles D and nonzero z, w(lambda) = 1/rho' + sum_i z_i^2 / (D_i - lambda)
-// has one root in (D_j, D_{j+1}) for j < K-1 and one in (D_{K-1}, D_{K-1} + rho' zsq)
-// for the last root.  In shifted coordinates lambda = D_org + tau with
-// Delta_i = (D_i - D_org) - tau the two poles that bracket the root keep full
-// relative accuracy.
-//
-// Iteration: evaluate w and its derivative split into the poles on the left of
-// the root (psi: i <= jl) and on the right (phi: i > jl), then take the root of the
-// two-pole rational model C + S1 / (Delta_jl - eta) + S2 / (Delta_jr - eta) that
-// matches w and w' (S1 = Delta_jl^2 psi', S2 = Delta_jr^2 phi'), kept inside a
-// bisection bracket.  The start is the midpoint of the interval, whose sign of w
-// also chooses the origin (the nearer pole).  Convergence: |w| below eps times a
-// running bound on the rounding error of its evaluation,
-// 8 (|psi| + |phi|) + 1/rho' + |tau| (psi' + phi').
-struct SecSums {
-  double psi, dpsi, phi, dphi;
-};
-
-__device__ __forceinline__ SecSums sec_sweep(const double* __restrict__ D,
-                                             const double* __restrict__ Z, int K, double dorg,
-                                             double tau, int jl) {
-  SecSums s{0.0, 0.0, 0.0, 0.0};
-  for (int i = 0; i < K; ++i) {
-    double zi = Z[i];
-    double delta = (D[i] - dorg) - tau;
-    double t = zi / delta;
-    double term = zi * t;
-    double dterm = t * t;
-    if (i <= jl) {
-      s.psi += term;
-      s.dpsi += dterm;
-    } else {
-      s.phi += term;
-      s.dphi += dterm;
-    }
-  }
-  return s;
-}
-
-// returns the number of pole sweeps; *ok = false if the iteration cap was hit
-__device__ int secular_root(const double* __restrict__ D, const double* __restrict__ Z, int K,
-                            int j, double rho, double zsq, int* org_out, double* tau_out,
-                            bool* ok) {
-  const double rhoinv = 1.0 / rho;
-  *ok = true;
-  if (K == 1) {
-    *org_out = 0;
-    *tau_out = rho * Z[0] * Z[0];
-    return 0;
-  }
-  int sweeps = 1;
-  int org, jl, jr;
-  double tau, tlo, thi;
-  SecSums s;
-  double w;
-  if (j < K - 1) {
-    jl = j;
-    jr = j + 1;
-    const double gap = D[j + 1] - D[j];
-    const double half = 0.5 * gap;
-    s = sec_sweep(D, Z, K, D[j], half, jl);
-    w = rhoinv + s.psi + s.phi;
-    if (w >= 0.0) {
-      org = j;
-      tau = half;
-      tlo = 0.0;
-      thi = half;
-    } else {
-      org = j + 1;
-      tau = -half;
-      tlo = -half;
-      thi = 0.0;
-    }
-  } else {
-    jl = K - 2;
-    jr = K - 1;
-    org = K - 1;
-    const double upper = rho * zsq;
-    tau = 0.5 * upper;
-    s = sec_sweep(D, Z, K, D[org], tau, jl);
-    w = rhoinv + s.psi + s.phi;
-    if (w >= 0.0) {
-      tlo = 0.0;
-      thi = tau;
-    } else {
-      tlo = tau;
-      thi = upper;
-    }
-  }
-  const double dorg = D[org];
-  const double ol = D[jl] - dorg, orr = D[jr] - dorg;  // pole offsets from the origin
-  int it = 0;
-  const int max_it = 64;
-  for (; it < max_it; ++it) {
-    const double erretm = 8.0 * (fabs(s.psi) + fabs(s.phi)) + rhoinv + fabs(tau) * (s.dpsi + s.dphi);
-    if (fabs(w) <= kEps * erretm) break;
-    if (w > 0.0)
-      thi = fmin(thi, tau);
-    else
-      tlo = fmax(tlo, tau);
-    const double a = ol - tau, b = orr - tau;  // Delta of the two model poles
-    const double S1 = a * a * s.dpsi, S2 = b * b * s.dphi;
-    const double C = w - S1 / a - S2 / b;
-    const double A = C * (a + b) + S1 + S2;
-    const double Bq = a * b * w;
-    double eta = 0.0;
-    bool have = false;
-    if (C == 0.0) {
-      if (A != 0.0) {
-        eta = Bq / A;
-        have = true;
-      }
-    } else {
-      double disc = fmax(A * A - 4.0 * Bq * C, 0.0);
-      double sq = sqrt(disc);
-      double q = 0.5 * (A >= 0.0 ? A + sq : A - sq);
-      double r1 = q / C;
-      double r2 = (q != 0.0) ? Bq / q : r1;
-      bool ok1 = (tau + r1 > tlo) && (tau + r1 < thi);
-      bool ok2 = (tau + r2 > tlo) && (tau + r2 < thi);
-      if (ok1 && ok2) {
-        eta = fabs(r1) < fabs(r2) ? r1 : r2;
-        have = true;
-      } else if (ok1) {
-        eta = r1;
-        have = true;
-      } else if (ok2) {
-        eta = r2;
-        have = true;
-      }
-    }
-    double ntau = tau + eta;
-    if (!have || !(ntau > tlo && ntau < thi)) ntau = 0.5 * (tlo + thi);
-    if (ntau == tau) break;
-    tau = ntau;
-    s = sec_sweep(D, Z, K, dorg, tau, jl);
-    ++sweeps;
-    w = rhoinv + s.psi + s.phi;
-    if (thi - tlo <= 2.0 * kEps * fmax(fabs(tlo), fabs(thi))) break;
-  }
-  *org_out = org;
-  *tau_out = tau;
-  *ok = it < max_it;
-  return sweeps;
-}
-
-struct RootArgs {
-  const Merge* M;
-  const MState* ms;
-  const int32_t* ROOTMAP;
-  const uint32_t* count;
-  const double *AD, *AZ, *ALO, *AHI;
-  double* TAU;
-  int32_t* ORG;
-  double* LAMA;  // aliases D
-  double* ZHAT;  // aliases Z
-  double *ROWLO, *ROWHI;  // alias RLO, RHI
-  Status* st;
-};
-
-__global__ void k_secular(RootArgs a) {
-  const uint32_t total = *a.count;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
-    const int g = a.ROOTMAP[r];
-    const MState ms = a.ms[g];
-    const int j = int(r) - ms.base;
-    const int lo = a.M[g].lo;
-    int org;
-    double tau;
-    bool ok;
-    int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, &org, &tau, &ok);
-    if (!ok) set_status(a.st, TDE_ENOCONV);
-    work_add(a.st, kWorkSecularPairs, unsigned(sweeps) * unsigned(ms.K));
-    work_add(a.st, kWorkSecularSweeps, unsigned(sweeps));
-    work_add(a.st, kWorkRoots, 1u);
-    a.TAU[lo + j] = tau;
-    a.ORG[lo + j] = org;
-    a.LAMA[lo + j] = a.AD[lo + org] + tau;
-  }
-}
-
-__global__ void k_lowner(RootArgs a) {
-  const uint32_t total = *a.count;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
-    const int g = a.ROOTMAP[r];
-    const Merge m = a.M[g];
-    if (uint32_t(m.info) & kRootBit) continue;
-    const MState ms = a.ms[g];
-    const int K = ms.K, i = int(r) - ms.base, lo = m.lo;
-    const double* AD = a.AD + lo;
-    const int32_t* ORG = a.ORG + lo;
-    const double* TAU = a.TAU + lo;
-    const double Di = AD[i];
-    double prod = ((AD[ORG[K - 1]] - Di) + TAU[K - 1]) / ms.rho;
-    for (int j = 0; j < K - 1; ++j) {
-      double num = (AD[ORG[j]] - Di) + TAU[j];
-      double den = (j < i ? AD[j] : AD[j + 1]) - Di;
-      prod *= num / den;
-    }
-    a.ZHAT[lo + i] = copysign(sqrt(fmax(prod, 0.0)), a.AZ[lo + i]);
-    work_add(a.st, kWorkLownerPairs, unsigned(K));
-  }
-}
-
-__global__ void k_rows(RootArgs a) {
-  const uint32_t total = *a.count;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
-    const int g = a.ROOTMAP[r];
-    const Merge m = a.M[g];
-    if (uint32_t(m.info) & kRootBit) continue;
-    const MState ms = a.ms[g];
-    const int K = ms.K, j = int(r) - ms.base, lo = m.lo;
-    const double* AD = a.AD + lo;
-    const double* ZH = a.ZHAT + lo;
-    const double* AL = a.ALO + lo;
-    const double* AH = a.AHI + lo;
-    const double dorg = AD[a.ORG[lo + j]];
-    const double tau = a.TAU[lo + j];
-    double s2 = 0.0, sl = 0.0, sh = 0.0;
-    for (int i = 0; i < K; ++i) {
-      double delta = (AD[i] - dorg) - tau;
-      double t = ZH[i] / delta;
-      s2 += t * t;
-      sl += AL[i] * t;
-      sh += AH[i] * t;
-    }
-    double inv = 1.0 / sqrt(s2);
-    a.ROWLO[lo + j] = sl * inv;
-    a.ROWHI[lo + j] = sh * inv;
-    work_add(a.st, kWorkRowsPairs, unsigned(K));
-  }
-}
-
-// ---------------------------------------------------------------------------
 __global__ void k_place(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
                         const MState* __restrict__ ms, const double* __restrict__ LAMA,
                         const double* __restrict__ ROWLO, const double* __restrict__ ROWHI,
@@ -811,36 +576,7 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   prof_begin(kKDeflate, s);
   k_deflate<<<def_grid, kNT, 0, s>>>(da);
   prof_end(kKDeflate, s);
-  RootArgs ra;
-  ra.M = M;
-  ra.ms = ws.mstate;
-  ra.ROOTMAP = ws.ROOTMAP;
-  ra.count = &ws.status->root_count[step];
-  ra.AD = ws.AD;
-  ra.AZ = ws.AZ;
-  ra.ALO = ws.ALO;
-  ra.AHI = ws.AHI;
-  ra.TAU = ws.TAU;
-  ra.ORG = ws.ORG;
-  ra.LAMA = ws.D;
-  ra.ZHAT = ws.Z;
-  ra.ROWLO = ws.RLO;
-  ra.ROWHI = ws.RHI;
-  ra.st = ws.status;
-  const int root_grid = int(std::min<int64_t>((nrows + 127) / 128, 148 * 8));
-  prof_begin(kKSecular, s);
-  k_secular<<<root_grid, 128, 0, s>>>(ra);
-  prof_end(kKSecular, s);
-  int launches = 4;
-  if (plan.step_has_nonroot[step]) {
-    prof_begin(kKLowner, s);
-    k_lowner<<<root_grid, 128, 0, s>>>(ra);
-    prof_end(kKLowner, s);
-    prof_begin(kKRows, s);
-    k_rows<<<root_grid, 128, 0, s>>>(ra);
-    prof_end(kKRows, s);
-    launches += 2;
-  }
+  int launches = 3 + launch_roots(plan, ws, step, M, s);
   prof_begin(kKPlace, s);
   k_place<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.mstate, ws.D, ws.RLO, ws.RHI, ws.AD,
                                     ws.ALO, ws.AHI, ws.sigma_bits, ws.LAM, ws.BLO, ws.BHI,

@@ -42,8 +42,11 @@ int build_plan(int64_t batch, const int64_t* off, int32_t leaf, Plan* plan) {
     if (L > p.steps) p.steps = L;
     if (L > kMaxSteps) return TDE_EINVAL;
     for (int s = 0; s < L; ++s) {
-      p.step_count[s] += int64_t(1) << (L - 1 - s);
-      if (L - 1 - s > 0) p.step_has_nonroot[s] = true;
+      const int h = L - 1 - s;
+      p.step_count[s] += int64_t(1) << h;
+      if (h > 0) p.step_has_nonroot[s] = true;
+      const int64_t size = (nk + (int64_t(1) << h) - 1) >> h;  // ceil(n / 2^h)
+      if (size > p.step_maxsize[s]) p.step_maxsize[s] = size;
     }
   }
   p.nrows = batch > 0 ? off[batch] : 0;

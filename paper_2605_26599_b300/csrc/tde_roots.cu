@@ -1,0 +1,525 @@
+// Root-level kernels of one merge step: the secular solve, the Lowner z-hat and
+// the boundary-row update (Sec. 4.1; Algorithm 1, "solve the local secular
+// equations ... compute (Q_v)_sigma by selected-row updates").
+//
+// All three are sweeps over the K active poles of a merge for each of its K roots
+// (or, for z-hat, over the K roots for each pole), so a merge costs O(K^2) FP64
+// work on O(K) data that stays in L1/L2.  On this part FP64 is the scarce
+// resource (an FP64 instruction occupies the pipe for the whole warp whether or
+// not its lanes are active), so the kernels keep every lane busy:
+//   * merges of order >= kWarpMinK: one warp per root (per pole for z-hat); the
+//     32 lanes stride over the poles and the partial sums are combined with
+//     shuffles, so the whole warp shares one root's iteration count;
+//   * smaller merges: one thread per root, consecutive roots in a warp.
+// Reciprocals use rcp_refined (three fused multiply-adds) instead of IEEE
+// division.
+#include <algorithm>
+
+#include "tde_internal.cuh"
+
+namespace tde {
+
+constexpr int kWarpMinK = 1024;
+
+struct RootArgs {
+  const Merge* M;
+  const MState* ms;
+  const int32_t* ROOTMAP;
+  const uint32_t* count;
+  const double *AD, *AZ, *ALO, *AHI;
+  double* TAU;
+  int32_t* ORG;
+  double* LAMA;           // aliases D: lambda_j of the active roots
+  double* ZHAT;           // aliases Z
+  double *ROWLO, *ROWHI;  // alias RLO, RHI: parent rows of the active columns
+  Status* st;
+};
+
+// ---------------------------------------------------------------------------
+// Secular equation.  For root j (0-based) of the active problem with sorted
+// distinct poles D and nonzero z, w(lambda) = 1/rho' + sum_i z_i^2 / (D_i - lambda)
+// has one root in (D_j, D_{j+1}) for j < K-1 and one in (D_{K-1}, D_{K-1} + rho' zsq)
+// for the last root.  In shifted coordinates lambda = D_org + tau with
+// Delta_i = (D_i - D_org) - tau the two poles that bracket the root keep full
+// relative accuracy.
+//
+// Iteration: evaluate w and its derivative split into the poles left of the root
+// (psi: i <= jl) and right of it (phi: i > jl), then take the root of the two-pole
+// rational model C + S1 / (Delta_jl - eta) + S2 / (Delta_jr - eta) that matches w
+// and w' (S1 = Delta_jl^2 psi', S2 = Delta_jr^2 phi'), kept inside a bisection
+// bracket.  The start is the midpoint of the interval, whose sign of w also
+// chooses the origin (the nearer pole).  Convergence: |w| below eps times a
+// running bound on the rounding error of its evaluation,
+// 8 (|psi| + |phi|) + 1/rho' + |tau| (psi' + phi').
+struct SecSums {
+  double psi, dpsi, phi, dphi;
+};
+
+struct SecState {
+  int org, jl, jr;
+  double tau, tlo, thi, w, dorg, ol, orr, rhoinv;
+  SecSums s;
+};
+
+// first sweep point and the bracket; `sweep(dorg, tau, jl)` evaluates the sums
+template <class Sweep>
+__device__ __forceinline__ void sec_init(const double* D, int K, int j, double rho, double zsq,
+                                         Sweep& sweep, SecState& q) {
+  q.rhoinv = 1.0 / rho;
+  if (j < K - 1) {
+    q.jl = j;
+    q.jr = j + 1;
+    const double half = 0.5 * (D[j + 1] - D[j]);
+    q.s = sweep(D[j], half, q.jl);
+    q.w = q.rhoinv + q.s.psi + q.s.phi;
+    if (q.w >= 0.0) {
+      q.org = j;
+      q.tau = half;
+      q.tlo = 0.0;
+      q.thi = half;
+    } else {
+      q.org = j + 1;
+      q.tau = -half;
+      q.tlo = -half;
+      q.thi = 0.0;
+    }
+  } else {
+    q.jl = K - 2;
+    q.jr = K - 1;
+    q.org = K - 1;
+    const double upper = rho * zsq;
+    q.tau = 0.5 * upper;
+    q.s = sweep(D[q.org], q.tau, q.jl);
+    q.w = q.rhoinv + q.s.psi + q.s.phi;
+    if (q.w >= 0.0) {
+      q.tlo = 0.0;
+      q.thi = q.tau;
+    } else {
+      q.tlo = q.tau;
+      q.thi = upper;
+    }
+  }
+  q.dorg = D[q.org];
+  q.ol = D[q.jl] - q.dorg;
+  q.orr = D[q.jr] - q.dorg;
+}
+
+// one iteration; returns false when converged (no new sweep needed)
+__device__ __forceinline__ bool sec_step(SecState& q) {
+  const double erretm =
+      8.0 * (fabs(q.s.psi) + fabs(q.s.phi)) + q.rhoinv + fabs(q.tau) * (q.s.dpsi + q.s.dphi);
+  if (fabs(q.w) <= kEps * erretm) return false;
+  if (q.w > 0.0)
+    q.thi = fmin(q.thi, q.tau);
+  else
+    q.tlo = fmax(q.tlo, q.tau);
+  if (q.thi - q.tlo <= 2.0 * kEps * fmax(fabs(q.tlo), fabs(q.thi))) return false;
+  const double a = q.ol - q.tau, b = q.orr - q.tau;  // Delta of the two model poles
+  const double S1 = a * a * q.s.dpsi, S2 = b * b * q.s.dphi;
+  const double C = q.w - S1 / a - S2 / b;
+  const double A = C * (a + b) + S1 + S2;
+  const double Bq = a * b * q.w;
+  double eta = 0.0;
+  bool have = false;
+  if (C == 0.0) {
+    if (A != 0.0) {
+      eta = Bq / A;
+      have = true;
+    }
+  } else {
+    const double sq = sqrt(fmax(A * A - 4.0 * Bq * C, 0.0));
+    const double qq = 0.5 * (A >= 0.0 ? A + sq : A - sq);
+    const double r1 = qq / C;
+    const double r2 = (qq != 0.0) ? Bq / qq : r1;
+    const bool ok1 = (q.tau + r1 > q.tlo) && (q.tau + r1 < q.thi);
+    const bool ok2 = (q.tau + r2 > q.tlo) && (q.tau + r2 < q.thi);
+    if (ok1 && ok2) {
+      eta = fabs(r1) < fabs(r2) ? r1 : r2;
+      have = true;
+    } else if (ok1) {
+      eta = r1;
+      have = true;
+    } else if (ok2) {
+      eta = r2;
+      have = true;
+    }
+  }
+  double ntau = q.tau + eta;
+  if (!have || !(ntau > q.tlo && ntau < q.thi)) ntau = 0.5 * (q.tlo + q.thi);
+  if (ntau == q.tau) return false;
+  q.tau = ntau;
+  return true;
+}
+
+constexpr int kMaxSweeps = 64;
+
+// Solves root j; returns the number of pole sweeps, *ok = false if capped.
+template <class Sweep>
+__device__ int secular_root(const double* D, const double* Z, int K, int j, double rho, double zsq,
+                            Sweep& sweep, int* org_out, double* tau_out, bool* ok) {
+  *ok = true;
+  if (K == 1) {
+    *org_out = 0;
+    *tau_out = rho * Z[0] * Z[0];
+    return 0;
+  }
+  SecState q;
+  sec_init(D, K, j, rho, zsq, sweep, q);
+  int sweeps = 1;
+  while (sec_step(q)) {
+    if (sweeps >= kMaxSweeps) {
+      *ok = false;
+      break;
+    }
+    q.s = sweep(q.dorg, q.tau, q.jl);
+    q.w = q.rhoinv + q.s.psi + q.s.phi;
+    ++sweeps;
+  }
+  *org_out = q.org;
+  *tau_out = q.tau;
+  return sweeps;
+}
+
+// one thread evaluates all K poles
+struct ThreadSweep {
+  const double* __restrict__ D;
+  const double* __restrict__ Z;
+  int K;
+  __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
+    SecSums s{0.0, 0.0, 0.0, 0.0};
+    for (int i = 0; i < K; ++i) {
+      const double zi = Z[i];
+      const double t = zi * rcp_refined((D[i] - dorg) - tau);
+      const bool left = i <= jl;
+      const double zl = left ? zi : 0.0, zr = left ? 0.0 : zi;
+      const double tl = left ? t : 0.0, tr = left ? 0.0 : t;
+      s.psi = fma(zl, t, s.psi);
+      s.dpsi = fma(tl, t, s.dpsi);
+      s.phi = fma(zr, t, s.phi);
+      s.dphi = fma(tr, t, s.dphi);
+    }
+    return s;
+  }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// the 32 lanes of a warp stride over the poles (left and right ranges separately)
+struct WarpSweep {
+  const double* __restrict__ D;
+  const double* __restrict__ Z;
+  int K;
+  int lane;
+  __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
+    double p0 = 0.0, dp0 = 0.0, p1 = 0.0, dp1 = 0.0;
+    int i = lane;
+    for (; i + 32 <= jl; i += 64) {
+      const double z0 = Z[i], z1 = Z[i + 32];
+      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+      const double t1 = z1 * rcp_refined((D[i + 32] - dorg) - tau);
+      p0 = fma(z0, t0, p0);
+      dp0 = fma(t0, t0, dp0);
+      p1 = fma(z1, t1, p1);
+      dp1 = fma(t1, t1, dp1);
+    }
+    for (; i <= jl; i += 32) {
+      const double z0 = Z[i];
+      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+      p0 = fma(z0, t0, p0);
+      dp0 = fma(t0, t0, dp0);
+    }
+    double f0 = 0.0, df0 = 0.0, f1 = 0.0, df1 = 0.0;
+    i = jl + 1 + lane;
+    for (; i + 32 < K; i += 64) {
+      const double z0 = Z[i], z1 = Z[i + 32];
+      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+      const double t1 = z1 * rcp_refined((D[i + 32] - dorg) - tau);
+      f0 = fma(z0, t0, f0);
+      df0 = fma(t0, t0, df0);
+      f1 = fma(z1, t1, f1);
+      df1 = fma(t1, t1, df1);
+    }
+    for (; i < K; i += 32) {
+      const double z0 = Z[i];
+      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+      f0 = fma(z0, t0, f0);
+      df0 = fma(t0, t0, df0);
+    }
+    SecSums s;
+    s.psi = warp_sum(p0 + p1);
+    s.dpsi = warp_sum(dp0 + dp1);
+    s.phi = warp_sum(f0 + f1);
+    s.dphi = warp_sum(df0 + df1);
+    return s;
+  }
+};
+
+__device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, int org, double tau,
+                                              int sweeps, int K, bool ok, bool leader) {
+  if (leader) {
+    if (!ok) set_status(a.st, TDE_ENOCONV);
+    a.TAU[lo + j] = tau;
+    a.ORG[lo + j] = org;
+    a.LAMA[lo + j] = a.AD[lo + org] + tau;
+  }
+}
+
+__global__ void k_secular_thread(RootArgs a) {
+  const uint32_t total = *a.count;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
+    const int g = a.ROOTMAP[r];
+    const MState ms = a.ms[g];
+    const int j = int(r) - ms.base, lo = a.M[g].lo;
+    ThreadSweep sw{a.AD + lo, a.AZ + lo, ms.K};
+    int org;
+    double tau;
+    bool ok;
+    const int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, &org, &tau, &ok);
+    secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, true);
+    work_add(a.st, kWorkSecularPairs, unsigned(sweeps) * unsigned(ms.K));
+    work_add(a.st, kWorkSecularSweeps, unsigned(sweeps));
+    work_add(a.st, kWorkRoots, 1u);
+  }
+}
+
+__global__ void k_secular_warp(RootArgs a) {
+  const uint32_t total = *a.count;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned pairs = 0, sweeps_acc = 0, roots = 0;
+  for (uint32_t r = warp; r < total; r += nwarps) {
+    const int g = a.ROOTMAP[r];
+    const MState ms = a.ms[g];
+    const int j = int(r) - ms.base, lo = a.M[g].lo;
+    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane};
+    int org;
+    double tau;
+    bool ok;
+    const int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, &org, &tau, &ok);
+    secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
+    pairs += unsigned(sweeps) * unsigned(ms.K);
+    sweeps_acc += unsigned(sweeps);
+    roots += 1;
+  }
+  if (lane == 0 && roots) {
+    atomicAdd(&a.st->work[kWorkSecularPairs], (unsigned long long)pairs);
+    atomicAdd(&a.st->work[kWorkSecularSweeps], (unsigned long long)sweeps_acc);
+    atomicAdd(&a.st->work[kWorkRoots], (unsigned long long)roots);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z-hat of pole i from all K roots (appendix "WPROD product chains"):
+//   zhat_i^2 = (lambda_K - D_i) / rho' * prod_{j<i} (lambda_j - D_i) / (D_j - D_i)
+//              * prod_{i<=j<K-1} (lambda_j - D_i) / (D_{j+1} - D_i)
+// (1-based K), every factor positive and below one by interlacing, so the partial
+// products neither overflow nor underflow before the full product does.
+// lambda_j - D_i = (D_org(j) - D_i) + tau_j keeps the near factors accurate.
+__device__ __forceinline__ double lowner_factor(const double* AD, const int32_t* ORG,
+                                                const double* TAU, int i, double Di, int j) {
+  const double num = (AD[ORG[j]] - Di) + TAU[j];
+  const double den = (j < i ? AD[j] : AD[j + 1]) - Di;
+  return num * rcp_refined(den);
+}
+
+__global__ void k_lowner_thread(RootArgs a) {
+  const uint32_t total = *a.count;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
+    const int g = a.ROOTMAP[r];
+    const Merge m = a.M[g];
+    if (uint32_t(m.info) & kRootBit) continue;
+    const MState ms = a.ms[g];
+    const int K = ms.K, i = int(r) - ms.base, lo = m.lo;
+    const double* AD = a.AD + lo;
+    const int32_t* ORG = a.ORG + lo;
+    const double* TAU = a.TAU + lo;
+    const double Di = AD[i];
+    double prod = ((AD[ORG[K - 1]] - Di) + TAU[K - 1]) / ms.rho;
+    for (int j = 0; j < K - 1; ++j) prod *= lowner_factor(AD, ORG, TAU, i, Di, j);
+    a.ZHAT[lo + i] = copysign(sqrt(fmax(prod, 0.0)), a.AZ[lo + i]);
+    work_add(a.st, kWorkLownerPairs, unsigned(K));
+  }
+}
+
+__global__ void k_lowner_warp(RootArgs a) {
+  const uint32_t total = *a.count;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned pairs = 0;
+  for (uint32_t r = warp; r < total; r += nwarps) {
+    const int g = a.ROOTMAP[r];
+    const Merge m = a.M[g];
+    if (uint32_t(m.info) & kRootBit) continue;
+    const MState ms = a.ms[g];
+    const int K = ms.K, i = int(r) - ms.base, lo = m.lo;
+    const double* AD = a.AD + lo;
+    const int32_t* ORG = a.ORG + lo;
+    const double* TAU = a.TAU + lo;
+    const double Di = AD[i];
+    double p0 = 1.0, p1 = 1.0;
+    int j = lane;
+    for (; j + 32 < K - 1; j += 64) {
+      p0 *= lowner_factor(AD, ORG, TAU, i, Di, j);
+      p1 *= lowner_factor(AD, ORG, TAU, i, Di, j + 32);
+    }
+    for (; j < K - 1; j += 32) p0 *= lowner_factor(AD, ORG, TAU, i, Di, j);
+    double prod = p0 * p1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, o);
+    prod *= ((AD[ORG[K - 1]] - Di) + TAU[K - 1]) / ms.rho;
+    if (lane == 0) a.ZHAT[lo + i] = copysign(sqrt(fmax(prod, 0.0)), a.AZ[lo + i]);
+    pairs += unsigned(K);
+  }
+  if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkLownerPairs], (unsigned long long)pairs);
+}
+
+// ---------------------------------------------------------------------------
+// Parent boundary rows of active column j (Sec. 4.1): with y_j(i) proportional to
+// zhat_i / Delta_ij, R_parent(:, j) = R_child y_j / ||zhat / Delta_:j||.
+__global__ void k_rows_thread(RootArgs a) {
+  const uint32_t total = *a.count;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
+    const int g = a.ROOTMAP[r];
+    const Merge m = a.M[g];
+    if (uint32_t(m.info) & kRootBit) continue;
+    const MState ms = a.ms[g];
+    const int K = ms.K, j = int(r) - ms.base, lo = m.lo;
+    const double* AD = a.AD + lo;
+    const double* ZH = a.ZHAT + lo;
+    const double* AL = a.ALO + lo;
+    const double* AH = a.AHI + lo;
+    const double dorg = AD[a.ORG[lo + j]];
+    const double tau = a.TAU[lo + j];
+    double s2 = 0.0, sl = 0.0, sh = 0.0;
+    for (int i = 0; i < K; ++i) {
+      const double t = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
+      s2 = fma(t, t, s2);
+      sl = fma(AL[i], t, sl);
+      sh = fma(AH[i], t, sh);
+    }
+    const double inv = 1.0 / sqrt(s2);
+    a.ROWLO[lo + j] = sl * inv;
+    a.ROWHI[lo + j] = sh * inv;
+    work_add(a.st, kWorkRowsPairs, unsigned(K));
+  }
+}
+
+__global__ void k_rows_warp(RootArgs a) {
+  const uint32_t total = *a.count;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  unsigned pairs = 0;
+  for (uint32_t r = warp; r < total; r += nwarps) {
+    const int g = a.ROOTMAP[r];
+    const Merge m = a.M[g];
+    if (uint32_t(m.info) & kRootBit) continue;
+    const MState ms = a.ms[g];
+    const int K = ms.K, j = int(r) - ms.base, lo = m.lo;
+    const double* AD = a.AD + lo;
+    const double* ZH = a.ZHAT + lo;
+    const double* AL = a.ALO + lo;
+    const double* AH = a.AHI + lo;
+    const double dorg = AD[a.ORG[lo + j]];
+    const double tau = a.TAU[lo + j];
+    double s2 = 0.0, sl = 0.0, sh = 0.0, s2b = 0.0, slb = 0.0, shb = 0.0;
+    int i = lane;
+    for (; i + 32 < K; i += 64) {
+      const double t0 = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
+      const double t1 = ZH[i + 32] * rcp_refined((AD[i + 32] - dorg) - tau);
+      s2 = fma(t0, t0, s2);
+      sl = fma(AL[i], t0, sl);
+      sh = fma(AH[i], t0, sh);
+      s2b = fma(t1, t1, s2b);
+      slb = fma(AL[i + 32], t1, slb);
+      shb = fma(AH[i + 32], t1, shb);
+    }
+    for (; i < K; i += 32) {
+      const double t0 = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
+      s2 = fma(t0, t0, s2);
+      sl = fma(AL[i], t0, sl);
+      sh = fma(AH[i], t0, sh);
+    }
+    s2 = warp_sum(s2 + s2b);
+    sl = warp_sum(sl + slb);
+    sh = warp_sum(sh + shb);
+    if (lane == 0) {
+      const double inv = 1.0 / sqrt(s2);
+      a.ROWLO[lo + j] = sl * inv;
+      a.ROWHI[lo + j] = sh * inv;
+    }
+    pairs += unsigned(K);
+  }
+  if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkRowsPairs], (unsigned long long)pairs);
+}
+
+// ---------------------------------------------------------------------------
+int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s) {
+  RootArgs ra;
+  ra.M = M;
+  ra.ms = ws.mstate;
+  ra.ROOTMAP = ws.ROOTMAP;
+  ra.count = &ws.status->root_count[step];
+  ra.AD = ws.AD;
+  ra.AZ = ws.AZ;
+  ra.ALO = ws.ALO;
+  ra.AHI = ws.AHI;
+  ra.TAU = ws.TAU;
+  ra.ORG = ws.ORG;
+  ra.LAMA = ws.D;
+  ra.ZHAT = ws.Z;
+  ra.ROWLO = ws.RLO;
+  ra.ROWHI = ws.RHI;
+  ra.st = ws.status;
+  const bool warp = plan.step_maxsize[step] >= kWarpMinK;
+  const int64_t nrows = plan.nrows;
+  // thread kernels: one thread per possible root; warp kernels: a persistent grid
+  const int tgrid = int(std::min<int64_t>((nrows + 127) / 128, 148 * 8));
+  const int wgrid = 148 * 8;
+  int launches = 1;
+  prof_begin(kKSecular, s);
+  if (warp)
+    k_secular_warp<<<wgrid, 128, 0, s>>>(ra);
+  else
+    k_secular_thread<<<tgrid, 128, 0, s>>>(ra);
+  prof_end(kKSecular, s);
+  if (plan.step_has_nonroot[step]) {
+    prof_begin(kKLowner, s);
+    if (warp)
+      k_lowner_warp<<<wgrid, 128, 0, s>>>(ra);
+    else
+      k_lowner_thread<<<tgrid, 128, 0, s>>>(ra);
+    prof_end(kKLowner, s);
+    prof_begin(kKRows, s);
+    if (warp)
+      k_rows_warp<<<wgrid, 128, 0, s>>>(ra);
+    else
+      k_rows_thread<<<tgrid, 128, 0, s>>>(ra);
+    prof_end(kKRows, s);
+    launches += 2;
+  }
+  return launches;
+}
+
+__global__ void k_check_reciprocal(int64_t n, const double* __restrict__ x, double* out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = rcp_refined(x[i]);
+}
+
+}  // namespace tde
+
+extern "C" int tde_check_reciprocal(int64_t n, const double* x, double* out, void* stream) {
+  using namespace tde;
+  if (n < 0 || (n > 0 && (x == nullptr || out == nullptr))) return TDE_EINVAL;
+  if (n == 0) return TDE_OK;
+  const int grid = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+  k_check_reciprocal<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(n, x, out);
+  return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
+}

@@ -1,0 +1,42 @@
+"""GPU checks of individual device building blocks through the C ABI."""
+import ctypes
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_26599_b300 import _lib
+
+    return _lib.load()
+
+
+def test_refined_reciprocal_matches_ieee_division(lib):
+    import torch
+
+    rng = np.random.default_rng(0)
+    mant = rng.uniform(1.0, 2.0, 200000)
+    expo = rng.integers(-100, 100, 200000)
+    sign = rng.choice([-1.0, 1.0], 200000)
+    x = sign * np.ldexp(mant, expo)
+    x = np.concatenate([x, [1.0, -1.0, 3.0, 0.1, 1e-30, 7e29, 1.0 - 2 ** -52, 1.0 + 2 ** -52]])
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    rc = lib.tde_check_reciprocal(x.shape[0], ctypes.c_void_p(xt.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()),
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    got = out.cpu().numpy()
+    ref = 1.0 / x
+    rel = np.abs(got - ref) / np.abs(ref)
+    # within one unit in the last place of IEEE 1/x
+    assert rel.max() <= 2 * EPS, rel.max()
