@@ -12,11 +12,11 @@
 //                         then the deflated eigenvalues of the merge, both sorted)
 //   compact roots         TAU (N doubles) + ORG (N int32): lambda_j = AD[ORG] + TAU
 //                         (Sec. 4.1 compact root representation)
-//   maps                  SEG, ROOTMAP, SURV (N int32), PFLAG, RFLAG (N bytes)
+//   maps                  SEG, ROOTMAP, ROOTMAP2, SURV (N int32), PFLAG, RFLAG (N bytes)
 //   sort scratch          KEYA, KEYB (N uint64), IDXA, IDXB (N int32)
 //   plan                  merge and leaf descriptors, per-step merge state
 // Aliases once a buffer is dead within a level: LAMA (roots) -> D, ZHAT -> Z,
-// parent rows of active columns -> RLO / RHI.
+// parent rows of active columns -> RLO / RHI, origin poles D_org(j) -> KEYA.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -42,11 +42,16 @@ struct Leaf {
 // Per-merge state of the current step.
 struct MState {
   int32_t K;     // active rank after deflation
-  int32_t base;  // first index of this merge's roots in ROOTMAP
+  int32_t base;  // first index of this merge's roots in its root list
   double rho;    // rho' = 2 |beta|
   double zsq;    // sum of active z^2
-  double pad;
+  int32_t big;   // 1: roots in the warp-per-root list (K >= kWarpMinK)
+  int32_t pad;
 };
+
+// Merges whose active rank K reaches this are solved one warp per root (per pole
+// for z-hat); smaller ones one thread per root.
+constexpr int kWarpMinK = 512;
 
 constexpr uint32_t kRootBit = 0x80000000u;
 
@@ -66,7 +71,8 @@ enum WorkCounter {
 struct Status {
   int32_t info;
   int32_t pad[31];
-  uint32_t root_count[kMaxSteps];  // roots allocated per step
+  uint32_t root_count[kMaxSteps];      // roots of small-K merges per step
+  uint32_t root_count_big[kMaxSteps];  // roots of merges with K >= kWarpMinK
   unsigned long long work[16];
 };
 
@@ -93,7 +99,7 @@ struct Workspace {
   double *D, *Z, *RLO, *RHI;
   double *AD, *AZ, *ALO, *AHI;
   double* TAU;
-  int32_t *ORG, *SEG, *ROOTMAP, *SURV;
+  int32_t *ORG, *SEG, *ROOTMAP, *ROOTMAP2, *SURV;
   uint8_t *PFLAG, *RFLAG;
   unsigned long long *KEYA, *KEYB;
   int32_t *IDXA, *IDXB;

@@ -193,7 +193,7 @@ __device__ void run_boundaries(int S, const int32_t* surv, const double* D, cons
 // Block merge sort of keys (with int payload) in global scratch; n entries.
 // Tiles of kTile are sorted in shared memory (bitonic), then merged pairwise.
 // Returns a pointer to the buffer (A or B) holding the result.
-constexpr int kTile = 2048;
+constexpr int kTile = 1024;
 __device__ int block_sort(int n, unsigned long long* KA, int32_t* IA, unsigned long long* KB,
                           int32_t* IB, unsigned long long* skey, int32_t* sidx) {
   for (int t0 = 0; t0 < n; t0 += kTile) {
@@ -276,7 +276,7 @@ struct DeflateArgs {
   const double* es;
   double *D, *Z, *RLO, *RHI;
   double *AD, *AZ, *ALO, *AHI;
-  int32_t *SURV, *ROOTMAP, *IDXA, *IDXB;
+  int32_t *SURV, *ROOTMAP, *ROOTMAP2, *IDXA, *IDXB;
   uint8_t *PFLAG, *RFLAG;
   unsigned long long *KEYA, *KEYB;
   MState* ms;
@@ -373,12 +373,21 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
         s_aggh[warp] = h ? 1 : 0;
       }
       __syncthreads();
-      if (tid == 0) {
-        T4 run = carry;
-        for (int w = 0; w < kNT / 32; ++w) {
-          s_pre[w] = run;
-          run = s_aggh[w] ? s_agg[w] : t4_add(run, s_agg[w]);
+      if (warp == 0) {  // prefix of each warp: carry, then the warp aggregates before it
+        T4 inc = lane < kNT / 32 ? s_agg[lane] : T4{0.0, 0.0, 0.0, 0.0};
+        bool hh = lane < kNT / 32 ? s_aggh[lane] != 0 : true;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          T4 vo = t4_shfl_up(inc, o);
+          bool ho = __shfl_up_sync(0xffffffffu, hh, o);
+          if (lane >= o) {
+            if (!hh) inc = t4_add(inc, vo);
+            hh = hh || ho;
+          }
         }
+        const T4 pv = t4_shfl_up(inc, 1);
+        const bool ph = __shfl_up_sync(0xffffffffu, hh, 1);
+        if (lane < kNT / 32) s_pre[lane] = lane == 0 ? carry : (ph ? pv : t4_add(carry, pv));
       }
       __syncthreads();
       if (!h) v = t4_add(v, s_pre[warp]);
@@ -399,7 +408,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
         D[pos] = val;
         RLO[pos] = (zk * prev.ulo - Wp * rl) * sc;
         RHI[pos] = (zk * prev.uhi - Wp * rh) * sc;
-        PFLAG[pos] = 1;
+        PFLAG[pos] = 2;
       }
       if (valid && runend) {
         double ad, az, al, ah;
@@ -431,69 +440,86 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       __syncthreads();
     }
 
-    // 5. deflated eigenvalues in position order after the active poles
-    const int F = n0 - K;
-    int f = 0;
+    // 5. deflated eigenvalues: those deflated for a negligible z (PFLAG 1) keep the
+    //    ascending order of D; rotated ones (PFLAG 2) may be out of order.  Collect
+    //    the positions of each kind, in position order.
+    int32_t* ZPOS = SURV;  // the survivor list is dead after step 4
+    int32_t* RPOS = a.IDXA + lo;
+    int FZ = 0, FR = 0;
     for (int c0 = 0; c0 < n0; c0 += kNT) {
-      int i = c0 + tid;
-      int is = (i < n0 && PFLAG[i]) ? 1 : 0;
+      const int i = c0 + tid;
+      const int pf = i < n0 ? PFLAG[i] : 0;
+      const int both = (pf == 1 ? 1 : 0) | (pf == 2 ? (1 << 16) : 0);
       int total;
-      int ex = block_excl_scan<kNT>(is, sm_int, &total);
-      if (is) {
-        int dst = lo + K + f + ex;
-        a.AD[dst] = D[i];
-        a.ALO[dst] = RLO[i];
-        a.AHI[dst] = RHI[i];
-      }
-      f += total;
+      const int ex = block_excl_scan<kNT>(both, sm_int, &total);
+      if (pf == 1) ZPOS[FZ + (ex & 0xffff)] = i;
+      if (pf == 2) RPOS[FR + (ex >> 16)] = i;
+      FZ += total & 0xffff;
+      FR += total >> 16;
     }
     if (tid == 0) s_flag = 0;
     __syncthreads();
-    // 6. rotations can leave the deflated list out of order: sort it if so
-    for (int i = tid; i + 1 < F; i += kNT)
-      if (a.AD[lo + K + i] > a.AD[lo + K + i + 1]) s_flag = 1;
+    // 6. sort the rotated ones by value if they are out of order
+    for (int k = tid; k + 1 < FR; k += kNT)
+      if (D[RPOS[k]] > D[RPOS[k + 1]]) s_flag = 1;
     __syncthreads();
     if (s_flag) {
-      double* FD = a.AD + lo + K;
-      double* FL = a.ALO + lo + K;
-      double* FH = a.AHI + lo + K;
-      for (int i = tid; i < F; i += kNT) {
-        a.KEYA[lo + i] = order_key(FD[i]);
-        a.IDXA[lo + i] = i;
-      }
+      for (int k = tid; k < FR; k += kNT) a.KEYA[lo + k] = order_key(D[RPOS[k]]);
       __syncthreads();
-      int which = block_sort(F, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);
-      const int32_t* I = which ? a.IDXB + lo : a.IDXA + lo;
-      for (int i = tid; i < F; i += kNT) {  // gather into dead scratch, copy back
-        int s = I[i];
-        D[i] = FD[s];
-        RLO[i] = FL[s];
-        RHI[i] = FH[s];
-      }
-      __syncthreads();
-      for (int i = tid; i < F; i += kNT) {
-        FD[i] = D[i];
-        FL[i] = RLO[i];
-        FH[i] = RHI[i];
-      }
+      const int which = block_sort(FR, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);
+      if (which) RPOS = a.IDXB + lo;
     }
     __syncthreads();
-    // 7. roots of this merge get a contiguous range of the step's root list
+    // 7. merge the two ascending lists into AD / ALO / AHI after the K active poles
+    for (int k = tid; k < FZ; k += kNT) {
+      const int pos = ZPOS[k];
+      const double x = D[pos];
+      int l = 0, h = FR;  // rotated entries strictly below x come first
+      while (l < h) {
+        const int md = (l + h) >> 1;
+        if (D[RPOS[md]] < x) l = md + 1; else h = md;
+      }
+      const int dst = lo + K + k + l;
+      a.AD[dst] = x;
+      a.ALO[dst] = RLO[pos];
+      a.AHI[dst] = RHI[pos];
+    }
+    for (int k = tid; k < FR; k += kNT) {
+      const int pos = RPOS[k];
+      const double x = D[pos];
+      int l = 0, h = FZ;  // negligible-z entries at or below x come first
+      while (l < h) {
+        const int md = (l + h) >> 1;
+        if (D[ZPOS[md]] <= x) l = md + 1; else h = md;
+      }
+      const int dst = lo + K + k + l;
+      a.AD[dst] = x;
+      a.ALO[dst] = RLO[pos];
+      a.AHI[dst] = RHI[pos];
+    }
+    __syncthreads();
+    // 7. roots of this merge get a contiguous range of one of the step's two root
+    //    lists: merges with K >= kWarpMinK are solved one warp per root
     __shared__ int s_base;
+    const bool big = K >= kWarpMinK;
     if (tid == 0) {
-      s_base = K > 0 ? int(atomicAdd(&a.st->root_count[a.step], unsigned(K))) : 0;
+      s_base = K > 0 ? int(atomicAdd(big ? &a.st->root_count_big[a.step] : &a.st->root_count[a.step],
+                                     unsigned(K)))
+                     : 0;
       MState st;
       st.K = K;
       st.base = s_base;
       st.rho = rho;
       st.zsq = zsq;
-      st.pad = 0.0;
+      st.big = big ? 1 : 0;
+      st.pad = 0;
       a.ms[g] = st;
       atomicAdd(&a.st->work[kWorkDeflated], (unsigned long long)(n0 - K));
       atomicAdd(&a.st->work[kWorkRotations], (unsigned long long)(S - K));
     }
     __syncthreads();
-    for (int j = tid; j < K; j += kNT) a.ROOTMAP[s_base + j] = int32_t(g);
+    int32_t* rmap = big ? a.ROOTMAP2 : a.ROOTMAP;
+    for (int j = tid; j < K; j += kNT) rmap[s_base + j] = int32_t(g);
     __syncthreads();
   }
 }
@@ -564,6 +590,7 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   da.AHI = ws.AHI;
   da.SURV = ws.SURV;
   da.ROOTMAP = ws.ROOTMAP;
+  da.ROOTMAP2 = ws.ROOTMAP2;
   da.IDXA = ws.IDXA;
   da.IDXB = ws.IDXB;
   da.PFLAG = ws.PFLAG;
@@ -576,7 +603,7 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   prof_begin(kKDeflate, s);
   k_deflate<<<def_grid, kNT, 0, s>>>(da);
   prof_end(kKDeflate, s);
-  int launches = 3 + launch_roots(plan, ws, step, M, s);
+  int launches = 3 + launch_roots(plan, ws, step, M, s);  // form, deflate, place + roots
   prof_begin(kKPlace, s);
   k_place<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.mstate, ws.D, ws.RLO, ws.RHI, ws.AD,
                                     ws.ALO, ws.AHI, ws.sigma_bits, ws.LAM, ws.BLO, ws.BHI,

@@ -7,9 +7,11 @@
 // work on O(K) data that stays in L1/L2.  On this part FP64 is the scarce
 // resource (an FP64 instruction occupies the pipe for the whole warp whether or
 // not its lanes are active), so the kernels keep every lane busy:
-//   * merges of order >= kWarpMinK: one warp per root (per pole for z-hat); the
-//     32 lanes stride over the poles and the partial sums are combined with
-//     shuffles, so the whole warp shares one root's iteration count;
+//   * merges whose active rank K >= kWarpMinK (known only on the device, after
+//     deflation; the deflation kernel files their roots in a second list): one
+//     warp per root (per pole for z-hat); the 32 lanes stride over the poles and
+//     the partial sums are combined with shuffles, so the whole warp shares one
+//     root's iteration count;
 //   * smaller merges: one thread per root, consecutive roots in a warp.
 // Reciprocals use rcp_refined (three fused multiply-adds) instead of IEEE
 // division.
@@ -19,19 +21,24 @@
 
 namespace tde {
 
-constexpr int kWarpMinK = 1024;
+// Below this many small-K roots in a step the thread-per-root kernels would leave
+// most SMs idle, so the warp-per-root kernels take the small list as well.
+constexpr uint32_t kSmallListMin = 148u * 4u * 32u;
 
 struct RootArgs {
   const Merge* M;
   const MState* ms;
-  const int32_t* ROOTMAP;
-  const uint32_t* count;
+  const int32_t* ROOTMAP;   // roots of merges with K < kWarpMinK
+  const int32_t* ROOTMAP2;  // roots of merges with K >= kWarpMinK
+  const uint32_t* count;    // lengths of the two lists (device)
+  const uint32_t* count2;
   const double *AD, *AZ, *ALO, *AHI;
   double* TAU;
   int32_t* ORG;
   double* LAMA;           // aliases D: lambda_j of the active roots
   double* ZHAT;           // aliases Z
   double *ROWLO, *ROWHI;  // alias RLO, RHI: parent rows of the active columns
+  double* DORG;           // alias KEYA: D_org(j) of every active root
   Status* st;
 };
 
@@ -104,16 +111,19 @@ __device__ __forceinline__ void sec_init(const double* D, int K, int j, double r
   q.orr = D[q.jr] - q.dorg;
 }
 
-// one iteration; returns false when converged (no new sweep needed)
-__device__ __forceinline__ bool sec_step(SecState& q) {
+// One iteration.  Returns 1 if tau moved and needs a new sweep, 0 if converged.
+// A model step below 2^-27 |tau| (about sqrt(eps)) is taken and accepted without
+// another sweep: the iteration converges at least quadratically, so the error
+// left after such a step is of order eps |tau|.
+__device__ __forceinline__ int sec_step(SecState& q) {
   const double erretm =
       8.0 * (fabs(q.s.psi) + fabs(q.s.phi)) + q.rhoinv + fabs(q.tau) * (q.s.dpsi + q.s.dphi);
-  if (fabs(q.w) <= kEps * erretm) return false;
+  if (fabs(q.w) <= kEps * erretm) return 0;
   if (q.w > 0.0)
     q.thi = fmin(q.thi, q.tau);
   else
     q.tlo = fmax(q.tlo, q.tau);
-  if (q.thi - q.tlo <= 2.0 * kEps * fmax(fabs(q.tlo), fabs(q.thi))) return false;
+  if (q.thi - q.tlo <= 2.0 * kEps * fmax(fabs(q.tlo), fabs(q.thi))) return 0;
   const double a = q.ol - q.tau, b = q.orr - q.tau;  // Delta of the two model poles
   const double S1 = a * a * q.s.dpsi, S2 = b * b * q.s.dphi;
   const double C = q.w - S1 / a - S2 / b;
@@ -145,10 +155,12 @@ __device__ __forceinline__ bool sec_step(SecState& q) {
     }
   }
   double ntau = q.tau + eta;
-  if (!have || !(ntau > q.tlo && ntau < q.thi)) ntau = 0.5 * (q.tlo + q.thi);
-  if (ntau == q.tau) return false;
+  const bool model = have && ntau > q.tlo && ntau < q.thi;
+  if (!model) ntau = 0.5 * (q.tlo + q.thi);
+  if (ntau == q.tau) return 0;
   q.tau = ntau;
-  return true;
+  if (model && fabs(eta) <= 0x1p-27 * fabs(ntau)) return 0;
+  return 1;
 }
 
 constexpr int kMaxSweeps = 64;
@@ -166,7 +178,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
   SecState q;
   sec_init(D, K, j, rho, zsq, sweep, q);
   int sweeps = 1;
-  while (sec_step(q)) {
+  while (sec_step(q) == 1) {
     if (sweeps >= kMaxSweeps) {
       *ok = false;
       break;
@@ -262,14 +274,17 @@ __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, 
                                               int sweeps, int K, bool ok, bool leader) {
   if (leader) {
     if (!ok) set_status(a.st, TDE_ENOCONV);
+    const double dorg = a.AD[lo + org];
     a.TAU[lo + j] = tau;
     a.ORG[lo + j] = org;
-    a.LAMA[lo + j] = a.AD[lo + org] + tau;
+    a.DORG[lo + j] = dorg;
+    a.LAMA[lo + j] = dorg + tau;
   }
 }
 
 __global__ void k_secular_thread(RootArgs a) {
   const uint32_t total = *a.count;
+  if (total < kSmallListMin) return;  // the warp kernel takes a short list
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const MState ms = a.ms[g];
@@ -286,16 +301,35 @@ __global__ void k_secular_thread(RootArgs a) {
   }
 }
 
+// Root r of the warp kernels' list: the large-K list, then the small-K list when
+// that one is too short for the thread kernels.
+__device__ __forceinline__ uint32_t warp_list_total(const RootArgs& a) {
+  const uint32_t small = *a.count;
+  return *a.count2 + (small < kSmallListMin ? small : 0u);
+}
+// Merge of entry r of that combined list; *in_list receives r's index within its
+// own list, which is what a merge's `base` refers to.
+__device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, int* in_list) {
+  const uint32_t nb = *a.count2;
+  if (r < nb) {
+    *in_list = int(r);
+    return a.ROOTMAP2[r];
+  }
+  *in_list = int(r - nb);
+  return a.ROOTMAP[r - nb];
+}
+
 __global__ void k_secular_warp(RootArgs a) {
-  const uint32_t total = *a.count;
+  const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned pairs = 0, sweeps_acc = 0, roots = 0;
   for (uint32_t r = warp; r < total; r += nwarps) {
-    const int g = a.ROOTMAP[r];
+    int rl;
+    const int g = warp_list_merge(a, r, &rl);
     const MState ms = a.ms[g];
-    const int j = int(r) - ms.base, lo = a.M[g].lo;
+    const int j = rl - ms.base, lo = a.M[g].lo;
     WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane};
     int org;
     double tau;
@@ -320,15 +354,53 @@ __global__ void k_secular_warp(RootArgs a) {
 // (1-based K), every factor positive and below one by interlacing, so the partial
 // products neither overflow nor underflow before the full product does.
 // lambda_j - D_i = (D_org(j) - D_i) + tau_j keeps the near factors accurate.
-__device__ __forceinline__ double lowner_factor(const double* AD, const int32_t* ORG,
-                                                const double* TAU, int i, double Di, int j) {
-  const double num = (AD[ORG[j]] - Di) + TAU[j];
-  const double den = (j < i ? AD[j] : AD[j + 1]) - Di;
-  return num * rcp_refined(den);
+//
+// The factors are accumulated as two separate products (numerators and
+// denominators, five FP64 operations per pair instead of a division) kept as a
+// mantissa in [1, 2) and an integer binary exponent, renormalised every eight
+// factors by integer operations on the exponent field.  Every factor lies in
+// (1e-38, 16) (distinct poles and roots of a scaled matrix), so eight of them
+// cannot leave the normal range.
+struct MantExp {
+  double m;
+  int e;
+};
+
+__device__ __forceinline__ void me_renorm(MantExp& x) {
+  const int hi = __double2hiint(x.m);
+  const int ex = (hi >> 20) & 0x7ff;
+  if (ex == 0 || ex == 0x7ff) return;  // zero, subnormal or non-finite: leave as is
+  x.e += ex - 1023;
+  x.m = __hiloint2double((hi & 0x800fffff) | (1023 << 20), __double2loint(x.m));
+}
+
+__device__ __forceinline__ void me_mul(MantExp& x, const MantExp& y) {
+  x.m *= y.m;
+  x.e += y.e;
+  me_renorm(x);
+}
+
+// num / den as one double (the result is O(1) or below: it is a z-hat square)
+__device__ __forceinline__ double me_ratio(const MantExp& num, const MantExp& den) {
+  return ldexp(num.m / den.m, num.e - den.e);
+}
+
+__device__ __forceinline__ void lowner_pair(const double* AD, const double* DORG, const double* TAU,
+                                            int i, double Di, int j, double& num, double& den) {
+  num *= (DORG[j] - Di) + TAU[j];
+  den *= (j < i ? AD[j] : AD[j + 1]) - Di;
+}
+
+__device__ __forceinline__ void lowner_store(const RootArgs& a, int lo, int i, double Di, int K,
+                                             double rho, MantExp num, MantExp den) {
+  const double last = ((a.DORG[lo + K - 1] - Di) + a.TAU[lo + K - 1]) / rho;
+  const double z2 = me_ratio(num, den) * last;
+  a.ZHAT[lo + i] = copysign(sqrt(fmax(z2, 0.0)), a.AZ[lo + i]);
 }
 
 __global__ void k_lowner_thread(RootArgs a) {
   const uint32_t total = *a.count;
+  if (total < kSmallListMin) return;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const Merge m = a.M[g];
@@ -336,44 +408,61 @@ __global__ void k_lowner_thread(RootArgs a) {
     const MState ms = a.ms[g];
     const int K = ms.K, i = int(r) - ms.base, lo = m.lo;
     const double* AD = a.AD + lo;
-    const int32_t* ORG = a.ORG + lo;
+    const double* DORG = a.DORG + lo;
     const double* TAU = a.TAU + lo;
     const double Di = AD[i];
-    double prod = ((AD[ORG[K - 1]] - Di) + TAU[K - 1]) / ms.rho;
-    for (int j = 0; j < K - 1; ++j) prod *= lowner_factor(AD, ORG, TAU, i, Di, j);
-    a.ZHAT[lo + i] = copysign(sqrt(fmax(prod, 0.0)), a.AZ[lo + i]);
+    MantExp num{1.0, 0}, den{1.0, 0};
+    int j = 0;
+    for (; j + 8 <= K - 1; j += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) lowner_pair(AD, DORG, TAU, i, Di, j + u, num.m, den.m);
+      me_renorm(num);
+      me_renorm(den);
+    }
+    for (; j < K - 1; ++j) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
+    me_renorm(num);
+    me_renorm(den);
+    lowner_store(a, lo, i, Di, K, ms.rho, num, den);
     work_add(a.st, kWorkLownerPairs, unsigned(K));
   }
 }
 
 __global__ void k_lowner_warp(RootArgs a) {
-  const uint32_t total = *a.count;
+  const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned pairs = 0;
   for (uint32_t r = warp; r < total; r += nwarps) {
-    const int g = a.ROOTMAP[r];
+    int rl;
+    const int g = warp_list_merge(a, r, &rl);
     const Merge m = a.M[g];
     if (uint32_t(m.info) & kRootBit) continue;
     const MState ms = a.ms[g];
-    const int K = ms.K, i = int(r) - ms.base, lo = m.lo;
+    const int K = ms.K, i = rl - ms.base, lo = m.lo;
     const double* AD = a.AD + lo;
-    const int32_t* ORG = a.ORG + lo;
+    const double* DORG = a.DORG + lo;
     const double* TAU = a.TAU + lo;
     const double Di = AD[i];
-    double p0 = 1.0, p1 = 1.0;
+    MantExp num{1.0, 0}, den{1.0, 0};
     int j = lane;
-    for (; j + 32 < K - 1; j += 64) {
-      p0 *= lowner_factor(AD, ORG, TAU, i, Di, j);
-      p1 *= lowner_factor(AD, ORG, TAU, i, Di, j + 32);
-    }
-    for (; j < K - 1; j += 32) p0 *= lowner_factor(AD, ORG, TAU, i, Di, j);
-    double prod = p0 * p1;
+    for (; j + 7 * 32 < K - 1; j += 8 * 32) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) prod *= __shfl_xor_sync(0xffffffffu, prod, o);
-    prod *= ((AD[ORG[K - 1]] - Di) + TAU[K - 1]) / ms.rho;
-    if (lane == 0) a.ZHAT[lo + i] = copysign(sqrt(fmax(prod, 0.0)), a.AZ[lo + i]);
+      for (int u = 0; u < 8; ++u) lowner_pair(AD, DORG, TAU, i, Di, j + 32 * u, num.m, den.m);
+      me_renorm(num);
+      me_renorm(den);
+    }
+    for (; j < K - 1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
+    me_renorm(num);
+    me_renorm(den);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      MantExp pn{__shfl_xor_sync(0xffffffffu, num.m, o), __shfl_xor_sync(0xffffffffu, num.e, o)};
+      MantExp pd{__shfl_xor_sync(0xffffffffu, den.m, o), __shfl_xor_sync(0xffffffffu, den.e, o)};
+      me_mul(num, pn);
+      me_mul(den, pd);
+    }
+    if (lane == 0) lowner_store(a, lo, i, Di, K, ms.rho, num, den);
     pairs += unsigned(K);
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkLownerPairs], (unsigned long long)pairs);
@@ -384,6 +473,7 @@ __global__ void k_lowner_warp(RootArgs a) {
 // zhat_i / Delta_ij, R_parent(:, j) = R_child y_j / ||zhat / Delta_:j||.
 __global__ void k_rows_thread(RootArgs a) {
   const uint32_t total = *a.count;
+  if (total < kSmallListMin) return;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const Merge m = a.M[g];
@@ -411,17 +501,18 @@ __global__ void k_rows_thread(RootArgs a) {
 }
 
 __global__ void k_rows_warp(RootArgs a) {
-  const uint32_t total = *a.count;
+  const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned pairs = 0;
   for (uint32_t r = warp; r < total; r += nwarps) {
-    const int g = a.ROOTMAP[r];
+    int rl;
+    const int g = warp_list_merge(a, r, &rl);
     const Merge m = a.M[g];
     if (uint32_t(m.info) & kRootBit) continue;
     const MState ms = a.ms[g];
-    const int K = ms.K, j = int(r) - ms.base, lo = m.lo;
+    const int K = ms.K, j = rl - ms.base, lo = m.lo;
     const double* AD = a.AD + lo;
     const double* ZH = a.ZHAT + lo;
     const double* AL = a.ALO + lo;
@@ -465,7 +556,9 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.M = M;
   ra.ms = ws.mstate;
   ra.ROOTMAP = ws.ROOTMAP;
+  ra.ROOTMAP2 = ws.ROOTMAP2;
   ra.count = &ws.status->root_count[step];
+  ra.count2 = &ws.status->root_count_big[step];
   ra.AD = ws.AD;
   ra.AZ = ws.AZ;
   ra.ALO = ws.ALO;
@@ -476,33 +569,29 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.ZHAT = ws.Z;
   ra.ROWLO = ws.RLO;
   ra.ROWHI = ws.RHI;
+  ra.DORG = reinterpret_cast<double*>(ws.KEYA);
   ra.st = ws.status;
-  const bool warp = plan.step_maxsize[step] >= kWarpMinK;
+  // The thread kernels cover the small-K list when it is long enough to fill the
+  // GPU; the warp kernels cover the large-K list and a short small-K list.  Which
+  // case applies is known only on the device, so both always launch.
   const int64_t nrows = plan.nrows;
-  // thread kernels: one thread per possible root; warp kernels: a persistent grid
   const int tgrid = int(std::min<int64_t>((nrows + 127) / 128, 148 * 8));
   const int wgrid = 148 * 8;
-  int launches = 1;
   prof_begin(kKSecular, s);
-  if (warp)
-    k_secular_warp<<<wgrid, 128, 0, s>>>(ra);
-  else
-    k_secular_thread<<<tgrid, 128, 0, s>>>(ra);
+  k_secular_thread<<<tgrid, 128, 0, s>>>(ra);
+  k_secular_warp<<<wgrid, 128, 0, s>>>(ra);
   prof_end(kKSecular, s);
+  int launches = 2;
   if (plan.step_has_nonroot[step]) {
     prof_begin(kKLowner, s);
-    if (warp)
-      k_lowner_warp<<<wgrid, 128, 0, s>>>(ra);
-    else
-      k_lowner_thread<<<tgrid, 128, 0, s>>>(ra);
+    k_lowner_thread<<<tgrid, 128, 0, s>>>(ra);
+    k_lowner_warp<<<wgrid, 128, 0, s>>>(ra);
     prof_end(kKLowner, s);
     prof_begin(kKRows, s);
-    if (warp)
-      k_rows_warp<<<wgrid, 128, 0, s>>>(ra);
-    else
-      k_rows_thread<<<tgrid, 128, 0, s>>>(ra);
+    k_rows_thread<<<tgrid, 128, 0, s>>>(ra);
+    k_rows_warp<<<wgrid, 128, 0, s>>>(ra);
     prof_end(kKRows, s);
-    launches += 2;
+    launches += 4;
   }
   return launches;
 }
