@@ -121,6 +121,10 @@ int64_t tde_last_launch_count(void);
  * Do not enable it while the stream is being captured into a CUDA graph. */
 int tde_profile_enable(int on);
 int tde_profile_collect(int nids, double* ms, int64_t* launches);
+/* Like tde_profile_collect, with a per-merge-step breakdown: ms and launches hold
+ * (nsteps + 1) rows of nids entries; row 0 is the total, row s + 1 the launches of
+ * merge step s (bottom-up level s of the split tree). */
+int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launches);
 
 /* Copies the workspace's device work counters (synchronises `stream`):
  * out[0] secular pole sweeps x K summed over roots (pair-evaluations),

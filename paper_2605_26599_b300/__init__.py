@@ -187,6 +187,19 @@ def profile_collect() -> dict:
     return {name: (float(ms[i]), int(cnt[i])) for i, name in enumerate(_lib.KERNEL_NAMES)}
 
 
+def profile_collect_steps(nsteps: int) -> list:
+    """Per-merge-step breakdown since the last collect: a list of nsteps dicts
+    {kernel class: (milliseconds, launches)} (synchronises)."""
+    n = len(_lib.KERNEL_NAMES)
+    rows = nsteps + 1
+    ms = (ctypes.c_double * (n * rows))()
+    cnt = (ctypes.c_int64 * (n * rows))()
+    _lib.check("tde_profile_collect_steps",
+               _lib.load().tde_profile_collect_steps(n, nsteps, ms, cnt))
+    return [{name: (float(ms[(s + 1) * n + i]), int(cnt[(s + 1) * n + i]))
+             for i, name in enumerate(_lib.KERNEL_NAMES)} for s in range(nsteps)]
+
+
 def read_work(ws: Workspace, stream=None) -> dict:
     """Device work counters of the last call that used ``ws`` (synchronises)."""
     n = len(_lib.WORK_NAMES)

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "TDE_OK", -1: "TDE_EINVAL", -2: "TDE_ECUDA", -3: "TDE_EWORKSP
 EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspace",
            "tde_eigvals_batched", "tde_get_info", "tde_measure_fp64_peak",
            "tde_last_launch_count", "tde_profile_enable", "tde_profile_collect", "tde_read_work",
-           "tde_eigvals_noalloc", "tde_plan_query", "tde_check_reciprocal")
+           "tde_eigvals_noalloc", "tde_plan_query", "tde_check_reciprocal",
+           "tde_profile_collect_steps")
 
 KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner", "rows", "place")
 WORK_NAMES = ("secular_pairs", "secular_sweeps", "lowner_pairs", "rows_pairs", "roots", "deflated",
@@ -68,6 +69,9 @@ def load() -> ctypes.CDLL:
     lib.tde_eigvals_noalloc.argtypes = [i64, vp, vp, vp, i32, vp]
     lib.tde_plan_query.argtypes = [i64, vp, i32, ctypes.POINTER(ctypes.c_int64)]
     lib.tde_check_reciprocal.argtypes = [i64, vp, vp, vp]
+    lib.tde_profile_collect_steps.argtypes = [ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_int64)]
     for name in EXPORTS:
         if name != "tde_last_launch_count":
             getattr(lib, name).restype = ctypes.c_int

@@ -12,8 +12,10 @@ namespace tde {
 // a stream is being captured into a graph.
 struct ProfRec {
   int id;
+  int step;  // merge step the launch belongs to, -1 before the first merge step
   cudaEvent_t a, b;
 };
+static thread_local int g_prof_step = -1;
 static thread_local bool g_prof_on = false;
 static thread_local std::vector<cudaEvent_t> g_pool;
 static thread_local size_t g_pool_next = 0;
@@ -38,7 +40,7 @@ void prof_end(int id, cudaStream_t s) {
   if (!g_prof_on) return;
   cudaEvent_t e = next_event();
   cudaEventRecord(e, s);
-  g_recs.push_back(ProfRec{id, g_open[id], e});
+  g_recs.push_back(ProfRec{id, g_prof_step, g_open[id], e});
 }
 
 __global__ void k_set_offsets(int64_t* off, int64_t n) {
@@ -51,10 +53,15 @@ int run_solver(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev
   if (cudaMemsetAsync(ws.status, 0, sizeof(Status), stream) != cudaSuccess) return TDE_ECUDA;
   if (cudaMemsetAsync(ws.sigma_bits, 0, 8 * size_t(plan.batch), stream) != cudaSuccess)
     return TDE_ECUDA;
+  g_prof_step = -1;
   launch_plan(plan, ws, offsets_dev, stream);
   launch_scale(plan, ws, offsets_dev, d, e, stream);
   launch_leaves(plan, ws, lambda, stream);
-  for (int s = 0; s < plan.steps; ++s) launch_step(plan, ws, s, lambda, stream);
+  for (int s = 0; s < plan.steps; ++s) {
+    g_prof_step = s;
+    launch_step(plan, ws, s, lambda, stream);
+  }
+  g_prof_step = -1;
   return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
 }
 
@@ -152,9 +159,16 @@ int tde_profile_enable(int on) {
   return TDE_OK;
 }
 
+int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launches);
 int tde_profile_collect(int nids, double* ms, int64_t* launches) {
-  if (nids < 0 || (nids > 0 && (ms == nullptr || launches == nullptr))) return TDE_EINVAL;
-  for (int i = 0; i < nids; ++i) {
+  return tde_profile_collect_steps(nids, 0, ms, launches);
+}
+
+int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launches) {
+  if (nids < 0 || nsteps < 0 || (nids > 0 && (ms == nullptr || launches == nullptr)))
+    return TDE_EINVAL;
+  const int rows = nsteps + 1;
+  for (int i = 0; i < nids * rows; ++i) {
     ms[i] = 0.0;
     launches[i] = 0;
   }
@@ -167,8 +181,13 @@ int tde_profile_collect(int nids, double* ms, int64_t* launches) {
     float t = 0.f;
     cudaEventElapsedTime(&t, r.a, r.b);
     if (r.id < nids) {
+      // row 0: every launch; row s + 1: launches of merge step s (when requested)
       ms[r.id] += t;
       launches[r.id] += 1;
+      if (r.step >= 0 && r.step < nsteps) {
+        ms[(r.step + 1) * nids + r.id] += t;
+        launches[(r.step + 1) * nids + r.id] += 1;
+      }
     }
   }
   g_recs.clear();

@@ -53,8 +53,12 @@ struct RootArgs {
 // Iteration: evaluate w and its derivative split into the poles left of the root
 // (psi: i <= jl) and right of it (phi: i > jl), then take the root of the two-pole
 // rational model C + S1 / (Delta_jl - eta) + S2 / (Delta_jr - eta) that matches w
-// and w' (S1 = Delta_jl^2 psi', S2 = Delta_jr^2 phi'), kept inside a bisection
-// bracket.  The start is the midpoint of the interval, whose sign of w also
+// and w', kept inside a bisection bracket.  The weights start as
+// S1 = Delta_jl^2 psi', S2 = Delta_jr^2 phi' (each side's derivative attributed to
+// its nearest pole); if a step fails to shrink |w| tenfold, the origin pole gets
+// its exact residue z_org^2 and the other pole the rest of w' from then on --
+// this rescues roots pressed against a pole with a tiny z, for which the first
+// weights overstate that pole's residue.  The start is the midpoint of the interval, whose sign of w also
 // chooses the origin (the nearer pole).  Convergence: |w| below eps times a
 // running bound on the rounding error of its evaluation,
 // 8 (|psi| + |phi|) + 1/rho' + |tau| (psi' + phi').
@@ -64,14 +68,15 @@ struct SecSums {
 
 struct SecState {
   int org, jl, jr;
-  double tau, tlo, thi, w, dorg, ol, orr, rhoinv;
+  bool exact;  // origin pole weighted by its exact residue
+  double tau, tlo, thi, w, wprev, dorg, ol, orr, rhoinv, zorg2;
   SecSums s;
 };
 
 // first sweep point and the bracket; `sweep(dorg, tau, jl)` evaluates the sums
 template <class Sweep>
-__device__ __forceinline__ void sec_init(const double* D, int K, int j, double rho, double zsq,
-                                         Sweep& sweep, SecState& q) {
+__device__ __forceinline__ void sec_init(const double* D, const double* Z, int K, int j, double rho,
+                                         double zsq, Sweep& sweep, SecState& q) {
   q.rhoinv = 1.0 / rho;
   if (j < K - 1) {
     q.jl = j;
@@ -107,8 +112,11 @@ __device__ __forceinline__ void sec_init(const double* D, int K, int j, double r
     }
   }
   q.dorg = D[q.org];
+  q.zorg2 = Z[q.org] * Z[q.org];
   q.ol = D[q.jl] - q.dorg;
   q.orr = D[q.jr] - q.dorg;
+  q.exact = false;
+  q.wprev = 0.0;
 }
 
 // One iteration.  Returns 1 if tau moved and needs a new sweep, 0 if converged.
@@ -125,7 +133,24 @@ __device__ __forceinline__ int sec_step(SecState& q) {
     q.tlo = fmax(q.tlo, q.tau);
   if (q.thi - q.tlo <= 2.0 * kEps * fmax(fabs(q.tlo), fabs(q.thi))) return 0;
   const double a = q.ol - q.tau, b = q.orr - q.tau;  // Delta of the two model poles
-  const double S1 = a * a * q.s.dpsi, S2 = b * b * q.s.dphi;
+  if (q.wprev != 0.0 && fabs(q.w) > 0.1 * fabs(q.wprev)) q.exact = true;
+  q.wprev = q.w;
+  double S1 = a * a * q.s.dpsi, S2 = b * b * q.s.dphi;
+  if (q.exact) {
+    const double dw = q.s.dpsi + q.s.dphi;
+    double e1, e2;
+    if (q.org == q.jl) {
+      e1 = q.zorg2;
+      e2 = b * b * (dw - e1 / (a * a));
+    } else {
+      e2 = q.zorg2;
+      e1 = a * a * (dw - e2 / (b * b));
+    }
+    if (e1 >= 0.0 && e2 >= 0.0) {
+      S1 = e1;
+      S2 = e2;
+    }
+  }
   const double C = q.w - S1 / a - S2 / b;
   const double A = C * (a + b) + S1 + S2;
   const double Bq = a * b * q.w;
@@ -176,7 +201,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
     return 0;
   }
   SecState q;
-  sec_init(D, K, j, rho, zsq, sweep, q);
+  sec_init(D, Z, K, j, rho, zsq, sweep, q);
   int sweeps = 1;
   while (sec_step(q) == 1) {
     if (sweeps >= kMaxSweeps) {
