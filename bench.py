@@ -168,9 +168,10 @@ def cpu_baseline(n: int, fams, target_s: float = 12.0) -> dict:
     t, _ = oracle_sample(n, probe, fams)
     per = int(max(probe, min(n, probe * target_s / max(t, 1e-3))))
     t, threads = oracle_sample(n, per, fams)
-    return {"value": 4 * per / t, "unit": UNIT, "cores": threads, "kind": "oracle",
+    nf = len(FAMILIES)
+    return {"value": nf * per / t, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"Sturm bisection of {per} evenly spaced eigenvalue indices of each of the "
-                      f"4 families at n={n} ({4 * per} eigenvalues, {t:.1f} s)"}
+                      f"{nf} families at n={n} ({nf * per} eigenvalues, {t:.1f} s)"}
 
 
 def run_reference(args, rank: int, world: int) -> None:
@@ -190,7 +191,7 @@ def run_reference(args, rank: int, world: int) -> None:
         t, threads = oracle_sample(n, per, fams)
         times.append(t)
     step = float(np.mean(times))
-    value = 4 * per / step
+    value = len(FAMILIES) * per / step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
@@ -288,7 +289,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     fam_ms = {name: float(np.mean([a.elapsed_time(b) for a, b in fam_ev[name]])) for name in FAMILIES}
     ms = slowest_rank_ms(float(np.mean(step_ms)), dist, dev)
-    value = job_value(ms, world, 4 * n)
+    value = job_value(ms, world, len(FAMILIES) * n)
 
     # device work of one step (identical every step)
     work = {k: 0 for k in ("secular_pairs", "lowner_pairs", "rows_pairs", "secular_sweeps", "roots",
@@ -320,7 +321,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
             e2e_ms.append(ev0.elapsed_time(ev1))
     e2e_step = slowest_rank_ms(float(np.mean(e2e_ms)), dist, dev)
     h2d = sum(host[nm][0].numel() * 8 + host[nm][1].numel() * 8 for nm in FAMILIES)
-    d2h = 4 * n * 8
+    d2h = len(FAMILIES) * n * 8
 
     if rank != 0:
         return
@@ -359,7 +360,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"single tridiagonals n={n}, families a-d (uniform(-1,1) seed 0, "
                                "Toeplitz 2/-1, Wilkinson W+, glued W+_21)",
-                   "n": n, "families": list(FAMILIES), "leaf": args.leaf or 32,
+                   "n": n, "families": list(FAMILIES), "leaf": args.leaf,
                    "l2": "flushed between steps (256 MB write outside the event-timed region); "
                          "inputs are smaller than L2",
                    "per_family_ms": fam_ms, "step_ms_min": float(min(step_ms)),
@@ -369,7 +370,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         "roofline": roof,
         "kernel_fp64_rates": kernel_rates,
         "cpu_baseline": cpu,
-        "e2e": {"value": job_value(e2e_step, world, 4 * n), "unit": UNIT, "h2d_bytes_per_step": h2d,
+        "e2e": {"value": job_value(e2e_step, world, len(FAMILIES) * n), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_step},
         "clocks": clocks,
         "source_hash": source_hash(),
@@ -393,19 +394,27 @@ def load_traffic(kernel: str):
 
 
 def main():
+    global FAMILIES
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=65536, help="matrix order n")
-    ap.add_argument("--leaf", type=int, default=0)
+    ap.add_argument("--leaf", type=int, default=8,
+                    help="largest leaf order of the split tree (8: fastest measured on B300)")
+    ap.add_argument("--families", default=",".join(FAMILIES),
+                    help="comma-separated subset of the four families (profiling runs)")
     ap.add_argument("--ref-sample", type=int, default=96,
                     help="eigenvalue indices per family per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    fams = tuple(f for f in args.families.split(",") if f)
+    if not fams or any(f not in FAMILIES for f in fams):
+        ap.error(f"--families must be a subset of {','.join(FAMILIES)}")
+    FAMILIES = fams
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
