@@ -97,6 +97,16 @@ int tde_get_info(const void* ws, void* stream, int32_t* info);
  * about 50 ms.  Returns TDE_OK and writes *fma_per_s. */
 int tde_measure_fp64_peak(double* fma_per_s);
 
+/* Launch-shape tuning for subsequent calls on this thread (0 restores a default):
+ *   warp_min_k      merges whose active rank reaches this solve one warp per root
+ *                   (default 512), smaller ones one thread per root;
+ *   small_list_min  a step with fewer small-merge roots than this hands them to the
+ *                   warp-per-root kernels too (default 18944 = 148 SMs x 4 warps x 32).
+ * The eigenvalues do not depend on these; only the time does. */
+int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min);
+/* out[0] = warp_min_k, out[1] = small_list_min of this thread. */
+int tde_get_tuning(int32_t* out);
+
 /* Host-only description of the split-tree plan for a packing (no device work):
  * out[0] merge steps (tree levels), out[1] leaves, out[2] merges, out[3] the
  * largest number of merges in one step.  Node (h, i) of a matrix of order n covers

@@ -161,6 +161,17 @@ def plan_query(offsets, leaf: int = 0) -> dict:
     return {"steps": int(out[0]), "leaves": int(out[1]), "merges": int(out[2]), "cmax": int(out[3])}
 
 
+def set_tuning(warp_min_k: int = 0, small_list_min: int = 0) -> None:
+    """Launch-shape tuning of later calls on this thread (0 = default)."""
+    _lib.check("tde_set_tuning", _lib.load().tde_set_tuning(int(warp_min_k), int(small_list_min)))
+
+
+def get_tuning() -> dict:
+    out = (ctypes.c_int32 * 2)()
+    _lib.check("tde_get_tuning", _lib.load().tde_get_tuning(out))
+    return {"warp_min_k": int(out[0]), "small_list_min": int(out[1])}
+
+
 def measure_fp64_peak() -> float:
     """Measured FP64 FMA instructions per second of the current device (all lanes)."""
     out = ctypes.c_double()

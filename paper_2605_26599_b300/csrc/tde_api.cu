@@ -16,6 +16,9 @@ struct ProfRec {
   cudaEvent_t a, b;
 };
 static thread_local int g_prof_step = -1;
+
+static thread_local Tuning g_tuning;
+Tuning& thread_tuning() { return g_tuning; }
 static thread_local bool g_prof_on = false;
 static thread_local std::vector<cudaEvent_t> g_pool;
 static thread_local size_t g_pool_next = 0;
@@ -141,6 +144,22 @@ int tde_get_info(const void* ws, void* stream, int32_t* info) {
 }
 
 int64_t tde_last_launch_count(void) { return g_launches; }
+
+int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min) {
+  if (warp_min_k < 0 || small_list_min < 0) return TDE_EINVAL;
+  Tuning t;
+  if (warp_min_k > 0) t.warp_min_k = warp_min_k;
+  if (small_list_min > 0) t.small_list_min = small_list_min;
+  g_tuning = t;
+  return TDE_OK;
+}
+
+int tde_get_tuning(int32_t* out) {
+  if (out == nullptr) return TDE_EINVAL;
+  out[0] = g_tuning.warp_min_k;
+  out[1] = g_tuning.small_list_min;
+  return TDE_OK;
+}
 
 int tde_plan_query(int64_t batch, const int64_t* offsets_host, int32_t leaf, int64_t* out) {
   if (out == nullptr) return TDE_EINVAL;

@@ -45,13 +45,21 @@ struct MState {
   int32_t base;  // first index of this merge's roots in its root list
   double rho;    // rho' = 2 |beta|
   double zsq;    // sum of active z^2
-  int32_t big;   // 1: roots in the warp-per-root list (K >= kWarpMinK)
+  int32_t big;   // 1: roots in the warp-per-root list (K >= warp_min_k)
   int32_t pad;
 };
 
-// Merges whose active rank K reaches this are solved one warp per root (per pole
-// for z-hat); smaller ones one thread per root.
-constexpr int kWarpMinK = 512;
+// Launch-shape parameters chosen per call (tde_set_tuning; the Python autotuner
+// searches them together with the leaf order):
+//   warp_min_k      merges whose active rank K reaches this are solved one warp per
+//                   root (per pole for z-hat); smaller ones one thread per root
+//   small_list_min  below this many small-K roots in a step the thread-per-root
+//                   kernels would leave SMs idle, so the warp kernels take them too
+struct Tuning {
+  int32_t warp_min_k = 512;
+  int32_t small_list_min = 148 * 4 * 32;
+};
+Tuning& thread_tuning();
 
 constexpr uint32_t kRootBit = 0x80000000u;
 
@@ -72,7 +80,7 @@ struct Status {
   int32_t info;
   int32_t pad[31];
   uint32_t root_count[kMaxSteps];      // roots of small-K merges per step
-  uint32_t root_count_big[kMaxSteps];  // roots of merges with K >= kWarpMinK
+  uint32_t root_count_big[kMaxSteps];  // roots of merges with K >= warp_min_k
   unsigned long long work[16];
 };
 
@@ -123,6 +131,7 @@ struct Plan {
   int64_t step_maxsize[kMaxSteps] = {0};  // largest merge order (K0) of the step
   int64_t step_base[kMaxSteps] = {0};
   bool step_has_nonroot[kMaxSteps] = {false};
+  Tuning tune;
 };
 
 int build_plan(int64_t batch, const int64_t* offsets_host, int32_t leaf, Plan* plan);

@@ -281,6 +281,7 @@ struct DeflateArgs {
   unsigned long long *KEYA, *KEYB;
   MState* ms;
   Status* st;
+  int32_t warp_min_k;
 };
 
 __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
@@ -499,9 +500,9 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
     }
     __syncthreads();
     // 7. roots of this merge get a contiguous range of one of the step's two root
-    //    lists: merges with K >= kWarpMinK are solved one warp per root
+    //    lists: merges with K >= warp_min_k are solved one warp per root
     __shared__ int s_base;
-    const bool big = K >= kWarpMinK;
+    const bool big = K >= a.warp_min_k;
     if (tid == 0) {
       s_base = K > 0 ? int(atomicAdd(big ? &a.st->root_count_big[a.step] : &a.st->root_count[a.step],
                                      unsigned(K)))
@@ -599,6 +600,7 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   da.KEYB = ws.KEYB;
   da.ms = ws.mstate;
   da.st = ws.status;
+  da.warp_min_k = plan.tune.warp_min_k;
   const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
   prof_begin(kKDeflate, s);
   k_deflate<<<def_grid, kNT, 0, s>>>(da);

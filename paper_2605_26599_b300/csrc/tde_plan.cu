@@ -32,6 +32,7 @@ int build_plan(int64_t batch, const int64_t* off, int32_t leaf, Plan* plan) {
   Plan p;
   p.batch = batch;
   p.leaf = leaf;
+  p.tune = thread_tuning();
   if (batch > 0 && off[0] != 0) return TDE_EINVAL;
   for (int64_t k = 0; k < batch; ++k) {
     int64_t nk = off[k + 1] - off[k];

@@ -7,7 +7,7 @@
 // work on O(K) data that stays in L1/L2.  On this part FP64 is the scarce
 // resource (an FP64 instruction occupies the pipe for the whole warp whether or
 // not its lanes are active), so the kernels keep every lane busy:
-//   * merges whose active rank K >= kWarpMinK (known only on the device, after
+//   * merges whose active rank K >= warp_min_k (known only on the device, after
 //     deflation; the deflation kernel files their roots in a second list): one
 //     warp per root (per pole for z-hat); the 32 lanes stride over the poles and
 //     the partial sums are combined with shuffles, so the whole warp shares one
@@ -21,15 +21,11 @@
 
 namespace tde {
 
-// Below this many small-K roots in a step the thread-per-root kernels would leave
-// most SMs idle, so the warp-per-root kernels take the small list as well.
-constexpr uint32_t kSmallListMin = 148u * 4u * 32u;
-
 struct RootArgs {
   const Merge* M;
   const MState* ms;
-  const int32_t* ROOTMAP;   // roots of merges with K < kWarpMinK
-  const int32_t* ROOTMAP2;  // roots of merges with K >= kWarpMinK
+  const int32_t* ROOTMAP;   // roots of merges with K < warp_min_k
+  const int32_t* ROOTMAP2;  // roots of merges with K >= warp_min_k
   const uint32_t* count;    // lengths of the two lists (device)
   const uint32_t* count2;
   const double *AD, *AZ, *ALO, *AHI;
@@ -40,6 +36,7 @@ struct RootArgs {
   double *ROWLO, *ROWHI;  // alias RLO, RHI: parent rows of the active columns
   double* DORG;           // alias KEYA: D_org(j) of every active root
   Status* st;
+  uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
 };
 
 // ---------------------------------------------------------------------------
@@ -309,7 +306,7 @@ __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, 
 
 __global__ void k_secular_thread(RootArgs a) {
   const uint32_t total = *a.count;
-  if (total < kSmallListMin) return;  // the warp kernel takes a short list
+  if (total < a.small_list_min) return;  // the warp kernel takes a short list
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const MState ms = a.ms[g];
@@ -330,7 +327,7 @@ __global__ void k_secular_thread(RootArgs a) {
 // that one is too short for the thread kernels.
 __device__ __forceinline__ uint32_t warp_list_total(const RootArgs& a) {
   const uint32_t small = *a.count;
-  return *a.count2 + (small < kSmallListMin ? small : 0u);
+  return *a.count2 + (small < a.small_list_min ? small : 0u);
 }
 // Merge of entry r of that combined list; *in_list receives r's index within its
 // own list, which is what a merge's `base` refers to.
@@ -425,7 +422,7 @@ __device__ __forceinline__ void lowner_store(const RootArgs& a, int lo, int i, d
 
 __global__ void k_lowner_thread(RootArgs a) {
   const uint32_t total = *a.count;
-  if (total < kSmallListMin) return;
+  if (total < a.small_list_min) return;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const Merge m = a.M[g];
@@ -498,7 +495,7 @@ __global__ void k_lowner_warp(RootArgs a) {
 // zhat_i / Delta_ij, R_parent(:, j) = R_child y_j / ||zhat / Delta_:j||.
 __global__ void k_rows_thread(RootArgs a) {
   const uint32_t total = *a.count;
-  if (total < kSmallListMin) return;
+  if (total < a.small_list_min) return;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const Merge m = a.M[g];
@@ -596,6 +593,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.ROWHI = ws.RHI;
   ra.DORG = reinterpret_cast<double*>(ws.KEYA);
   ra.st = ws.status;
+  ra.small_list_min = uint32_t(plan.tune.small_list_min);
   // The thread kernels cover the small-K list when it is long enough to fill the
   // GPU; the warp kernels cover the large-K list and a short small-K list.  Which
   // case applies is known only on the device, so both always launch.

@@ -1,0 +1,139 @@
+"""GPU parity of the batched solver (a forest of uneven split trees processed
+level by level in shared launches) against the oracle and against the
+single-matrix entry point."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_26599_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def tde():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2605_26599_b300 as tde_mod
+
+    return tde_mod
+
+
+def solve_batched(tde, d, e, offsets, leaf=0):
+    import torch
+
+    return tde.eigvals_batched(torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda(), offsets,
+                               leaf=leaf).cpu().numpy()
+
+
+def check_each(d, e, offsets, lam, sample=None):
+    worst = 0.0
+    for k in range(len(offsets) - 1):
+        a, b = int(offsets[k]), int(offsets[k + 1])
+        if b == a:
+            continue
+        dk, ek = d[a:b], e[a:b - 1]
+        gate = 8 * (b - a) * EPS * oracle.norm1(dk, ek) + 1e-300
+        lk = lam[a:b]
+        assert np.all(np.diff(lk) >= 0)
+        if sample is None or b - a <= sample:
+            ref = oracle.eigvals_bisect(dk, ek)
+            err = np.max(np.abs(lk - ref))
+        else:
+            ks = np.unique(np.linspace(0, b - a - 1, sample).astype(np.int64))
+            err = np.max(np.abs(lk[ks] - oracle.eigvals_select(dk, ek, ks)))
+        assert err <= gate, (k, b - a, err, gate)
+        worst = max(worst, err / gate if gate > 0 else 0)
+    return worst
+
+
+@pytest.mark.parametrize("leaf", [4, 8, 32])
+def test_batched_lanczos_small_batch(tde, leaf):
+    d, e, off = inputs.batched_lanczos(batch=48, lo=64, hi=700, seed=3)
+    lam = solve_batched(tde, d, e, off, leaf)
+    check_each(d, e, off, lam)
+
+
+def test_batched_equals_single_matrix_solves(tde):
+    import torch
+
+    d, e, off = inputs.batched_lanczos(batch=24, lo=64, hi=1500, seed=5)
+    lam = solve_batched(tde, d, e, off, 8)
+    for k in range(len(off) - 1):
+        a, b = int(off[k]), int(off[k + 1])
+        single = tde.eigvals(torch.from_numpy(d[a:b].copy()).cuda(), torch.from_numpy(e[a:b].copy()).cuda(),
+                             leaf=8).cpu().numpy()
+        gate = 8 * (b - a) * EPS * oracle.norm1(d[a:b], e[a:b - 1])
+        assert np.max(np.abs(single - lam[a:b])) <= gate
+
+
+def test_batched_edge_packings(tde):
+    # empty matrices, order 1 and 2, a leaf-sized one and a larger one, mixed families
+    parts = [inputs.uniform11(0), inputs.uniform11(1, seed=1), inputs.toeplitz(2), inputs.uniform11(0),
+             inputs.wilkinson_plus(8), inputs.glued_wilkinson(300), inputs.normal_absnormal(1025, seed=2),
+             inputs.uniform11(1, seed=9)]
+    sizes = [len(p[0]) for p in parts]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    d = np.concatenate([p[0] for p in parts])
+    e = np.zeros(len(d))
+    for (dk, ek), a in zip(parts, off[:-1]):
+        e[a:a + len(ek)] = ek
+    for leaf in (1, 8, 64):
+        lam = solve_batched(tde, d, e, off, leaf)
+        check_each(d, e, off, lam)
+
+
+def test_batched_full_forest_sampled(tde):
+    # the 4096-matrix Lanczos-style forest, every matrix checked on sampled indices
+    d, e, off = inputs.batched_lanczos()
+    lam = solve_batched(tde, d, e, off, 8)
+    idx = np.random.default_rng(0).choice(len(off) - 1, 256, replace=False)
+    for k in idx:
+        a, b = int(off[k]), int(off[k + 1])
+        sub = np.array([0, b - a], dtype=np.int64)
+        check_each(d[a:b], e[a:b], sub, lam[a:b], sample=24)
+    # trace invariant of every matrix at once
+    for k in range(len(off) - 1):
+        a, b = int(off[k]), int(off[k + 1])
+        tn = oracle.norm1(d[a:b], e[a:b - 1])
+        assert abs(lam[a:b].sum() - d[a:b].sum()) <= (b - a) * 8 * (b - a) * EPS * tn
+
+
+def test_graph_replay_matches_direct_call_bitwise(tde):
+    import torch
+
+    from paper_2605_26599_b300.batched import BatchedSolver
+
+    d, e, off = inputs.batched_lanczos(batch=64, lo=64, hi=2048, seed=7)
+    dt, et = torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda()
+    direct = tde.eigvals_batched(dt, et, off, leaf=8).cpu().numpy()
+    solver = BatchedSolver(off, leaf=8)
+    first = solver(dt, et).cpu().numpy()
+    second = solver(dt, et).cpu().numpy()
+    assert np.array_equal(first, direct) and np.array_equal(second, direct)
+    # new inputs through the same graph
+    d2, e2, _ = inputs.batched_lanczos(batch=64, lo=64, hi=2048, seed=7)
+    d2 = d2 * 3.0 + 1.0
+    lam2 = solver(torch.from_numpy(d2).cuda(), et).cpu().numpy()
+    check_each(d2, e, off, lam2, sample=16)
+
+
+def test_autotune_picks_valid_shape_and_keeps_results(tde, tmp_path):
+    import torch
+
+    from paper_2605_26599_b300.batched import BatchedSolver, autotune
+
+    d, e, off = inputs.batched_lanczos(batch=96, lo=64, hi=1024, seed=11)
+    dt, et = torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda()
+    cache = str(tmp_path / "tune.json")
+    best = autotune(off, dt, et, leaves=(8, 16), warp_min_ks=(256, 512), reps=1, cache_path=cache)
+    assert best["leaf"] in (8, 16) and best["warp_min_k"] in (256, 512)
+    again = autotune(off, dt, et, cache_path=cache)
+    assert again["cached"] and again["leaf"] == best["leaf"]
+    lam = BatchedSolver(off, leaf=best["leaf"])(dt, et).cpu().numpy()
+    check_each(d, e, off, lam, sample=16)
+    tde.set_tuning()
