@@ -86,6 +86,31 @@ int tde_eigvals_batched(int64_t batch, const int64_t* offsets_host, const int64_
                         const double* d, const double* e, double* lambda, int32_t leaf,
                         void* ws, size_t ws_bytes, void* stream);
 
+/* Workspace for tde_eigvals_backward with the given packing (leaf <= 32). */
+int tde_eigvals_backward_workspace(int64_t batch, const int64_t* offsets_host, int32_t leaf,
+                                   size_t* bytes);
+
+/* Gradient of a loss of the eigenvalues with respect to d and e (reverse mode),
+ * for a packed batch as in tde_eigvals_batched (batch = 1 with offsets {0, n} for
+ * one matrix).
+ *   grad_lambda [N]  dL/dlambda, aligned with the ascending eigenvalues
+ *   lambda      [N]  output: the eigenvalues (may be NULL)
+ *   grad_d      [N]  output: dL/dd
+ *   grad_e      [N]  output: dL/de (entry at the last row of each matrix is 0)
+ * Method: a forward pass that checkpoints the boundary-row state at every tree
+ * level, then a reverse sweep over the merges (top-down) that rebuilds each
+ * merge from its checkpoint and pulls the adjoints back through the placement,
+ * the secular eigen-decomposition (implicit differentiation of every root and of
+ * the Cauchy form of the boundary rows), the deflation and the formation of the
+ * merge problem; the leaves use the adjoint of their full eigen-decomposition and
+ * the tearing d -= |beta| of Eq. (1).  Deflation decisions and the tree are
+ * constants of the differentiation.  Simple (distinct) eigenvalues are assumed.
+ * Workspace: O(n log n) (3 n doubles of checkpoint per level). */
+int tde_eigvals_backward(int64_t batch, const int64_t* offsets_host, const int64_t* offsets_dev,
+                         const double* d, const double* e, const double* grad_lambda,
+                         double* lambda, double* grad_d, double* grad_e, int32_t leaf,
+                         void* ws, size_t ws_bytes, void* stream);
+
 /* Reads the device status word of a workspace used by a previous call on
  * `stream` (synchronises that stream).  *info receives 0 or a positive
  * tde_status code.  The word is reset at the start of every compute call. */

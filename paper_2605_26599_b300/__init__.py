@@ -19,7 +19,7 @@ import numpy as np
 from . import _lib
 from ._lib import TdeError  # noqa: F401
 
-__all__ = ["eigvals", "eigvals_batched", "workspace_bytes", "batched_workspace_bytes",
+__all__ = ["eigvals", "eigvals_batched", "eigvals_backward", "TdeEigvals", "eigvals_autograd", "workspace_bytes", "batched_workspace_bytes",
            "get_info", "measure_fp64_peak", "last_launch_count", "TdeError", "Workspace",
            "profile_enable", "profile_collect", "read_work"]
 
@@ -170,6 +170,98 @@ def get_tuning() -> dict:
     out = (ctypes.c_int32 * 2)()
     _lib.check("tde_get_tuning", _lib.load().tde_get_tuning(out))
     return {"warp_min_k": int(out[0]), "small_list_min": int(out[1])}
+
+
+def backward_workspace_bytes(offsets, leaf: int = 8) -> int:
+    """Device workspace bytes for tde_eigvals_backward on a packing."""
+    off = _host_offsets(offsets)
+    out = ctypes.c_size_t()
+    _lib.check("tde_eigvals_backward_workspace",
+               _lib.load().tde_eigvals_backward_workspace(off.shape[0] - 1, off.ctypes.data, int(leaf),
+                                                          ctypes.byref(out)))
+    return int(out.value)
+
+
+def eigvals_backward(d, e, grad_lambda, offsets=None, leaf: int = 8, ws: Workspace | None = None,
+                     stream=None, check: bool = True, offsets_dev=None, lam_out=None):
+    """(lambda, dL/dd, dL/de) for dL/dlambda = grad_lambda, by the adjoint sweep of
+    tde_eigvals_backward.  offsets=None means one matrix of order len(d); e is
+    packed like d (the entry at each matrix's last row is ignored, its gradient 0)."""
+    torch = _torch()
+    _check_tensor(d, "d")
+    _check_tensor(grad_lambda, "grad_lambda")
+    n = d.shape[0]
+    off = _host_offsets(offsets if offsets is not None else [0, n])
+    total = int(off[-1])
+    if e is None or e.shape[0] < total:
+        e_full = torch.zeros(max(total, 1), dtype=torch.float64, device=d.device)
+        if e is not None and e.shape[0] > 0:
+            e_full[: e.shape[0]] = e
+        e = e_full
+    _check_tensor(e, "e")
+    lam = lam_out if lam_out is not None else torch.empty(total, dtype=torch.float64, device=d.device)
+    gd = torch.empty(total, dtype=torch.float64, device=d.device)
+    ge = torch.empty(max(total, 1), dtype=torch.float64, device=d.device)
+    if total == 0:
+        return lam, gd, ge[:0]
+    if offsets_dev is None:
+        offsets_dev = torch.from_numpy(off).to(d.device)
+    need = backward_workspace_bytes(off, leaf)
+    ws = Workspace(need, d.device) if ws is None else ws.ensure(need)
+    rc = _lib.load().tde_eigvals_backward(
+        off.shape[0] - 1, off.ctypes.data, ctypes.c_void_p(offsets_dev.data_ptr()),
+        ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(e.data_ptr()),
+        ctypes.c_void_p(grad_lambda.data_ptr()), ctypes.c_void_p(lam.data_ptr()),
+        ctypes.c_void_p(gd.data_ptr()), ctypes.c_void_p(ge.data_ptr()), int(leaf),
+        ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream))
+    _lib.check("tde_eigvals_backward", rc)
+    if check:
+        info = get_info(ws, stream)
+        if info != 0:
+            raise TdeError("tde_eigvals_backward (device status)", info)
+    return lam, gd, ge[:total]
+
+
+def _make_autograd():
+    torch = _torch()
+
+    class TdeEigvals(torch.autograd.Function):
+        """lambda = eigvals(tridiag(e, d, e)) with a hand-written adjoint (the reverse
+        merge sweep of tde_eigvals_backward).  offsets (host) packs several matrices."""
+
+        @staticmethod
+        def forward(ctx, d, e, offsets=None, leaf=8):
+            n = d.shape[0]
+            off = _host_offsets(offsets if offsets is not None else [0, n])
+            ctx.save_for_backward(d, e)
+            ctx.off = off
+            ctx.leaf = leaf
+            if offsets is None:
+                return eigvals(d, e, leaf=leaf)
+            return eigvals_batched(d, e, off, leaf=leaf)
+
+        @staticmethod
+        def backward(ctx, grad_lambda):
+            d, e = ctx.saved_tensors
+            _, gd, ge = eigvals_backward(d, e, grad_lambda.contiguous(), offsets=ctx.off, leaf=ctx.leaf)
+            return gd, ge[: e.shape[0]], None, None
+
+    return TdeEigvals
+
+
+class _Lazy:
+    cls = None
+
+
+def TdeEigvals():  # noqa: N802 - mirrors a class name
+    if _Lazy.cls is None:
+        _Lazy.cls = _make_autograd()
+    return _Lazy.cls
+
+
+def eigvals_autograd(d, e, offsets=None, leaf: int = 8):
+    """Differentiable eigenvalues (see TdeEigvals)."""
+    return TdeEigvals().apply(d, e, offsets, leaf)
 
 
 def measure_fp64_peak() -> float:

@@ -25,7 +25,8 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
            "tde_eigvals_batched", "tde_get_info", "tde_measure_fp64_peak",
            "tde_last_launch_count", "tde_profile_enable", "tde_profile_collect", "tde_read_work",
            "tde_eigvals_noalloc", "tde_plan_query", "tde_check_reciprocal",
-           "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning")
+           "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning",
+           "tde_eigvals_backward_workspace", "tde_eigvals_backward")
 
 KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner", "rows", "place")
 WORK_NAMES = ("secular_pairs", "secular_sweeps", "lowner_pairs", "rows_pairs", "roots", "deflated",
@@ -70,6 +71,8 @@ def load() -> ctypes.CDLL:
     lib.tde_plan_query.argtypes = [i64, vp, i32, ctypes.POINTER(ctypes.c_int64)]
     lib.tde_check_reciprocal.argtypes = [i64, vp, vp, vp]
     lib.tde_set_tuning.argtypes = [i32, i32]
+    lib.tde_eigvals_backward_workspace.argtypes = [i64, vp, i32, szp]
+    lib.tde_eigvals_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.tde_get_tuning.argtypes = [ctypes.POINTER(ctypes.c_int32)]
     lib.tde_profile_collect_steps.argtypes = [ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_double),

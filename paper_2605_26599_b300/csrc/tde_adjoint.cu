@@ -1,0 +1,745 @@
+// Adjoint of the boundary-row D&C: d(loss)/d(d) and d(loss)/d(e) from the
+// gradient of the loss with respect to the eigenvalues.
+//
+// Structure (a reverse sweep over the split tree, top-down):
+//   1. forward recomputation with a checkpoint of the boundary-row state (lambda,
+//      blo, bhi) at the input of every merge step;
+//   2. for every step from the top down: rebuild the step's merge internals from
+//      its checkpoint (form, deflation, secular roots, z-hat, rows at every merge,
+//      root merges included), then pull the adjoints of the parents' (lambda, blo,
+//      bhi) back through
+//        - the ascending placement (a permutation),
+//        - the secular eigen-decomposition A = diag(D) + rho' z z^T = Y L Y^T,
+//          whose outputs are the roots L and the boundary rows blo = Y^T RLO,
+//          bhi = Y^T RHI: the adjoint of a symmetric eigen-decomposition,
+//          A_bar = Y (L_bar + F o (Y^T Y_bar)) Y^T, F_jk = 1/(l_k - l_j),
+//          Y^T Y_bar = W with W_jk = blo_j blo_bar_k + bhi_j bhi_bar_k (rank two),
+//          evaluated in O(K^2) through the Cauchy form of the secular
+//          eigenvectors y_sj = zhat_s / (nu_j (D_s - l_j)):
+//            D_bar_s = A_bar_ss = sum_j lbar_j y_sj^2 + zhat_s^2 sum_j g_j / (D_s - l_j),
+//            g_j = -sum_{k != j} (W_jk - W_kj) / (nu_j nu_k (l_j - l_k)^2)
+//          (partial fractions of 1 / ((D_s - l_j)(D_s - l_k))), and with
+//          c = Y^T z, h_j = sum_{k != j} (W_jk - W_kj) c_k / (l_k - l_j):
+//            z_bar = rho' (A_bar + A_bar^T) z = rho' Y (2 lbar o c + h),
+//            rho'_bar = z^T A_bar z = sum_j (lbar_j c_j^2 + c_j h_j / 2),
+//            RLO_bar = Y blo_bar, RHI_bar = Y bhi_bar;
+//          root differences are formed as (D_org(j) - D_org(k)) + (tau_j - tau_k),
+//        - the deflation (negligible z: pass-through; close-pole rotation runs:
+//          the prefix-sum formulas reversed run by run).  A rotation drops the
+//          coupling kappa_m = u_keep^T diag(D) u_def,m between a deflated direction
+//          and its run's kept pole; kappa is at most tol, so the eigenvalues do not
+//          see it to first order, but d kappa / dD is O(1) and the eigenvectors
+//          (hence the propagated rows) do: the first-order mixing
+//          dy_j = f_m kappa y_aj / (l_j - v_m), df_m = sum_k y_k kappa y_ak / (v_m - l_k)
+//          gives kappa_bar_m = sum_j y_aj [(blo_bar_j r_m + bhi_bar_j r'_m)
+//          - (blo_bar_m blo_j + bhi_bar_m bhi_j)] / (l_j - v_m), pulled back
+//          through kappa_m = z_m sqrt(W_{m-1}) (c_{m-1} - D_m) / sqrt(W_m W_L)
+//          (W prefix sums of z^2 over the run, c the running weighted mean); its
+//          terms proportional to (c - D) are of order tol and are dropped.
+//          Couplings between two deflated directions of one run are not modelled.
+//        - the formation of D, z, RLO, RHI from the children (a permutation; z
+//          carries 1/sqrt(2) and the sign of the cut coupling beta; rho' = 2|beta|);
+//   3. at the leaves: the standard adjoint of a symmetric eigen-decomposition,
+//      A_bar = Q (diag(lambda_bar) + F o (Q^T Q_bar)) Q^T with F_jk = 1/(l_k - l_j),
+//      Q_bar nonzero only in the first and last rows, then d_bar_i = A_bar_ii,
+//      e_bar_i = 2 A_bar_i,i+1, and the tearing d_cut -= |beta| gives
+//      e_bar_cut -= sgn(beta) (d_bar of the two torn diagonal entries).
+// Deflation decisions, the tree and the scaling are constants of the
+// differentiation (eigenvalue derivatives are scale invariant).  Memory: the
+// checkpoints hold 3 n doubles per merge step (n log n overall); every other
+// buffer is O(n).
+#include <algorithm>
+
+#include "tde_internal.cuh"
+
+namespace tde {
+
+constexpr int kMaxBwdLeaf = 32;
+
+struct AdjWorkspace {
+  Workspace fw;
+  double* CK;                          // steps x 3 x N checkpoints
+  double *GL, *GBL, *GBH;              // adjoint of the current level's state
+  double *ALB, *ABL, *ABH;             // adjoints of a merge's [active | deflated] outputs
+  double *RLT, *RAL, *RBE, *RGA, *RINU, *RC;  // per active root scalars (g, h, ..., 1/nu, c)
+  double *PDB, *PZB, *PRLB, *PRHB;     // adjoints of the active poles
+  double *MDB, *MZB, *MRLB, *MRHB;     // adjoints at the sorted merge positions
+  double* RHOBAR;                      // per merge of a step: adjoint of rho'
+  double* KBAR;                        // per rotation-deflated position: adjoint of its coupling
+  double* LAMOUT;                      // eigenvalues when the caller passes none
+  size_t bytes;
+};
+
+static size_t align_up_adj(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t carve_adjoint(const Plan& plan, void* base, AdjWorkspace* aw) {
+  AdjWorkspace w{};
+  size_t off = carve_workspace(plan, base, &w.fw);
+  off = align_up_adj(off);
+  const size_t N = size_t(std::max<int64_t>(plan.nrows, 1));
+  char* b = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> double* {
+    double* p = b ? reinterpret_cast<double*>(b + off) : nullptr;
+    off += align_up_adj(bytes);
+    return p;
+  };
+  w.CK = take(8 * N * 3 * size_t(std::max(plan.steps, 1)));
+  double** arrs[] = {&w.GL,  &w.GBL, &w.GBH, &w.ALB,  &w.ABL, &w.ABH, &w.RLT,  &w.RAL,
+                     &w.RBE, &w.RGA, &w.RINU, &w.RC,  &w.PDB, &w.PZB, &w.PRLB, &w.PRHB,
+                     &w.MDB, &w.MZB, &w.MRLB, &w.MRHB, &w.KBAR, &w.LAMOUT};
+  for (double** p : arrs) *p = take(8 * N);
+  w.RHOBAR = take(8 * size_t(std::max<int64_t>(plan.cmax, 1)));
+  w.bytes = off;
+  if (aw) *aw = w;
+  return off;
+}
+
+static LevelState checkpoint(const AdjWorkspace& w, int s, int64_t N) {
+  double* base = w.CK + size_t(s) * 3 * size_t(N);
+  return LevelState{base, base + N, base + 2 * N};
+}
+
+__device__ __forceinline__ int64_t adj_find_merge(const Merge* M, int64_t cnt, int64_t p) {
+  int64_t lo = 0, hi = cnt;
+  while (hi - lo > 1) {
+    int64_t m = (lo + hi) >> 1;
+    if (M[m].lo <= p) lo = m; else hi = m;
+  }
+  return lo;
+}
+__device__ __forceinline__ int adj_count_less(const double* a, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (a[m] < x) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+__device__ __forceinline__ int adj_count_leq(const double* a, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (a[m] <= x) lo = m + 1; else hi = m;
+  }
+  return lo;
+}
+
+struct AdjArgs {
+  const Merge* M;
+  int64_t cnt;
+  int64_t nrows;
+  const MState* ms;
+  const int32_t *ROOTMAP, *ROOTMAP2;
+  const uint32_t *count, *count2;
+  const double *LAMA, *AD, *AZ, *ALO, *AHI, *TAU, *DORG, *ZHAT, *ROWLO, *ROWHI;
+  const double *D, *Z, *RLO, *RHI;  // the merge problem (restored before the deflation adjoint)
+  const double* es;
+  const int32_t *SURV, *OUTIDX, *ACTMAP, *KEEPIDX;
+  const uint8_t *PFLAG, *RFLAG;
+  LevelState in;  // children's state (checkpoint of this step)
+  AdjWorkspace w;
+  double* grad_e;
+};
+
+// parents' adjoints (ascending order) -> [active | deflated] order of each merge
+__global__ void k_adj_place(AdjArgs a) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < a.nrows;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = adj_find_merge(a.M, a.cnt, p);
+    const Merge m = a.M[g];
+    if (p < m.lo || p >= m.hi) continue;
+    const int K = a.ms[g].K, lo = m.lo, F = (m.hi - m.lo) - K, local = int(p - lo);
+    int rank;
+    if (local < K)
+      rank = local + adj_count_less(a.AD + lo + K, F, a.LAMA[p]);
+    else
+      rank = (local - K) + adj_count_leq(a.LAMA + lo, K, a.AD[p]);
+    const int src = lo + rank;
+    a.w.ALB[p] = a.w.GL[src];
+    a.w.ABL[p] = a.w.GBL[src];
+    a.w.ABH[p] = a.w.GBH[src];
+  }
+}
+
+__device__ __forceinline__ double adj_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// root r of both lists (large-K first)
+__device__ __forceinline__ int adj_list_merge(const AdjArgs& a, uint32_t r, int* in_list) {
+  const uint32_t nb = *a.count2;
+  if (r < nb) {
+    *in_list = int(r);
+    return a.ROOTMAP2[r];
+  }
+  *in_list = int(r - nb);
+  return a.ROOTMAP[r - nb];
+}
+
+// Per active root j: 1 / nu_j and c_j = z^T y_j (one sweep over the poles).
+__global__ void k_adj_roots(AdjArgs a) {
+  const uint32_t total = *a.count + *a.count2;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = warp; r < total; r += nwarps) {
+    int rl;
+    const int g = adj_list_merge(a, r, &rl);
+    const MState ms = a.ms[g];
+    const int K = ms.K, j = rl - ms.base, lo = a.M[g].lo;
+    const double dorg = a.DORG[lo + j], tau = a.TAU[lo + j];
+    double nu2 = 0.0, C = 0.0;
+    for (int i = lane; i < K; i += 32) {
+      const double zh = a.ZHAT[lo + i];
+      const double t = zh * rcp_refined((a.AD[lo + i] - dorg) - tau);
+      nu2 = fma(t, t, nu2);
+      C = fma(zh, t, C);
+    }
+    nu2 = adj_warp_sum(nu2);
+    C = adj_warp_sum(C);
+    if (lane == 0) {
+      const double inu = 1.0 / sqrt(nu2);
+      a.w.RINU[lo + j] = inu;
+      a.w.RC[lo + j] = C * inu;
+    }
+  }
+}
+
+// Per active root j, a sweep over the other roots k of its merge: g_j and h_j,
+// and the merge's rho' adjoint sum_j (lbar_j c_j^2 + c_j h_j / 2).
+__global__ void k_adj_pairs(AdjArgs a) {
+  const uint32_t total = *a.count + *a.count2;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = warp; r < total; r += nwarps) {
+    int rl;
+    const int g = adj_list_merge(a, r, &rl);
+    const MState ms = a.ms[g];
+    const int K = ms.K, j = rl - ms.base, lo = a.M[g].lo;
+    const double oj = a.DORG[lo + j], tj = a.TAU[lo + j];
+    const double bl = a.ROWLO[lo + j], bh = a.ROWHI[lo + j];
+    const double gbl = a.w.ABL[lo + j], gbh = a.w.ABH[lo + j];
+    const double inuj = a.w.RINU[lo + j];
+    double gs = 0.0, hs = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      if (k == j) continue;
+      const double dl = (oj - a.DORG[lo + k]) + (tj - a.TAU[lo + k]);  // l_j - l_k
+      const double idl = 1.0 / dl;
+      const double wd = (bl * a.w.ABL[lo + k] + bh * a.w.ABH[lo + k]) -
+                        (a.ROWLO[lo + k] * gbl + a.ROWHI[lo + k] * gbh);  // W_jk - W_kj
+      gs -= wd * inuj * a.w.RINU[lo + k] * idl * idl;
+      hs -= wd * a.w.RC[lo + k] * idl;
+    }
+    gs = adj_warp_sum(gs);
+    hs = adj_warp_sum(hs);
+    if (lane == 0) {
+      a.w.RLT[lo + j] = gs;
+      a.w.RAL[lo + j] = hs;
+      const double c = a.w.RC[lo + j];
+      atomicAdd(&a.w.RHOBAR[g], a.w.ALB[lo + j] * c * c + 0.5 * c * hs);
+    }
+  }
+}
+
+// Per active pole s: adjoints of D_s, z_s (through zhat ~ z), RLO_s, RHI_s.
+__global__ void k_adj_poles(AdjArgs a) {
+  const uint32_t total = *a.count + *a.count2;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = warp; r < total; r += nwarps) {
+    int rl;
+    const int g = adj_list_merge(a, r, &rl);
+    const MState ms = a.ms[g];
+    const int K = ms.K, i = rl - ms.base, lo = a.M[g].lo;
+    const double Di = a.AD[lo + i], zh = a.ZHAT[lo + i];
+    double db = 0.0, zb = 0.0, rlb = 0.0, rhb = 0.0;
+    for (int j = lane; j < K; j += 32) {
+      const double t = zh * rcp_refined((Di - a.DORG[lo + j]) - a.TAU[lo + j]);
+      const double y = t * a.w.RINU[lo + j];
+      const double lb = a.w.ALB[lo + j];
+      db += lb * y * y + zh * a.w.RLT[lo + j] * t;
+      zb += y * (2.0 * lb * a.w.RC[lo + j] + a.w.RAL[lo + j]);
+      rlb = fma(a.w.ABL[lo + j], y, rlb);
+      rhb = fma(a.w.ABH[lo + j], y, rhb);
+    }
+    db = adj_warp_sum(db);
+    zb = adj_warp_sum(zb);
+    rlb = adj_warp_sum(rlb);
+    rhb = adj_warp_sum(rhb);
+    if (lane == 0) {
+      a.w.PDB[lo + i] = db;
+      a.w.PZB[lo + i] = ms.rho * zb;
+      a.w.PRLB[lo + i] = rlb;
+      a.w.PRHB[lo + i] = rhb;
+    }
+  }
+}
+
+// Per rotation-deflated position: kappa_bar (see the header) by a sweep over the
+// active roots of its merge (one warp per position).
+__global__ void k_adj_kappa(AdjArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t p = warp; p < a.nrows; p += nwarps) {
+    const int64_t g = adj_find_merge(a.M, a.cnt, p);
+    const Merge m = a.M[g];
+    if (p < m.lo || p >= m.hi) continue;
+    if (a.PFLAG[p] != 2) continue;
+    const int lo = m.lo;
+    const int K = a.ms[g].K;
+    const int idx = lo + a.OUTIDX[p];
+    const int ia = lo + a.KEEPIDX[p];
+    const double v = a.AD[idx], rl = a.ALO[idx], rh = a.AHI[idx];
+    const double gbl = a.w.ABL[idx], gbh = a.w.ABH[idx];
+    const double Da = a.AD[ia], za = a.ZHAT[ia];
+    double kb = 0.0;
+    for (int j = lane; j < K; j += 32) {
+      const double oj = a.DORG[lo + j], tj = a.TAU[lo + j];
+      const double y = za * rcp_refined((Da - oj) - tj) * a.w.RINU[lo + j];
+      const double num = (a.w.ABL[lo + j] * rl + a.w.ABH[lo + j] * rh) -
+                         (gbl * a.ROWLO[lo + j] + gbh * a.ROWHI[lo + j]);
+      kb += y * num / ((oj - v) + tj);
+    }
+    kb = adj_warp_sum(kb);
+    if (lane == 0) a.w.KBAR[p] = kb;
+  }
+}
+
+// Deflation adjoint of one merge (one block per merge).  Negligible-z entries pass
+// their adjoints through; every rotation run (survivors k0..kL, kept pole = the
+// z^2-weighted mean, deflated entries = cross-weighted means, rows rotated) is
+// reversed by one thread through its prefix sums W, S = sum D w, U = sum z R.
+__global__ void k_adj_deflate(AdjArgs a) {
+  for (int64_t g = blockIdx.x; g < a.cnt; g += gridDim.x) {
+    const Merge m = a.M[g];
+    const int lo = m.lo, n0 = m.hi - m.lo;
+    const double* D = a.D + lo;
+    const double* Z = a.Z + lo;
+    const double* RL = a.RLO + lo;
+    const double* RH = a.RHI + lo;
+    int S = 0;  // survivors = positions not deflated for a negligible z
+    for (int p = threadIdx.x; p < n0; p += blockDim.x) {
+      if (a.PFLAG[lo + p] == 1) {
+        const int idx = lo + a.OUTIDX[lo + p];
+        a.w.MDB[lo + p] = a.w.ALB[idx];
+        a.w.MZB[lo + p] = 0.0;
+        a.w.MRLB[lo + p] = a.w.ABL[idx];
+        a.w.MRHB[lo + p] = a.w.ABH[idx];
+      }
+    }
+    {
+      int c = 0;
+      for (int p = threadIdx.x; p < n0; p += blockDim.x) c += a.PFLAG[lo + p] != 1 ? 1 : 0;
+      __shared__ int s_cnt;
+      if (threadIdx.x == 0) s_cnt = 0;
+      __syncthreads();
+      atomicAdd(&s_cnt, c);
+      __syncthreads();
+      S = s_cnt;
+      __syncthreads();
+    }
+    double* PW = a.w.RLT + lo;  // per-survivor prefix scratch (the root scalars are dead)
+    double* PS = a.w.RAL + lo;
+    double* PUL = a.w.RBE + lo;
+    double* PUH = a.w.RGA + lo;
+    for (int k0 = threadIdx.x; k0 < S; k0 += blockDim.x) {
+      if (a.RFLAG[lo + k0] == 0) continue;  // not a run start
+      int kL = k0;
+      while (kL + 1 < S && a.RFLAG[lo + kL + 1] == 0) ++kL;
+      const int L = kL - k0;
+      const int act = lo + a.ACTMAP[lo + kL];
+      if (L == 0) {
+        const int p = a.SURV[lo + k0] - lo;
+        a.w.MDB[lo + p] = a.w.PDB[act];
+        a.w.MZB[lo + p] = a.w.PZB[act];
+        a.w.MRLB[lo + p] = a.w.PRLB[act];
+        a.w.MRHB[lo + p] = a.w.PRHB[act];
+        continue;
+      }
+      // forward prefix sums
+      double W = 0.0, Sx = 0.0, UL = 0.0, UH = 0.0;
+      for (int q = 0; q <= L; ++q) {
+        const int p = a.SURV[lo + k0 + q] - lo;
+        const double z = Z[p], w = z * z;
+        W += w;
+        Sx += D[p] * w;
+        UL += z * RL[p];
+        UH += z * RH[p];
+        PW[k0 + q] = W;
+        PS[k0 + q] = Sx;
+        PUL[k0 + q] = UL;
+        PUH[k0 + q] = UH;
+      }
+      // adjoint of the kept pole (prefix L)
+      const double cbar = a.w.PDB[act], zabar = a.w.PZB[act];
+      const double ralbar = a.w.PRLB[act], rahbar = a.w.PRHB[act];
+      const double za = sqrt(W);
+      double aW = -cbar * Sx / (W * W) + zabar / (2.0 * za) -
+                  (ralbar * UL + rahbar * UH) / (2.0 * za * za * za);
+      double aS = cbar / W;
+      double aUL = ralbar / za, aUH = rahbar / za;
+      double GW = 0.0, GS = 0.0, GUL = 0.0, GUH = 0.0;
+      for (int q = L; q >= 0; --q) {
+        const int p = a.SURV[lo + k0 + q] - lo;
+        const double Dm = D[p], zm = Z[p], wm = zm * zm, Rl = RL[p], Rh = RH[p];
+        GW += aW;
+        GS += aS;
+        GUL += aUL;
+        GUH += aUH;
+        double wbar = GW + GS * Dm;
+        double dbar = GS * wm;
+        double zbar = GUL * Rl + GUH * Rh;
+        double rlbar = GUL * zm, rhbar = GUH * zm;
+        aW = aS = aUL = aUH = 0.0;
+        if (q >= 1) {  // deflated entry q uses prefix q-1
+          // dropped coupling to the kept pole: kappa = Km (c_{q-1} - D_q)
+          {
+            const double Pw = PW[k0 + q - 1];
+            const double Km = zm * sqrt(Pw) / sqrt(PW[k0 + q] * W);
+            const double kb = a.w.KBAR[lo + p] * Km;
+            dbar -= kb;
+            aS += kb / Pw;                                // c = S / W over prefix q-1
+            aW -= kb * PS[k0 + q - 1] / (Pw * Pw);
+          }
+          const int idx = lo + a.OUTIDX[lo + p];
+          const double vbar = a.w.ALB[idx], rbl = a.w.ABL[idx], rbh = a.w.ABH[idx];
+          const double P = PW[k0 + q - 1], Sp = PS[k0 + q - 1];
+          const double Upl = PUL[k0 + q - 1], Uph = PUH[k0 + q - 1];
+          const double Q = P + wm;
+          const double v = (wm * (Sp / P) + P * Dm) / Q;
+          const double sig = 1.0 / sqrt(P * Q);
+          const double numl = zm * Upl - P * Rl, numh = zm * Uph - P * Rh;
+          const double dsig_dP = -sig * (Q + P) / (2.0 * P * Q);
+          const double dsig_dw = -sig / (2.0 * Q);
+          // value
+          aW += vbar * (Dm - wm * Sp / (P * P) - v) / Q;
+          aS += vbar * (wm / P) / Q;
+          wbar += vbar * (Sp / P - v) / Q;
+          dbar += vbar * P / Q;
+          // rows
+          aW += rbl * (-Rl * sig + numl * dsig_dP) + rbh * (-Rh * sig + numh * dsig_dP);
+          aUL += rbl * zm * sig;
+          aUH += rbh * zm * sig;
+          wbar += (rbl * numl + rbh * numh) * dsig_dw;
+          zbar += (rbl * Upl + rbh * Uph) * sig;
+          rlbar += -P * sig * rbl;
+          rhbar += -P * sig * rbh;
+        }
+        zbar += 2.0 * zm * wbar;
+        a.w.MDB[lo + p] = dbar;
+        a.w.MZB[lo + p] = zbar;
+        a.w.MRLB[lo + p] = rlbar;
+        a.w.MRHB[lo + p] = rhbar;
+      }
+    }
+    if (threadIdx.x == 0) {
+      // rho' = 2 |beta|, beta = e at the cut
+      const double beta = a.es[m.mid - 1];
+      const double sg = beta >= 0.0 ? 1.0 : -1.0;
+      atomicAdd(&a.grad_e[m.mid - 1], 2.0 * sg * a.w.RHOBAR[g]);
+    }
+    __syncthreads();
+  }
+}
+
+// merge-position adjoints -> the children's (lambda, blo, bhi) adjoints
+__global__ void k_adj_form(AdjArgs a) {
+  const double inv_sqrt2 = 0.70710678118654752440;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < a.nrows;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const Merge m = a.M[adj_find_merge(a.M, a.cnt, p)];
+    if (p < m.lo || p >= m.hi) continue;
+    const double beta = a.es[m.mid - 1];
+    const double sgn = beta >= 0.0 ? 1.0 : -1.0;
+    const double x = a.in.lam[p];
+    if (p < m.mid) {
+      const int out = m.lo + int(p - m.lo) + adj_count_less(a.in.lam + m.mid, m.hi - m.mid, x);
+      a.w.GL[p] = a.w.MDB[out];
+      a.w.GBH[p] = a.w.MZB[out] * inv_sqrt2;
+      a.w.GBL[p] = a.w.MRLB[out];
+    } else {
+      const int out = m.lo + int(p - m.mid) + adj_count_leq(a.in.lam + m.lo, m.mid - m.lo, x);
+      a.w.GL[p] = a.w.MDB[out];
+      a.w.GBL[p] = sgn * a.w.MZB[out] * inv_sqrt2;
+      a.w.GBH[p] = a.w.MRHB[out];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Leaves: full eigen-decomposition of the torn leaf by the same implicit QR with
+// all rotations accumulated into Q (m <= 32), then the symmetric eigen adjoint.
+__device__ bool leaf_qr_full(int m, double* a, double* b, double* Q) {
+  int hi = m - 1, steps = 0;
+  while (hi > 0) {
+    int lo = hi;
+    while (lo > 0) {
+      if (fabs(b[lo - 1]) <= kEps * (fabs(a[lo - 1]) + fabs(a[lo]))) {
+        b[lo - 1] = 0.0;
+        break;
+      }
+      --lo;
+    }
+    if (lo == hi) {
+      --hi;
+      continue;
+    }
+    if (++steps > 40 * m) return false;
+    const double bh = b[hi - 1];
+    const double half = 0.5 * (a[hi - 1] - a[hi]);
+    const double root = sqrt(half * half + bh * bh);
+    double mu = a[hi] - bh * bh / (half + (half >= 0.0 ? root : -root));
+    if (!isfinite(mu)) mu = a[hi];
+    double x = a[lo] - mu, y = b[lo];
+    for (int i = lo; i < hi; ++i) {
+      const double r = sqrt(x * x + y * y);
+      double c = 1.0, s = 0.0;
+      if (r > 0.0) {  // the same arithmetic as the forward leaf solver
+        const double inv = 1.0 / r;
+        c = x * inv;
+        s = y * inv;
+      }
+      if (i > lo) b[i - 1] = r;
+      const double ai = a[i], aj = a[i + 1], bi = b[i];
+      const double cc = c * c, ss = s * s, cs = c * s;
+      a[i] = cc * ai + 2.0 * cs * bi + ss * aj;
+      a[i + 1] = ss * ai - 2.0 * cs * bi + cc * aj;
+      b[i] = cs * (aj - ai) + (cc - ss) * bi;
+      if (i + 1 < hi) {
+        const double bn = b[i + 1];
+        y = s * bn;
+        b[i + 1] = c * bn;
+        x = b[i];
+      }
+      for (int r0 = 0; r0 < m; ++r0) {
+        const double p = Q[r0 * kMaxBwdLeaf + i], q = Q[r0 * kMaxBwdLeaf + i + 1];
+        Q[r0 * kMaxBwdLeaf + i] = c * p + s * q;
+        Q[r0 * kMaxBwdLeaf + i + 1] = c * q - s * p;
+      }
+    }
+  }
+  return true;
+}
+
+__global__ void k_adj_leaves(const Leaf* __restrict__ leaves, int64_t nleaves,
+                             const double* __restrict__ ds, const double* __restrict__ es,
+                             const double* __restrict__ GL, const double* __restrict__ GBL,
+                             const double* __restrict__ GBH, LevelState fwd, double* grad_d,
+                             double* grad_e, Status* st) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < nleaves;
+       t += int64_t(gridDim.x) * blockDim.x) {
+    const Leaf lf = leaves[t];
+    const int m = lf.hi - lf.lo;
+    double a[kMaxBwdLeaf], b[kMaxBwdLeaf], Q[kMaxBwdLeaf * kMaxBwdLeaf];
+    for (int j = 0; j < m; ++j) {
+      a[j] = ds[lf.lo + j];
+      b[j] = (j + 1 < m) ? es[lf.lo + j] : 0.0;
+      for (int k = 0; k < m; ++k) Q[j * kMaxBwdLeaf + k] = (j == k) ? 1.0 : 0.0;
+    }
+    if (lf.flags & 1) a[0] -= fabs(es[lf.lo - 1]);
+    if (lf.flags & 2) a[m - 1] -= fabs(es[lf.hi - 1]);
+    if (!leaf_qr_full(m, a, b, Q)) set_status(st, TDE_ENOCONV);
+    // ascending order; the columns of Q follow their eigenvalue
+    for (int j = 0; j < m; ++j) {
+      int best = j;
+      for (int k = j + 1; k < m; ++k)
+        if (a[k] < a[best]) best = k;
+      if (best != j) {
+        const double tv = a[j];
+        a[j] = a[best];
+        a[best] = tv;
+        for (int r = 0; r < m; ++r) {
+          const double tq = Q[r * kMaxBwdLeaf + j];
+          Q[r * kMaxBwdLeaf + j] = Q[r * kMaxBwdLeaf + best];
+          Q[r * kMaxBwdLeaf + best] = tq;
+        }
+      }
+    }
+    // eigenvector signs are arbitrary: align every column with the rows the
+    // forward pass stored (the row adjoints refer to those), using the larger of
+    // the two boundary entries
+    if (!(lf.flags & 4)) {
+      for (int k = 0; k < m; ++k) {
+        const double f0 = fwd.blo[lf.lo + k], f1 = fwd.bhi[lf.lo + k];
+        const double q0 = Q[0 * kMaxBwdLeaf + k], q1 = Q[(m - 1) * kMaxBwdLeaf + k];
+        const bool flip = fabs(f0) >= fabs(f1) ? (q0 * f0 < 0.0) : (q1 * f1 < 0.0);
+        if (flip)
+          for (int r = 0; r < m; ++r) Q[r * kMaxBwdLeaf + k] = -Q[r * kMaxBwdLeaf + k];
+      }
+    }
+    // H = Q G with G_jk = lbar_j [j == k] + (Q_0j blobar_k + Q_{m-1}j bhibar_k) / (l_k - l_j)
+    double hprev[kMaxBwdLeaf];
+    for (int i = 0; i < m; ++i) {
+      double hrow[kMaxBwdLeaf];
+      for (int k = 0; k < m; ++k) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < m; ++j) {
+          if (j == k || a[k] == a[j]) continue;
+          const double f = Q[i * kMaxBwdLeaf + j] / (a[k] - a[j]);
+          s0 += f * Q[0 * kMaxBwdLeaf + j];
+          s1 += f * Q[(m - 1) * kMaxBwdLeaf + j];
+        }
+        hrow[k] = Q[i * kMaxBwdLeaf + k] * GL[lf.lo + k] + GBL[lf.lo + k] * s0 +
+                  GBH[lf.lo + k] * s1;
+      }
+      double dbar = 0.0;
+      for (int k = 0; k < m; ++k) dbar += hrow[k] * Q[i * kMaxBwdLeaf + k];
+      grad_d[lf.lo + i] = dbar;
+      if (i > 0) {  // e between rows i-1 and i: A_bar(i-1, i) + A_bar(i, i-1)
+        double eb = 0.0;
+        for (int k = 0; k < m; ++k)
+          eb += hprev[k] * Q[i * kMaxBwdLeaf + k] + hrow[k] * Q[(i - 1) * kMaxBwdLeaf + k];
+        atomicAdd(&grad_e[lf.lo + i - 1], eb);
+      }
+      if (i == 0 && (lf.flags & 1)) {
+        const double c = es[lf.lo - 1];
+        atomicAdd(&grad_e[lf.lo - 1], -(c >= 0.0 ? 1.0 : -1.0) * dbar);
+      }
+      if (i == m - 1 && (lf.flags & 2)) {
+        const double c = es[lf.hi - 1];
+        atomicAdd(&grad_e[lf.hi - 1], -(c >= 0.0 ? 1.0 : -1.0) * dbar);
+      }
+      for (int k = 0; k < m; ++k) hprev[k] = hrow[k];
+    }
+  }
+}
+
+__global__ void k_adj_init(int64_t nrows, const double* __restrict__ grad_lambda, double* GL,
+                           double* GBL, double* GBH, double* grad_e) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < nrows;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    GL[p] = grad_lambda[p];
+    GBL[p] = 0.0;
+    GBH[p] = 0.0;
+    grad_e[p] = 0.0;
+  }
+}
+
+void launch_leaves_to(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s,
+                      LevelState out);
+
+int run_adjoint(const Plan& plan, const AdjWorkspace& w, const int64_t* offsets_dev,
+                const double* d, const double* e, const double* grad_lambda, double* lambda,
+                double* grad_d, double* grad_e, cudaStream_t s) {
+  const Workspace& ws = w.fw;
+  const int64_t N = plan.nrows;
+  if (lambda == nullptr) lambda = w.LAMOUT;
+  if (cudaMemsetAsync(ws.status, 0, sizeof(Status), s) != cudaSuccess) return TDE_ECUDA;
+  if (cudaMemsetAsync(ws.sigma_bits, 0, 8 * size_t(plan.batch), s) != cudaSuccess)
+    return TDE_ECUDA;
+  // 1. forward with checkpoints
+  launch_plan(plan, ws, offsets_dev, s);
+  launch_scale(plan, ws, offsets_dev, d, e, s);
+  const LevelState scratch{ws.LAM, ws.BLO, ws.BHI};
+  launch_leaves_to(plan, ws, lambda, s, plan.steps > 0 ? checkpoint(w, 0, N) : scratch);
+  for (int st = 0; st < plan.steps; ++st) {
+    const LevelState out = st + 1 < plan.steps ? checkpoint(w, st + 1, N) : scratch;
+    launch_step(plan, ws, st, lambda, s, checkpoint(w, st, N), out);
+  }
+  const int flat = int(std::min<int64_t>((N + 255) / 256, 148 * 8));
+  k_adj_init<<<flat, 256, 0, s>>>(N, grad_lambda, w.GL, w.GBL, w.GBH, grad_e);
+  g_launches += 1;
+  // 2. reverse sweep
+  for (int st = plan.steps - 1; st >= 0; --st) {
+    const Merge* M = ws.merges + plan.step_base[st];
+    const int64_t cnt = plan.step_count[st];
+    if (cudaMemsetAsync(&ws.status->root_count[st], 0, 4, s) != cudaSuccess) return TDE_ECUDA;
+    if (cudaMemsetAsync(&ws.status->root_count_big[st], 0, 4, s) != cudaSuccess) return TDE_ECUDA;
+    if (cudaMemsetAsync(w.RHOBAR, 0, 8 * size_t(cnt), s) != cudaSuccess) return TDE_ECUDA;
+    const LevelState in = checkpoint(w, st, N);
+    launch_step(plan, ws, st, lambda, s, in, scratch, /*recompute=*/true);
+    AdjArgs a;
+    a.M = M;
+    a.cnt = cnt;
+    a.nrows = N;
+    a.ms = ws.mstate;
+    a.ROOTMAP = ws.ROOTMAP;
+    a.ROOTMAP2 = ws.ROOTMAP2;
+    a.count = &ws.status->root_count[st];
+    a.count2 = &ws.status->root_count_big[st];
+    a.LAMA = ws.D;
+    a.AD = ws.AD;
+    a.AZ = ws.AZ;
+    a.ALO = ws.ALO;
+    a.AHI = ws.AHI;
+    a.TAU = ws.TAU;
+    a.DORG = reinterpret_cast<const double*>(ws.KEYA);
+    a.ZHAT = ws.Z;
+    a.ROWLO = ws.RLO;
+    a.ROWHI = ws.RHI;
+    a.D = ws.D;
+    a.Z = ws.Z;
+    a.RLO = ws.RLO;
+    a.RHI = ws.RHI;
+    a.es = ws.es;
+    a.SURV = ws.SURV;
+    a.OUTIDX = ws.OUTIDX;
+    a.ACTMAP = ws.ACTMAP;
+    a.KEEPIDX = ws.KEEPIDX;
+    a.PFLAG = ws.PFLAG;
+    a.RFLAG = ws.RFLAG;
+    a.in = in;
+    a.w = w;
+    a.grad_e = grad_e;
+    k_adj_place<<<flat, 256, 0, s>>>(a);
+    k_adj_roots<<<148 * 8, 128, 0, s>>>(a);
+    k_adj_pairs<<<148 * 8, 128, 0, s>>>(a);
+    k_adj_poles<<<148 * 8, 128, 0, s>>>(a);
+    k_adj_kappa<<<148 * 8, 128, 0, s>>>(a);
+    launch_form(plan, ws, st, in, s);  // restore D, z, RLO, RHI of the merge problem
+    const int dgrid = int(std::min<int64_t>(cnt, 148 * 8));
+    k_adj_deflate<<<dgrid, 256, 0, s>>>(a);
+    k_adj_form<<<flat, 256, 0, s>>>(a);
+    g_launches += 8;
+  }
+  // 3. leaves
+  const int lgrid = int(std::min<int64_t>((plan.nleaves + 63) / 64, 148 * 32));
+  const LevelState leafstate = plan.steps > 0 ? checkpoint(w, 0, N) : scratch;
+  k_adj_leaves<<<std::max(lgrid, 1), 64, 0, s>>>(ws.leaves, plan.nleaves, ws.ds, ws.es, w.GL,
+                                                  w.GBL, w.GBH, leafstate, grad_d, grad_e,
+                                                  ws.status);
+  g_launches += 1;
+  return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
+}
+
+}  // namespace tde
+
+using namespace tde;
+
+extern "C" int tde_eigvals_backward_workspace(int64_t batch, const int64_t* offsets_host,
+                                              int32_t leaf, size_t* bytes) {
+  if (bytes == nullptr) return TDE_EINVAL;
+  Plan p;
+  int rc = build_plan(batch, offsets_host, leaf, &p);
+  if (rc != TDE_OK) return rc;
+  if (p.leaf > kMaxBwdLeaf) return TDE_EINVAL;
+  *bytes = carve_adjoint(p, nullptr, nullptr);
+  return TDE_OK;
+}
+
+extern "C" int tde_eigvals_backward(int64_t batch, const int64_t* offsets_host,
+                                    const int64_t* offsets_dev, const double* d, const double* e,
+                                    const double* grad_lambda, double* lambda, double* grad_d,
+                                    double* grad_e, int32_t leaf, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  g_launches = 0;
+  Plan p;
+  int rc = build_plan(batch, offsets_host, leaf, &p);
+  if (rc != TDE_OK) return rc;
+  if (p.leaf > kMaxBwdLeaf) return TDE_EINVAL;
+  if (p.nrows == 0) return TDE_OK;
+  if (offsets_dev == nullptr || d == nullptr || grad_lambda == nullptr || grad_d == nullptr ||
+      grad_e == nullptr || ws == nullptr || (p.nrows > 1 && e == nullptr))
+    return TDE_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return TDE_EINVAL;
+  AdjWorkspace w;
+  size_t need = carve_adjoint(p, ws, &w);
+  if (ws_bytes < need) return TDE_EWORKSPACE;
+  return run_adjoint(p, w, offsets_dev, d, e, grad_lambda, lambda, grad_d, grad_e,
+                     static_cast<cudaStream_t>(stream));
+}

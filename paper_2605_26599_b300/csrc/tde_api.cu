@@ -60,9 +60,10 @@ int run_solver(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev
   launch_plan(plan, ws, offsets_dev, stream);
   launch_scale(plan, ws, offsets_dev, d, e, stream);
   launch_leaves(plan, ws, lambda, stream);
+  const LevelState state{ws.LAM, ws.BLO, ws.BHI};
   for (int s = 0; s < plan.steps; ++s) {
     g_prof_step = s;
-    launch_step(plan, ws, s, lambda, stream);
+    launch_step(plan, ws, s, lambda, stream, state, state);
   }
   g_prof_step = -1;
   return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;

@@ -108,6 +108,10 @@ struct Workspace {
   double *AD, *AZ, *ALO, *AHI;
   double* TAU;
   int32_t *ORG, *SEG, *ROOTMAP, *ROOTMAP2, *SURV;
+  int32_t* ZPOS;    // negligible-z deflated positions of a merge (deflation step 5)
+  int32_t* OUTIDX;  // per merge position: index of its deflated entry in [active | deflated]
+  int32_t* ACTMAP;  // per survivor: index of the active pole its run ends in
+  int32_t* KEEPIDX; // per rotation-deflated position: active index of its run's kept pole
   uint8_t *PFLAG, *RFLAG;
   unsigned long long *KEYA, *KEYB;
   int32_t *IDXA, *IDXB;
@@ -230,10 +234,20 @@ void launch_plan(const Plan& plan, const Workspace& ws, const int64_t* offsets_d
 void launch_scale(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev,
                   const double* d, const double* e, cudaStream_t s);
 void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s);
-void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda,
-                 cudaStream_t s);
+// Boundary-row state (eigenvalues, first and last eigenvector rows) of one level.
+struct LevelState {
+  double *lam, *blo, *bhi;
+};
+// One merge step: reads the children's state from `in` and writes the parents'
+// state to `out` (in == out is allowed: a merge's children occupy its own rows).
+// With recompute = true only the merge internals are rebuilt (no place): used by
+// the adjoint, which also forces z-hat and rows at root merges.
+void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
+                 LevelState in, LevelState out, bool recompute = false);
+void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in, cudaStream_t s);
 // secular, Lowner and boundary-row kernels of one step; returns the launch count
-int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s);
+int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s,
+                 bool all_merges = false);
 
 // Reciprocal in about three FP64 fused multiply-adds: a hardware approximation r0
 // of 1/x refined by the third-order (Householder) step for 1/x,

@@ -131,16 +131,21 @@ __global__ void k_leaves(const Leaf* __restrict__ leaves, int64_t nleaves,
   }
 }
 
-void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s) {
+void launch_leaves_to(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s,
+                      LevelState out) {
   if (plan.nleaves == 0) return;
   int block = 64;
   int64_t grid = (plan.nleaves + block - 1) / block;
   if (grid > 148 * 32) grid = 148 * 32;
   prof_begin(kKLeaves, s);
   k_leaves<<<int(grid), block, 0, s>>>(ws.leaves, plan.nleaves, ws.ds, ws.es, ws.sigma_bits,
-                                       ws.LAM, ws.BLO, ws.BHI, lambda, ws.status);
+                                       out.lam, out.blo, out.bhi, lambda, ws.status);
   prof_end(kKLeaves, s);
   g_launches += 1;
+}
+
+void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s) {
+  launch_leaves_to(plan, ws, lambda, s, LevelState{ws.LAM, ws.BLO, ws.BHI});
 }
 
 }  // namespace tde

@@ -276,7 +276,7 @@ struct DeflateArgs {
   const double* es;
   double *D, *Z, *RLO, *RHI;
   double *AD, *AZ, *ALO, *AHI;
-  int32_t *SURV, *ROOTMAP, *ROOTMAP2, *IDXA, *IDXB;
+  int32_t *SURV, *ROOTMAP, *ROOTMAP2, *IDXA, *IDXB, *ZPOS, *OUTIDX, *ACTMAP, *KEEPIDX;
   uint8_t *PFLAG, *RFLAG;
   unsigned long long *KEYA, *KEYB;
   MState* ms;
@@ -410,8 +410,10 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
         RLO[pos] = (zk * prev.ulo - Wp * rl) * sc;
         RHI[pos] = (zk * prev.uhi - Wp * rh) * sc;
         PFLAG[pos] = 2;
+        a.KEEPIDX[lo + pos] = K + act;  // its run ends in the next run end, active index K + act
       }
       if (valid && runend) {
+        a.ACTMAP[lo + k] = K + act;
         double ad, az, al, ah;
         if (head) {
           ad = Dk;
@@ -444,7 +446,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
     // 5. deflated eigenvalues: those deflated for a negligible z (PFLAG 1) keep the
     //    ascending order of D; rotated ones (PFLAG 2) may be out of order.  Collect
     //    the positions of each kind, in position order.
-    int32_t* ZPOS = SURV;  // the survivor list is dead after step 4
+    int32_t* ZPOS = a.ZPOS + lo;  // SURV stays intact for the adjoint
     int32_t* RPOS = a.IDXA + lo;
     int FZ = 0, FR = 0;
     for (int c0 = 0; c0 < n0; c0 += kNT) {
@@ -484,6 +486,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       a.AD[dst] = x;
       a.ALO[dst] = RLO[pos];
       a.AHI[dst] = RHI[pos];
+      a.OUTIDX[lo + pos] = K + k + l;
     }
     for (int k = tid; k < FR; k += kNT) {
       const int pos = RPOS[k];
@@ -497,6 +500,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       a.AD[dst] = x;
       a.ALO[dst] = RLO[pos];
       a.AHI[dst] = RHI[pos];
+      a.OUTIDX[lo + pos] = K + k + l;
     }
     __syncthreads();
     // 7. roots of this merge get a contiguous range of one of the step's two root
@@ -567,14 +571,22 @@ __global__ void k_place(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
 }
 
 // ---------------------------------------------------------------------------
-void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s) {
+void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in, cudaStream_t s) {
+  const Merge* M = ws.merges + plan.step_base[step];
+  const int64_t nrows = plan.nrows;
+  const int flat_grid = int(std::min<int64_t>((nrows + 255) / 256, 148 * 8));
+  k_form<<<flat_grid, 256, 0, s>>>(M, plan.step_count[step], nrows, in.lam, in.blo, in.bhi, ws.es,
+                                   ws.D, ws.Z, ws.RLO, ws.RHI);
+}
+
+void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
+                 LevelState in, LevelState out, bool recompute) {
   const Merge* M = ws.merges + plan.step_base[step];
   const int64_t cnt = plan.step_count[step];
   const int64_t nrows = plan.nrows;
   const int flat_grid = int(std::min<int64_t>((nrows + 255) / 256, 148 * 8));
   prof_begin(kKForm, s);
-  k_form<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.LAM, ws.BLO, ws.BHI, ws.es, ws.D, ws.Z,
-                                   ws.RLO, ws.RHI);
+  launch_form(plan, ws, step, in, s);
   prof_end(kKForm, s);
   DeflateArgs da;
   da.M = M;
@@ -592,6 +604,10 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   da.SURV = ws.SURV;
   da.ROOTMAP = ws.ROOTMAP;
   da.ROOTMAP2 = ws.ROOTMAP2;
+  da.ZPOS = ws.ZPOS;
+  da.OUTIDX = ws.OUTIDX;
+  da.ACTMAP = ws.ACTMAP;
+  da.KEEPIDX = ws.KEEPIDX;
   da.IDXA = ws.IDXA;
   da.IDXB = ws.IDXB;
   da.PFLAG = ws.PFLAG;
@@ -605,10 +621,15 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   prof_begin(kKDeflate, s);
   k_deflate<<<def_grid, kNT, 0, s>>>(da);
   prof_end(kKDeflate, s);
-  int launches = 3 + launch_roots(plan, ws, step, M, s);  // form, deflate, place + roots
+  int launches = 2 + launch_roots(plan, ws, step, M, s, recompute);  // form, deflate + roots
+  if (recompute) {
+    g_launches += launches;
+    return;
+  }
+  ++launches;  // place
   prof_begin(kKPlace, s);
   k_place<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.mstate, ws.D, ws.RLO, ws.RHI, ws.AD,
-                                    ws.ALO, ws.AHI, ws.sigma_bits, ws.LAM, ws.BLO, ws.BHI,
+                                    ws.ALO, ws.AHI, ws.sigma_bits, out.lam, out.blo, out.bhi,
                                     lambda);
   prof_end(kKPlace, s);
   g_launches += launches;

@@ -37,6 +37,7 @@ struct RootArgs {
   double* DORG;           // alias KEYA: D_org(j) of every active root
   Status* st;
   uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
+  int all_merges;           // also build z-hat and rows at root merges (adjoint)
 };
 
 // ---------------------------------------------------------------------------
@@ -426,7 +427,7 @@ __global__ void k_lowner_thread(RootArgs a) {
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const Merge m = a.M[g];
-    if (uint32_t(m.info) & kRootBit) continue;
+    if ((uint32_t(m.info) & kRootBit) && !a.all_merges) continue;
     const MState ms = a.ms[g];
     const int K = ms.K, i = int(r) - ms.base, lo = m.lo;
     const double* AD = a.AD + lo;
@@ -459,7 +460,7 @@ __global__ void k_lowner_warp(RootArgs a) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
     const Merge m = a.M[g];
-    if (uint32_t(m.info) & kRootBit) continue;
+    if ((uint32_t(m.info) & kRootBit) && !a.all_merges) continue;
     const MState ms = a.ms[g];
     const int K = ms.K, i = rl - ms.base, lo = m.lo;
     const double* AD = a.AD + lo;
@@ -499,7 +500,7 @@ __global__ void k_rows_thread(RootArgs a) {
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const Merge m = a.M[g];
-    if (uint32_t(m.info) & kRootBit) continue;
+    if ((uint32_t(m.info) & kRootBit) && !a.all_merges) continue;
     const MState ms = a.ms[g];
     const int K = ms.K, j = int(r) - ms.base, lo = m.lo;
     const double* AD = a.AD + lo;
@@ -532,7 +533,7 @@ __global__ void k_rows_warp(RootArgs a) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
     const Merge m = a.M[g];
-    if (uint32_t(m.info) & kRootBit) continue;
+    if ((uint32_t(m.info) & kRootBit) && !a.all_merges) continue;
     const MState ms = a.ms[g];
     const int K = ms.K, j = rl - ms.base, lo = m.lo;
     const double* AD = a.AD + lo;
@@ -573,7 +574,8 @@ __global__ void k_rows_warp(RootArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s) {
+int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s,
+                 bool all_merges) {
   RootArgs ra;
   ra.M = M;
   ra.ms = ws.mstate;
@@ -594,6 +596,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.DORG = reinterpret_cast<double*>(ws.KEYA);
   ra.st = ws.status;
   ra.small_list_min = uint32_t(plan.tune.small_list_min);
+  ra.all_merges = all_merges ? 1 : 0;
   // The thread kernels cover the small-K list when it is long enough to fill the
   // GPU; the warp kernels cover the large-K list and a short small-K list.  Which
   // case applies is known only on the device, so both always launch.
@@ -605,7 +608,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   k_secular_warp<<<wgrid, 128, 0, s>>>(ra);
   prof_end(kKSecular, s);
   int launches = 2;
-  if (plan.step_has_nonroot[step]) {
+  if (plan.step_has_nonroot[step] || all_merges) {
     prof_begin(kKLowner, s);
     k_lowner_thread<<<tgrid, 128, 0, s>>>(ra);
     k_lowner_warp<<<wgrid, 128, 0, s>>>(ra);
