@@ -354,6 +354,10 @@ def run_ours(args, rank: int, world: int, dist) -> None:
                                "frac_of_peak": fl / (ktimes[k] * 1e-3) / 1e12 / peak_tflops}
 
     cpu = cpu_baseline(n, fams) if (world == 1 and not args.no_cpu_baseline) else None
+    extras = {}
+    if not args.no_extras:
+        extras["batched"] = batched_section(args, dev)
+        extras["backward"] = backward_section(args, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -375,7 +379,129 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         "clocks": clocks,
         "source_hash": source_hash(),
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
+
+
+def batched_section(args, dev) -> dict:
+    """Config 3: 4096 Lanczos-style tridiagonals (orders log-uniform in [64, 4096]) solved
+    by one CUDA-graph replay of the forest solver (launch shape autotuned on a 512-matrix
+    sample), against the plain per-matrix loop on one stream."""
+    import torch
+
+    import oracle
+    import paper_2605_26599_b300 as tde
+    from paper_2605_26599_b300.batched import BatchedSolver, autotune
+
+    d, e, off = inputs.batched_lanczos()
+    B = len(off) - 1
+    dt, et = torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev)
+    best = autotune(off, dt, et, leaves=(4, 8, 16), warp_min_ks=(256, 512, 1024), reps=2,
+                    sample=512)
+    solver = BatchedSolver(off, leaf=best["leaf"], device=dev)
+    solver(dt, et)
+    for _ in range(args.warmup):
+        solver.run()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    reps = max(args.steps, 3)
+    ev[0].record()
+    for _ in range(reps):
+        solver.run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    lam = solver.run().cpu().numpy()
+    # accuracy on 48 sampled matrices, 12 sampled eigenvalues each
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    for k in rng.choice(B, 48, replace=False):
+        a, b = int(off[k]), int(off[k + 1])
+        ks = np.unique(np.linspace(0, b - a - 1, 12).astype(np.int64))
+        ref = oracle.eigvals_select(d[a:b], e[a:b - 1], ks)
+        gate = 8 * (b - a) * np.finfo(np.float64).eps * oracle.norm1(d[a:b], e[a:b - 1])
+        worst = max(worst, float(np.max(np.abs(lam[a:b][ks] - ref)) / gate))
+    # the plain per-matrix loop (single-matrix entry point, one stream)
+    ws = tde.Workspace(tde.workspace_bytes(4096, best["leaf"]), dev)
+    out = torch.empty_like(dt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(B):
+        a, b = int(off[k]), int(off[k + 1])
+        tde.eigvals(dt[a:b], et[a:b], leaf=best["leaf"], out=out[a:b], ws=ws, check=False)
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    tde.set_tuning()
+    return {"workload": f"{B} Lanczos-style tridiagonals, n_k log-uniform [64, 4096], "
+                        f"{int(off[-1])} rows (seed 0)",
+            "solves_per_s": B / (ms * 1e-3), "ms_per_batch": ms, "graph": True,
+            "tuned": {"leaf": best["leaf"], "warp_min_k": best["warp_min_k"],
+                      "trials": len(best.get("trials", []))},
+            "per_matrix_loop_solves_per_s": B / loop_s, "per_matrix_loop_ms": loop_s * 1e3,
+            "speedup_vs_loop": (B / (ms * 1e-3)) / (B / loop_s),
+            "max_err_over_gate_sampled": worst}
+
+
+def backward_section(args, dev) -> dict:
+    """Config 4: 256 tridiagonals of order 8192 (d ~ N(0,1), e ~ |N(0,0.5)|), loss
+    L = sum_i w_i lambda_i^2: forward (batched) and the hand-written adjoint, timed
+    separately; gradient error against the dense-eigh gradient on n = 256 copies."""
+    import torch
+
+    import oracle
+    import paper_2605_26599_b300 as tde
+
+    d, e, off, w = inputs.grad_batch()
+    dt, et = torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev)
+    wt = torch.from_numpy(w).to(dev)
+    leaf = 8
+    fws = tde.Workspace(tde.batched_workspace_bytes(off, leaf), dev)
+    bws = tde.Workspace(tde.backward_workspace_bytes(off, leaf), dev)
+    offd = torch.from_numpy(off).to(dev)
+    lam = torch.empty_like(dt)
+    gl = torch.empty_like(dt)
+
+    def fwd():
+        tde.eigvals_batched(dt, et, off, leaf=leaf, out=lam, ws=fws, check=False, offsets_dev=offd)
+
+    def bwd():
+        torch.mul(wt, lam, out=gl)
+        gl.mul_(2.0)
+        return tde.eigvals_backward(dt, et, gl, offsets=off, leaf=leaf, ws=bws, check=False,
+                                    offsets_dev=offd)
+
+    for _ in range(2):
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    reps = max(args.steps, 3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev[0].record()
+    for _ in range(reps):
+        fwd()
+    ev[1].record()
+    for _ in range(reps):
+        bwd()
+    ev[2].record()
+    torch.cuda.synchronize()
+    fms = ev[0].elapsed_time(ev[1]) / reps
+    bms = ev[1].elapsed_time(ev[2]) / reps
+    # accuracy on n = 256 copies of the family against the dense-eigh gradient
+    worst = 0.0
+    for seed in range(4):
+        dd, ee = inputs.normal_absnormal(256, seed=100 + seed, e_scale=0.5)
+        ww = np.random.default_rng(200 + seed).uniform(0, 1, 256)
+        ddt = torch.from_numpy(dd).to(dev)
+        eet = torch.from_numpy(np.concatenate([ee, [0.0]])).to(dev)
+        lm = tde.eigvals(ddt, eet, leaf=leaf)
+        _, gd, ge = tde.eigvals_backward(ddt, eet, 2.0 * torch.from_numpy(ww).to(dev) * lm, leaf=leaf)
+        rd, re_ = oracle.grad_dense(dd, ee, ww)
+        worst = max(worst, float(np.max(np.abs(gd.cpu().numpy() - rd)) / np.max(np.abs(rd))),
+                    float(np.max(np.abs(ge.cpu().numpy()[:255] - re_)) / np.max(np.abs(re_))))
+    return {"workload": "256 tridiagonals n=8192, d~N(0,1), e~|N(0,0.5)|, L=sum w lambda^2",
+            "forward_ms": fms, "backward_ms": bms, "bwd_over_fwd": bms / fms,
+            "backward_workspace_bytes": bws.nbytes, "forward_workspace_bytes": fws.nbytes,
+            "rows": int(off[-1]), "grad_rel_err_vs_dense_eigh_n256": worst, "leaf": leaf}
 
 
 def load_traffic(kernel: str):
@@ -408,6 +534,8 @@ def main():
     ap.add_argument("--ref-sample", type=int, default=96,
                     help="eigenvalue indices per family per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (config 3) and backward (config 4) measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
