@@ -165,7 +165,8 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
  * out[0] secular pole sweeps x K summed over roots (pair-evaluations),
  * out[1] secular sweeps, out[2] Lowner pairs, out[3] boundary-row pairs,
  * out[4] roots solved, out[5] deflated eigenvalues, out[6] close-pole rotations,
- * out[7] leaf plane rotations.  n <= 16 entries are copied.  The counters are
+ * out[7] leaf plane rotations, out[8] merges whose rotated deflated eigenvalues
+ * needed sorting, out[9] entries sorted.  n <= 16 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 

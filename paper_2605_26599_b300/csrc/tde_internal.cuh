@@ -73,6 +73,8 @@ enum WorkCounter {
   kWorkDeflated,          // eigenvalues deflated (small z or rotation)
   kWorkRotations,         // close-pole rotations
   kWorkLeafRotations,     // plane rotations in the leaf QR sweeps
+  kWorkSorts,             // merges whose rotated deflated list needed a sort
+  kWorkSortedEntries,     // entries in those sorts
   kNumWork
 };
 

@@ -125,20 +125,24 @@ __device__ __forceinline__ T4 t4_shfl_up(const T4& v, int o) {
   return T4{shfl_up_d(v.w, o), shfl_up_d(v.dw, o), shfl_up_d(v.ulo, o), shfl_up_d(v.uhi, o)};
 }
 
-// Run boundaries of the survivor list (one warp).  The sequential rule -- walk the
-// survivors in ascending order and let each one join the current run if the test
-// passes -- is evaluated 32 survivors at a time: every lane first assumes the
+// Run boundaries of survivors [begin, end) (one warp).  The sequential rule -- walk
+// the survivors in ascending order and let each one join the current run if the
+// test passes -- is evaluated 32 survivors at a time: every lane first assumes the
 // run of its predecessor is that predecessor alone, the assumed runs are summed
 // with a segmented scan, the test is re-evaluated against them, and the first
 // lane whose decision changes is fixed; lanes before it are already exact.
+// (cW, cDW) carries the (W, DW) of the run open at `begin` (`have` = one is open)
+// and returns the one open at the end.  With `stop_when_equal`, a chunk whose
+// decisions equal those already in rflag and which contains a run start ends the
+// walk early (returns false): from that start on the old decisions are exact.
 // RFLAG[k] = 1 iff survivor k starts a run.
-__device__ void run_boundaries(int S, const int32_t* surv, const double* D, const double* Z,
-                               double tol2, uint8_t* rflag) {
+__device__ bool run_segment(int begin, int end, const int32_t* surv, const double* D,
+                            const double* Z, double tol2, uint8_t* rflag, double& cW,
+                            double& cDW, bool have, bool stop_when_equal) {
   const int lane = threadIdx.x & 31;
-  double cW = 0.0, cDW = 0.0;
-  for (int base = 0; base < S; base += 32) {
+  for (int base = begin; base < end; base += 32) {
     const int k = base + lane;
-    const bool valid = k < S;
+    const bool valid = k < end;
     double Dk = 0.0, wk = 0.0;
     if (valid) {
       int pos = surv[k];
@@ -149,7 +153,7 @@ __device__ void run_boundaries(int S, const int32_t* surv, const double* D, cons
     const double Dp = shfl_up_d(Dk, 1), wp = shfl_up_d(wk, 1);
     bool guess;
     if (lane == 0)
-      guess = valid && base > 0 && continues_run(cW, cDW, Dk, wk, tol2);
+      guess = valid && have && continues_run(cW, cDW, Dk, wk, tol2);
     else
       guess = valid && continues_run(wp, Dp * wp, Dk, wk, tol2);
     int start = 0;
@@ -183,10 +187,70 @@ __device__ void run_boundaries(int S, const int32_t* surv, const double* D, cons
       if (lane == f) guess = truth;
       start = f + 1;
     }
-    if (valid) rflag[k] = guess ? 0 : 1;
-    int last = min(31, S - 1 - base);
+    const uint8_t flag = guess ? 0 : 1;
+    bool same = true;
+    if (stop_when_equal && valid) same = rflag[k] == flag;
+    const bool all_same = __all_sync(0xffffffffu, same);
+    const bool any_start = __any_sync(0xffffffffu, valid && flag == 1);
+    if (valid) rflag[k] = flag;
+    int last = min(31, end - 1 - base);
     cW = __shfl_sync(0xffffffffu, W, last);
     cDW = __shfl_sync(0xffffffffu, DWv, last);
+    have = true;
+    if (stop_when_equal && all_same && any_start) return false;
+  }
+  return true;
+}
+
+// Run boundaries of all S survivors by the warps of the block.  Long lists are cut
+// into one segment per warp; each warp walks its segment assuming the segment's
+// first survivor is tested against its predecessor alone, then warp 0 re-walks the
+// segments in order with the true carry until the decisions agree again.
+template <int NT>
+__device__ void run_boundaries(int S, const int32_t* surv, const double* D, const double* Z,
+                               double tol2, uint8_t* rflag, double* s_cw, double* s_cdw) {
+  constexpr int NW = NT / 32;
+  const int warp = threadIdx.x >> 5;
+  if (S < 64 * NW) {
+    if (warp == 0) {
+      double cW = 0.0, cDW = 0.0;
+      run_segment(0, S, surv, D, Z, tol2, rflag, cW, cDW, false, false);
+    }
+    return;
+  }
+  const int seg = ((S + NW - 1) / NW + 31) & ~31;
+  {
+    const int b = warp * seg, e = min(S, b + seg);
+    double cW = 0.0, cDW = 0.0;
+    bool have = false;
+    if (b < e) {
+      if (b > 0) {  // speculative carry: the predecessor alone
+        const int pos = surv[b - 1];
+        const double z = Z[pos];
+        cW = z * z;
+        cDW = D[pos] * cW;
+        have = true;
+      }
+      run_segment(b, e, surv, D, Z, tol2, rflag, cW, cDW, have, false);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      s_cw[warp] = cW;
+      s_cdw[warp] = cDW;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < NW; ++w) {
+      const int b = w * seg, e = min(S, b + seg);
+      if (b >= e) break;
+      double cW = s_cw[w - 1], cDW = s_cdw[w - 1];
+      const bool completed = run_segment(b, e, surv, D, Z, tol2, rflag, cW, cDW, true, true);
+      if (completed && (threadIdx.x & 31) == 0) {
+        s_cw[w] = cW;
+        s_cdw[w] = cDW;
+      }
+      __syncwarp();
+    }
   }
 }
 
@@ -332,8 +396,9 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
     }
     __syncthreads();
 
-    // 3. close poles: run boundaries over the survivors (warp 0)
-    if (warp == 0) run_boundaries(S, SURV, a.D, a.Z, tol2, RFLAG);
+    // 3. close poles: run boundaries over the survivors
+    __shared__ double s_cw[kNT / 32], s_cdw[kNT / 32];
+    run_boundaries<kNT>(S, SURV, a.D, a.Z, tol2, RFLAG, s_cw, s_cdw);
     __syncthreads();
 
     // 4. emit: continuing survivors deflate in place, run ends become active poles
@@ -467,6 +532,10 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       if (D[RPOS[k]] > D[RPOS[k + 1]]) s_flag = 1;
     __syncthreads();
     if (s_flag) {
+      if (tid == 0) {
+        atomicAdd(&a.st->work[kWorkSorts], 1ull);
+        atomicAdd(&a.st->work[kWorkSortedEntries], (unsigned long long)FR);
+      }
       for (int k = tid; k < FR; k += kNT) a.KEYA[lo + k] = order_key(D[RPOS[k]]);
       __syncthreads();
       const int which = block_sort(FR, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);

@@ -244,51 +244,53 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // the 32 lanes of a warp stride over the poles (left and right ranges separately)
+// Sum of z_i^2 / Delta_i and (z_i / Delta_i)^2 over i = b + lane, b + lane + 32, ...
+// below e, four independent chains per lane.
+__device__ __forceinline__ void lane_sums(const double* __restrict__ D, const double* __restrict__ Z,
+                                          int b, int e, int lane, double dorg, double tau,
+                                          double& sum, double& dsum) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+  int i = b + lane;
+  for (; i + 96 < e; i += 128) {
+    const double z0 = Z[i], z1 = Z[i + 32], z2 = Z[i + 64], z3 = Z[i + 96];
+    const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+    const double t1 = z1 * rcp_refined((D[i + 32] - dorg) - tau);
+    const double t2 = z2 * rcp_refined((D[i + 64] - dorg) - tau);
+    const double t3 = z3 * rcp_refined((D[i + 96] - dorg) - tau);
+    a0 = fma(z0, t0, a0);
+    d0 = fma(t0, t0, d0);
+    a1 = fma(z1, t1, a1);
+    d1 = fma(t1, t1, d1);
+    a2 = fma(z2, t2, a2);
+    d2 = fma(t2, t2, d2);
+    a3 = fma(z3, t3, a3);
+    d3 = fma(t3, t3, d3);
+  }
+  for (; i < e; i += 32) {
+    const double z0 = Z[i];
+    const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+    a0 = fma(z0, t0, a0);
+    d0 = fma(t0, t0, d0);
+  }
+  sum = (a0 + a1) + (a2 + a3);
+  dsum = (d0 + d1) + (d2 + d3);
+}
+
+// the 32 lanes of a warp stride over the poles (left and right ranges separately)
 struct WarpSweep {
   const double* __restrict__ D;
   const double* __restrict__ Z;
   int K;
   int lane;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
-    double p0 = 0.0, dp0 = 0.0, p1 = 0.0, dp1 = 0.0;
-    int i = lane;
-    for (; i + 32 <= jl; i += 64) {
-      const double z0 = Z[i], z1 = Z[i + 32];
-      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
-      const double t1 = z1 * rcp_refined((D[i + 32] - dorg) - tau);
-      p0 = fma(z0, t0, p0);
-      dp0 = fma(t0, t0, dp0);
-      p1 = fma(z1, t1, p1);
-      dp1 = fma(t1, t1, dp1);
-    }
-    for (; i <= jl; i += 32) {
-      const double z0 = Z[i];
-      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
-      p0 = fma(z0, t0, p0);
-      dp0 = fma(t0, t0, dp0);
-    }
-    double f0 = 0.0, df0 = 0.0, f1 = 0.0, df1 = 0.0;
-    i = jl + 1 + lane;
-    for (; i + 32 < K; i += 64) {
-      const double z0 = Z[i], z1 = Z[i + 32];
-      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
-      const double t1 = z1 * rcp_refined((D[i + 32] - dorg) - tau);
-      f0 = fma(z0, t0, f0);
-      df0 = fma(t0, t0, df0);
-      f1 = fma(z1, t1, f1);
-      df1 = fma(t1, t1, df1);
-    }
-    for (; i < K; i += 32) {
-      const double z0 = Z[i];
-      const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
-      f0 = fma(z0, t0, f0);
-      df0 = fma(t0, t0, df0);
-    }
+    double p, dp, f, df;
+    lane_sums(D, Z, 0, jl + 1, lane, dorg, tau, p, dp);
+    lane_sums(D, Z, jl + 1, K, lane, dorg, tau, f, df);
     SecSums s;
-    s.psi = warp_sum(p0 + p1);
-    s.dpsi = warp_sum(dp0 + dp1);
-    s.phi = warp_sum(f0 + f1);
-    s.dphi = warp_sum(df0 + df1);
+    s.psi = warp_sum(p);
+    s.dpsi = warp_sum(dp);
+    s.phi = warp_sum(f);
+    s.dphi = warp_sum(df);
     return s;
   }
 };
@@ -342,7 +344,7 @@ __device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, in
   return a.ROOTMAP[r - nb];
 }
 
-__global__ void k_secular_warp(RootArgs a) {
+__global__ void __launch_bounds__(128, 8) k_secular_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
