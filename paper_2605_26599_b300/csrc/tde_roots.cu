@@ -295,6 +295,61 @@ struct WarpSweep {
   }
 };
 
+// G lanes (a power of two below 32, aligned) share one root: they stride over the
+// poles with the left / right split uniform inside the group and combine with
+// shuffles restricted to the group, so groups of one warp may diverge safely.
+template <int G>
+__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+template <int G>
+__device__ __forceinline__ void group_lane_sums(const double* __restrict__ D,
+                                                const double* __restrict__ Z, int b, int e, int gl,
+                                                double dorg, double tau, double& sum, double& dsum) {
+  double a0 = 0.0, a1 = 0.0, d0 = 0.0, d1 = 0.0;
+  int i = b + gl;
+  for (; i + G < e; i += 2 * G) {
+    const double z0 = Z[i], z1 = Z[i + G];
+    const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+    const double t1 = z1 * rcp_refined((D[i + G] - dorg) - tau);
+    a0 = fma(z0, t0, a0);
+    d0 = fma(t0, t0, d0);
+    a1 = fma(z1, t1, a1);
+    d1 = fma(t1, t1, d1);
+  }
+  for (; i < e; i += G) {
+    const double z0 = Z[i];
+    const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+    a0 = fma(z0, t0, a0);
+    d0 = fma(t0, t0, d0);
+  }
+  sum = a0 + a1;
+  dsum = d0 + d1;
+}
+
+template <int G>
+struct GroupSweep {
+  const double* __restrict__ D;
+  const double* __restrict__ Z;
+  int K;
+  int gl;
+  unsigned mask;
+  __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
+    double p, dp, f, df;
+    group_lane_sums<G>(D, Z, 0, jl + 1, gl, dorg, tau, p, dp);
+    group_lane_sums<G>(D, Z, jl + 1, K, gl, dorg, tau, f, df);
+    SecSums s;
+    s.psi = group_sum<G>(p, mask);
+    s.dpsi = group_sum<G>(dp, mask);
+    s.phi = group_sum<G>(f, mask);
+    s.dphi = group_sum<G>(df, mask);
+    return s;
+  }
+};
+
 __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, int org, double tau,
                                               int sweeps, int K, bool ok, bool leader) {
   if (leader) {
@@ -323,6 +378,37 @@ __global__ void k_secular_thread(RootArgs a) {
     work_add(a.st, kWorkSecularPairs, unsigned(sweeps) * unsigned(ms.K));
     work_add(a.st, kWorkSecularSweeps, unsigned(sweeps));
     work_add(a.st, kWorkRoots, 1u);
+  }
+}
+
+// small-K list, G lanes per root (the host picks G from the step's merge order)
+template <int G>
+__global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
+  const uint32_t total = *a.count;
+  if (total < a.small_list_min) return;  // the warp kernel takes a short list
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const unsigned mask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
+  const uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const uint32_t ngrp = (gridDim.x * blockDim.x) / G;
+  unsigned pairs = 0, sweeps_acc = 0, roots = 0;
+  for (uint32_t r = grp; r < total; r += ngrp) {
+    const int g = a.ROOTMAP[r];
+    const MState ms = a.ms[g];
+    const int j = int(r) - ms.base, lo = a.M[g].lo;
+    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, ms.K, gl, mask};
+    int org;
+    double tau;
+    bool ok;
+    const int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, &org, &tau, &ok);
+    secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, gl == 0);
+    pairs += unsigned(sweeps) * unsigned(ms.K);
+    sweeps_acc += unsigned(sweeps);
+    roots += 1;
+  }
+  if (gl == 0 && roots) {
+    atomicAdd(&a.st->work[kWorkSecularPairs], (unsigned long long)pairs);
+    atomicAdd(&a.st->work[kWorkSecularSweeps], (unsigned long long)sweeps_acc);
+    atomicAdd(&a.st->work[kWorkRoots], (unsigned long long)roots);
   }
 }
 
@@ -605,8 +691,17 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   const int64_t nrows = plan.nrows;
   const int tgrid = int(std::min<int64_t>((nrows + 127) / 128, 148 * 8));
   const int wgrid = 148 * 8;
+  // lanes per root for the small-K list, from the largest merge order of the step
+  const int64_t k0 = plan.step_maxsize[step];
+  const int G = k0 <= 24 ? 1 : (k0 <= 96 ? 4 : (k0 <= 384 ? 8 : 16));
+  const int ggrid = int(std::min<int64_t>((nrows * G + 127) / 128, 148 * 16));
   prof_begin(kKSecular, s);
-  k_secular_thread<<<tgrid, 128, 0, s>>>(ra);
+  switch (G) {
+    case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
+    case 4: k_secular_group<4><<<ggrid, 128, 0, s>>>(ra); break;
+    case 8: k_secular_group<8><<<ggrid, 128, 0, s>>>(ra); break;
+    default: k_secular_group<16><<<ggrid, 128, 0, s>>>(ra); break;
+  }
   k_secular_warp<<<wgrid, 128, 0, s>>>(ra);
   prof_end(kKSecular, s);
   int launches = 2;
