@@ -162,11 +162,12 @@ int tde_profile_collect(int nids, double* ms, int64_t* launches);
 int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launches);
 
 /* Copies the workspace's device work counters (synchronises `stream`):
- * out[0] secular pole sweeps x K summed over roots (pair-evaluations),
- * out[1] secular sweeps, out[2] Lowner pairs, out[3] boundary-row pairs,
+ * out[0] FP64 secular pole sweeps x K summed over roots (pair-evaluations),
+ * out[1] FP64 secular sweeps, out[2] Lowner pairs, out[3] boundary-row pairs,
  * out[4] roots solved, out[5] deflated eigenvalues, out[6] close-pole rotations,
  * out[7] leaf plane rotations, out[8] merges whose rotated deflated eigenvalues
- * needed sorting, out[9] entries sorted.  n <= 16 entries are copied.  The counters are
+ * needed sorting, out[9] entries sorted, out[10] single-precision secular pole
+ * sweeps x K, out[11] single-precision secular sweeps.  n <= 16 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 

@@ -30,7 +30,8 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
 
 KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner", "rows", "place")
 WORK_NAMES = ("secular_pairs", "secular_sweeps", "lowner_pairs", "rows_pairs", "roots", "deflated",
-              "rotations", "leaf_rotations", "sorts", "sorted_entries")
+              "rotations", "leaf_rotations", "sorts", "sorted_entries", "secular32_pairs",
+              "secular32_sweeps")
 
 
 class TdeError(RuntimeError):

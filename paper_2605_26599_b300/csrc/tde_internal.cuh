@@ -75,6 +75,8 @@ enum WorkCounter {
   kWorkLeafRotations,     // plane rotations in the leaf QR sweeps
   kWorkSorts,             // merges whose rotated deflated list needed a sort
   kWorkSortedEntries,     // entries in those sorts
+  kWorkSecular32Pairs,    // sum over roots of K x (number of single-precision pole sweeps)
+  kWorkSecular32Sweeps,   // sum over roots of the number of single-precision pole sweeps
   kNumWork
 };
 

@@ -572,7 +572,20 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       a.OUTIDX[lo + pos] = K + k + l;
     }
     __syncthreads();
-    // 7. roots of this merge get a contiguous range of one of the step's two root
+    // 8. single-precision copies of the active poles for the first stage of the
+    //    secular solver: D_i as an unevaluated float pair hi + lo (about 48 bits)
+    //    and z_i rounded to float.  KEYB / IDXB held the sort scratch until here.
+    {
+      float2* AD32 = reinterpret_cast<float2*>(a.KEYB) + lo;
+      float* AZ32 = reinterpret_cast<float*>(a.IDXB) + lo;
+      for (int k = tid; k < K; k += kNT) {
+        const double x = a.AD[lo + k];
+        const float hi = __double2float_rn(x);
+        AD32[k] = make_float2(hi, __double2float_rn(x - double(hi)));
+        AZ32[k] = __double2float_rn(a.AZ[lo + k]);
+      }
+    }
+    // 9. roots of this merge get a contiguous range of one of the step's two root
     //    lists: merges with K >= warp_min_k are solved one warp per root
     __shared__ int s_base;
     const bool big = K >= a.warp_min_k;

@@ -29,6 +29,8 @@ struct RootArgs {
   const uint32_t* count;    // lengths of the two lists (device)
   const uint32_t* count2;
   const double *AD, *AZ, *ALO, *AHI;
+  const float2* AD32;  // alias KEYB: active D as an unevaluated float pair (hi, lo)
+  const float* AZ32;   // alias IDXB: active z rounded to float
   double* TAU;
   int32_t* ORG;
   double* LAMA;           // aliases D: lambda_j of the active roots
@@ -48,20 +50,45 @@ struct RootArgs {
 // Delta_i = (D_i - D_org) - tau the two poles that bracket the root keep full
 // relative accuracy.
 //
-// Iteration: evaluate w and its derivative split into the poles left of the root
-// (psi: i <= jl) and right of it (phi: i > jl), then take the root of the two-pole
-// rational model C + S1 / (Delta_jl - eta) + S2 / (Delta_jr - eta) that matches w
-// and w', kept inside a bisection bracket.  The weights start as
-// S1 = Delta_jl^2 psi', S2 = Delta_jr^2 phi' (each side's derivative attributed to
-// its nearest pole); if a step fails to shrink |w| tenfold, the origin pole gets
-// its exact residue z_org^2 and the other pole the rest of w' from then on --
-// this rescues roots pressed against a pole with a tiny z, for which the first
-// weights overstate that pole's residue.  The start is the midpoint of the interval, whose sign of w also
-// chooses the origin (the nearer pole).  Convergence: |w| below eps times a
-// running bound on the rounding error of its evaluation,
-// 8 (|psi| + |phi|) + 1/rho' + |tau| (psi' + phi').
+// Each iteration evaluates w and its derivatives and takes the root of a rational
+// model C + S1 / (Delta_jl - eta) + S2 / (Delta_jr - eta) of w around the current
+// point, kept inside a bisection bracket:
+//   * third-order model: S1, S2 and C fitted to w, w' and w''/2 = sum z^2/Delta^3
+//     (the fitted weights are nonnegative in exact arithmetic for every root but
+//     the last);
+//   * two-term model: S1 = Delta_jl^2 psi', S2 = Delta_jr^2 phi' with psi / phi the
+//     poles left (i <= jl) and right of the root (each side's derivative attributed
+//     to its nearest pole); if a step fails to shrink |w| tenfold, the origin pole
+//     gets its exact residue z_org^2 and the other pole the rest of w' from then on
+//     -- this rescues roots pressed against a pole with a tiny z.
+//
+// Two precisions.  On this part an FP64 instruction costs about forty times the
+// issue slots of an FP32 one, so every root starts with a single-precision stage:
+// pole offsets from an unevaluated float pair per pole (D_i = hi + lo, about 48
+// bits, so D_i - D_org keeps its relative accuracy), hardware reciprocal
+// approximations and a compensated sum for w.  It starts at the midpoint of the
+// interval (whose sign of w chooses the origin, the nearer pole), iterates the
+// third-order model until the step is below 2^-10 |tau| and ends with one sweep at
+// the final tau, which also supplies w'' there.  The FP64 stage starts from that
+// tau with the whole interval as bracket; each FP64 sweep gives w and w' to full
+// accuracy, w'' comes from a single-precision sweep at the same point (its error
+// enters the step at second order), and a third-order step below 2^-18 |tau| is
+// accepted without another sweep (the error it leaves is of order
+// (2^-18)^3 |tau|), a two-term step below 2^-27 |tau| likewise (order
+// (2^-27)^2 |tau|).  Anything non-finite or a negative fitted weight sends a step
+// to the two-term model.  A root whose interval is narrower than 2^-28 of the
+// pole magnitude (where the float pair cannot resolve the offsets), or whose
+// single-precision stage fails, starts in FP64 at the midpoint and iterates with
+// the two-term model only.  Convergence: |w| below eps times a running bound on the
+// rounding error of its evaluation, 8 (|psi| + |phi|) + 1/rho' + |tau| (psi' + phi').
 struct SecSums {
   double psi, dpsi, phi, dphi;
+};
+
+// single-precision sums: psi, phi (compensated), their derivatives, and
+// hw = sum z^2 / Delta^3 over all poles
+struct Sec32 {
+  float psi, dpsi, phi, dphi, hw;
 };
 
 struct SecState {
@@ -71,7 +98,8 @@ struct SecState {
   SecSums s;
 };
 
-// first sweep point and the bracket; `sweep(dorg, tau, jl)` evaluates the sums
+// FP64 start: midpoint sweep and the half-interval bracket; `sweep(dorg, tau, jl)`
+// evaluates the sums
 template <class Sweep>
 __device__ __forceinline__ void sec_init(const double* D, const double* Z, int K, int j, double rho,
                                          double zsq, Sweep& sweep, SecState& q) {
@@ -117,11 +145,60 @@ __device__ __forceinline__ void sec_init(const double* D, const double* Z, int K
   q.wprev = 0.0;
 }
 
-// One iteration.  Returns 1 if tau moved and needs a new sweep, 0 if converged.
-// A model step below 2^-27 |tau| (about sqrt(eps)) is taken and accepted without
-// another sweep: the iteration converges at least quadratically, so the error
-// left after such a step is of order eps |tau|.
-__device__ __forceinline__ int sec_step(SecState& q) {
+// Weights of the third-order model at poles a = Delta_jl, b = Delta_jr from
+// w' = dw and w''/2 = hw, as P1 = S1 / a^2 = a (hw b - dw) / (b - a) and
+// P2 = S2 / b^2 = b (dw - hw a) / (b - a).  False if either is negative or not
+// finite.  T is double (FP64 stage) or float (single-precision stage).
+__device__ __forceinline__ double fast_rcp(double x) { return rcp_refined(x); }
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+
+template <class T>
+__device__ __forceinline__ bool fit3(T a, T b, T dw, T hw, T* P1, T* P2) {
+  const T inv = fast_rcp(b - a);
+  const T p1 = a * (hw * b - dw) * inv;
+  const T p2 = b * (dw - hw * a) * inv;
+  if (!(p1 >= T(0) && p2 >= T(0) && isfinite(p1 + p2))) return false;
+  *P1 = p1;
+  *P2 = p2;
+  return true;
+}
+
+// Root eta of the model w(tau + eta) ~ C + S1 / (a - eta) + S2 / (b - eta) with
+// S1 = P1 a^2, S2 = P2 b^2 and value w at eta = 0, such that tau + eta lies in
+// (tlo, thi); the smaller one if both roots do.  False if neither does (or on
+// non-finite values).  Reciprocals need no correct rounding here: a step is an
+// approximation whose own error is relative to its size.
+template <class T>
+__device__ __forceinline__ bool model_root(T w, T a, T b, T P1, T P2, T tau, T tlo, T thi, T* eta) {
+  const T C = w - P1 * a - P2 * b;
+  const T A = C * (a + b) + P1 * a * a + P2 * b * b;
+  const T Bq = a * b * w;
+  if (C == T(0)) {
+    if (A == T(0)) return false;
+    *eta = Bq * fast_rcp(A);
+    return true;
+  }
+  const T disc = A * A - T(4) * Bq * C;
+  const T sq = sqrt(disc > T(0) ? disc : T(0));
+  const T qq = T(0.5) * (A >= T(0) ? A + sq : A - sq);
+  const T r1 = qq * fast_rcp(C);
+  const T r2 = (qq != T(0)) ? Bq * fast_rcp(qq) : r1;
+  const bool ok1 = (tau + r1 > tlo) && (tau + r1 < thi);
+  const bool ok2 = (tau + r2 > tlo) && (tau + r2 < thi);
+  if (ok1 && ok2) {
+    *eta = fabs(r1) < fabs(r2) ? r1 : r2;
+    return true;
+  }
+  if (ok1 || ok2) {
+    *eta = ok1 ? r1 : r2;
+    return true;
+  }
+  return false;
+}
+
+// One FP64 iteration; hw = w''/2 at tau when `third`.  Returns 1 if tau moved and
+// needs a new sweep, 0 if converged.
+__device__ __forceinline__ int sec_step(SecState& q, double hw, bool third) {
   const double erretm =
       8.0 * (fabs(q.s.psi) + fabs(q.s.phi)) + q.rhoinv + fabs(q.tau) * (q.s.dpsi + q.s.dphi);
   if (fabs(q.w) <= kEps * erretm) return 0;
@@ -133,78 +210,157 @@ __device__ __forceinline__ int sec_step(SecState& q) {
   const double a = q.ol - q.tau, b = q.orr - q.tau;  // Delta of the two model poles
   if (q.wprev != 0.0 && fabs(q.w) > 0.1 * fabs(q.wprev)) q.exact = true;
   q.wprev = q.w;
-  double S1 = a * a * q.s.dpsi, S2 = b * b * q.s.dphi;
-  if (q.exact) {
-    const double dw = q.s.dpsi + q.s.dphi;
-    double e1, e2;
-    if (q.org == q.jl) {
-      e1 = q.zorg2;
-      e2 = b * b * (dw - e1 / (a * a));
-    } else {
-      e2 = q.zorg2;
-      e1 = a * a * (dw - e2 / (b * b));
-    }
-    if (e1 >= 0.0 && e2 >= 0.0) {
-      S1 = e1;
-      S2 = e2;
+  double P1, P2;
+  const bool cubic = third && fit3(a, b, q.s.dpsi + q.s.dphi, hw, &P1, &P2);
+  if (!cubic) {
+    P1 = q.s.dpsi;
+    P2 = q.s.dphi;
+    if (q.exact) {
+      const double dw = q.s.dpsi + q.s.dphi;
+      const double e = (q.org == q.jl) ? q.zorg2 * fast_rcp(a * a) : q.zorg2 * fast_rcp(b * b);
+      if (e <= dw) {
+        P1 = (q.org == q.jl) ? e : dw - e;
+        P2 = dw - P1;
+      }
     }
   }
-  const double C = q.w - S1 / a - S2 / b;
-  const double A = C * (a + b) + S1 + S2;
-  const double Bq = a * b * q.w;
   double eta = 0.0;
-  bool have = false;
-  if (C == 0.0) {
-    if (A != 0.0) {
-      eta = Bq / A;
-      have = true;
-    }
-  } else {
-    const double sq = sqrt(fmax(A * A - 4.0 * Bq * C, 0.0));
-    const double qq = 0.5 * (A >= 0.0 ? A + sq : A - sq);
-    const double r1 = qq / C;
-    const double r2 = (qq != 0.0) ? Bq / qq : r1;
-    const bool ok1 = (q.tau + r1 > q.tlo) && (q.tau + r1 < q.thi);
-    const bool ok2 = (q.tau + r2 > q.tlo) && (q.tau + r2 < q.thi);
-    if (ok1 && ok2) {
-      eta = fabs(r1) < fabs(r2) ? r1 : r2;
-      have = true;
-    } else if (ok1) {
-      eta = r1;
-      have = true;
-    } else if (ok2) {
-      eta = r2;
-      have = true;
-    }
-  }
+  const bool have = model_root(q.w, a, b, P1, P2, q.tau, q.tlo, q.thi, &eta);
   double ntau = q.tau + eta;
   const bool model = have && ntau > q.tlo && ntau < q.thi;
   if (!model) ntau = 0.5 * (q.tlo + q.thi);
   if (ntau == q.tau) return 0;
   q.tau = ntau;
-  if (model && fabs(eta) <= 0x1p-27 * fabs(ntau)) return 0;
+  if (model && fabs(eta) <= (cubic ? 0x1p-18 : 0x1p-27) * fabs(ntau)) return 0;
   return 1;
 }
 
 constexpr int kMaxSweeps = 64;
+constexpr int kMaxSweeps32 = 6;
 
-// Solves root j; returns the number of pole sweeps, *ok = false if capped.
-template <class Sweep>
+// Single-precision stage for root j, all of it in float.  On success fills q for
+// the FP64 stage (origin, tau, the whole interval as bracket) and *hw with w''/2
+// at tau, and returns true; *n32 receives the single-precision sweeps spent
+// either way.  It is skipped (false) where the float pair cannot resolve the
+// interval: width below 2^-28 of the pole magnitude.  `sw32(org, jl, tau)`
+// evaluates the sums.
+template <class Sweep32>
+__device__ __forceinline__ bool sec_stage32(const double* D, const double* Z, int K, int j, double rho,
+                                            double zsq, Sweep32& sw32, SecState& q, double* hw,
+                                            int* n32) {
+  *n32 = 0;
+  const int jl = (j < K - 1) ? j : K - 2, jr = jl + 1;
+  const double Dl = D[jl], Dr = D[jr];
+  const double width = (j < K - 1) ? Dr - Dl : rho * zsq;
+  if (!(width >= 0x1p-28 * fmax(fabs(Dl), fabs(Dr)))) return false;
+  const float rhoinv = float(1.0 / rho);
+  int org;
+  float tau, tlo, thi, lo_int, hi_int;  // stage bracket; interval of the root (tau of org)
+  Sec32 s;
+  if (j < K - 1) {
+    const float gap = float(width);
+    const float h32 = 0.5f * gap;
+    s = sw32(j, jl, h32);
+    if (rhoinv + s.psi + s.phi >= 0.0f) {
+      org = j;
+      tau = h32;
+      tlo = 0.0f;
+      thi = h32;
+      lo_int = 0.0f;
+      hi_int = gap;
+    } else {
+      org = j + 1;
+      tau = h32 - gap;
+      tlo = tau;
+      thi = 0.0f;
+      lo_int = -gap;
+      hi_int = 0.0f;
+    }
+  } else {
+    org = K - 1;
+    hi_int = float(width);
+    lo_int = 0.0f;
+    tau = 0.5f * hi_int;
+    s = sw32(org, jl, tau);
+    tlo = 0.0f;
+    thi = hi_int;
+  }
+  int sweeps = 1;
+  const double dorg = D[org];
+  const float ol = float(Dl - dorg), orr = float(Dr - dorg);
+  for (;;) {
+    const float w = rhoinv + s.psi + s.phi;
+    if (!isfinite(w)) break;
+    if (w > 0.0f)
+      thi = fminf(thi, tau);
+    else
+      tlo = fmaxf(tlo, tau);
+    const float a = ol - tau, b = orr - tau;
+    float P1, P2;
+    if (!fit3(a, b, s.dpsi + s.dphi, s.hw, &P1, &P2)) {
+      P1 = s.dpsi;
+      P2 = s.dphi;
+    }
+    float eta = 0.0f;
+    const bool have = model_root(w, a, b, P1, P2, tau, tlo, thi, &eta);
+    const float nt = have ? tau + eta : 0.5f * (tlo + thi);
+    if (nt == tau || !(nt > lo_int && nt < hi_int)) break;  // no move: s is at tau
+    tau = nt;
+    s = sw32(org, jl, tau);
+    ++sweeps;
+    if ((have && fabsf(eta) <= 0x1p-10f * fabsf(nt)) || sweeps >= kMaxSweeps32) break;
+  }
+  *n32 = sweeps;
+  if (!(isfinite(rhoinv + s.psi + s.phi) && isfinite(s.hw) && tau > lo_int && tau < hi_int))
+    return false;
+  q.org = org;
+  q.jl = jl;
+  q.jr = jr;
+  q.tau = double(tau);
+  q.tlo = double(lo_int);
+  q.thi = double(hi_int);
+  q.rhoinv = 1.0 / rho;
+  q.dorg = dorg;
+  q.zorg2 = Z[org] * Z[org];
+  q.ol = Dl - dorg;
+  q.orr = Dr - dorg;
+  q.exact = false;
+  q.wprev = 0.0;
+  *hw = double(s.hw);
+  return true;
+}
+
+// Solves root j; returns the number of FP64 pole sweeps (*n32 the single-precision
+// ones), *ok = false if capped.
+template <class Sweep, class Sweep32>
 __device__ int secular_root(const double* D, const double* Z, int K, int j, double rho, double zsq,
-                            Sweep& sweep, int* org_out, double* tau_out, bool* ok) {
+                            Sweep& sweep, Sweep32& sw32, int* org_out, double* tau_out, bool* ok,
+                            int* n32) {
   *ok = true;
+  *n32 = 0;
   if (K == 1) {
     *org_out = 0;
     *tau_out = rho * Z[0] * Z[0];
     return 0;
   }
   SecState q;
-  sec_init(D, Z, K, j, rho, zsq, sweep, q);
+  double hw = 0.0;
+  const bool third = sec_stage32(D, Z, K, j, rho, zsq, sw32, q, &hw, n32);
+  if (third) {
+    q.s = sweep(q.dorg, q.tau, q.jl);
+    q.w = q.rhoinv + q.s.psi + q.s.phi;
+  } else {
+    sec_init(D, Z, K, j, rho, zsq, sweep, q);
+  }
   int sweeps = 1;
-  while (sec_step(q) == 1) {
+  while (sec_step(q, hw, third) == 1) {
     if (sweeps >= kMaxSweeps) {
       *ok = false;
       break;
+    }
+    if (third) {
+      hw = double(sw32(q.org, q.jl, float(q.tau)).hw);
+      ++*n32;
     }
     q.s = sweep(q.dorg, q.tau, q.jl);
     q.w = q.rhoinv + q.s.psi + q.s.phi;
@@ -276,7 +432,6 @@ __device__ __forceinline__ void lane_sums(const double* __restrict__ D, const do
   dsum = (d0 + d1) + (d2 + d3);
 }
 
-// the 32 lanes of a warp stride over the poles (left and right ranges separately)
 struct WarpSweep {
   const double* __restrict__ D;
   const double* __restrict__ Z;
@@ -298,8 +453,8 @@ struct WarpSweep {
 // G lanes (a power of two below 32, aligned) share one root: they stride over the
 // poles with the left / right split uniform inside the group and combine with
 // shuffles restricted to the group, so groups of one warp may diverge safely.
-template <int G>
-__device__ __forceinline__ double group_sum(double v, unsigned mask) {
+template <int G, class T>
+__device__ __forceinline__ T group_sum(T v, unsigned mask) {
 #pragma unroll
   for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
   return v;
@@ -350,6 +505,78 @@ struct GroupSweep {
   }
 };
 
+// ---- single-precision sweeps -------------------------------------------------
+__device__ __forceinline__ float rcp_approx32(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Terms of poles b + l0, b + l0 + st, ... below e at offset tau from the origin
+// pole ho, in single precision: w = sum z^2/Delta (compensated: c carries the
+// negated low part lost so far), dw = sum z^2/Delta^2, hw = sum z^2/Delta^3.
+// Delta = ((hi_i - hi_o) + (lo_i - lo_o)) - tau: the hi difference is exact for
+// nearby poles, so the offset keeps about 24 bits relative to its own size.
+__device__ __forceinline__ void range32(const float2* __restrict__ H, const float* __restrict__ Z,
+                                        int b, int e, int l0, int st, float2 ho, float tau,
+                                        float& w, float& dw, float& hw) {
+  float s = 0.f, c = 0.f, d = 0.f, h = 0.f;
+  for (int i = b + l0; i < e; i += st) {
+    const float2 p = H[i];
+    const float z = Z[i];
+    const float del = ((p.x - ho.x) + (p.y - ho.y)) - tau;
+    const float r = rcp_approx32(del);
+    const float t = z * r;
+    const float y = fmaf(z, t, -c);
+    const float ns = s + y;
+    c = (ns - s) - y;
+    s = ns;
+    d = fmaf(t, t, d);
+    h = fmaf(t, t * r, h);
+  }
+  w = s - c;
+  dw = d;
+  hw = h;
+}
+
+struct ThreadSweep32 {
+  const float2* __restrict__ H;
+  const float* __restrict__ Z;
+  int K;
+  __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau) const {
+    const float2 ho = H[org];
+    Sec32 s;
+    float hl, hr;
+    range32(H, Z, 0, jl + 1, 0, 1, ho, tau, s.psi, s.dpsi, hl);
+    range32(H, Z, jl + 1, K, 0, 1, ho, tau, s.phi, s.dphi, hr);
+    s.hw = hl + hr;
+    return s;
+  }
+};
+
+template <int G>
+struct GroupSweep32 {
+  const float2* __restrict__ H;
+  const float* __restrict__ Z;
+  int K;
+  int gl;
+  unsigned mask;
+  __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau) const {
+    const float2 ho = H[org];
+    float p, dp, hl, f, df, hr;
+    range32(H, Z, 0, jl + 1, gl, G, ho, tau, p, dp, hl);
+    range32(H, Z, jl + 1, K, gl, G, ho, tau, f, df, hr);
+    Sec32 s;
+    s.psi = group_sum<G>(p, mask);
+    s.dpsi = group_sum<G>(dp, mask);
+    s.phi = group_sum<G>(f, mask);
+    s.dphi = group_sum<G>(df, mask);
+    s.hw = group_sum<G>(hl + hr, mask);
+    return s;
+  }
+};
+
+// ---- kernels ------------------------------------------------------------------
 __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, int org, double tau,
                                               int sweeps, int K, bool ok, bool leader) {
   if (leader) {
@@ -362,23 +589,45 @@ __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, 
   }
 }
 
+// per-thread tallies of the device work counters, flushed once per thread
+struct SecTally {
+  unsigned pairs = 0, sweeps = 0, pairs32 = 0, sweeps32 = 0, roots = 0;
+  __device__ __forceinline__ void add(int n64, int n32, int K) {
+    pairs += unsigned(n64) * unsigned(K);
+    sweeps += unsigned(n64);
+    pairs32 += unsigned(n32) * unsigned(K);
+    sweeps32 += unsigned(n32);
+    roots += 1;
+  }
+  __device__ __forceinline__ void flush(Status* st) const {
+    if (!roots) return;
+    atomicAdd(&st->work[kWorkSecularPairs], (unsigned long long)pairs);
+    atomicAdd(&st->work[kWorkSecularSweeps], (unsigned long long)sweeps);
+    atomicAdd(&st->work[kWorkSecular32Pairs], (unsigned long long)pairs32);
+    atomicAdd(&st->work[kWorkSecular32Sweeps], (unsigned long long)sweeps32);
+    atomicAdd(&st->work[kWorkRoots], (unsigned long long)roots);
+  }
+};
+
 __global__ void k_secular_thread(RootArgs a) {
   const uint32_t total = *a.count;
   if (total < a.small_list_min) return;  // the warp kernel takes a short list
+  SecTally tally;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
     const int g = a.ROOTMAP[r];
     const MState ms = a.ms[g];
     const int j = int(r) - ms.base, lo = a.M[g].lo;
     ThreadSweep sw{a.AD + lo, a.AZ + lo, ms.K};
-    int org;
+    ThreadSweep32 sw32{a.AD32 + lo, a.AZ32 + lo, ms.K};
+    int org, n32;
     double tau;
     bool ok;
-    const int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, &org, &tau, &ok);
+    const int sweeps =
+        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok, &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, true);
-    work_add(a.st, kWorkSecularPairs, unsigned(sweeps) * unsigned(ms.K));
-    work_add(a.st, kWorkSecularSweeps, unsigned(sweeps));
-    work_add(a.st, kWorkRoots, 1u);
+    tally.add(sweeps, n32, ms.K);
   }
+  tally.flush(a.st);
 }
 
 // small-K list, G lanes per root (the host picks G from the step's merge order)
@@ -390,26 +639,22 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
   const unsigned mask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
   const uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const uint32_t ngrp = (gridDim.x * blockDim.x) / G;
-  unsigned pairs = 0, sweeps_acc = 0, roots = 0;
+  SecTally tally;
   for (uint32_t r = grp; r < total; r += ngrp) {
     const int g = a.ROOTMAP[r];
     const MState ms = a.ms[g];
     const int j = int(r) - ms.base, lo = a.M[g].lo;
     GroupSweep<G> sw{a.AD + lo, a.AZ + lo, ms.K, gl, mask};
-    int org;
+    GroupSweep32<G> sw32{a.AD32 + lo, a.AZ32 + lo, ms.K, gl, mask};
+    int org, n32;
     double tau;
     bool ok;
-    const int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, &org, &tau, &ok);
+    const int sweeps =
+        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok, &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, gl == 0);
-    pairs += unsigned(sweeps) * unsigned(ms.K);
-    sweeps_acc += unsigned(sweeps);
-    roots += 1;
+    tally.add(sweeps, n32, ms.K);
   }
-  if (gl == 0 && roots) {
-    atomicAdd(&a.st->work[kWorkSecularPairs], (unsigned long long)pairs);
-    atomicAdd(&a.st->work[kWorkSecularSweeps], (unsigned long long)sweeps_acc);
-    atomicAdd(&a.st->work[kWorkRoots], (unsigned long long)roots);
-  }
+  if (gl == 0) tally.flush(a.st);
 }
 
 // Root r of the warp kernels' list: the large-K list, then the small-K list when
@@ -430,32 +675,28 @@ __device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, in
   return a.ROOTMAP[r - nb];
 }
 
-__global__ void __launch_bounds__(128, 8) k_secular_warp(RootArgs a) {
+__global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned pairs = 0, sweeps_acc = 0, roots = 0;
+  SecTally tally;
   for (uint32_t r = warp; r < total; r += nwarps) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
     const MState ms = a.ms[g];
     const int j = rl - ms.base, lo = a.M[g].lo;
     WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane};
-    int org;
+    GroupSweep32<32> sw32{a.AD32 + lo, a.AZ32 + lo, ms.K, lane, 0xffffffffu};
+    int org, n32;
     double tau;
     bool ok;
-    const int sweeps = secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, &org, &tau, &ok);
+    const int sweeps =
+        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok, &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
-    pairs += unsigned(sweeps) * unsigned(ms.K);
-    sweeps_acc += unsigned(sweeps);
-    roots += 1;
+    tally.add(sweeps, n32, ms.K);
   }
-  if (lane == 0 && roots) {
-    atomicAdd(&a.st->work[kWorkSecularPairs], (unsigned long long)pairs);
-    atomicAdd(&a.st->work[kWorkSecularSweeps], (unsigned long long)sweeps_acc);
-    atomicAdd(&a.st->work[kWorkRoots], (unsigned long long)roots);
-  }
+  if (lane == 0) tally.flush(a.st);
 }
 
 // ---------------------------------------------------------------------------
@@ -675,6 +916,8 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.AZ = ws.AZ;
   ra.ALO = ws.ALO;
   ra.AHI = ws.AHI;
+  ra.AD32 = reinterpret_cast<const float2*>(ws.KEYB);
+  ra.AZ32 = reinterpret_cast<const float*>(ws.IDXB);
   ra.TAU = ws.TAU;
   ra.ORG = ws.ORG;
   ra.LAMA = ws.D;
