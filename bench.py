@@ -164,9 +164,14 @@ def oracle_sample(n: int, per_family: int, fams) -> tuple[float, int]:
 
 
 def cpu_baseline(n: int, fams, target_s: float = 12.0) -> dict:
-    probe = 8
-    t, _ = oracle_sample(n, probe, fams)
-    per = int(max(probe, min(n, probe * target_s / max(t, 1e-3))))
+    # grow the probe until it is long enough to extrapolate from (at least one index
+    # per thread, about a second), then size the sample for target_s of oracle work
+    per = 64
+    t, _ = oracle_sample(n, per, fams)
+    while t < 1.0 and per < n:
+        per = min(n, per * 4)
+        t, _ = oracle_sample(n, per, fams)
+    per = int(min(n, max(per, per * target_s / max(t, 1e-3))))
     t, threads = oracle_sample(n, per, fams)
     nf = len(FAMILIES)
     return {"value": nf * per / t, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -292,7 +297,8 @@ def run_ours(args, rank: int, world: int, dist) -> None:
     value = job_value(ms, world, len(FAMILIES) * n)
 
     # device work of one step (identical every step)
-    work = {k: 0 for k in ("secular_pairs", "lowner_pairs", "rows_pairs", "secular_sweeps", "roots",
+    work = {k: 0 for k in ("secular_pairs", "secular32_pairs", "lowner_pairs", "rows_pairs", "secular_sweeps",
+                           "secular32_sweeps", "roots",
                            "deflated", "rotations", "leaf_rotations")}
     per_family_work = {}
     for name in FAMILIES:
