@@ -68,6 +68,32 @@ int tde_eigvals_workspace(int64_t n, int32_t leaf, size_t* bytes);
 int tde_eigvals(int64_t n, const double* d, const double* e, double* lambda, int32_t leaf,
                 void* ws, size_t ws_bytes, void* stream);
 
+/* Maximum number of requested rows of one tde_eigvecs_rows call. */
+#define TDE_MAX_SEL_ROWS 1024
+
+/* Bytes of workspace tde_eigvecs_rows needs for order n, nsel requested rows and
+ * the given leaf order: the tde_eigvals workspace plus about 24 nsel n bytes. */
+int tde_eigvecs_rows_workspace(int64_t n, int64_t nsel, int32_t leaf, size_t* bytes);
+
+/* Eigenvalues and requested rows of the eigenvector matrix (Algorithm 1 with a
+ * general requested row list sigma: the requested rows are carried through the
+ * merge tree beside the boundary rows and updated by the selected-row lemma, so
+ * Q itself is never formed).
+ *   n, d, e, lambda, leaf   as for tde_eigvals
+ *   nsel    number of requests, 0 <= nsel <= TDE_MAX_SEL_ROWS (0: eigenvalues only)
+ *   rows    [nsel] device int64, row indices in [0, n), any order, repeats allowed
+ *   qrows   [nsel * n] device output, row-major: qrows[q * n + j] = Q[rows[q]][j],
+ *           where Q is orthogonal, T = Q diag(lambda) Q^T and column j belongs to
+ *           lambda[j].  All requested rows come from the same Q, so every column's
+ *           sign is consistent across them (the sign itself is arbitrary).
+ *   ws      tde_eigvecs_rows_workspace bytes, 256-byte aligned, caller-owned
+ * Argument errors return TDE_EINVAL before any launch.  A requested row outside
+ * [0, n) sets the device status (tde_get_info) to TDE_EINVAL and its output row to
+ * zeros.  Cost: the eigenvalue solve plus O(n^2) per distinct requested row. */
+int tde_eigvecs_rows(int64_t n, const double* d, const double* e, int64_t nsel,
+                     const int64_t* rows, double* lambda, double* qrows, int32_t leaf, void* ws,
+                     size_t ws_bytes, void* stream);
+
 /* Workspace for tde_eigvals_batched with the given packing (host offsets). */
 int tde_eigvals_batched_workspace(int64_t batch, const int64_t* offsets_host, int32_t leaf,
                                   size_t* bytes);

@@ -204,6 +204,31 @@ def boundary_rows_dense(d, e):
     return lam, q[0, :].copy(), q[-1, :].copy()
 
 
+def eigvec_rows(d, e, rows):
+    """(lambda, Q[rows, :]): eigenvalues ascending and the requested rows of the
+    eigenvector matrix (Algorithm 1's selected rows (Q_v)_sigma at the root node,
+    sigma any row list), from the dense eigen-decomposition.  Columns carry an
+    arbitrary sign each."""
+    lam, q = eigh_dense(d, e)
+    return lam, q[np.asarray(rows, dtype=np.int64), :].copy()
+
+
+def principal_block(d, e, rows) -> np.ndarray:
+    """T[rows][:, rows] of tridiag(e, d, e), entry by entry from the definition of T
+    (d on the diagonal, e_i between rows i and i+1, zero elsewhere)."""
+    d = np.asarray(d, dtype=np.float64)
+    e = np.asarray(e, dtype=np.float64)
+    r = np.asarray(rows, dtype=np.int64)
+    out = np.zeros((len(r), len(r)))
+    for a, i in enumerate(r):
+        for b, j in enumerate(r):
+            if i == j:
+                out[a, b] = d[i]
+            elif abs(int(i) - int(j)) == 1:
+                out[a, b] = e[min(i, j)]
+    return out
+
+
 def torn_subproblem(d, e, cut):
     """Cuppen tearing at position ``cut`` (Eq. 1 / Eq. dc-split): returns
     (d_left, e_left, d_right, e_right, rho, s) with T = diag(T_L, T_R) + rho u u^T,

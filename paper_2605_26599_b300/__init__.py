@@ -121,6 +121,56 @@ def eigvals(d, e, leaf: int = 0, out=None, ws: Workspace | None = None, stream=N
     return lam
 
 
+def eigvecs_rows_workspace_bytes(n: int, nsel: int, leaf: int = 0) -> int:
+    """Bytes of workspace ``eigvecs_rows`` needs (tde_eigvecs_rows_workspace)."""
+    b = ctypes.c_size_t()
+    _lib.check("tde_eigvecs_rows_workspace",
+               _lib.load().tde_eigvecs_rows_workspace(int(n), int(nsel), int(leaf), ctypes.byref(b)))
+    return b.value
+
+
+def eigvecs_rows(d, e, rows, leaf: int = 0, out=None, qrows=None, ws: Workspace | None = None,
+                 stream=None, check: bool = True):
+    """Eigenvalues (ascending) and the requested rows of the eigenvector matrix Q of
+    tridiag(e, d, e): returns (lam, qrows) with qrows[q, j] = Q[rows[q], j], column j
+    belonging to lam[j] (T = Q diag(lam) Q^T; column signs arbitrary but shared by
+    all requested rows).  ``rows``: int64 CUDA tensor (or a sequence, copied to the
+    device), any order, repeats allowed, at most MAX_SEL_ROWS entries."""
+    torch = _torch()
+    _check_tensor(d, "d")
+    n = d.shape[0]
+    if n > 1:
+        _check_tensor(e, "e")
+        if e.shape[0] < n - 1:
+            raise ValueError("e must hold at least n-1 entries")
+    if not (hasattr(rows, "is_cuda") and rows.is_cuda):
+        rows = torch.as_tensor(np.asarray(rows, dtype=np.int64)).to(d.device)
+    if rows.dtype != torch.int64 or rows.dim() != 1:
+        raise ValueError("rows must be a 1-D int64 tensor")
+    rows = rows.contiguous()
+    nsel = rows.shape[0]
+    if nsel > _lib.MAX_SEL_ROWS:
+        raise ValueError(f"at most {_lib.MAX_SEL_ROWS} requested rows per call")
+    lam = out if out is not None else torch.empty(n, dtype=torch.float64, device=d.device)
+    q = qrows if qrows is not None else torch.empty((nsel, n), dtype=torch.float64, device=d.device)
+    if n == 0:
+        return lam, q
+    need = eigvecs_rows_workspace_bytes(n, nsel, leaf)
+    ws = Workspace(need, d.device) if ws is None else ws.ensure(need)
+    rc = _lib.load().tde_eigvecs_rows(n, ctypes.c_void_p(d.data_ptr()),
+                                      ctypes.c_void_p(e.data_ptr() if n > 1 else 0), nsel,
+                                      ctypes.c_void_p(rows.data_ptr() if nsel else 0),
+                                      ctypes.c_void_p(lam.data_ptr()),
+                                      ctypes.c_void_p(q.data_ptr() if nsel else 0), int(leaf),
+                                      ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream))
+    _lib.check("tde_eigvecs_rows", rc)
+    if check:
+        info = get_info(ws, stream)
+        if info != 0:
+            raise TdeError("tde_eigvecs_rows (device status)", info)
+    return lam, q
+
+
 def eigvals_batched(d, e, offsets, leaf: int = 0, out=None, ws: Workspace | None = None,
                     stream=None, check: bool = True, offsets_dev=None):
     """Eigenvalues of a packed batch: matrix k owns rows offsets[k]:offsets[k+1] of d,

@@ -26,7 +26,10 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
            "tde_last_launch_count", "tde_profile_enable", "tde_profile_collect", "tde_read_work",
            "tde_eigvals_noalloc", "tde_plan_query", "tde_check_reciprocal",
            "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning",
-           "tde_eigvals_backward_workspace", "tde_eigvals_backward")
+           "tde_eigvals_backward_workspace", "tde_eigvals_backward", "tde_eigvecs_rows_workspace",
+           "tde_eigvecs_rows")
+
+MAX_SEL_ROWS = 1024  # TDE_MAX_SEL_ROWS
 
 KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner", "rows", "place")
 WORK_NAMES = ("secular_pairs", "secular_sweeps", "lowner_pairs", "rows_pairs", "roots", "deflated",
@@ -61,6 +64,8 @@ def load() -> ctypes.CDLL:
     lib.tde_eigvals_batched_workspace.argtypes = [i64, vp, i32, szp]
     lib.tde_eigvals_batched.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.tde_get_info.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.tde_eigvecs_rows_workspace.argtypes = [i64, i64, i32, szp]
+    lib.tde_eigvecs_rows.argtypes = [i64, vp, vp, i64, vp, vp, vp, i32, vp, sz, vp]
     lib.tde_measure_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.tde_last_launch_count.restype = ctypes.c_int64
     lib.tde_last_launch_count.argtypes = []

@@ -99,31 +99,6 @@ static LevelState checkpoint(const AdjWorkspace& w, int s, int64_t N) {
   return LevelState{base, base + N, base + 2 * N};
 }
 
-__device__ __forceinline__ int64_t adj_find_merge(const Merge* M, int64_t cnt, int64_t p) {
-  int64_t lo = 0, hi = cnt;
-  while (hi - lo > 1) {
-    int64_t m = (lo + hi) >> 1;
-    if (M[m].lo <= p) lo = m; else hi = m;
-  }
-  return lo;
-}
-__device__ __forceinline__ int adj_count_less(const double* a, int n, double x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int m = (lo + hi) >> 1;
-    if (a[m] < x) lo = m + 1; else hi = m;
-  }
-  return lo;
-}
-__device__ __forceinline__ int adj_count_leq(const double* a, int n, double x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int m = (lo + hi) >> 1;
-    if (a[m] <= x) lo = m + 1; else hi = m;
-  }
-  return lo;
-}
-
 struct AdjArgs {
   const Merge* M;
   int64_t cnt;
@@ -145,15 +120,15 @@ struct AdjArgs {
 __global__ void k_adj_place(AdjArgs a) {
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < a.nrows;
        p += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t g = adj_find_merge(a.M, a.cnt, p);
+    const int64_t g = find_merge(a.M, a.cnt, p);
     const Merge m = a.M[g];
     if (p < m.lo || p >= m.hi) continue;
     const int K = a.ms[g].K, lo = m.lo, F = (m.hi - m.lo) - K, local = int(p - lo);
     int rank;
     if (local < K)
-      rank = local + adj_count_less(a.AD + lo + K, F, a.LAMA[p]);
+      rank = local + count_less(a.AD + lo + K, F, a.LAMA[p]);
     else
-      rank = (local - K) + adj_count_leq(a.LAMA + lo, K, a.AD[p]);
+      rank = (local - K) + count_leq(a.LAMA + lo, K, a.AD[p]);
     const int src = lo + rank;
     a.w.ALB[p] = a.w.GL[src];
     a.w.ABL[p] = a.w.GBL[src];
@@ -286,7 +261,7 @@ __global__ void k_adj_kappa(AdjArgs a) {
   const int64_t warp = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   for (int64_t p = warp; p < a.nrows; p += nwarps) {
-    const int64_t g = adj_find_merge(a.M, a.cnt, p);
+    const int64_t g = find_merge(a.M, a.cnt, p);
     const Merge m = a.M[g];
     if (p < m.lo || p >= m.hi) continue;
     if (a.PFLAG[p] != 2) continue;
@@ -452,18 +427,18 @@ __global__ void k_adj_form(AdjArgs a) {
   const double inv_sqrt2 = 0.70710678118654752440;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < a.nrows;
        p += int64_t(gridDim.x) * blockDim.x) {
-    const Merge m = a.M[adj_find_merge(a.M, a.cnt, p)];
+    const Merge m = a.M[find_merge(a.M, a.cnt, p)];
     if (p < m.lo || p >= m.hi) continue;
     const double beta = a.es[m.mid - 1];
     const double sgn = beta >= 0.0 ? 1.0 : -1.0;
     const double x = a.in.lam[p];
     if (p < m.mid) {
-      const int out = m.lo + int(p - m.lo) + adj_count_less(a.in.lam + m.mid, m.hi - m.mid, x);
+      const int out = m.lo + int(p - m.lo) + count_less(a.in.lam + m.mid, m.hi - m.mid, x);
       a.w.GL[p] = a.w.MDB[out];
       a.w.GBH[p] = a.w.MZB[out] * inv_sqrt2;
       a.w.GBL[p] = a.w.MRLB[out];
     } else {
-      const int out = m.lo + int(p - m.mid) + adj_count_leq(a.in.lam + m.lo, m.mid - m.lo, x);
+      const int out = m.lo + int(p - m.mid) + count_leq(a.in.lam + m.lo, m.mid - m.lo, x);
       a.w.GL[p] = a.w.MDB[out];
       a.w.GBL[p] = sgn * a.w.MZB[out] * inv_sqrt2;
       a.w.GBH[p] = a.w.MRHB[out];

@@ -1,4 +1,5 @@
 // C ABI of the solver (declarations and contracts in include/tde.h).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -67,6 +68,40 @@ int run_solver(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev
   }
   g_prof_step = -1;
   return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
+}
+
+// Workspace of tde_eigvecs_rows: the eigenvalue workspace, then the requested-row
+// section (U, its count, the request map, and the three row arrays X, XD, AX of
+// nsel x N doubles each).
+static size_t carve_sel(const Plan& plan, int64_t nsel, void* base, Workspace* w, SelArgs* sa,
+                        int32_t** U, int32_t** nu, int32_t** MAP) {
+  size_t off = carve_workspace(plan, base, w);
+  auto take = [&](size_t bytes) -> char* {
+    char* ptr = base ? static_cast<char*>(base) + off : nullptr;
+    off += (bytes + 255) & ~size_t(255);
+    return ptr;
+  };
+  const size_t N = size_t(std::max<int64_t>(plan.nrows, 1));
+  const size_t ns = size_t(std::max<int64_t>(nsel, 1));
+  int32_t* u = reinterpret_cast<int32_t*>(take(4 * ns));
+  int32_t* cnt = reinterpret_cast<int32_t*>(take(4));
+  int32_t* map = reinterpret_cast<int32_t*>(take(4 * ns));
+  double* X = reinterpret_cast<double*>(take(8 * ns * N));
+  double* XD = reinterpret_cast<double*>(take(8 * ns * N));
+  double* AX = reinterpret_cast<double*>(take(8 * ns * N));
+  if (sa) {
+    sa->U = u;
+    sa->nu = cnt;
+    sa->nsel = int32_t(nsel);
+    sa->N = int64_t(N);
+    sa->X = X;
+    sa->XD = XD;
+    sa->AX = AX;
+    *U = u;
+    *nu = cnt;
+    *MAP = map;
+  }
+  return off;
 }
 
 }  // namespace tde
@@ -142,6 +177,58 @@ int tde_get_info(const void* ws, void* stream, int32_t* info) {
     return TDE_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return TDE_ECUDA;
   return TDE_OK;
+}
+
+int tde_eigvecs_rows_workspace(int64_t n, int64_t nsel, int32_t leaf, size_t* bytes) {
+  if (n < 0 || nsel < 0 || nsel > kMaxSel || bytes == nullptr) return TDE_EINVAL;
+  int64_t off[2] = {0, n};
+  Plan p;
+  int rc = build_plan(1, off, leaf, &p);
+  if (rc != TDE_OK) return rc;
+  *bytes = carve_sel(p, nsel, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  return TDE_OK;
+}
+
+int tde_eigvecs_rows(int64_t n, const double* d, const double* e, int64_t nsel,
+                     const int64_t* rows, double* lambda, double* qrows, int32_t leaf, void* ws,
+                     size_t ws_bytes, void* stream) {
+  g_launches = 0;
+  if (n < 0 || nsel < 0 || nsel > kMaxSel) return TDE_EINVAL;
+  if (n == 0) return TDE_OK;
+  if (d == nullptr || lambda == nullptr || ws == nullptr || (n > 1 && e == nullptr) ||
+      (nsel > 0 && (rows == nullptr || qrows == nullptr)))
+    return TDE_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return TDE_EINVAL;
+  int64_t off[2] = {0, n};
+  Plan p;
+  int rc = build_plan(1, off, leaf, &p);
+  if (rc != TDE_OK) return rc;
+  Workspace w;
+  SelArgs sa;
+  int32_t *U = nullptr, *nu = nullptr, *MAP = nullptr;
+  const size_t need = carve_sel(p, nsel, ws, &w, &sa, &U, &nu, &MAP);
+  if (ws_bytes < need) return TDE_EWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(w.status, 0, sizeof(Status), s) != cudaSuccess) return TDE_ECUDA;
+  if (cudaMemsetAsync(w.sigma_bits, 0, 8, s) != cudaSuccess) return TDE_ECUDA;
+  k_set_offsets<<<1, 1, 0, s>>>(w.offsets, n);
+  g_launches += 1;
+  g_prof_step = -1;
+  launch_plan(p, w, w.offsets, s);
+  launch_scale(p, w, w.offsets, d, e, s);
+  launch_leaves(p, w, lambda, s);
+  if (nsel > 0) {
+    launch_sel_prepare(sa, rows, n, U, nu, MAP, w.status, s);
+    launch_sel_leaves(p, w, sa, s);
+  }
+  const LevelState state{w.LAM, w.BLO, w.BHI};
+  for (int st = 0; st < p.steps; ++st) {
+    g_prof_step = st;
+    launch_step(p, w, st, lambda, s, state, state, false, nsel > 0 ? &sa : nullptr);
+  }
+  g_prof_step = -1;
+  if (nsel > 0) launch_sel_gather(sa, MAP, nsel, n, qrows, s);
+  return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
 }
 
 int64_t tde_last_launch_count(void) { return g_launches; }

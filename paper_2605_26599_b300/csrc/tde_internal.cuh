@@ -46,7 +46,7 @@ struct MState {
   double rho;    // rho' = 2 |beta|
   double zsq;    // sum of active z^2
   int32_t big;   // 1: roots in the warp-per-root list (K >= warp_min_k)
-  int32_t pad;
+  int32_t surv;  // survivors of the negligible-z test (active + rotation-deflated)
 };
 
 // Launch-shape parameters chosen per call (tde_set_tuning; the Python autotuner
@@ -153,6 +153,45 @@ __device__ __forceinline__ void set_status(Status* st, int code) {
   atomicCAS(&st->info, 0, code);
 }
 
+// Merge of a step containing row p: the last merge with lo <= p (merges of a step
+// are ordered by lo).
+__device__ __forceinline__ int64_t find_merge(const Merge* M, int64_t cnt, int64_t p) {
+  int64_t lo = 0, hi = cnt;  // M[lo].lo <= p
+  while (hi - lo > 1) {
+    int64_t m = (lo + hi) >> 1;
+    if (M[m].lo <= p)
+      lo = m;
+    else
+      hi = m;
+  }
+  return lo;
+}
+
+// number of entries of the ascending array a[0..n) strictly below x
+__device__ __forceinline__ int count_less(const double* a, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (a[m] < x)
+      lo = m + 1;
+    else
+      hi = m;
+  }
+  return lo;
+}
+// number of entries of the ascending array a[0..n) less than or equal to x
+__device__ __forceinline__ int count_leq(const double* a, int n, double x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int m = (lo + hi) >> 1;
+    if (a[m] <= x)
+      lo = m + 1;
+    else
+      hi = m;
+  }
+  return lo;
+}
+
 // Levels of a matrix of order n with leaves of order <= leaf: the smallest L with
 // ceil(n / 2^L) <= leaf (node (h, i) covers [floor(i n / 2^h), floor((i+1) n / 2^h))),
 // but never so deep that a leaf would be empty (2^L <= n); with leaf = 1 and n not
@@ -242,12 +281,44 @@ void launch_leaves(const Plan& plan, const Workspace& ws, double* lambda, cudaSt
 struct LevelState {
   double *lam, *blo, *bhi;
 };
+// Requested rows of the eigenvector matrix (Algorithm 1 with a general row list
+// sigma_v; tde_rows_sel.cu).  Row u of each array belongs to the distinct
+// requested row U[u] and holds, over the columns of the node containing U[u] at
+// the current level (the node's row range [lo, hi) indexes its columns too), the
+// entries of that node's eigenvector row.
+constexpr int kMaxSel = TDE_MAX_SEL_ROWS;  // requested rows per call
+struct SelArgs {
+  const int32_t* U;   // distinct requested rows, ascending; entries past *nu hold INT32_MAX
+  const int32_t* nu;  // number of distinct rows (device)
+  int32_t nsel;       // capacity of U (requests of the call)
+  int64_t N;          // stride between the rows of X, XD, AX
+  double* X;          // level state (children's rows in, parent's rows out)
+  double* XD;         // rows of the merge problem, then of the active roots' columns
+  double* AX;         // rows of the deflated problem (active columns, then deflated)
+};
+void launch_sel_prepare(const SelArgs& sa, const int64_t* rows, int64_t nrows_total, int32_t* U,
+                        int32_t* nu, int32_t* MAP, Status* st, cudaStream_t s);
+void launch_sel_leaves(const Plan& plan, const Workspace& ws, const SelArgs& sa, cudaStream_t s);
+void launch_sel_form(const Plan& plan, const Workspace& ws, const SelArgs& sa, int step,
+                     LevelState in, cudaStream_t s);
+void launch_sel_deflate(const Plan& plan, const Workspace& ws, const SelArgs& sa, int step,
+                        cudaStream_t s);
+void launch_sel_rows(const Plan& plan, const Workspace& ws, const SelArgs& sa, int step,
+                     cudaStream_t s);
+void launch_sel_place(const Plan& plan, const Workspace& ws, const SelArgs& sa, int step,
+                      cudaStream_t s);
+void launch_sel_gather(const SelArgs& sa, const int32_t* MAP, int64_t nsel, int64_t n,
+                       double* qrows, cudaStream_t s);
+
 // One merge step: reads the children's state from `in` and writes the parents'
 // state to `out` (in == out is allowed: a merge's children occupy its own rows).
 // With recompute = true only the merge internals are rebuilt (no place): used by
-// the adjoint, which also forces z-hat and rows at root merges.
+// the adjoint, which also forces z-hat and rows at root merges.  With `sel` the
+// requested eigenvector rows are carried through the step as well (z-hat and the
+// row update then run at root merges too).
 void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
-                 LevelState in, LevelState out, bool recompute = false);
+                 LevelState in, LevelState out, bool recompute = false,
+                 const SelArgs* sel = nullptr);
 void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in, cudaStream_t s);
 // secular, Lowner and boundary-row kernels of one step; returns the launch count
 int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s,

@@ -20,8 +20,10 @@ namespace tde {
 // first row r0 and last row r1 of the accumulated rotation product.
 // Returns false if an unreduced block needed more than 40 steps per row; adds the
 // number of plane rotations applied to *rot.
-__device__ bool leaf_qr_two_rows(int m, double* a, double* b, double* r0, double* r1,
-                                 unsigned* rot) {
+// Kept out of line so that every kernel runs one compiled body: the requested-row
+// leaves (k_sel_leaves) rely on reproducing the rotations of k_leaves bit for bit.
+__device__ __noinline__ bool leaf_qr_two_rows(int m, double* a, double* b, double* r0, double* r1,
+                                              unsigned* rot) {
   int hi = m - 1;
   int steps = 0;
   const int max_steps = 40 * m;
@@ -141,6 +143,63 @@ void launch_leaves_to(const Plan& plan, const Workspace& ws, double* lambda, cud
   k_leaves<<<int(grid), block, 0, s>>>(ws.leaves, plan.nleaves, ws.ds, ws.es, ws.sigma_bits,
                                        out.lam, out.blo, out.bhi, lambda, ws.status);
   prof_end(kKLeaves, s);
+  g_launches += 1;
+}
+
+// Requested rows at the leaves (Algorithm 1, leaf branch: "return the requested
+// rows of the leaf eigenvector matrix").  For each distinct requested row r the
+// leaf holding it is diagonalised again by the same QR with the tracked rows
+// e_r and e_last: the rotations depend on the leaf's (d, e) only, so they -- and
+// the ascending sort -- are those of k_leaves, and the tracked row is row r of
+// the very Q whose first and last rows k_leaves stored.
+__global__ void k_sel_leaves(SelArgs sa, const Leaf* __restrict__ leaves, int64_t nleaves,
+                             const double* __restrict__ ds, const double* __restrict__ es) {
+  const int nu = *sa.nu;
+  for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nu; u += gridDim.x * blockDim.x) {
+    const int r = sa.U[u];
+    int64_t lo_t = 0, hi_t = nleaves;  // last leaf with lo <= r
+    while (hi_t - lo_t > 1) {
+      const int64_t md = (lo_t + hi_t) >> 1;
+      if (leaves[md].lo <= r)
+        lo_t = md;
+      else
+        hi_t = md;
+    }
+    const Leaf lf = leaves[lo_t];
+    const int m = lf.hi - lf.lo;
+    double a[kMaxLeaf], b[kMaxLeaf], r0[kMaxLeaf], r1[kMaxLeaf];
+    for (int j = 0; j < m; ++j) {
+      a[j] = ds[lf.lo + j];
+      b[j] = (j + 1 < m) ? es[lf.lo + j] : 0.0;
+      r0[j] = (j == r - lf.lo) ? 1.0 : 0.0;
+      r1[j] = (j == m - 1) ? 1.0 : 0.0;
+    }
+    if (lf.flags & 1) a[0] -= fabs(es[lf.lo - 1]);
+    if (lf.flags & 2) a[m - 1] -= fabs(es[lf.hi - 1]);
+    unsigned rot = 0;
+    leaf_qr_two_rows(m, a, b, r0, r1, &rot);  // a failure is reported by k_leaves
+    for (int j = 1; j < m; ++j) {
+      double v = a[j], p = r0[j], q = r1[j];
+      int i = j - 1;
+      while (i >= 0 && a[i] > v) {
+        a[i + 1] = a[i];
+        r0[i + 1] = r0[i];
+        r1[i + 1] = r1[i];
+        --i;
+      }
+      a[i + 1] = v;
+      r0[i + 1] = p;
+      r1[i + 1] = q;
+    }
+    double* x = sa.X + int64_t(u) * sa.N + lf.lo;
+    for (int j = 0; j < m; ++j) x[j] = r0[j];
+  }
+}
+
+void launch_sel_leaves(const Plan& plan, const Workspace& ws, const SelArgs& sa, cudaStream_t s) {
+  if (plan.nleaves == 0 || sa.nsel == 0) return;
+  const int grid = (sa.nsel + 63) / 64;
+  k_sel_leaves<<<grid, 64, 0, s>>>(sa, ws.leaves, plan.nleaves, ws.ds, ws.es);
   g_launches += 1;
 }
 

@@ -31,43 +31,6 @@ namespace tde {
 
 constexpr int kNT = 256;  // threads of the per-merge deflation block
 
-__device__ __forceinline__ int64_t find_merge(const Merge* M, int64_t cnt, int64_t p) {
-  int64_t lo = 0, hi = cnt;  // M[lo].lo <= p
-  while (hi - lo > 1) {
-    int64_t m = (lo + hi) >> 1;
-    if (M[m].lo <= p)
-      lo = m;
-    else
-      hi = m;
-  }
-  return lo;
-}
-
-// number of entries of the ascending array a[0..n) strictly below x
-__device__ __forceinline__ int count_less(const double* a, int n, double x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int m = (lo + hi) >> 1;
-    if (a[m] < x)
-      lo = m + 1;
-    else
-      hi = m;
-  }
-  return lo;
-}
-// number of entries of the ascending array a[0..n) less than or equal to x
-__device__ __forceinline__ int count_leq(const double* a, int n, double x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int m = (lo + hi) >> 1;
-    if (a[m] <= x)
-      lo = m + 1;
-    else
-      hi = m;
-  }
-  return lo;
-}
-
 // ---------------------------------------------------------------------------
 __global__ void k_form(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
                        const double* __restrict__ LAM, const double* __restrict__ BLO,
@@ -599,7 +562,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       st.rho = rho;
       st.zsq = zsq;
       st.big = big ? 1 : 0;
-      st.pad = 0;
+      st.surv = S;
       a.ms[g] = st;
       atomicAdd(&a.st->work[kWorkDeflated], (unsigned long long)(n0 - K));
       atomicAdd(&a.st->work[kWorkRotations], (unsigned long long)(S - K));
@@ -662,13 +625,14 @@ void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in,
 }
 
 void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
-                 LevelState in, LevelState out, bool recompute) {
+                 LevelState in, LevelState out, bool recompute, const SelArgs* sel) {
   const Merge* M = ws.merges + plan.step_base[step];
   const int64_t cnt = plan.step_count[step];
   const int64_t nrows = plan.nrows;
   const int flat_grid = int(std::min<int64_t>((nrows + 255) / 256, 148 * 8));
   prof_begin(kKForm, s);
   launch_form(plan, ws, step, in, s);
+  if (sel) launch_sel_form(plan, ws, *sel, step, in, s);
   prof_end(kKForm, s);
   DeflateArgs da;
   da.M = M;
@@ -702,8 +666,11 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
   prof_begin(kKDeflate, s);
   k_deflate<<<def_grid, kNT, 0, s>>>(da);
+  if (sel) launch_sel_deflate(plan, ws, *sel, step, s);
   prof_end(kKDeflate, s);
-  int launches = 2 + launch_roots(plan, ws, step, M, s, recompute);  // form, deflate + roots
+  // form, deflate + roots
+  int launches = 2 + launch_roots(plan, ws, step, M, s, recompute || sel != nullptr);
+  if (sel) launch_sel_rows(plan, ws, *sel, step, s);
   if (recompute) {
     g_launches += launches;
     return;
@@ -713,6 +680,7 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   k_place<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.mstate, ws.D, ws.RLO, ws.RHI, ws.AD,
                                     ws.ALO, ws.AHI, ws.sigma_bits, out.lam, out.blo, out.bhi,
                                     lambda);
+  if (sel) launch_sel_place(plan, ws, *sel, step, s);
   prof_end(kKPlace, s);
   g_launches += launches;
 }

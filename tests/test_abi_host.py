@@ -109,6 +109,20 @@ def test_argument_validation_without_device_work():
     off = np.array([1, 5], dtype=np.int64)  # offsets[0] != 0
     assert lib.tde_eigvals_batched_workspace(1, off.ctypes.data, 0, ctypes.byref(sz)) == _lib.TDE_EINVAL
     assert lib.tde_eigvals_noalloc(16385, fake, fake, fake, 0, None) == _lib.TDE_EWORKSPACE
+    # requested eigenvector rows
+    assert lib.tde_eigvecs_rows_workspace(100, _lib.MAX_SEL_ROWS + 1, 0, ctypes.byref(sz)) == _lib.TDE_EINVAL
+    assert lib.tde_eigvecs_rows_workspace(100, -1, 0, ctypes.byref(sz)) == _lib.TDE_EINVAL
+    assert lib.tde_eigvecs_rows_workspace(100, 4, 0, ctypes.byref(sz)) == _lib.TDE_OK
+    need = sz.value
+    assert lib.tde_eigvals_workspace(100, 0, ctypes.byref(sz)) == _lib.TDE_OK
+    assert need >= sz.value + 3 * 8 * 4 * 100
+    big = 1 << 40
+    assert lib.tde_eigvecs_rows(0, None, None, 4, None, None, None, 0, None, 0, None) == _lib.TDE_OK
+    assert lib.tde_eigvecs_rows(10, fake, fake, 3, None, fake, fake, 0, fake, big, None) == _lib.TDE_EINVAL
+    assert lib.tde_eigvecs_rows(10, fake, fake, 3, fake, fake, None, 0, fake, big, None) == _lib.TDE_EINVAL
+    assert lib.tde_eigvecs_rows(10, fake, fake, _lib.MAX_SEL_ROWS + 1, fake, fake, fake, 0, fake, big,
+                                None) == _lib.TDE_EINVAL
+    assert lib.tde_eigvecs_rows(10, fake, fake, 3, fake, fake, fake, 0, fake, 64, None) == _lib.TDE_EWORKSPACE
 
 
 def test_python_binding_refuses_cpu_tensors():

@@ -151,6 +151,46 @@ def test_boundary_rows_toeplitz_closed_form(oracle_mod):
     assert np.allclose(np.abs(v[0]), np.abs(blo), atol=1e-12)
 
 
+def test_eigvec_rows_toeplitz_closed_form(oracle_mod):
+    # Algorithm 1's (Q)_sigma for a row list with repeats and any order, against the
+    # closed-form eigenvectors of tridiag(-1, 2, -1): Q[r, k] = +-sqrt(2/(n+1)) sin((r+1)(k+1) pi/(n+1)),
+    # one sign per column shared by all rows.
+    n = 40
+    d, e = inputs.toeplitz(n, 2.0, -1.0)
+    rows = [17, 0, n - 1, 17, 5]
+    lam, q = oracle_mod.eigvec_rows(d, e, rows)
+    k = np.arange(1, n + 1)
+    ref = np.sqrt(2.0 / (n + 1)) * np.sin(np.outer(np.asarray(rows) + 1, k) * np.pi / (n + 1))
+    sign = np.sign(np.sum(q * ref, axis=0))
+    assert np.all(sign != 0)
+    assert np.allclose(q * sign, ref, atol=1e-13)
+    assert np.array_equal(q[0], q[3])
+
+
+def test_eigvec_rows_two_by_two_brute_force(oracle_mod):
+    # [[a, b], [b, c]]: eigenvector of lambda is proportional to (b, lambda - a)
+    a, b, c = 0.3, -1.7, 2.2
+    lam, q = oracle_mod.eigvec_rows(np.array([a, c]), np.array([b]), [1, 0])
+    for j in range(2):
+        v = np.array([b, lam[j] - a])
+        v /= np.linalg.norm(v)
+        assert min(np.abs(q[::-1, j] - v).max(), np.abs(q[::-1, j] + v).max()) < 1e-15
+
+
+@pytest.mark.parametrize("fam", ["uniform11", "normal", "wilkinson"])
+def test_eigvec_rows_invariants(oracle_mod, fam):
+    # T = Q diag(lambda) Q^T with Q orthogonal, restricted to the requested rows:
+    # Q_s Q_s^T = I and Q_s diag(lambda) Q_s^T = T[s][:, s] (principal block from the definition)
+    n = 57
+    d, e = inputs.family(fam, n)
+    rows = [3, 4, 56, 0, 30, 31, 4]
+    lam, q = oracle_mod.eigvec_rows(d, e, rows)
+    blk = oracle_mod.principal_block(d, e[: n - 1], rows)
+    assert blk[0, 1] == e[3] and blk[1, 0] == e[3] and blk[0, 0] == d[3] and blk[4, 5] == e[30]
+    assert np.abs(q @ q.T - (np.asarray(rows)[:, None] == np.asarray(rows)[None, :])).max() < 1e-13
+    assert np.abs((q * lam) @ q.T - blk).max() < 1e-13 * max(1.0, oracle_mod.norm1(d, e[: n - 1]))
+
+
 def test_merge_problem_boundary_sufficiency(oracle_mod):
     # Lemma "boundary sufficiency" + Eq. merge-problem: the spectrum of
     # diag(D) + rho' z z^T built from child boundary rows is the spectrum of T.
