@@ -361,9 +361,13 @@ def run_ours(args, rank: int, world: int, dist) -> None:
 
     cpu = cpu_baseline(n, fams) if (world == 1 and not args.no_cpu_baseline) else None
     extras = {}
-    if not args.no_extras:
+    which = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
+    if "batched" in which:
         extras["batched"] = batched_section(args, dev)
+    if "backward" in which:
         extras["backward"] = backward_section(args, dev)
+    if "rows" in which:
+        extras["eigvec_rows"] = rows_section(args, dev, fma_per_s)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -446,6 +450,65 @@ def batched_section(args, dev) -> dict:
             "per_matrix_loop_solves_per_s": B / loop_s, "per_matrix_loop_ms": loop_s * 1e3,
             "speedup_vs_loop": (B / (ms * 1e-3)) / (B / loop_s),
             "max_err_over_gate_sampled": worst}
+
+
+def rows_section(args, dev, fma_per_s: float) -> dict:
+    """Requested eigenvector rows (Algorithm 1 with a general row list): 16 rows spread
+    over the n = --size matrix, Toeplitz (weak deflation: the costly case) and
+    uniform(-1, 1).  Time against the eigenvalues alone, the FP64 pipe use of the
+    requested-row update (7 FP64 instructions per (pole, root) sweep shared by up to
+    four rows, plus one fused multiply-add per row), and the identities
+    Q_s Q_s^T = I, Q_s diag(lambda) Q_s^T = T[s][:, s] at full size."""
+    import torch
+
+    import oracle
+    import paper_2605_26599_b300 as tde
+
+    n, leaf, nsel = args.size, args.leaf, 16
+    rows = np.linspace(0, n - 1, nsel).astype(np.int64)
+    fams = family_inputs(n)
+    res = {"rows_requested": nsel, "n": n, "leaf": leaf}
+    for name in ("b_toeplitz", "a_uniform11"):
+        d, e = fams[name]
+        dt, et = torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev)
+        rt = torch.from_numpy(rows).to(dev)
+        ws = tde.Workspace(tde.eigvecs_rows_workspace_bytes(n, nsel, leaf), dev)
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+        q = torch.empty((nsel, n), dtype=torch.float64, device=dev)
+        ews = tde.Workspace(tde.workspace_bytes(n, leaf), dev)
+        tde.eigvecs_rows(dt, et, rt, leaf=leaf, out=lam, qrows=q, ws=ws)
+        tde.eigvals(dt, et, leaf=leaf, out=lam, ws=ews)
+        torch.cuda.synchronize()
+        reps = 2
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        for _ in range(reps):
+            tde.eigvals(dt, et, leaf=leaf, out=lam, ws=ews, check=False)
+        ev[1].record()
+        tde.profile_enable(True)
+        for _ in range(reps):
+            tde.eigvecs_rows(dt, et, rt, leaf=leaf, out=lam, qrows=q, ws=ws, check=False)
+        ev[2].record()
+        torch.cuda.synchronize()
+        tde.profile_enable(False)
+        kp = tde.profile_collect()
+        w = tde.read_work(ws)
+        info = tde.get_info(ws)
+        vals_ms = ev[0].elapsed_time(ev[1]) / reps
+        rows_ms = ev[1].elapsed_time(ev[2]) / reps
+        upd_ms = kp["sel_rows"][0] / reps
+        instr = 7 * w["sel_sweep_pairs"] + w["sel_row_pairs"]
+        qn, ln = q.cpu().numpy(), lam.cpu().numpy()
+        blk = oracle.principal_block(d, e[: n - 1], rows)
+        res[name] = {
+            "eigvals_ms": vals_ms, "eigvecs_rows_ms": rows_ms, "extra_ms_per_row": (rows_ms - vals_ms) / nsel,
+            "row_update_ms": upd_ms, "row_bookkeeping_ms": kp["sel"][0] / reps,
+            "row_pairs": w["sel_row_pairs"], "sweep_pairs": w["sel_sweep_pairs"],
+            "row_update_fp64_pipe_frac": instr / (upd_ms * 1e-3) / fma_per_s if upd_ms > 0 else None,
+            "orthonormality_err": float(np.abs(qn @ qn.T - np.eye(nsel)).max()),
+            "block_identity_err": float(np.abs((qn * ln) @ qn.T - blk).max()),
+            "device_status": info}
+    return res
 
 
 def backward_section(args, dev) -> dict:
@@ -541,7 +604,9 @@ def main():
                     help="eigenvalue indices per family per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched (config 3) and backward (config 4) measurements")
+                    help="skip the batched, backward and requested-row measurements")
+    ap.add_argument("--extras", default="batched,backward,rows",
+                    help="which extra measurements to run (comma list of batched, backward, rows)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

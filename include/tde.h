@@ -178,7 +178,8 @@ int64_t tde_last_launch_count(void);
  * on this thread records a CUDA event pair around each kernel launch; collect
  * synchronises on those events, writes per-kernel-class milliseconds and launch
  * counts into ms[0..nids) / launches[0..nids) (classes: 0 plan, 1 scale, 2 leaves,
- * 3 form, 4 deflate, 5 secular, 6 lowner, 7 rows, 8 place) and clears the record.
+ * 3 form, 4 deflate, 5 secular, 6 lowner, 7 rows, 8 place, 9 requested-row form,
+ * deflation and placement, 10 requested-row update) and clears the record.
  * Do not enable it while the stream is being captured into a CUDA graph. */
 int tde_profile_enable(int on);
 int tde_profile_collect(int nids, double* ms, int64_t* launches);
@@ -193,7 +194,9 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
  * out[4] roots solved, out[5] deflated eigenvalues, out[6] close-pole rotations,
  * out[7] leaf plane rotations, out[8] merges whose rotated deflated eigenvalues
  * needed sorting, out[9] entries sorted, out[10] single-precision secular pole
- * sweeps x K, out[11] single-precision secular sweeps.  n <= 16 entries are copied.  The counters are
+ * sweeps x K, out[11] single-precision secular sweeps, out[12] requested-row
+ * updates as (pole, root, row) triples, out[13] their (pole, root) sweeps (one per
+ * group of up to four rows of a merge).  n <= 16 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 

@@ -31,10 +31,11 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
 
 MAX_SEL_ROWS = 1024  # TDE_MAX_SEL_ROWS
 
-KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner", "rows", "place")
+KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner", "rows", "place",
+                "sel", "sel_rows")
 WORK_NAMES = ("secular_pairs", "secular_sweeps", "lowner_pairs", "rows_pairs", "roots", "deflated",
               "rotations", "leaf_rotations", "sorts", "sorted_entries", "secular32_pairs",
-              "secular32_sweeps")
+              "secular32_sweeps", "sel_row_pairs", "sel_sweep_pairs")
 
 
 class TdeError(RuntimeError):

@@ -77,6 +77,8 @@ enum WorkCounter {
   kWorkSortedEntries,     // entries in those sorts
   kWorkSecular32Pairs,    // sum over roots of K x (number of single-precision pole sweeps)
   kWorkSecular32Sweeps,   // sum over roots of the number of single-precision pole sweeps
+  kWorkSelRowPairs,       // requested-row updates: (pole, root, requested row) triples
+  kWorkSelSweepPairs,     // requested-row updates: (pole, root) pairs per sweep of up to four rows
   kNumWork
 };
 
@@ -90,7 +92,7 @@ struct Status {
 
 // Kernel classes timed by the optional per-launch event profiler.
 enum KernelId { kKPlan = 0, kKScale, kKLeaves, kKForm, kKDeflate, kKSecular, kKLowner, kKRows,
-                kKPlace, kNumKernelIds };
+                kKPlace, kKSel, kKSelRows, kNumKernelIds };
 void prof_begin(int id, cudaStream_t s);
 void prof_end(int id, cudaStream_t s);
 

@@ -632,8 +632,12 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   const int flat_grid = int(std::min<int64_t>((nrows + 255) / 256, 148 * 8));
   prof_begin(kKForm, s);
   launch_form(plan, ws, step, in, s);
-  if (sel) launch_sel_form(plan, ws, *sel, step, in, s);
   prof_end(kKForm, s);
+  if (sel) {
+    prof_begin(kKSel, s);
+    launch_sel_form(plan, ws, *sel, step, in, s);
+    prof_end(kKSel, s);
+  }
   DeflateArgs da;
   da.M = M;
   da.cnt = cnt;
@@ -666,11 +670,19 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
   prof_begin(kKDeflate, s);
   k_deflate<<<def_grid, kNT, 0, s>>>(da);
-  if (sel) launch_sel_deflate(plan, ws, *sel, step, s);
   prof_end(kKDeflate, s);
+  if (sel) {
+    prof_begin(kKSel, s);
+    launch_sel_deflate(plan, ws, *sel, step, s);
+    prof_end(kKSel, s);
+  }
   // form, deflate + roots
   int launches = 2 + launch_roots(plan, ws, step, M, s, recompute || sel != nullptr);
-  if (sel) launch_sel_rows(plan, ws, *sel, step, s);
+  if (sel) {
+    prof_begin(kKSelRows, s);
+    launch_sel_rows(plan, ws, *sel, step, s);
+    prof_end(kKSelRows, s);
+  }
   if (recompute) {
     g_launches += launches;
     return;
@@ -680,8 +692,12 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   k_place<<<flat_grid, 256, 0, s>>>(M, cnt, nrows, ws.mstate, ws.D, ws.RLO, ws.RHI, ws.AD,
                                     ws.ALO, ws.AHI, ws.sigma_bits, out.lam, out.blo, out.bhi,
                                     lambda);
-  if (sel) launch_sel_place(plan, ws, *sel, step, s);
   prof_end(kKPlace, s);
+  if (sel) {
+    prof_begin(kKSel, s);
+    launch_sel_place(plan, ws, *sel, step, s);
+    prof_end(kKSel, s);
+  }
   g_launches += launches;
 }
 

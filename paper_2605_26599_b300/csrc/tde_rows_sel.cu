@@ -194,6 +194,7 @@ struct SelRowsArgs {
   int64_t cnt;
   const MState* ms;
   const double *AD, *ZH, *DORG, *TAU;
+  Status* st;
 };
 
 // Block row y = requested row u; a block works only if u starts a group of up to
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(128) k_sel_rows(SelArgs sa, SelRowsArgs a) {
   const double* ZH = a.ZH + lo;
   const double* x0 = sa.AX + int64_t(u) * sa.N + lo;
   const int64_t N = sa.N;
+  unsigned long long sweeps = 0;
   for (int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < K;
        j += gridDim.x * (blockDim.x >> 5)) {
     const double dorg = a.DORG[lo + j], tau = a.TAU[lo + j];
@@ -240,6 +242,11 @@ __global__ void __launch_bounds__(128) k_sel_rows(SelArgs sa, SelRowsArgs a) {
       if (nr > 2) out[2 * N] = c2 * inv;
       if (nr > 3) out[3 * N] = c3 * inv;
     }
+    sweeps += unsigned(K);
+  }
+  if (lane == 0 && sweeps) {
+    atomicAdd(&a.st->work[kWorkSelSweepPairs], sweeps);
+    atomicAdd(&a.st->work[kWorkSelRowPairs], sweeps * unsigned(nr));
   }
 }
 
@@ -322,6 +329,7 @@ void launch_sel_rows(const Plan& plan, const Workspace& ws, const SelArgs& sa, i
   a.ZH = ws.Z;
   a.DORG = reinterpret_cast<const double*>(ws.KEYA);
   a.TAU = ws.TAU;
+  a.st = ws.status;
   const dim3 grid(sel_grid_x(plan, step, 4), sa.nsel);
   k_sel_rows<<<grid, 128, 0, s>>>(sa, a);
   g_launches += 1;
