@@ -84,7 +84,9 @@ enum WorkCounter {
 
 struct Status {
   int32_t info;
-  int32_t pad[31];
+  uint32_t claim_next;  // next entry of a dynamically claimed work list (see claim_begin)
+  uint32_t claim_done;  // blocks of the claiming launch that have finished
+  int32_t pad[29];
   uint32_t root_count[kMaxSteps];      // roots of small-K merges per step
   uint32_t root_count_big[kMaxSteps];  // roots of merges with K >= warp_min_k
   unsigned long long work[16];
@@ -150,6 +152,27 @@ int run_solver(const Plan& plan, const Workspace& ws, const int64_t* offsets_dev
                const double* d, const double* e, double* lambda, cudaStream_t stream);
 
 // ---- device helpers -------------------------------------------------------
+
+// Dynamic work claiming for kernels whose items differ in cost: each warp takes
+// the next item index from st->claim_next; the last block to finish resets the
+// counter, so consecutive launches on one stream (and graph replays) start at 0.
+// At most one claiming kernel may run at a time per workspace.
+__device__ __forceinline__ uint32_t claim_next_item(Status* st) {
+  uint32_t r = 0;
+  if ((threadIdx.x & 31) == 0) r = atomicAdd(&st->claim_next, 1u);
+  return __shfl_sync(0xffffffffu, r, 0);
+}
+__device__ __forceinline__ void claim_finish_block(Status* st) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&st->claim_done, 1u) == gridDim.x - 1) {
+      st->claim_next = 0;
+      st->claim_done = 0;
+      __threadfence();
+    }
+  }
+}
 
 __device__ __forceinline__ void set_status(Status* st, int code) {
   atomicCAS(&st->info, 0, code);

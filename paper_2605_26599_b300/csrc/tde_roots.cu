@@ -675,13 +675,13 @@ __device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, in
   return a.ROOTMAP[r - nb];
 }
 
+// Roots differ in cost (one to several sweeps in each precision), so warps claim
+// them one at a time instead of a fixed stride, which would leave a tail.
 __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   SecTally tally;
-  for (uint32_t r = warp; r < total; r += nwarps) {
+  for (uint32_t r = claim_next_item(a.st); r < total; r = claim_next_item(a.st)) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
     const MState ms = a.ms[g];
@@ -697,6 +697,7 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     tally.add(sweeps, n32, ms.K);
   }
   if (lane == 0) tally.flush(a.st);
+  claim_finish_block(a.st);
 }
 
 // ---------------------------------------------------------------------------
