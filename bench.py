@@ -368,6 +368,8 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         extras["backward"] = backward_section(args, dev)
     if "rows" in which:
         extras["eigvec_rows"] = rows_section(args, dev, fma_per_s)
+    if "dense" in which:
+        extras["dense"] = dense_section(args, dev, fma_per_s)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -511,6 +513,52 @@ def rows_section(args, dev, fma_per_s: float) -> dict:
     return res
 
 
+def dense_section(args, dev, fma_per_s: float) -> dict:
+    """Dense front end (Householder reduction to tridiagonal form, then the
+    boundary-row solver): a dense symmetric (G + G^T)/2 of order 8192, time and FP64
+    rate of the reduction ((2/3) n^3 FMAs), trace / Frobenius invariants of the
+    spectrum; the oracle (LAPACK on the host cores) timed beside it at n = 2048."""
+    import time
+
+    import torch
+
+    import oracle
+    import paper_2605_26599_b300 as tde
+
+    res = {}
+    for n in (2048, 8192):
+        a = inputs.dense_goe(n, seed=1)
+        at = torch.from_numpy(a).to(dev)
+        ws = tde.Workspace(tde.dense_eigvals_workspace_bytes(n, args.leaf), dev)
+        lam = tde.dense_eigvals(at, leaf=args.leaf, ws=ws)
+        torch.cuda.synchronize()
+        tde.profile_enable(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        lam = tde.dense_eigvals(at, leaf=args.leaf, ws=ws, check=False)
+        ev[1].record()
+        torch.cuda.synchronize()
+        tde.profile_enable(False)
+        tri_ms = sum(v[0] for v in tde.profile_collect().values())
+        ms = ev[0].elapsed_time(ev[1])
+        fmas = sum(2 * m * (m + 1) for m in range(1, n))
+        ln = lam.cpu().numpy()
+        nrm = float(np.linalg.norm(a))
+        r = {"ms": ms, "tridiagonal_solve_ms": tri_ms, "reduction_ms": ms - tri_ms,
+             "reduction_fp64_fma_frac": fmas / ((ms - tri_ms) * 1e-3) / fma_per_s,
+             "trace_err_rel": abs(ln.sum() - np.trace(a)) / nrm,
+             "frobenius_err_rel": abs((ln ** 2).sum() - nrm ** 2) / nrm ** 2,
+             "device_status": tde.get_info(ws)}
+        if n == 2048:
+            t0 = time.perf_counter()
+            ref = oracle.dense_eigvals(a)
+            r["oracle_cpu_ms"] = (time.perf_counter() - t0) * 1e3
+            r["max_err_vs_oracle_over_gate"] = float(np.abs(ln - ref).max() / (8 * n * np.finfo(float).eps * nrm))
+        res[f"n{n}"] = r
+    res["workload"] = "dense symmetric (G + G^T)/2, G iid N(0,1), seed 1"
+    return res
+
+
 def backward_section(args, dev) -> dict:
     """Config 4: 256 tridiagonals of order 8192 (d ~ N(0,1), e ~ |N(0,0.5)|), loss
     L = sum_i w_i lambda_i^2: forward (batched) and the hand-written adjoint, timed
@@ -604,9 +652,9 @@ def main():
                     help="eigenvalue indices per family per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched, backward and requested-row measurements")
-    ap.add_argument("--extras", default="batched,backward,rows",
-                    help="which extra measurements to run (comma list of batched, backward, rows)")
+                    help="skip the batched, backward, requested-row and dense measurements")
+    ap.add_argument("--extras", default="batched,backward,rows,dense",
+                    help="which extra measurements to run (comma list of batched, backward, rows, dense)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -94,6 +94,24 @@ int tde_eigvecs_rows(int64_t n, const double* d, const double* e, int64_t nsel,
                      const int64_t* rows, double* lambda, double* qrows, int32_t leaf, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* Bytes of workspace tde_dense_eigvals needs: 8 n^2 for the reduced copy of A, a
+ * few n-vectors, and the tridiagonal solver's workspace. */
+int tde_dense_eigvals_workspace(int64_t n, int32_t leaf, size_t* bytes);
+
+/* All eigenvalues of a dense symmetric matrix (the dense pipeline of Sec. 2: an
+ * orthogonal reduction A = Q T Q^T to tridiagonal form, then the boundary-row
+ * solver on T; Q is not kept).
+ *   A       [lda * n] device, read only; column j is A[j * lda .. j * lda + n).
+ *           Only the lower triangle of that column-major layout is read (the upper
+ *           triangle of a row-major array), so a full symmetric matrix may be passed
+ *           in either order.
+ *   lambda  [n] output, ascending
+ *   ws      tde_dense_eigvals_workspace bytes, 256-byte aligned, caller-owned
+ * Householder reflections, one column at a time: an FP64 sweep over the trailing
+ * lower triangle per column (4 FMAs per stored element), so about (2/3) n^3 FMAs. */
+int tde_dense_eigvals(int64_t n, const double* A, int64_t lda, double* lambda, int32_t leaf,
+                      void* ws, size_t ws_bytes, void* stream);
+
 /* Workspace for tde_eigvals_batched with the given packing (host offsets). */
 int tde_eigvals_batched_workspace(int64_t batch, const int64_t* offsets_host, int32_t leaf,
                                   size_t* bytes);

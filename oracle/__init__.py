@@ -213,6 +213,13 @@ def eigvec_rows(d, e, rows):
     return lam, q[np.asarray(rows, dtype=np.int64), :].copy()
 
 
+def dense_eigvals(a) -> np.ndarray:
+    """Eigenvalues (ascending) of a dense symmetric matrix (the problem the dense
+    pipeline of Sec. 2 solves), by LAPACK's symmetric eigensolver on the full matrix."""
+    a = np.asarray(a, dtype=np.float64)
+    return np.linalg.eigvalsh(0.5 * (a + a.T))
+
+
 def principal_block(d, e, rows) -> np.ndarray:
     """T[rows][:, rows] of tridiag(e, d, e), entry by entry from the definition of T
     (d on the diagonal, e_i between rows i and i+1, zero elsewhere)."""

@@ -171,6 +171,45 @@ def eigvecs_rows(d, e, rows, leaf: int = 0, out=None, qrows=None, ws: Workspace 
     return lam, q
 
 
+def dense_eigvals_workspace_bytes(n: int, leaf: int = 0) -> int:
+    """Bytes of workspace ``dense_eigvals`` needs (tde_dense_eigvals_workspace)."""
+    b = ctypes.c_size_t()
+    _lib.check("tde_dense_eigvals_workspace",
+               _lib.load().tde_dense_eigvals_workspace(int(n), int(leaf), ctypes.byref(b)))
+    return b.value
+
+
+def dense_eigvals(A, leaf: int = 0, out=None, ws: Workspace | None = None, stream=None,
+                  check: bool = True):
+    """All eigenvalues (ascending) of a dense symmetric float64 CUDA matrix A (n x n):
+    Householder reduction to tridiagonal form, then the boundary-row solver.  Only one
+    triangle is read (the upper one of the row-major tensor)."""
+    torch = _torch()
+    if not isinstance(A, torch.Tensor) or not A.is_cuda:
+        raise TypeError("A must be a CUDA tensor (the solver has no CPU path)")
+    if A.dtype != torch.float64:
+        raise TypeError("A must be float64")
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square matrix")
+    if A.stride(1) != 1 or A.stride(0) < A.shape[0]:
+        raise ValueError("A must have unit stride along its second dimension and rows of at least n")
+    n = A.shape[0]
+    lam = out if out is not None else torch.empty(n, dtype=torch.float64, device=A.device)
+    if n == 0:
+        return lam
+    need = dense_eigvals_workspace_bytes(n, leaf)
+    ws = Workspace(need, A.device) if ws is None else ws.ensure(need)
+    rc = _lib.load().tde_dense_eigvals(n, ctypes.c_void_p(A.data_ptr()), int(A.stride(0)),
+                                       ctypes.c_void_p(lam.data_ptr()), int(leaf),
+                                       ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream))
+    _lib.check("tde_dense_eigvals", rc)
+    if check:
+        info = get_info(ws, stream)
+        if info != 0:
+            raise TdeError("tde_dense_eigvals (device status)", info)
+    return lam
+
+
 def eigvals_batched(d, e, offsets, leaf: int = 0, out=None, ws: Workspace | None = None,
                     stream=None, check: bool = True, offsets_dev=None):
     """Eigenvalues of a packed batch: matrix k owns rows offsets[k]:offsets[k+1] of d,

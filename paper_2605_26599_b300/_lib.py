@@ -27,7 +27,7 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
            "tde_eigvals_noalloc", "tde_plan_query", "tde_check_reciprocal",
            "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning",
            "tde_eigvals_backward_workspace", "tde_eigvals_backward", "tde_eigvecs_rows_workspace",
-           "tde_eigvecs_rows")
+           "tde_eigvecs_rows", "tde_dense_eigvals_workspace", "tde_dense_eigvals")
 
 MAX_SEL_ROWS = 1024  # TDE_MAX_SEL_ROWS
 
@@ -66,6 +66,8 @@ def load() -> ctypes.CDLL:
     lib.tde_eigvals_batched.argtypes = [i64, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.tde_get_info.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int32)]
     lib.tde_eigvecs_rows_workspace.argtypes = [i64, i64, i32, szp]
+    lib.tde_dense_eigvals_workspace.argtypes = [i64, i32, szp]
+    lib.tde_dense_eigvals.argtypes = [i64, vp, i64, vp, i32, vp, sz, vp]
     lib.tde_eigvecs_rows.argtypes = [i64, vp, vp, i64, vp, vp, vp, i32, vp, sz, vp]
     lib.tde_measure_fp64_peak.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.tde_last_launch_count.restype = ctypes.c_int64

@@ -231,6 +231,40 @@ int tde_eigvecs_rows(int64_t n, const double* d, const double* e, int64_t nsel,
   return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
 }
 
+int tde_dense_eigvals_workspace(int64_t n, int32_t leaf, size_t* bytes) {
+  if (n < 0 || bytes == nullptr) return TDE_EINVAL;
+  int64_t off[2] = {0, n};
+  Plan p;
+  int rc = build_plan(1, off, leaf, &p);
+  if (rc != TDE_OK) return rc;
+  *bytes = dense_workspace(n, carve_workspace(p, nullptr, nullptr));
+  return TDE_OK;
+}
+
+int tde_dense_eigvals(int64_t n, const double* A, int64_t lda, double* lambda, int32_t leaf,
+                      void* ws, size_t ws_bytes, void* stream) {
+  g_launches = 0;
+  if (n < 0) return TDE_EINVAL;
+  if (n == 0) return TDE_OK;
+  if (A == nullptr || lambda == nullptr || ws == nullptr || lda < n) return TDE_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return TDE_EINVAL;
+  int64_t off[2] = {0, n};
+  Plan p;
+  int rc = build_plan(1, off, leaf, &p);
+  if (rc != TDE_OK) return rc;
+  const size_t tri = carve_workspace(p, nullptr, nullptr);
+  if (ws_bytes < dense_workspace(n, tri)) return TDE_EWORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double *d = nullptr, *e = nullptr;
+  rc = dense_reduce(n, A, lda, ws, tri, &d, &e, s);
+  if (rc != TDE_OK) return rc;
+  Workspace w;
+  carve_workspace(p, ws, &w);
+  k_set_offsets<<<1, 1, 0, s>>>(w.offsets, n);
+  g_launches += 1;
+  return run_solver(p, w, w.offsets, d, e, lambda, s);
+}
+
 int64_t tde_last_launch_count(void) { return g_launches; }
 
 int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min) {

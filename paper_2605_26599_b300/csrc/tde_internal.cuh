@@ -332,6 +332,13 @@ void launch_sel_rows(const Plan& plan, const Workspace& ws, const SelArgs& sa, i
                      cudaStream_t s);
 void launch_sel_place(const Plan& plan, const Workspace& ws, const SelArgs& sa, int step,
                       cudaStream_t s);
+// Dense symmetric front end (tde_dense.cu): tri_bytes of tridiagonal-solver
+// workspace (at offset 0) followed by the reduction's buffers; the reduction copies
+// A (leading dimension lda) into the workspace, reduces it and returns pointers to
+// d and e (e with n entries, the last zero).
+size_t dense_workspace(int64_t n, size_t tri_bytes);
+int dense_reduce(int64_t n, const double* A, int64_t lda, void* ws, size_t tri_bytes, double** d_out,
+                 double** e_out, cudaStream_t s);
 void launch_sel_gather(const SelArgs& sa, const int32_t* MAP, int64_t nsel, int64_t n,
                        double* qrows, cudaStream_t s);
 

@@ -137,6 +137,29 @@ def paper_clustered(n: int):
     return d, 1e-4 * (1.0 + 0.1 * np.cos(0.33 * j))
 
 
+def dense_goe(n: int, seed: int = 0):
+    """Dense symmetric (G + G^T) / 2 with G iid N(0, 1), float64, C order."""
+    g = np.random.default_rng(seed).standard_normal((n, n))
+    return 0.5 * (g + g.T)
+
+
+def dense_planted(n: int, seed: int = 0, reflectors: int = 4):
+    """(A, lam): A = H_k ... H_1 diag(lam) H_1 ... H_k with lam iid U(-1, 1) (sorted)
+    and k random Householder reflectors H = I - 2 u u^T / u^T u, so A is dense with a
+    spectrum known up to the rounding of forming it."""
+    rng = np.random.default_rng(seed)
+    lam = np.sort(rng.uniform(-1.0, 1.0, n))
+    a = np.diag(lam)
+    for _ in range(reflectors):
+        u = rng.standard_normal(n)
+        u /= np.linalg.norm(u)
+        au = a @ u
+        # H a H = a - 2 u (a u)^T - 2 (a u) u^T + 4 (u^T a u) u u^T
+        a = a - 2.0 * np.outer(u, au) - 2.0 * np.outer(au, u) + 4.0 * float(u @ au) * np.outer(u, u)
+    a = 0.5 * (a + a.T)
+    return a, lam
+
+
 FAMILIES = {
     "uniform11": uniform11,
     "toeplitz": lambda n, seed=0: toeplitz(n, 2.0, -1.0),

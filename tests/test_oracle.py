@@ -191,6 +191,24 @@ def test_eigvec_rows_invariants(oracle_mod, fam):
     assert np.abs((q * lam) @ q.T - blk).max() < 1e-13 * max(1.0, oracle_mod.norm1(d, e[: n - 1]))
 
 
+def test_dense_eigvals_planted_spectrum_and_invariants(oracle_mod):
+    # the dense oracle returns the spectrum planted by orthogonal similarity; trace and
+    # Frobenius norm are invariant under it
+    a, lam = inputs.dense_planted(120, seed=5)
+    assert np.abs(a - np.diag(np.diag(a))).max() > 1e-2  # genuinely dense
+    w = oracle_mod.dense_eigvals(a)
+    assert np.abs(w - lam).max() < 1e-13
+    assert abs(w.sum() - np.trace(a)) < 1e-12
+    assert abs((w ** 2).sum() - (a ** 2).sum()) < 1e-12
+
+
+def test_dense_eigvals_two_by_two_closed_form(oracle_mod):
+    p, q, r = 1.5, -0.25, 0.75  # [[p, q], [q, r]]: (p + r)/2 +- sqrt(((p - r)/2)^2 + q^2)
+    h = math.sqrt(((p - r) / 2) ** 2 + q * q)
+    w = oracle_mod.dense_eigvals(np.array([[p, q], [q, r]]))
+    assert np.allclose(w, [(p + r) / 2 - h, (p + r) / 2 + h], atol=1e-15, rtol=0)
+
+
 def test_merge_problem_boundary_sufficiency(oracle_mod):
     # Lemma "boundary sufficiency" + Eq. merge-problem: the spectrum of
     # diag(D) + rho' z z^T built from child boundary rows is the spectrum of T.
