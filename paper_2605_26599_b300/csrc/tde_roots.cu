@@ -98,21 +98,34 @@ struct SecState {
   SecSums s;
 };
 
-// FP64 start: midpoint sweep and the half-interval bracket; `sweep(dorg, tau, jl)`
-// evaluates the sums
-template <class Sweep>
-__device__ __forceinline__ void sec_init(const double* D, const double* Z, int K, int j, double rho,
-                                         double zsq, Sweep& sweep, SecState& q) {
+// FP64 start at the interval midpoint: sec_init_point sets the evaluation point
+// (origin j, or K-1 for the last root, and the half width), the caller sweeps
+// there, and sec_init_finish picks the origin (the nearer pole) from the sign of
+// w and sets the half-interval bracket.
+__device__ __forceinline__ void sec_init_point(const double* D, int K, int j, double rho, double zsq,
+                                               SecState& q) {
   q.rhoinv = 1.0 / rho;
   if (j < K - 1) {
     q.jl = j;
     q.jr = j + 1;
-    const double half = 0.5 * (D[j + 1] - D[j]);
-    q.s = sweep(D[j], half, q.jl);
-    q.w = q.rhoinv + q.s.psi + q.s.phi;
+    q.dorg = D[j];
+    q.tau = 0.5 * (D[j + 1] - D[j]);
+  } else {
+    q.jl = K - 2;
+    q.jr = K - 1;
+    q.org = K - 1;
+    q.dorg = D[K - 1];
+    q.tau = 0.5 * (rho * zsq);
+  }
+}
+
+__device__ __forceinline__ void sec_init_finish(const double* D, const double* Z, int K, int j,
+                                                double rho, double zsq, SecState& q) {
+  q.w = q.rhoinv + q.s.psi + q.s.phi;
+  if (j < K - 1) {
+    const double half = q.tau;
     if (q.w >= 0.0) {
       q.org = j;
-      q.tau = half;
       q.tlo = 0.0;
       q.thi = half;
     } else {
@@ -122,13 +135,7 @@ __device__ __forceinline__ void sec_init(const double* D, const double* Z, int K
       q.thi = 0.0;
     }
   } else {
-    q.jl = K - 2;
-    q.jr = K - 1;
-    q.org = K - 1;
     const double upper = rho * zsq;
-    q.tau = 0.5 * upper;
-    q.s = sweep(D[q.org], q.tau, q.jl);
-    q.w = q.rhoinv + q.s.psi + q.s.phi;
     if (q.w >= 0.0) {
       q.tlo = 0.0;
       q.thi = q.tau;
@@ -238,100 +245,133 @@ __device__ __forceinline__ int sec_step(SecState& q, double hw, bool third) {
 constexpr int kMaxSweeps = 64;
 constexpr int kMaxSweeps32 = 6;
 
-// Single-precision stage for root j, all of it in float.  On success fills q for
-// the FP64 stage (origin, tau, the whole interval as bracket) and *hw with w''/2
-// at tau, and returns true; *n32 receives the single-precision sweeps spent
-// either way.  It is skipped (false) where the float pair cannot resolve the
-// interval: width below 2^-28 of the pole magnitude.  `sw32(org, jl, tau)`
-// evaluates the sums.
-template <class Sweep32>
-__device__ __forceinline__ bool sec_stage32(const double* D, const double* Z, int K, int j, double rho,
-                                            double zsq, Sweep32& sw32, SecState& q, double* hw,
-                                            int* n32) {
-  *n32 = 0;
-  const int jl = (j < K - 1) ? j : K - 2, jr = jl + 1;
-  const double Dl = D[jl], Dr = D[jr];
+// Single-precision stage for root j, all of it in float, as steps that a driver
+// interleaves with its sweeps (`sw32(org, jl, tau)` evaluates the sums):
+//   s32_begin   applicability and the first point (interval midpoint); the stage is
+//               skipped where the float pair cannot resolve the interval (width
+//               below 2^-28 of the pole magnitude)
+//   s32_first   after the first sweep: the origin (nearer pole) and its bracket
+//   s32_step    one model step; false when the stage stops (no move, non-finite)
+//   s32_after   after the sweep at the new point: stop below 2^-10 |tau| or at
+//               kMaxSweeps32 sweeps
+//   s32_finish  on success fills q for the FP64 stage (origin, tau, the whole
+//               interval as bracket) and *hw with w''/2 at tau
+struct Stage32 {
+  int org, jl, jr, sweeps;
+  bool live;
+  float rhoinv, tau, tlo, thi, lo_int, hi_int, ol, orr, gap;
+  double dorg;
+  Sec32 s;
+};
+
+__device__ __forceinline__ bool s32_begin(const double* D, int K, int j, double rho, double zsq,
+                                          Stage32& st) {
+  st.jl = (j < K - 1) ? j : K - 2;
+  st.jr = st.jl + 1;
+  const double Dl = D[st.jl], Dr = D[st.jr];
   const double width = (j < K - 1) ? Dr - Dl : rho * zsq;
   if (!(width >= 0x1p-28 * fmax(fabs(Dl), fabs(Dr)))) return false;
-  const float rhoinv = float(1.0 / rho);
-  int org;
-  float tau, tlo, thi, lo_int, hi_int;  // stage bracket; interval of the root (tau of org)
-  Sec32 s;
+  st.rhoinv = float(1.0 / rho);
+  st.sweeps = 0;
+  st.live = false;
   if (j < K - 1) {
-    const float gap = float(width);
-    const float h32 = 0.5f * gap;
-    s = sw32(j, jl, h32);
-    if (rhoinv + s.psi + s.phi >= 0.0f) {
-      org = j;
-      tau = h32;
-      tlo = 0.0f;
-      thi = h32;
-      lo_int = 0.0f;
-      hi_int = gap;
-    } else {
-      org = j + 1;
-      tau = h32 - gap;
-      tlo = tau;
-      thi = 0.0f;
-      lo_int = -gap;
-      hi_int = 0.0f;
-    }
+    st.gap = float(width);
+    st.org = j;
+    st.tau = 0.5f * st.gap;
   } else {
-    org = K - 1;
-    hi_int = float(width);
-    lo_int = 0.0f;
-    tau = 0.5f * hi_int;
-    s = sw32(org, jl, tau);
-    tlo = 0.0f;
-    thi = hi_int;
+    st.org = K - 1;
+    st.hi_int = float(width);
+    st.lo_int = 0.0f;
+    st.tau = 0.5f * st.hi_int;
+    st.tlo = 0.0f;
+    st.thi = st.hi_int;
   }
-  int sweeps = 1;
-  const double dorg = D[org];
-  const float ol = float(Dl - dorg), orr = float(Dr - dorg);
-  for (;;) {
-    const float w = rhoinv + s.psi + s.phi;
-    if (!isfinite(w)) break;
-    if (w > 0.0f)
-      thi = fminf(thi, tau);
-    else
-      tlo = fmaxf(tlo, tau);
-    const float a = ol - tau, b = orr - tau;
-    float P1, P2;
-    if (!fit3(a, b, s.dpsi + s.dphi, s.hw, &P1, &P2)) {
-      P1 = s.dpsi;
-      P2 = s.dphi;
+  return true;
+}
+
+__device__ __forceinline__ void s32_first(const double* D, int K, int j, Stage32& st) {
+  st.sweeps = 1;
+  if (j < K - 1) {
+    const float h32 = st.tau;
+    if (st.rhoinv + st.s.psi + st.s.phi >= 0.0f) {
+      st.org = j;
+      st.tlo = 0.0f;
+      st.thi = h32;
+      st.lo_int = 0.0f;
+      st.hi_int = st.gap;
+    } else {
+      st.org = j + 1;
+      st.tau = h32 - st.gap;
+      st.tlo = st.tau;
+      st.thi = 0.0f;
+      st.lo_int = -st.gap;
+      st.hi_int = 0.0f;
     }
-    float eta = 0.0f;
-    const bool have = model_root(w, a, b, P1, P2, tau, tlo, thi, &eta);
-    const float nt = have ? tau + eta : 0.5f * (tlo + thi);
-    if (nt == tau || !(nt > lo_int && nt < hi_int)) break;  // no move: s is at tau
-    tau = nt;
-    s = sw32(org, jl, tau);
-    ++sweeps;
-    if ((have && fabsf(eta) <= 0x1p-10f * fabsf(nt)) || sweeps >= kMaxSweeps32) break;
   }
-  *n32 = sweeps;
-  if (!(isfinite(rhoinv + s.psi + s.phi) && isfinite(s.hw) && tau > lo_int && tau < hi_int))
+  st.dorg = D[st.org];
+  st.ol = float(D[st.jl] - st.dorg);
+  st.orr = float(D[st.jr] - st.dorg);
+  st.live = true;
+}
+
+__device__ __forceinline__ bool s32_step(Stage32& st, float* eta_out, bool* have_out) {
+  const float w = st.rhoinv + st.s.psi + st.s.phi;
+  if (!isfinite(w)) {
+    st.live = false;
     return false;
-  q.org = org;
-  q.jl = jl;
-  q.jr = jr;
-  q.tau = double(tau);
-  q.tlo = double(lo_int);
-  q.thi = double(hi_int);
+  }
+  if (w > 0.0f)
+    st.thi = fminf(st.thi, st.tau);
+  else
+    st.tlo = fmaxf(st.tlo, st.tau);
+  const float a = st.ol - st.tau, b = st.orr - st.tau;
+  float P1, P2;
+  if (!fit3(a, b, st.s.dpsi + st.s.dphi, st.s.hw, &P1, &P2)) {
+    P1 = st.s.dpsi;
+    P2 = st.s.dphi;
+  }
+  float eta = 0.0f;
+  const bool have = model_root(w, a, b, P1, P2, st.tau, st.tlo, st.thi, &eta);
+  const float nt = have ? st.tau + eta : 0.5f * (st.tlo + st.thi);
+  if (nt == st.tau || !(nt > st.lo_int && nt < st.hi_int)) {  // no move: s is at tau
+    st.live = false;
+    return false;
+  }
+  st.tau = nt;
+  *eta_out = eta;
+  *have_out = have;
+  return true;
+}
+
+__device__ __forceinline__ void s32_after(Stage32& st, float eta, bool have) {
+  ++st.sweeps;
+  if ((have && fabsf(eta) <= 0x1p-10f * fabsf(st.tau)) || st.sweeps >= kMaxSweeps32) st.live = false;
+}
+
+__device__ __forceinline__ bool s32_finish(const double* D, const double* Z, double rho,
+                                           const Stage32& st, SecState& q, double* hw) {
+  if (!(isfinite(st.rhoinv + st.s.psi + st.s.phi) && isfinite(st.s.hw) && st.tau > st.lo_int &&
+        st.tau < st.hi_int))
+    return false;
+  q.org = st.org;
+  q.jl = st.jl;
+  q.jr = st.jr;
+  q.tau = double(st.tau);
+  q.tlo = double(st.lo_int);
+  q.thi = double(st.hi_int);
   q.rhoinv = 1.0 / rho;
-  q.dorg = dorg;
-  q.zorg2 = Z[org] * Z[org];
-  q.ol = Dl - dorg;
-  q.orr = Dr - dorg;
+  q.dorg = st.dorg;
+  q.zorg2 = Z[st.org] * Z[st.org];
+  q.ol = D[st.jl] - st.dorg;
+  q.orr = D[st.jr] - st.dorg;
   q.exact = false;
   q.wprev = 0.0;
-  *hw = double(s.hw);
+  *hw = double(st.s.hw);
   return true;
 }
 
 // Solves root j; returns the number of FP64 pole sweeps (*n32 the single-precision
-// ones), *ok = false if capped.
+// ones), *ok = false if capped.  One root per caller (a warp or a thread).
 template <class Sweep, class Sweep32>
 __device__ int secular_root(const double* D, const double* Z, int K, int j, double rho, double zsq,
                             Sweep& sweep, Sweep32& sw32, int* org_out, double* tau_out, bool* ok,
@@ -345,12 +385,29 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
   }
   SecState q;
   double hw = 0.0;
-  const bool third = sec_stage32(D, Z, K, j, rho, zsq, sw32, q, &hw, n32);
+  Stage32 st;
+  bool third = false;
+  if (s32_begin(D, K, j, rho, zsq, st)) {
+    st.s = sw32(st.org, st.jl, st.tau);
+    s32_first(D, K, j, st);
+    for (;;) {
+      float eta = 0.0f;
+      bool have = false;
+      if (!s32_step(st, &eta, &have)) break;
+      st.s = sw32(st.org, st.jl, st.tau);
+      s32_after(st, eta, have);
+      if (!st.live) break;
+    }
+    *n32 = st.sweeps;
+    third = s32_finish(D, Z, rho, st, q, &hw);
+  }
   if (third) {
     q.s = sweep(q.dorg, q.tau, q.jl);
     q.w = q.rhoinv + q.s.psi + q.s.phi;
   } else {
-    sec_init(D, Z, K, j, rho, zsq, sweep, q);
+    sec_init_point(D, K, j, rho, zsq, q);
+    q.s = sweep(q.dorg, q.tau, q.jl);
+    sec_init_finish(D, Z, K, j, rho, zsq, q);
   }
   int sweeps = 1;
   while (sec_step(q, hw, third) == 1) {
@@ -365,6 +422,87 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
     q.s = sweep(q.dorg, q.tau, q.jl);
     q.w = q.rhoinv + q.s.psi + q.s.phi;
     ++sweeps;
+  }
+  *org_out = q.org;
+  *tau_out = q.tau;
+  return sweeps;
+}
+
+// Warp-synchronous form for kernels in which one warp solves several roots at a
+// time (one thread or G lanes per root; `valid` false for lanes without a root).
+// Every phase change and loop exit is a warp vote, so the roots of a warp run
+// each kind of sweep in the same rounds: an FP64 instruction costs the whole
+// warp's issue slot however few lanes are active, and roots at different phases
+// would otherwise pay for one another's sweeps.  Same steps and stopping rules as
+// secular_root; all 32 lanes must call it together.
+template <class Sweep, class Sweep32>
+__device__ int secular_root_sync(const double* D, const double* Z, int K, int j, double rho,
+                                 double zsq, bool valid, Sweep& sweep, Sweep32& sw32, int* org_out,
+                                 double* tau_out, bool* ok, int* n32) {
+  constexpr unsigned kFull = 0xffffffffu;
+  *ok = true;
+  *n32 = 0;
+  const bool act = valid && K > 1;
+  Stage32 st;
+  st.live = false;
+  const bool in32 = act && s32_begin(D, K, j, rho, zsq, st);
+  if (in32) {
+    st.s = sw32(st.org, st.jl, st.tau);
+    s32_first(D, K, j, st);
+  }
+  for (;;) {
+    float eta = 0.0f;
+    bool have = false;
+    const bool need = in32 && st.live && s32_step(st, &eta, &have);
+    if (!__any_sync(kFull, need)) break;
+    if (need) {
+      st.s = sw32(st.org, st.jl, st.tau);
+      s32_after(st, eta, have);
+    }
+  }
+  SecState q;
+  q.org = 0;
+  q.tau = 0.0;
+  double hw = 0.0;
+  bool third = false;
+  if (in32) {
+    *n32 = st.sweeps;
+    third = s32_finish(D, Z, rho, st, q, &hw);
+  }
+  if (act && !third) sec_init_point(D, K, j, rho, zsq, q);
+  if (act) q.s = sweep(q.dorg, q.tau, q.jl);
+  if (act) {
+    if (third)
+      q.w = q.rhoinv + q.s.psi + q.s.phi;
+    else
+      sec_init_finish(D, Z, K, j, rho, zsq, q);
+  }
+  int sweeps = act ? 1 : 0;
+  bool go = act;
+  for (;;) {
+    if (go) {
+      if (sec_step(q, hw, third) == 0) {
+        go = false;
+      } else if (sweeps >= kMaxSweeps) {
+        *ok = false;
+        go = false;
+      }
+    }
+    if (!__any_sync(kFull, go)) break;
+    if (go && third) {
+      hw = double(sw32(q.org, q.jl, float(q.tau)).hw);
+      ++*n32;
+    }
+    if (go) {
+      q.s = sweep(q.dorg, q.tau, q.jl);
+      q.w = q.rhoinv + q.s.psi + q.s.phi;
+      ++sweeps;
+    }
+  }
+  if (valid && K == 1) {
+    *org_out = 0;
+    *tau_out = rho * Z[0] * Z[0];
+    return 0;
   }
   *org_out = q.org;
   *tau_out = q.tau;
@@ -609,50 +747,65 @@ struct SecTally {
   }
 };
 
+// One thread per root.  The loop over roots advances a whole warp at a time (32
+// consecutive roots), which keeps every lane in step for the warp votes of
+// secular_root_sync.
 __global__ void k_secular_thread(RootArgs a) {
   const uint32_t total = *a.count;
   if (total < a.small_list_min) return;  // the warp kernel takes a short list
+  const int lane = threadIdx.x & 31;
   SecTally tally;
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < total; r += gridDim.x * blockDim.x) {
-    const int g = a.ROOTMAP[r];
-    const MState ms = a.ms[g];
-    const int j = int(r) - ms.base, lo = a.M[g].lo;
-    ThreadSweep sw{a.AD + lo, a.AZ + lo, ms.K};
-    ThreadSweep32 sw32{a.AD32 + lo, a.AZ32 + lo, ms.K};
-    int org, n32;
-    double tau;
-    bool ok;
-    const int sweeps =
-        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok, &n32);
-    secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, true);
-    tally.add(sweeps, n32, ms.K);
+  for (uint32_t base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; base < total;
+       base += gridDim.x * blockDim.x) {
+    const uint32_t r = base + lane;
+    const bool valid = r < total;
+    const int g = valid ? a.ROOTMAP[r] : 0;
+    const MState ms = valid ? a.ms[g] : MState{};
+    const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
+    ThreadSweep sw{a.AD + lo, a.AZ + lo, K};
+    ThreadSweep32 sw32{a.AD32 + lo, a.AZ32 + lo, K};
+    int org = 0, n32 = 0;
+    double tau = 0.0;
+    bool ok = true;
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw, sw32,
+                                         &org, &tau, &ok, &n32);
+    if (valid) {
+      secular_store(a, lo, j, org, tau, sweeps, K, ok, true);
+      tally.add(sweeps, n32, K);
+    }
   }
   tally.flush(a.st);
 }
 
-// small-K list, G lanes per root (the host picks G from the step's merge order)
+// small-K list, G lanes per root (the host picks G from the step's merge order);
+// a warp takes 32 / G consecutive roots per round, in step for secular_root_sync.
 template <int G>
 __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
   const uint32_t total = *a.count;
   if (total < a.small_list_min) return;  // the warp kernel takes a short list
   const int lane = threadIdx.x & 31, gl = lane & (G - 1);
   const unsigned mask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
-  const uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const uint32_t ngrp = (gridDim.x * blockDim.x) / G;
+  const uint32_t per = 32 / G;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   SecTally tally;
-  for (uint32_t r = grp; r < total; r += ngrp) {
-    const int g = a.ROOTMAP[r];
-    const MState ms = a.ms[g];
-    const int j = int(r) - ms.base, lo = a.M[g].lo;
-    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, ms.K, gl, mask};
-    GroupSweep32<G> sw32{a.AD32 + lo, a.AZ32 + lo, ms.K, gl, mask};
-    int org, n32;
-    double tau;
-    bool ok;
-    const int sweeps =
-        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok, &n32);
-    secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, gl == 0);
-    tally.add(sweeps, n32, ms.K);
+  for (uint32_t base = gw * per; base < total; base += nw * per) {
+    const uint32_t r = base + uint32_t(lane) / G;
+    const bool valid = r < total;
+    const int g = valid ? a.ROOTMAP[r] : 0;
+    const MState ms = valid ? a.ms[g] : MState{};
+    const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
+    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, K, gl, mask};
+    GroupSweep32<G> sw32{a.AD32 + lo, a.AZ32 + lo, K, gl, mask};
+    int org = 0, n32 = 0;
+    double tau = 0.0;
+    bool ok = true;
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw, sw32,
+                                         &org, &tau, &ok, &n32);
+    if (valid) {
+      secular_store(a, lo, j, org, tau, sweeps, K, ok, gl == 0);
+      tally.add(sweeps, n32, K);
+    }
   }
   if (gl == 0) tally.flush(a.st);
 }
@@ -937,7 +1090,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   const int wgrid = 148 * 8;
   // lanes per root for the small-K list, from the largest merge order of the step
   const int64_t k0 = plan.step_maxsize[step];
-  const int G = k0 <= 24 ? 1 : (k0 <= 96 ? 4 : (k0 <= 384 ? 8 : 16));
+  const int G = k0 <= 24 ? 1 : 4;
   const int ggrid = int(std::min<int64_t>((nrows * G + 127) / 128, 148 * 16));
   prof_begin(kKSecular, s);
   switch (G) {
