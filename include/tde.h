@@ -141,15 +141,16 @@ int tde_eigvals_backward_workspace(int64_t batch, const int64_t* offsets_host, i
  *   lambda      [N]  output: the eigenvalues (may be NULL)
  *   grad_d      [N]  output: dL/dd
  *   grad_e      [N]  output: dL/de (entry at the last row of each matrix is 0)
- * Method: a forward pass that checkpoints the boundary-row state at every tree
- * level, then a reverse sweep over the merges (top-down) that rebuilds each
- * merge from its checkpoint and pulls the adjoints back through the placement,
+ * Method: a forward pass that checkpoints the boundary-row state and the secular
+ * roots at every tree level, then a reverse sweep over the merges (top-down) that
+ * rebuilds each merge from its checkpoints (the roots are restored, not solved
+ * again) and pulls the adjoints back through the placement,
  * the secular eigen-decomposition (implicit differentiation of every root and of
  * the Cauchy form of the boundary rows), the deflation and the formation of the
  * merge problem; the leaves use the adjoint of their full eigen-decomposition and
  * the tearing d -= |beta| of Eq. (1).  Deflation decisions and the tree are
  * constants of the differentiation.  Simple (distinct) eigenvalues are assumed.
- * Workspace: O(n log n) (3 n doubles of checkpoint per level). */
+ * Workspace: O(n log n) (5 n doubles of checkpoint per level). */
 int tde_eigvals_backward(int64_t batch, const int64_t* offsets_host, const int64_t* offsets_dev,
                          const double* d, const double* e, const double* grad_lambda,
                          double* lambda, double* grad_d, double* grad_e, int32_t leaf,

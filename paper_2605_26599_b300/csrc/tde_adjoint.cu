@@ -3,11 +3,12 @@
 //
 // Structure (a reverse sweep over the split tree, top-down):
 //   1. forward recomputation with a checkpoint of the boundary-row state (lambda,
-//      blo, bhi) at the input of every merge step;
+//      blo, bhi) at the input of every merge step and of the step's secular roots
+//      (tau, D_org);
 //   2. for every step from the top down: rebuild the step's merge internals from
-//      its checkpoint (form, deflation, secular roots, z-hat, rows at every merge,
-//      root merges included), then pull the adjoints of the parents' (lambda, blo,
-//      bhi) back through
+//      its checkpoints (form, deflation, the saved roots, z-hat, rows at every
+//      merge, root merges included), then pull the adjoints of the parents'
+//      (lambda, blo, bhi) back through
 //        - the ascending placement (a permutation),
 //        - the secular eigen-decomposition A = diag(D) + rho' z z^T = Y L Y^T,
 //          whose outputs are the roots L and the boundary rows blo = Y^T RLO,
@@ -46,7 +47,7 @@
 //      e_bar_cut -= sgn(beta) (d_bar of the two torn diagonal entries).
 // Deflation decisions, the tree and the scaling are constants of the
 // differentiation (eigenvalue derivatives are scale invariant).  Memory: the
-// checkpoints hold 3 n doubles per merge step (n log n overall); every other
+// checkpoints hold 5 n doubles per merge step (n log n overall); every other
 // buffer is O(n).
 #include <algorithm>
 
@@ -59,9 +60,10 @@ constexpr int kMaxBwdLeaf = 32;
 struct AdjWorkspace {
   Workspace fw;
   double* CK;                          // steps x 3 x N checkpoints
+  double* CR;                          // steps x 2 x N saved roots (tau, D_org)
   double *GL, *GBL, *GBH;              // adjoint of the current level's state
   double *ALB, *ABL, *ABH;             // adjoints of a merge's [active | deflated] outputs
-  double *RLT, *RAL, *RBE, *RGA, *RINU, *RC;  // per active root scalars (g, h, ..., 1/nu, c)
+  double *RLT, *RAL, *RBE, *RGA, *RINU, *RC;  // per active root: g, h, scratch, 1/nu, 2 lbar c + h
   double *PDB, *PZB, *PRLB, *PRHB;     // adjoints of the active poles
   double *MDB, *MZB, *MRLB, *MRHB;     // adjoints at the sorted merge positions
   double* RHOBAR;                      // per merge of a step: adjoint of rho'
@@ -84,6 +86,7 @@ size_t carve_adjoint(const Plan& plan, void* base, AdjWorkspace* aw) {
     return p;
   };
   w.CK = take(8 * N * 3 * size_t(std::max(plan.steps, 1)));
+  w.CR = take(8 * N * 2 * size_t(std::max(plan.steps, 1)));
   double** arrs[] = {&w.GL,  &w.GBL, &w.GBH, &w.ALB,  &w.ABL, &w.ABH, &w.RLT,  &w.RAL,
                      &w.RBE, &w.RGA, &w.RINU, &w.RC,  &w.PDB, &w.PZB, &w.PRLB, &w.PRHB,
                      &w.MDB, &w.MZB, &w.MRLB, &w.MRHB, &w.KBAR, &w.LAMOUT};
@@ -142,111 +145,95 @@ __device__ __forceinline__ double adj_warp_sum(double v) {
   return v;
 }
 
-// root r of both lists (large-K first)
-__device__ __forceinline__ int adj_list_merge(const AdjArgs& a, uint32_t r, int* in_list) {
-  const uint32_t nb = *a.count2;
-  if (r < nb) {
-    *in_list = int(r);
-    return a.ROOTMAP2[r];
-  }
-  *in_list = int(r - nb);
-  return a.ROOTMAP[r - nb];
-}
-
-// Per active root j: 1 / nu_j and c_j = z^T y_j (one sweep over the poles).
-__global__ void k_adj_roots(AdjArgs a) {
-  const uint32_t total = *a.count + *a.count2;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t r = warp; r < total; r += nwarps) {
-    int rl;
-    const int g = adj_list_merge(a, r, &rl);
-    const MState ms = a.ms[g];
-    const int K = ms.K, j = rl - ms.base, lo = a.M[g].lo;
-    const double dorg = a.DORG[lo + j], tau = a.TAU[lo + j];
-    double nu2 = 0.0, C = 0.0;
-    for (int i = lane; i < K; i += 32) {
-      const double zh = a.ZHAT[lo + i];
-      const double t = zh * rcp_refined((a.AD[lo + i] - dorg) - tau);
-      nu2 = fma(t, t, nu2);
-      C = fma(zh, t, C);
-    }
-    nu2 = adj_warp_sum(nu2);
-    C = adj_warp_sum(C);
-    if (lane == 0) {
-      const double inu = 1.0 / sqrt(nu2);
-      a.w.RINU[lo + j] = inu;
-      a.w.RC[lo + j] = C * inu;
-    }
-  }
-}
-
 // Per active root j, a sweep over the other roots k of its merge: g_j and h_j,
-// and the merge's rho' adjoint sum_j (lbar_j c_j^2 + c_j h_j / 2).
-__global__ void k_adj_pairs(AdjArgs a) {
-  const uint32_t total = *a.count + *a.count2;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t r = warp; r < total; r += nwarps) {
-    int rl;
-    const int g = adj_list_merge(a, r, &rl);
+// and the merge's rho' adjoint sum_j (lbar_j c_j^2 + c_j h_j / 2).  1 / nu_j comes
+// from the recomputed row kernels; c_j = zhat^T y_j = (1 / nu_j) sum_s zhat_s^2 /
+// (D_s - l_j) = -1 / (rho' nu_j), because the roots solve the secular equation
+// of zhat exactly (that is how zhat is built).  Per pair: the root difference,
+// a refined reciprocal and W_jk - W_kj; the factors of j are applied after the
+// sum.  Lane 0 also stores 2 lbar_j c_j + h_j, the z_bar coefficient of root j.
+// G lanes per root (an aligned power of two; G = 32: a warp), over the small-K
+// root list (big = 0) or the large-K one (big = 1).
+template <int G>
+__device__ __forceinline__ double adj_group_sum(double v, unsigned mask) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+  return v;
+}
+
+template <int G>
+__global__ void __launch_bounds__(128) k_adj_pairs(AdjArgs a, int big) {
+  const uint32_t total = big ? *a.count2 : *a.count;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const uint32_t ngrp = (gridDim.x * blockDim.x) / G;
+  for (uint32_t r = grp; r < total; r += ngrp) {
+    const int g = big ? a.ROOTMAP2[r] : a.ROOTMAP[r];
     const MState ms = a.ms[g];
-    const int K = ms.K, j = rl - ms.base, lo = a.M[g].lo;
+    const int K = ms.K, j = int(r) - ms.base, lo = a.M[g].lo;
     const double oj = a.DORG[lo + j], tj = a.TAU[lo + j];
     const double bl = a.ROWLO[lo + j], bh = a.ROWHI[lo + j];
     const double gbl = a.w.ABL[lo + j], gbh = a.w.ABH[lo + j];
-    const double inuj = a.w.RINU[lo + j];
     double gs = 0.0, hs = 0.0;
-    for (int k = lane; k < K; k += 32) {
+    for (int k = gl; k < K; k += G) {
       if (k == j) continue;
-      const double dl = (oj - a.DORG[lo + k]) + (tj - a.TAU[lo + k]);  // l_j - l_k
-      const double idl = 1.0 / dl;
-      const double wd = (bl * a.w.ABL[lo + k] + bh * a.w.ABH[lo + k]) -
-                        (a.ROWLO[lo + k] * gbl + a.ROWHI[lo + k] * gbh);  // W_jk - W_kj
-      gs -= wd * inuj * a.w.RINU[lo + k] * idl * idl;
-      hs -= wd * a.w.RC[lo + k] * idl;
+      const double idl = rcp_refined((oj - a.DORG[lo + k]) + (tj - a.TAU[lo + k]));  // 1/(l_j - l_k)
+      const double wd = fma(bl, a.w.ABL[lo + k], bh * a.w.ABH[lo + k]) -
+                        fma(a.ROWLO[lo + k], gbl, a.ROWHI[lo + k] * gbh);  // W_jk - W_kj
+      const double u = wd * a.w.RINU[lo + k] * idl;
+      gs = fma(u, idl, gs);
+      hs += u;
     }
-    gs = adj_warp_sum(gs);
-    hs = adj_warp_sum(hs);
-    if (lane == 0) {
-      a.w.RLT[lo + j] = gs;
-      a.w.RAL[lo + j] = hs;
-      const double c = a.w.RC[lo + j];
-      atomicAdd(&a.w.RHOBAR[g], a.w.ALB[lo + j] * c * c + 0.5 * c * hs);
+    gs = adj_group_sum<G>(gs, mask);
+    hs = adj_group_sum<G>(hs, mask);
+    if (gl == 0) {
+      const double inuj = a.w.RINU[lo + j];
+      const double gj = -inuj * gs;      // -sum_k W' / (nu_j nu_k (l_j - l_k)^2)
+      const double hj = hs / ms.rho;     // sum_k W' c_k / (l_k - l_j) with c_k = -inu_k / rho'
+      const double c = -inuj / ms.rho;
+      const double lb = a.w.ALB[lo + j];
+      a.w.RLT[lo + j] = gj;
+      a.w.RAL[lo + j] = hj;
+      a.w.RC[lo + j] = fma(2.0 * lb, c, hj);
+      atomicAdd(&a.w.RHOBAR[g], lb * c * c + 0.5 * c * hj);
     }
   }
 }
 
-// Per active pole s: adjoints of D_s, z_s (through zhat ~ z), RLO_s, RHI_s.
-__global__ void k_adj_poles(AdjArgs a) {
-  const uint32_t total = *a.count + *a.count2;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t r = warp; r < total; r += nwarps) {
-    int rl;
-    const int g = adj_list_merge(a, r, &rl);
+// Per active pole s: adjoints of D_s, z_s (through zhat ~ z), RLO_s, RHI_s, as
+// sums over the roots j with y_sj = t_sj / nu_j, t_sj = zhat_s / (D_s - l_j):
+//   D_bar = sum lbar_j y^2 + zhat_s sum g_j t,  z_bar = rho' sum y (2 lbar_j c_j + h_j),
+//   RLO_bar = sum blo_bar_j y,  RHI_bar = sum bhi_bar_j y.
+template <int G>
+__global__ void __launch_bounds__(128) k_adj_poles(AdjArgs a, int big) {
+  const uint32_t total = big ? *a.count2 : *a.count;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const unsigned mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const uint32_t grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const uint32_t ngrp = (gridDim.x * blockDim.x) / G;
+  for (uint32_t r = grp; r < total; r += ngrp) {
+    const int g = big ? a.ROOTMAP2[r] : a.ROOTMAP[r];
     const MState ms = a.ms[g];
-    const int K = ms.K, i = rl - ms.base, lo = a.M[g].lo;
+    const int K = ms.K, i = int(r) - ms.base, lo = a.M[g].lo;
     const double Di = a.AD[lo + i], zh = a.ZHAT[lo + i];
-    double db = 0.0, zb = 0.0, rlb = 0.0, rhb = 0.0;
-    for (int j = lane; j < K; j += 32) {
+    double s1 = 0.0, s2 = 0.0, zb = 0.0, rlb = 0.0, rhb = 0.0;
+    for (int j = gl; j < K; j += G) {
       const double t = zh * rcp_refined((Di - a.DORG[lo + j]) - a.TAU[lo + j]);
       const double y = t * a.w.RINU[lo + j];
-      const double lb = a.w.ALB[lo + j];
-      db += lb * y * y + zh * a.w.RLT[lo + j] * t;
-      zb += y * (2.0 * lb * a.w.RC[lo + j] + a.w.RAL[lo + j]);
+      s1 = fma(y * a.w.ALB[lo + j], y, s1);
+      s2 = fma(t, a.w.RLT[lo + j], s2);
+      zb = fma(y, a.w.RC[lo + j], zb);
       rlb = fma(a.w.ABL[lo + j], y, rlb);
       rhb = fma(a.w.ABH[lo + j], y, rhb);
     }
-    db = adj_warp_sum(db);
-    zb = adj_warp_sum(zb);
-    rlb = adj_warp_sum(rlb);
-    rhb = adj_warp_sum(rhb);
-    if (lane == 0) {
-      a.w.PDB[lo + i] = db;
+    s1 = adj_group_sum<G>(s1, mask);
+    s2 = adj_group_sum<G>(s2, mask);
+    zb = adj_group_sum<G>(zb, mask);
+    rlb = adj_group_sum<G>(rlb, mask);
+    rhb = adj_group_sum<G>(rhb, mask);
+    if (gl == 0) {
+      a.w.PDB[lo + i] = fma(zh, s2, s1);
       a.w.PZB[lo + i] = ms.rho * zb;
       a.w.PRLB[lo + i] = rlb;
       a.w.PRHB[lo + i] = rhb;
@@ -260,28 +247,35 @@ __global__ void k_adj_kappa(AdjArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-  for (int64_t p = warp; p < a.nrows; p += nwarps) {
-    const int64_t g = find_merge(a.M, a.cnt, p);
-    const Merge m = a.M[g];
-    if (p < m.lo || p >= m.hi) continue;
-    if (a.PFLAG[p] != 2) continue;
-    const int lo = m.lo;
-    const int K = a.ms[g].K;
-    const int idx = lo + a.OUTIDX[p];
-    const int ia = lo + a.KEEPIDX[p];
-    const double v = a.AD[idx], rl = a.ALO[idx], rh = a.AHI[idx];
-    const double gbl = a.w.ABL[idx], gbh = a.w.ABH[idx];
-    const double Da = a.AD[ia], za = a.ZHAT[ia];
-    double kb = 0.0;
-    for (int j = lane; j < K; j += 32) {
-      const double oj = a.DORG[lo + j], tj = a.TAU[lo + j];
-      const double y = za * rcp_refined((Da - oj) - tj) * a.w.RINU[lo + j];
-      const double num = (a.w.ABL[lo + j] * rl + a.w.ABH[lo + j] * rh) -
-                         (gbl * a.ROWLO[lo + j] + gbh * a.ROWHI[lo + j]);
-      kb += y * num / ((oj - v) + tj);
+  // 32 positions per warp round: a ballot of the rotation-deflated ones, each
+  // then swept by the whole warp
+  for (int64_t base = warp * 32; base < a.nrows; base += nwarps * 32) {
+    const int64_t pl = base + lane;
+    unsigned cand = __ballot_sync(0xffffffffu, pl < a.nrows && a.PFLAG[pl] == 2);
+    while (cand) {
+      const int64_t p = base + (__ffs(cand) - 1);
+      cand &= cand - 1;
+      const int64_t g = find_merge(a.M, a.cnt, p);
+      const Merge m = a.M[g];
+      if (p < m.lo || p >= m.hi) continue;  // a row outside this step's merges
+      const int lo = m.lo;
+      const int K = a.ms[g].K;
+      const int idx = lo + a.OUTIDX[p];
+      const int ia = lo + a.KEEPIDX[p];
+      const double v = a.AD[idx], rl = a.ALO[idx], rh = a.AHI[idx];
+      const double gbl = a.w.ABL[idx], gbh = a.w.ABH[idx];
+      const double Da = a.AD[ia], za = a.ZHAT[ia];
+      double kb = 0.0;
+      for (int j = lane; j < K; j += 32) {
+        const double oj = a.DORG[lo + j], tj = a.TAU[lo + j];
+        const double y = za * rcp_refined((Da - oj) - tj) * a.w.RINU[lo + j];
+        const double num = (a.w.ABL[lo + j] * rl + a.w.ABH[lo + j] * rh) -
+                           (gbl * a.ROWLO[lo + j] + gbh * a.ROWHI[lo + j]);
+        kb = fma(y * num, rcp_refined((oj - v) + tj), kb);
+      }
+      kb = adj_warp_sum(kb);
+      if (lane == 0) a.w.KBAR[p] = kb;
     }
-    kb = adj_warp_sum(kb);
-    if (lane == 0) a.w.KBAR[p] = kb;
   }
 }
 
@@ -615,6 +609,10 @@ int run_adjoint(const Plan& plan, const AdjWorkspace& w, const int64_t* offsets_
   for (int st = 0; st < plan.steps; ++st) {
     const LevelState out = st + 1 < plan.steps ? checkpoint(w, st + 1, N) : scratch;
     launch_step(plan, ws, st, lambda, s, checkpoint(w, st, N), out);
+    double* cr = w.CR + size_t(st) * 2 * size_t(N);
+    if (cudaMemcpyAsync(cr, ws.TAU, 8 * size_t(N), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(cr + N, ws.KEYA, 8 * size_t(N), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return TDE_ECUDA;
   }
   const int flat = int(std::min<int64_t>((N + 255) / 256, 148 * 8));
   k_adj_init<<<flat, 256, 0, s>>>(N, grad_lambda, w.GL, w.GBL, w.GBH, grad_e);
@@ -627,7 +625,9 @@ int run_adjoint(const Plan& plan, const AdjWorkspace& w, const int64_t* offsets_
     if (cudaMemsetAsync(&ws.status->root_count_big[st], 0, 4, s) != cudaSuccess) return TDE_ECUDA;
     if (cudaMemsetAsync(w.RHOBAR, 0, 8 * size_t(cnt), s) != cudaSuccess) return TDE_ECUDA;
     const LevelState in = checkpoint(w, st, N);
-    launch_step(plan, ws, st, lambda, s, in, scratch, /*recompute=*/true);
+    const double* cr = w.CR + size_t(st) * 2 * size_t(N);
+    const RootsCheckpoint roots{cr, cr + N};
+    launch_step(plan, ws, st, lambda, s, in, scratch, /*recompute=*/true, nullptr, w.RINU, &roots);
     AdjArgs a;
     a.M = M;
     a.cnt = cnt;
@@ -661,16 +661,18 @@ int run_adjoint(const Plan& plan, const AdjWorkspace& w, const int64_t* offsets_
     a.in = in;
     a.w = w;
     a.grad_e = grad_e;
+    const int ggrid = int(std::min<int64_t>((N * 4 + 127) / 128, 148 * 16));
     k_adj_place<<<flat, 256, 0, s>>>(a);
-    k_adj_roots<<<148 * 8, 128, 0, s>>>(a);
-    k_adj_pairs<<<148 * 8, 128, 0, s>>>(a);
-    k_adj_poles<<<148 * 8, 128, 0, s>>>(a);
+    k_adj_pairs<4><<<ggrid, 128, 0, s>>>(a, 0);
+    k_adj_pairs<32><<<148 * 8, 128, 0, s>>>(a, 1);
+    k_adj_poles<4><<<ggrid, 128, 0, s>>>(a, 0);
+    k_adj_poles<32><<<148 * 8, 128, 0, s>>>(a, 1);
     k_adj_kappa<<<148 * 8, 128, 0, s>>>(a);
     launch_form(plan, ws, st, in, s);  // restore D, z, RLO, RHI of the merge problem
     const int dgrid = int(std::min<int64_t>(cnt, 148 * 8));
     k_adj_deflate<<<dgrid, 256, 0, s>>>(a);
     k_adj_form<<<flat, 256, 0, s>>>(a);
-    g_launches += 8;
+    g_launches += 9;
   }
   // 3. leaves
   const int lgrid = int(std::min<int64_t>((plan.nleaves + 63) / 64, 148 * 32));

@@ -348,13 +348,24 @@ void launch_sel_gather(const SelArgs& sa, const int32_t* MAP, int64_t nsel, int6
 // the adjoint, which also forces z-hat and rows at root merges.  With `sel` the
 // requested eigenvector rows are carried through the step as well (z-hat and the
 // row update then run at root merges too).
+// Saved secular roots of one step (tau and D_org of every active root, at the
+// rows of its merge): the adjoint checkpoints them in its forward pass and
+// restores them when it rebuilds the step, instead of solving again.
+struct RootsCheckpoint {
+  const double* tau;
+  const double* dorg;
+};
 void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
                  LevelState in, LevelState out, bool recompute = false,
-                 const SelArgs* sel = nullptr);
+                 const SelArgs* sel = nullptr, double* rows_inu = nullptr,
+                 const RootsCheckpoint* roots = nullptr);
 void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in, cudaStream_t s);
-// secular, Lowner and boundary-row kernels of one step; returns the launch count
+// secular, Lowner and boundary-row kernels of one step; returns the launch count.
+// rows_inu (optional) receives 1 / nu_j, the inverse norm of every active root's
+// secular eigenvector, from the row kernels.
 int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s,
-                 bool all_merges = false);
+                 bool all_merges = false, double* rows_inu = nullptr,
+                 const RootsCheckpoint* roots = nullptr);
 
 // Reciprocal in about three FP64 fused multiply-adds: a hardware approximation r0
 // of 1/x refined by the third-order (Householder) step for 1/x,

@@ -625,7 +625,8 @@ void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in,
 }
 
 void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
-                 LevelState in, LevelState out, bool recompute, const SelArgs* sel) {
+                 LevelState in, LevelState out, bool recompute, const SelArgs* sel,
+                 double* rows_inu, const RootsCheckpoint* roots) {
   const Merge* M = ws.merges + plan.step_base[step];
   const int64_t cnt = plan.step_count[step];
   const int64_t nrows = plan.nrows;
@@ -677,7 +678,8 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
     prof_end(kKSel, s);
   }
   // form, deflate + roots
-  int launches = 2 + launch_roots(plan, ws, step, M, s, recompute || sel != nullptr);
+  int launches =
+      2 + launch_roots(plan, ws, step, M, s, recompute || sel != nullptr, rows_inu, roots);
   if (sel) {
     prof_begin(kKSelRows, s);
     launch_sel_rows(plan, ws, *sel, step, s);

@@ -40,6 +40,7 @@ struct RootArgs {
   Status* st;
   uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
   int all_merges;           // also build z-hat and rows at root merges (adjoint)
+  double* RINU;             // optional: 1 / nu_j of every active root (adjoint)
 };
 
 // ---------------------------------------------------------------------------
@@ -990,7 +991,7 @@ __global__ void k_rows_thread(RootArgs a) {
     const double* ZH = a.ZHAT + lo;
     const double* AL = a.ALO + lo;
     const double* AH = a.AHI + lo;
-    const double dorg = AD[a.ORG[lo + j]];
+    const double dorg = a.DORG[lo + j];
     const double tau = a.TAU[lo + j];
     double s2 = 0.0, sl = 0.0, sh = 0.0;
     for (int i = 0; i < K; ++i) {
@@ -1000,6 +1001,7 @@ __global__ void k_rows_thread(RootArgs a) {
       sh = fma(AH[i], t, sh);
     }
     const double inv = 1.0 / sqrt(s2);
+    if (a.RINU) a.RINU[lo + j] = inv;
     a.ROWLO[lo + j] = sl * inv;
     a.ROWHI[lo + j] = sh * inv;
     work_add(a.st, kWorkRowsPairs, unsigned(K));
@@ -1023,7 +1025,7 @@ __global__ void k_rows_warp(RootArgs a) {
     const double* ZH = a.ZHAT + lo;
     const double* AL = a.ALO + lo;
     const double* AH = a.AHI + lo;
-    const double dorg = AD[a.ORG[lo + j]];
+    const double dorg = a.DORG[lo + j];
     const double tau = a.TAU[lo + j];
     double s2 = 0.0, sl = 0.0, sh = 0.0, s2b = 0.0, slb = 0.0, shb = 0.0;
     int i = lane;
@@ -1048,6 +1050,7 @@ __global__ void k_rows_warp(RootArgs a) {
     sh = warp_sum(sh + shb);
     if (lane == 0) {
       const double inv = 1.0 / sqrt(s2);
+      if (a.RINU) a.RINU[lo + j] = inv;
       a.ROWLO[lo + j] = sl * inv;
       a.ROWHI[lo + j] = sh * inv;
     }
@@ -1057,9 +1060,27 @@ __global__ void k_rows_warp(RootArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Restores the saved roots of one step: tau, D_org and lambda = D_org + tau (the
+// same expression the secular kernels store) at the active rows of every merge.
+__global__ void k_restore_roots(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
+                                const MState* __restrict__ ms, RootsCheckpoint ck, double* TAU,
+                                double* DORG, double* LAMA) {
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < nrows;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = find_merge(M, cnt, p);
+    const Merge m = M[g];
+    if (p < m.lo || p >= m.hi || p - m.lo >= ms[g].K) continue;
+    const double tau = ck.tau[p], dorg = ck.dorg[p];
+    TAU[p] = tau;
+    DORG[p] = dorg;
+    LAMA[p] = dorg + tau;
+  }
+}
+
 int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M, cudaStream_t s,
-                 bool all_merges) {
+                 bool all_merges, double* rows_inu, const RootsCheckpoint* roots) {
   RootArgs ra;
+  ra.RINU = rows_inu;
   ra.M = M;
   ra.ms = ws.mstate;
   ra.ROOTMAP = ws.ROOTMAP;
@@ -1092,7 +1113,14 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   const int64_t k0 = plan.step_maxsize[step];
   const int G = k0 <= 24 ? 1 : 4;
   const int ggrid = int(std::min<int64_t>((nrows * G + 127) / 128, 148 * 16));
+  int launches = 2;
   prof_begin(kKSecular, s);
+  if (roots) {
+    const int fgrid = int(std::min<int64_t>((nrows + 255) / 256, 148 * 8));
+    k_restore_roots<<<fgrid, 256, 0, s>>>(M, plan.step_count[step], nrows, ws.mstate, *roots, ws.TAU,
+                                          reinterpret_cast<double*>(ws.KEYA), ws.D);
+    launches = 1;
+  } else {
   switch (G) {
     case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
     case 4: k_secular_group<4><<<ggrid, 128, 0, s>>>(ra); break;
@@ -1100,8 +1128,8 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
     default: k_secular_group<16><<<ggrid, 128, 0, s>>>(ra); break;
   }
   k_secular_warp<<<wgrid, 128, 0, s>>>(ra);
+  }
   prof_end(kKSecular, s);
-  int launches = 2;
   if (plan.step_has_nonroot[step] || all_merges) {
     prof_begin(kKLowner, s);
     k_lowner_thread<<<tgrid, 128, 0, s>>>(ra);
