@@ -29,7 +29,7 @@
 
 namespace tde {
 
-constexpr int kNT = 256;  // threads of the per-merge deflation block
+constexpr int kNT = 256;  // threads of the per-merge deflation block (small merges)
 
 // ---------------------------------------------------------------------------
 __global__ void k_form(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
@@ -311,13 +311,16 @@ struct DeflateArgs {
   int32_t warp_min_k;
 };
 
-__global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
-  __shared__ int sm_int[kNT / 32];
-  __shared__ double sm_dbl[kNT / 32];
-  __shared__ T4 s_agg[kNT / 32];
-  __shared__ int s_aggh[kNT / 32];
-  __shared__ T4 s_pre[kNT / 32];
-  __shared__ T4 s_incl[kNT];
+// One CTA of NT threads per merge: 256, or 1024 for steps with merges above
+// 8192 rows, where a single CTA walks the whole merge in NT-row chunks.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
+  __shared__ int sm_int[NT / 32];
+  __shared__ double sm_dbl[NT / 32];
+  __shared__ T4 s_agg[NT / 32];
+  __shared__ int s_aggh[NT / 32];
+  __shared__ T4 s_pre[NT / 32];
+  __shared__ T4 s_incl[NT];
   __shared__ unsigned long long s_key[kTile];
   __shared__ int32_t s_idx[kTile];
   __shared__ int s_flag;
@@ -337,15 +340,15 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
 
     // 1. tol = 8 eps max(max|D|, max|z|)   (D is sorted)
     double zm = 0.0;
-    for (int i = tid; i < n0; i += kNT) zm = fmax(zm, fabs(Z[i]));
-    zm = block_max<kNT>(zm, sm_dbl);
+    for (int i = tid; i < n0; i += NT) zm = fmax(zm, fabs(Z[i]));
+    zm = block_max<NT>(zm, sm_dbl);
     const double dmax = fmax(fabs(D[0]), fabs(D[n0 - 1]));
     const double tol = 8.0 * kEps * fmax(dmax, zm);
     const double tol2 = tol * tol;
 
     // 2. negligible z: rho' |z_i| <= tol deflates pole i with its rows unchanged
     int S = 0;
-    for (int c0 = 0; c0 < n0; c0 += kNT) {
+    for (int c0 = 0; c0 < n0; c0 += NT) {
       int i = c0 + tid;
       int keep = 0;
       if (i < n0) {
@@ -353,22 +356,22 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
         PFLAG[i] = keep ? 0 : 1;
       }
       int total;
-      int ex = block_excl_scan<kNT>(keep, sm_int, &total);
+      int ex = block_excl_scan<NT>(keep, sm_int, &total);
       if (keep) SURV[S + ex] = lo + i;
       S += total;
     }
     __syncthreads();
 
     // 3. close poles: run boundaries over the survivors
-    __shared__ double s_cw[kNT / 32], s_cdw[kNT / 32];
-    run_boundaries<kNT>(S, SURV, a.D, a.Z, tol2, RFLAG, s_cw, s_cdw);
+    __shared__ double s_cw[NT / 32], s_cdw[NT / 32];
+    run_boundaries<NT>(S, SURV, a.D, a.Z, tol2, RFLAG, s_cw, s_cdw);
     __syncthreads();
 
     // 4. emit: continuing survivors deflate in place, run ends become active poles
     T4 carry{0.0, 0.0, 0.0, 0.0};
     int K = 0;
     double zsq = 0.0;
-    for (int c0 = 0; c0 < S; c0 += kNT) {
+    for (int c0 = 0; c0 < S; c0 += NT) {
       const int k = c0 + tid;
       const bool valid = k < S;
       int pos = 0;
@@ -403,8 +406,8 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       }
       __syncthreads();
       if (warp == 0) {  // prefix of each warp: carry, then the warp aggregates before it
-        T4 inc = lane < kNT / 32 ? s_agg[lane] : T4{0.0, 0.0, 0.0, 0.0};
-        bool hh = lane < kNT / 32 ? s_aggh[lane] != 0 : true;
+        T4 inc = lane < NT / 32 ? s_agg[lane] : T4{0.0, 0.0, 0.0, 0.0};
+        bool hh = lane < NT / 32 ? s_aggh[lane] != 0 : true;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           T4 vo = t4_shfl_up(inc, o);
@@ -416,7 +419,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
         }
         const T4 pv = t4_shfl_up(inc, 1);
         const bool ph = __shfl_up_sync(0xffffffffu, hh, 1);
-        if (lane < kNT / 32) s_pre[lane] = lane == 0 ? carry : (ph ? pv : t4_add(carry, pv));
+        if (lane < NT / 32) s_pre[lane] = lane == 0 ? carry : (ph ? pv : t4_add(carry, pv));
       }
       __syncthreads();
       if (!h) v = t4_add(v, s_pre[warp]);
@@ -426,7 +429,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       bool runend = false;
       if (valid) runend = (k == S - 1) || RFLAG[k + 1] != 0;
       int ex_total;
-      int act = block_excl_scan<kNT>(runend ? 1 : 0, sm_int, &ex_total);
+      int act = block_excl_scan<NT>(runend ? 1 : 0, sm_int, &ex_total);
       double zact2 = 0.0;
       if (valid && !head) {
         // deflated by rotation against the run prefix `prev`
@@ -463,10 +466,10 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
         a.AHI[idx] = ah;
         zact2 = az * az;
       }
-      zsq += block_sum<kNT>(zact2, sm_dbl);
+      zsq += block_sum<NT>(zact2, sm_dbl);
       K += ex_total;
       // carry: inclusive value of the last survivor of this chunk
-      int last = min(kNT - 1, S - 1 - c0);
+      int last = min(NT - 1, S - 1 - c0);
       carry = s_incl[last];
       __syncthreads();
     }
@@ -477,12 +480,12 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
     int32_t* ZPOS = a.ZPOS + lo;  // SURV stays intact for the adjoint
     int32_t* RPOS = a.IDXA + lo;
     int FZ = 0, FR = 0;
-    for (int c0 = 0; c0 < n0; c0 += kNT) {
+    for (int c0 = 0; c0 < n0; c0 += NT) {
       const int i = c0 + tid;
       const int pf = i < n0 ? PFLAG[i] : 0;
       const int both = (pf == 1 ? 1 : 0) | (pf == 2 ? (1 << 16) : 0);
       int total;
-      const int ex = block_excl_scan<kNT>(both, sm_int, &total);
+      const int ex = block_excl_scan<NT>(both, sm_int, &total);
       if (pf == 1) ZPOS[FZ + (ex & 0xffff)] = i;
       if (pf == 2) RPOS[FR + (ex >> 16)] = i;
       FZ += total & 0xffff;
@@ -491,7 +494,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
     if (tid == 0) s_flag = 0;
     __syncthreads();
     // 6. sort the rotated ones by value if they are out of order
-    for (int k = tid; k + 1 < FR; k += kNT)
+    for (int k = tid; k + 1 < FR; k += NT)
       if (D[RPOS[k]] > D[RPOS[k + 1]]) s_flag = 1;
     __syncthreads();
     if (s_flag) {
@@ -499,14 +502,14 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
         atomicAdd(&a.st->work[kWorkSorts], 1ull);
         atomicAdd(&a.st->work[kWorkSortedEntries], (unsigned long long)FR);
       }
-      for (int k = tid; k < FR; k += kNT) a.KEYA[lo + k] = order_key(D[RPOS[k]]);
+      for (int k = tid; k < FR; k += NT) a.KEYA[lo + k] = order_key(D[RPOS[k]]);
       __syncthreads();
       const int which = block_sort(FR, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);
       if (which) RPOS = a.IDXB + lo;
     }
     __syncthreads();
     // 7. merge the two ascending lists into AD / ALO / AHI after the K active poles
-    for (int k = tid; k < FZ; k += kNT) {
+    for (int k = tid; k < FZ; k += NT) {
       const int pos = ZPOS[k];
       const double x = D[pos];
       int l = 0, h = FR;  // rotated entries strictly below x come first
@@ -520,7 +523,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
       a.AHI[dst] = RHI[pos];
       a.OUTIDX[lo + pos] = K + k + l;
     }
-    for (int k = tid; k < FR; k += kNT) {
+    for (int k = tid; k < FR; k += NT) {
       const int pos = RPOS[k];
       const double x = D[pos];
       int l = 0, h = FZ;  // negligible-z entries at or below x come first
@@ -541,7 +544,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
     {
       float2* AD32 = reinterpret_cast<float2*>(a.KEYB) + lo;
       float* AZ32 = reinterpret_cast<float*>(a.IDXB) + lo;
-      for (int k = tid; k < K; k += kNT) {
+      for (int k = tid; k < K; k += NT) {
         const double x = a.AD[lo + k];
         const float hi = __double2float_rn(x);
         AD32[k] = make_float2(hi, __double2float_rn(x - double(hi)));
@@ -569,7 +572,7 @@ __global__ void __launch_bounds__(kNT) k_deflate(DeflateArgs a) {
     }
     __syncthreads();
     int32_t* rmap = big ? a.ROOTMAP2 : a.ROOTMAP;
-    for (int j = tid; j < K; j += kNT) rmap[s_base + j] = int32_t(g);
+    for (int j = tid; j < K; j += NT) rmap[s_base + j] = int32_t(g);
     __syncthreads();
   }
 }
@@ -670,7 +673,10 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   da.warp_min_k = plan.tune.warp_min_k;
   const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
   prof_begin(kKDeflate, s);
-  k_deflate<<<def_grid, kNT, 0, s>>>(da);
+  if (plan.step_maxsize[step] > 8192)
+    k_deflate<1024><<<def_grid, 1024, 0, s>>>(da);
+  else
+    k_deflate<kNT><<<def_grid, kNT, 0, s>>>(da);
   prof_end(kKDeflate, s);
   if (sel) {
     prof_begin(kKSel, s);
