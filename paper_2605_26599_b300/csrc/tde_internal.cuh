@@ -32,7 +32,8 @@ constexpr double kEps = 2.220446049250313e-16;  // DBL_EPSILON = 2^-52
 // One merge of the split tree: children [lo, mid) and [mid, hi) (global rows).
 struct Merge {
   int32_t lo, mid, hi;
-  int32_t info;  // bits 0..30: matrix index; bit 31: root merge (roots only)
+  int32_t info;  // bits 0..28: matrix index; bit 29: first node of its tree level (left
+                 // spine); bit 30: last node of its level (right spine); bit 31: root merge
 };
 // One leaf [lo, hi) of matrix `mat`.  flags: 1 = torn at lo (d[lo] -= |e[lo-1]|),
 // 2 = torn at hi (d[hi-1] -= |e[hi-1]|), 4 = the leaf is the whole matrix.
@@ -62,6 +63,12 @@ struct Tuning {
 Tuning& thread_tuning();
 
 constexpr uint32_t kRootBit = 0x80000000u;
+// Rows a merge's ancestors need (Algorithm 1: sigma_v holds exactly the rows demanded
+// by ancestors): the left spine of a tree feeds only bhi upwards (its blo would
+// only ever reach the root's blo, which nothing reads), the right spine only blo.
+constexpr uint32_t kRightSpineBit = 0x40000000u;
+constexpr uint32_t kLeftSpineBit = 0x20000000u;
+constexpr uint32_t kMatMask = 0x1fffffffu;
 
 // Work counters accumulated on the device by every call (reset per call):
 enum WorkCounter {

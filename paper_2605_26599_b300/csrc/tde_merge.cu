@@ -607,7 +607,7 @@ __global__ void k_place(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
     }
     const int dst = lo + rank;
     if (uint32_t(m.info) & kRootBit) {
-      double s = __longlong_as_double((long long)sigma_bits[m.info & 0x7fffffff]);
+      double s = __longlong_as_double((long long)sigma_bits[uint32_t(m.info) & kMatMask]);
       int ex = (s > 0.0 && isfinite(s)) ? ilogb(s) : 0;
       out[dst] = ldexp(x, ex);
     } else {

@@ -27,6 +27,7 @@ thread_local int64_t g_launches = 0;
 
 int build_plan(int64_t batch, const int64_t* off, int32_t leaf, Plan* plan) {
   if (batch < 0 || (batch > 0 && off == nullptr) || plan == nullptr) return TDE_EINVAL;
+  if (batch > int64_t(kMatMask) + 1) return TDE_EINVAL;  // matrix index bits of Merge::info
   if (leaf == 0) leaf = 32;
   if (leaf < 1 || leaf > kMaxLeaf) return TDE_EINVAL;
   Plan p;
@@ -171,7 +172,8 @@ __global__ void k_plan_fill(const int64_t* __restrict__ off, PlanArgs a,
       m.lo = int32_t(o + ((i * n) >> h));
       m.hi = int32_t(o + (((i + 1) * n) >> h));
       m.mid = int32_t(o + (((2 * i + 1) * n) >> (h + 1)));
-      m.info = int32_t(k) | (h == 0 ? int32_t(kRootBit) : 0);
+      m.info = int32_t(uint32_t(k) | (h == 0 ? kRootBit : 0u) | (i == 0 ? kLeftSpineBit : 0u) |
+                       (i == (int64_t(1) << h) - 1 ? kRightSpineBit : 0u));
       merges[g] = m;
     } else {
       int64_t local = g - a.nmerges;

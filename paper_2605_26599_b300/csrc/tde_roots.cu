@@ -977,7 +977,30 @@ __global__ void k_lowner_warp(RootArgs a) {
 
 // ---------------------------------------------------------------------------
 // Parent boundary rows of active column j (Sec. 4.1): with y_j(i) proportional to
-// zhat_i / Delta_ij, R_parent(:, j) = R_child y_j / ||zhat / Delta_:j||.
+// zhat_i / Delta_ij, R_parent(:, j) = R_child y_j / ||zhat / Delta_:j||.  Only the
+// rows the merge's ancestors need are formed (kLeftSpineBit / kRightSpineBit;
+// both when all_merges asks for every merge's full state): MODE 3 both rows,
+// 1 the low row only, 2 the high row only -- 8 instead of 9 FP64 instructions
+// per pair on the two spines of every tree.
+__device__ __forceinline__ int rows_mode(const RootArgs& a, const Merge& m) {
+  if (a.all_merges) return 3;
+  const uint32_t f = uint32_t(m.info);
+  return ((f & kLeftSpineBit) ? 0 : 1) | ((f & kRightSpineBit) ? 0 : 2);
+}
+
+template <int MODE>
+__device__ __forceinline__ void rows_thread_sweep(const double* AD, const double* ZH, const double* AL,
+                                                  const double* AH, int K, double dorg, double tau,
+                                                  double& s2, double& sl, double& sh) {
+  s2 = sl = sh = 0.0;
+  for (int i = 0; i < K; ++i) {
+    const double t = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
+    s2 = fma(t, t, s2);
+    if (MODE & 1) sl = fma(AL[i], t, sl);
+    if (MODE & 2) sh = fma(AH[i], t, sh);
+  }
+}
+
 __global__ void k_rows_thread(RootArgs a) {
   const uint32_t total = *a.count;
   if (total < a.small_list_min) return;
@@ -993,12 +1016,11 @@ __global__ void k_rows_thread(RootArgs a) {
     const double* AH = a.AHI + lo;
     const double dorg = a.DORG[lo + j];
     const double tau = a.TAU[lo + j];
-    double s2 = 0.0, sl = 0.0, sh = 0.0;
-    for (int i = 0; i < K; ++i) {
-      const double t = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
-      s2 = fma(t, t, s2);
-      sl = fma(AL[i], t, sl);
-      sh = fma(AH[i], t, sh);
+    double s2, sl, sh;
+    switch (rows_mode(a, m)) {
+      case 1: rows_thread_sweep<1>(AD, ZH, AL, AH, K, dorg, tau, s2, sl, sh); break;
+      case 2: rows_thread_sweep<2>(AD, ZH, AL, AH, K, dorg, tau, s2, sl, sh); break;
+      default: rows_thread_sweep<3>(AD, ZH, AL, AH, K, dorg, tau, s2, sl, sh); break;
     }
     const double inv = 1.0 / sqrt(s2);
     if (a.RINU) a.RINU[lo + j] = inv;
@@ -1006,6 +1028,34 @@ __global__ void k_rows_thread(RootArgs a) {
     a.ROWHI[lo + j] = sh * inv;
     work_add(a.st, kWorkRowsPairs, unsigned(K));
   }
+}
+
+// lanes stride over the poles, two independent chains per lane
+template <int MODE>
+__device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* ZH, const double* AL,
+                                                const double* AH, int K, int lane, double dorg,
+                                                double tau, double& s2o, double& slo, double& sho) {
+  double s2 = 0.0, sl = 0.0, sh = 0.0, s2b = 0.0, slb = 0.0, shb = 0.0;
+  int i = lane;
+  for (; i + 32 < K; i += 64) {
+    const double t0 = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
+    const double t1 = ZH[i + 32] * rcp_refined((AD[i + 32] - dorg) - tau);
+    s2 = fma(t0, t0, s2);
+    if (MODE & 1) sl = fma(AL[i], t0, sl);
+    if (MODE & 2) sh = fma(AH[i], t0, sh);
+    s2b = fma(t1, t1, s2b);
+    if (MODE & 1) slb = fma(AL[i + 32], t1, slb);
+    if (MODE & 2) shb = fma(AH[i + 32], t1, shb);
+  }
+  for (; i < K; i += 32) {
+    const double t0 = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
+    s2 = fma(t0, t0, s2);
+    if (MODE & 1) sl = fma(AL[i], t0, sl);
+    if (MODE & 2) sh = fma(AH[i], t0, sh);
+  }
+  s2o = warp_sum(s2 + s2b);
+  slo = (MODE & 1) ? warp_sum(sl + slb) : 0.0;
+  sho = (MODE & 2) ? warp_sum(sh + shb) : 0.0;
 }
 
 __global__ void k_rows_warp(RootArgs a) {
@@ -1027,27 +1077,12 @@ __global__ void k_rows_warp(RootArgs a) {
     const double* AH = a.AHI + lo;
     const double dorg = a.DORG[lo + j];
     const double tau = a.TAU[lo + j];
-    double s2 = 0.0, sl = 0.0, sh = 0.0, s2b = 0.0, slb = 0.0, shb = 0.0;
-    int i = lane;
-    for (; i + 32 < K; i += 64) {
-      const double t0 = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
-      const double t1 = ZH[i + 32] * rcp_refined((AD[i + 32] - dorg) - tau);
-      s2 = fma(t0, t0, s2);
-      sl = fma(AL[i], t0, sl);
-      sh = fma(AH[i], t0, sh);
-      s2b = fma(t1, t1, s2b);
-      slb = fma(AL[i + 32], t1, slb);
-      shb = fma(AH[i + 32], t1, shb);
+    double s2, sl, sh;
+    switch (rows_mode(a, m)) {
+      case 1: rows_warp_sweep<1>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
+      case 2: rows_warp_sweep<2>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
+      default: rows_warp_sweep<3>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
     }
-    for (; i < K; i += 32) {
-      const double t0 = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
-      s2 = fma(t0, t0, s2);
-      sl = fma(AL[i], t0, sl);
-      sh = fma(AH[i], t0, sh);
-    }
-    s2 = warp_sum(s2 + s2b);
-    sl = warp_sum(sl + slb);
-    sh = warp_sum(sh + shb);
     if (lane == 0) {
       const double inv = 1.0 / sqrt(s2);
       if (a.RINU) a.RINU[lo + j] = inv;
@@ -1059,7 +1094,6 @@ __global__ void k_rows_warp(RootArgs a) {
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkRowsPairs], (unsigned long long)pairs);
 }
 
-// ---------------------------------------------------------------------------
 // Restores the saved roots of one step: tau, D_org and lambda = D_org + tau (the
 // same expression the secular kernels store) at the active rows of every merge.
 __global__ void k_restore_roots(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
