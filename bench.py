@@ -370,6 +370,8 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         extras["eigvec_rows"] = rows_section(args, dev, fma_per_s)
     if "dense" in which:
         extras["dense"] = dense_section(args, dev, fma_per_s)
+    if "context" in which:
+        extras["paper_context"] = context_section(args, dev)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -559,6 +561,50 @@ def dense_section(args, dev, fma_per_s: float) -> dict:
     return res
 
 
+# The paper's GPU table (Sec. 5, H100 PCIe, values-only D&C, N = 49152): its families
+# and milliseconds, for context only (different matrices: its generator is not
+# reproducible; different GPU).
+PAPER_H100_MS = {"paper_normal": 78.73, "paper_uniform": 85.75, "toeplitz025": 480.81,
+                 "paper_clustered": 697.22}
+
+
+def context_section(args, dev) -> dict:
+    """The paper's four GPU families at N = 49152 with its protocol (2 warm-up, 5 timed
+    runs, mean), beside its H100 milliseconds; max error against sampled oracle
+    eigenvalues in units of the 8 N eps ||T||_1 gate."""
+    import torch
+
+    import oracle
+    import paper_2605_26599_b300 as tde
+
+    n = 49152
+    res = {"n": n, "leaf": args.leaf, "protocol": "2 warm-up + 5 timed runs, mean, CUDA events"}
+    for fam, h100 in PAPER_H100_MS.items():
+        d, e = inputs.family(fam, n, seed=0)
+        e = e[: n - 1]
+        dt = torch.from_numpy(d).to(dev)
+        et = torch.from_numpy(np.concatenate([e, [0.0]])).to(dev)
+        ws = tde.Workspace(tde.workspace_bytes(n, args.leaf), dev)
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            tde.eigvals(dt, et, leaf=args.leaf, out=lam, ws=ws)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record()
+        for _ in range(5):
+            tde.eigvals(dt, et, leaf=args.leaf, out=lam, ws=ws, check=False)
+        ev[1].record()
+        torch.cuda.synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / 5
+        ks = np.unique(np.concatenate([np.linspace(0, n - 1, 64).astype(np.int64), [0, 1, n - 2, n - 1]]))
+        ref = oracle.eigvals_select(d, e, ks)
+        err = float(np.abs(np.sort(lam.cpu().numpy())[ks] - ref).max())
+        res[fam] = {"ms": ms, "paper_h100_ms": h100, "h100_over_b300": h100 / ms,
+                    "max_err_over_gate_sampled": err / (8 * n * np.finfo(float).eps * oracle.norm1(d, e)),
+                    "device_status": tde.get_info(ws)}
+    return res
+
+
 def backward_section(args, dev) -> dict:
     """Config 4: 256 tridiagonals of order 8192 (d ~ N(0,1), e ~ |N(0,0.5)|), loss
     L = sum_i w_i lambda_i^2: forward (batched) and the hand-written adjoint, timed
@@ -652,9 +698,10 @@ def main():
                     help="eigenvalue indices per family per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the batched, backward, requested-row and dense measurements")
-    ap.add_argument("--extras", default="batched,backward,rows,dense",
-                    help="which extra measurements to run (comma list of batched, backward, rows, dense)")
+                    help="skip every extra measurement (see --extras)")
+    ap.add_argument("--extras", default="batched,backward,rows,dense,context",
+                    help="which extra measurements to run (comma list of batched, backward, rows, "
+                         "dense, context)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
