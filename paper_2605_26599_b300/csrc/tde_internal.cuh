@@ -48,6 +48,7 @@ struct MState {
   double zsq;    // sum of active z^2
   int32_t big;   // 1: roots in the warp-per-root list (K >= warp_min_k)
   int32_t surv;  // survivors of the negligible-z test (active + rotation-deflated)
+  double shift;  // the active poles' single-precision copies hold D - shift (their midrange)
 };
 
 // Launch-shape parameters chosen per call (tde_set_tuning; the Python autotuner

@@ -539,13 +539,16 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
     }
     __syncthreads();
     // 8. single-precision copies of the active poles for the first stage of the
-    //    secular solver: D_i as an unevaluated float pair hi + lo (about 48 bits)
-    //    and z_i rounded to float.  KEYB / IDXB held the sort scratch until here.
+    //    secular solver: D_i - shift as an unevaluated float pair hi + lo (about 48
+    //    bits relative to the spread of the merge's poles, not to their magnitude:
+    //    the offsets D_i - D_org the solver forms are shift-invariant) and z_i
+    //    rounded to float.  KEYB / IDXB held the sort scratch until here.
+    const double shift = K > 0 ? 0.5 * (a.AD[lo] + a.AD[lo + K - 1]) : 0.0;
     {
       float2* AD32 = reinterpret_cast<float2*>(a.KEYB) + lo;
       float* AZ32 = reinterpret_cast<float*>(a.IDXB) + lo;
       for (int k = tid; k < K; k += NT) {
-        const double x = a.AD[lo + k];
+        const double x = a.AD[lo + k] - shift;
         const float hi = __double2float_rn(x);
         AD32[k] = make_float2(hi, __double2float_rn(x - double(hi)));
         AZ32[k] = __double2float_rn(a.AZ[lo + k]);
@@ -566,6 +569,7 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
       st.zsq = zsq;
       st.big = big ? 1 : 0;
       st.surv = S;
+      st.shift = shift;
       a.ms[g] = st;
       atomicAdd(&a.st->work[kWorkDeflated], (unsigned long long)(n0 - K));
       atomicAdd(&a.st->work[kWorkRotations], (unsigned long long)(S - K));

@@ -250,7 +250,7 @@ constexpr int kMaxSweeps32 = 6;
 // interleaves with its sweeps (`sw32(org, jl, tau)` evaluates the sums):
 //   s32_begin   applicability and the first point (interval midpoint); the stage is
 //               skipped where the float pair cannot resolve the interval (width
-//               below 2^-28 of the pole magnitude)
+//               below 2^-28 of the shifted pole magnitude |D - shift|)
 //   s32_first   after the first sweep: the origin (nearer pole) and its bracket
 //   s32_step    one model step; false when the stage stops (no move, non-finite)
 //   s32_after   after the sweep at the new point: stop below 2^-10 |tau| or at
@@ -266,12 +266,12 @@ struct Stage32 {
 };
 
 __device__ __forceinline__ bool s32_begin(const double* D, int K, int j, double rho, double zsq,
-                                          Stage32& st) {
+                                          double shift, Stage32& st) {
   st.jl = (j < K - 1) ? j : K - 2;
   st.jr = st.jl + 1;
   const double Dl = D[st.jl], Dr = D[st.jr];
   const double width = (j < K - 1) ? Dr - Dl : rho * zsq;
-  if (!(width >= 0x1p-28 * fmax(fabs(Dl), fabs(Dr)))) return false;
+  if (!(width >= 0x1p-28 * fmax(fabs(Dl - shift), fabs(Dr - shift)))) return false;
   st.rhoinv = float(1.0 / rho);
   st.sweeps = 0;
   st.live = false;
@@ -375,8 +375,8 @@ __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, dou
 // ones), *ok = false if capped.  One root per caller (a warp or a thread).
 template <class Sweep, class Sweep32>
 __device__ int secular_root(const double* D, const double* Z, int K, int j, double rho, double zsq,
-                            Sweep& sweep, Sweep32& sw32, int* org_out, double* tau_out, bool* ok,
-                            int* n32) {
+                            double shift, Sweep& sweep, Sweep32& sw32, int* org_out,
+                            double* tau_out, bool* ok, int* n32) {
   *ok = true;
   *n32 = 0;
   if (K == 1) {
@@ -388,7 +388,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
   double hw = 0.0;
   Stage32 st;
   bool third = false;
-  if (s32_begin(D, K, j, rho, zsq, st)) {
+  if (s32_begin(D, K, j, rho, zsq, shift, st)) {
     st.s = sw32(st.org, st.jl, st.tau);
     s32_first(D, K, j, st);
     for (;;) {
@@ -438,15 +438,15 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
 // secular_root; all 32 lanes must call it together.
 template <class Sweep, class Sweep32>
 __device__ int secular_root_sync(const double* D, const double* Z, int K, int j, double rho,
-                                 double zsq, bool valid, Sweep& sweep, Sweep32& sw32, int* org_out,
-                                 double* tau_out, bool* ok, int* n32) {
+                                 double zsq, double shift, bool valid, Sweep& sweep, Sweep32& sw32,
+                                 int* org_out, double* tau_out, bool* ok, int* n32) {
   constexpr unsigned kFull = 0xffffffffu;
   *ok = true;
   *n32 = 0;
   const bool act = valid && K > 1;
   Stage32 st;
   st.live = false;
-  const bool in32 = act && s32_begin(D, K, j, rho, zsq, st);
+  const bool in32 = act && s32_begin(D, K, j, rho, zsq, shift, st);
   if (in32) {
     st.s = sw32(st.org, st.jl, st.tau);
     s32_first(D, K, j, st);
@@ -768,8 +768,8 @@ __global__ void k_secular_thread(RootArgs a) {
     int org = 0, n32 = 0;
     double tau = 0.0;
     bool ok = true;
-    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw, sw32,
-                                         &org, &tau, &ok, &n32);
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, ms.shift,
+                                         valid, sw, sw32, &org, &tau, &ok, &n32);
     if (valid) {
       secular_store(a, lo, j, org, tau, sweeps, K, ok, true);
       tally.add(sweeps, n32, K);
@@ -801,8 +801,8 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
     int org = 0, n32 = 0;
     double tau = 0.0;
     bool ok = true;
-    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw, sw32,
-                                         &org, &tau, &ok, &n32);
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, ms.shift,
+                                         valid, sw, sw32, &org, &tau, &ok, &n32);
     if (valid) {
       secular_store(a, lo, j, org, tau, sweeps, K, ok, gl == 0);
       tally.add(sweeps, n32, K);
@@ -846,7 +846,8 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     double tau;
     bool ok;
     const int sweeps =
-        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok, &n32);
+        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, ms.shift, sw, sw32, &org, &tau,
+                     &ok, &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
     tally.add(sweeps, n32, ms.K);
   }
