@@ -8,8 +8,10 @@ four single-matrix families of the n = 65536 workload back to back on one stream
 
 Printed as one JSON line (rank 0).  Besides the base keys it carries:
   roofline      dominant kernel's algorithmic FP64 rate (per-kernel CUDA events
-                inside the timed region, work from the device counters) against the
-                FP64 FMA peak measured in the same run (x2 flops / FMA)
+                inside the timed region, work from the device counters, FP64
+                operations per pair with an FMA or a reciprocal counted once)
+                against the FP64 FMA rate measured in the same run; the nominal
+                rate of the part is reported beside it
   cpu_baseline  the CPU oracle (Sturm bisection) on a bounded sample, host cores
   e2e           the same metric through the public API with pinned host inputs,
                 host->device copies and the device->host read of the eigenvalues
@@ -50,7 +52,14 @@ FAMILIES = ("a_uniform11", "b_toeplitz", "c_wilkinson", "d_glued_wilkinson")
 #                                 z t (1), accumulate (1), t t (1), accumulate (1)
 #   Lowner, per pair:             numerator (2), denominator (1), ratio (1), product (1)
 #   rows, per pair:               Delta (2), zhat / Delta (1), t^2 + acc (2), two row FMAs (4)
-FLOPS_PER_UNIT = {"secular": 7, "lowner": 5, "rows": 9}
+# Algorithmic work per (pole, root) pair, in FP64 operations with an add, multiply,
+# fused multiply-add, reciprocal or division each counted once: per secular sweep
+# 1 reciprocal + 4 (Delta, z^2 t, the psi and psi' sums); Lowner 1 division + 2;
+# boundary rows 1 reciprocal + 6 (Delta, zhat t, t^2, low row, high row, norm).
+OPS_PER_UNIT = {"secular": 5, "lowner": 3, "rows": 7}
+# nominal FP64 rate of the part (1.25 TFLOP/s, an FMA counting two), in operations per
+# second with an FMA counting one: 148 SMs x 2.032 GHz x about 2.08 FMA per SM clock
+NOMINAL_FP64_OPS = 0.625e12
 WORK_OF = {"secular": "secular_pairs", "lowner": "lowner_pairs", "rows": "rows_pairs"}
 
 
@@ -333,19 +342,23 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         return
     # roofline of the dominant kernel
     fma_per_s = tde.measure_fp64_peak()
-    peak_tflops = 2.0 * fma_per_s / 1e12
+    peak_tops = fma_per_s / 1e12  # FP64 operations per second, one per FMA
     ktimes = {k: v[0] / args.steps for k, v in kprof.items()}
     klaunch = {k: v[1] / args.steps for k, v in kprof.items()}
     total_k = sum(ktimes.values())
     dominant = max(ktimes, key=ktimes.get)
-    roof = {"bound": "alu", "kernel": dominant, "unit": "TFLOP/s", "peak": peak_tflops,
-            "peak_source": "FP64 FMA-chain microbenchmark run in this process (x2 flops/FMA); "
-                           "MEASURED_PEAKS.json carries no FP64 figure"}
-    if dominant in FLOPS_PER_UNIT:
-        flops = FLOPS_PER_UNIT[dominant] * work[WORK_OF[dominant]]
-        achieved = flops / (ktimes[dominant] * 1e-3) / 1e12
-        roof.update({"achieved": achieved, "frac": achieved / peak_tflops,
-                     "algorithmic_flops_per_step": flops,
+    roof = {"bound": "alu", "kernel": dominant, "unit": "T FP64 ops/s (FMA counted once)",
+            "peak": peak_tops,
+            "peak_source": "FP64 FMA-chain microbenchmark run in this process; "
+                           "MEASURED_PEAKS.json carries no FP64 figure",
+            "peak_nominal": NOMINAL_FP64_OPS / 1e12,
+            "ops_per_unit": OPS_PER_UNIT}
+    if dominant in OPS_PER_UNIT:
+        ops = OPS_PER_UNIT[dominant] * work[WORK_OF[dominant]]
+        achieved = ops / (ktimes[dominant] * 1e-3) / 1e12
+        roof.update({"achieved": achieved, "frac": achieved / peak_tops,
+                     "frac_nominal": achieved / (NOMINAL_FP64_OPS / 1e12),
+                     "algorithmic_ops_per_step": ops, "units_per_step": work[WORK_OF[dominant]],
                      "launches_per_step": klaunch[dominant],
                      "avg_launch_ms": ktimes[dominant] / max(klaunch[dominant], 1)})
     else:
@@ -353,11 +366,11 @@ def run_ours(args, rank: int, world: int, dist) -> None:
                      "note": f"dominant kernel {dominant} is not an FP64 pair kernel"})
     roof["traffic"] = load_traffic(dominant)
     kernel_rates = {}
-    for k in FLOPS_PER_UNIT:
+    for k in OPS_PER_UNIT:
         if ktimes.get(k, 0) > 0:
-            fl = FLOPS_PER_UNIT[k] * work[WORK_OF[k]]
-            kernel_rates[k] = {"ms_per_step": ktimes[k], "tflops": fl / (ktimes[k] * 1e-3) / 1e12,
-                               "frac_of_peak": fl / (ktimes[k] * 1e-3) / 1e12 / peak_tflops}
+            ops = OPS_PER_UNIT[k] * work[WORK_OF[k]]
+            kernel_rates[k] = {"ms_per_step": ktimes[k], "tops": ops / (ktimes[k] * 1e-3) / 1e12,
+                               "frac_of_peak": ops / (ktimes[k] * 1e-3) / 1e12 / peak_tops}
 
     cpu = cpu_baseline(n, fams) if (world == 1 and not args.no_cpu_baseline) else None
     extras = {}
