@@ -25,9 +25,13 @@
 //              root merge only the eigenvalues, unscaled, into the output.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "tde_internal.cuh"
 
 namespace tde {
+
+namespace cg = cooperative_groups;
 
 constexpr int kNT = 256;  // threads of the per-merge deflation block (small merges)
 
@@ -582,6 +586,479 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Deflation of a few large merges by thread-block clusters: the C CTAs of a
+// cluster share one merge, so its element-wise work (the FP64 run sums, rotations
+// and compaction of steps 2-5, 7-9 of k_deflate) is spread over C SMs instead of
+// one.  The steps and their results are those of k_deflate; what changes is how
+// the sequential pieces are cut:
+//   * compactions (steps 2 and 5) count per CTA slice, exchange the counts and
+//     write at the exclusive prefix of the CTAs before;
+//   * run boundaries (step 3): each warp of the cluster walks one segment of the
+//     survivors speculatively (k_deflate's rule), then all segments re-check their
+//     start against their predecessor's final carry in parallel rounds until no
+//     carry changes.  Segment 0 is exact, and a round in which segment s re-walks
+//     against an exact predecessor makes it exact, so at most one round per
+//     segment is needed (usually one in all);
+//   * the segmented run sums (step 4) take as carry-in the sum from the last run
+//     start in the CTAs before, from per-CTA aggregates;
+//   * the sort of rotated eigenvalues (step 6, rare) runs in CTA 0.
+// Values a CTA publishes live in its shared memory (ClusterSlot) and are read
+// through distributed shared memory after a cluster barrier; each field is
+// written once per merge and the merge loop ends with a barrier before reuse.
+struct ClusterSlot {
+  double zmax, zsq;
+  T4 agg;
+  int nkeep, nend, has_head, nz, nr, unsorted, which, base;
+  int changed[2];
+};
+
+// Cluster barrier after making this thread's global writes visible device-wide.
+__device__ __forceinline__ void cluster_sync_mem(cg::cluster_group& cl) {
+  __threadfence();
+  cl.sync();
+}
+
+// Sum of an int field over the ranks before r and over all C ranks, computed by
+// every warp on its own (lane q reads rank q).
+template <class F>
+__device__ __forceinline__ void cluster_scan_int(cg::cluster_group& cl, ClusterSlot& slot, int C,
+                                                 int r, F field, int* before, int* total) {
+  const int lane = threadIdx.x & 31;
+  int v = lane < C ? field(*cl.map_shared_rank(&slot, lane)) : 0;
+  int b = lane < r ? v : 0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v += __shfl_xor_sync(0xffffffffu, v, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  *before = b;
+  *total = v;
+}
+
+template <int NT>
+__device__ __forceinline__ int block_max_int(int v, int* sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = __reduce_max_sync(0xffffffffu, v);
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  int r = sm[0];
+  for (int w = 1; w < NT / 32; ++w) r = max(r, sm[w]);
+  __syncthreads();
+  return r;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
+  constexpr int NW = NT / 32;
+  __shared__ int sm_int[NW];
+  __shared__ double sm_dbl[NW];
+  __shared__ T4 s_agg[NW];
+  __shared__ int s_aggh[NW];
+  __shared__ T4 s_pre[NW];
+  __shared__ T4 s_incl[NT];
+  __shared__ unsigned long long s_key[kTile];
+  __shared__ int32_t s_idx[kTile];
+  __shared__ double s_cw[2][NW], s_cdw[2][NW];
+  __shared__ T4 s_carry;
+  __shared__ ClusterSlot slot;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = int(cl.num_blocks()), r = int(cl.block_rank());
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t ncl = gridDim.x / C;
+
+  for (int64_t g = blockIdx.x / C; g < a.cnt; g += ncl) {
+    const Merge m = a.M[g];
+    const int lo = m.lo, n0 = m.hi - m.lo;
+    const double rho = 2.0 * fabs(a.es[m.mid - 1]);
+    double* D = a.D + lo;
+    double* Z = a.Z + lo;
+    double* RLO = a.RLO + lo;
+    double* RHI = a.RHI + lo;
+    uint8_t* PFLAG = a.PFLAG + lo;
+    int32_t* SURV = a.SURV + lo;
+    uint8_t* RFLAG = a.RFLAG + lo;
+    const int L = (n0 + C - 1) / C;  // positions of this CTA: [eb, ee)
+    const int eb = min(n0, r * L), ee = min(n0, eb + L);
+
+    // 1. tol = 8 eps max(max|D|, max|z|)
+    double zm = 0.0;
+    for (int i = eb + tid; i < ee; i += NT) zm = fmax(zm, fabs(Z[i]));
+    zm = block_max<NT>(zm, sm_dbl);
+    if (tid == 0) slot.zmax = zm;
+    cl.sync();
+    zm = lane < C ? cl.map_shared_rank(&slot, lane)->zmax : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) zm = fmax(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+    const double dmax = fmax(fabs(D[0]), fabs(D[n0 - 1]));
+    const double tol = 8.0 * kEps * fmax(dmax, zm);
+    const double tol2 = tol * tol;
+
+    // 2. negligible z, compacted into SURV at the survivors of the CTAs before
+    int cnt = 0;
+    for (int c0 = eb; c0 < ee; c0 += NT) {
+      const int i = c0 + tid;
+      int keep = 0;
+      if (i < ee) {
+        keep = rho * fabs(Z[i]) > tol ? 1 : 0;
+        PFLAG[i] = keep ? 0 : 1;
+      }
+      cnt += __syncthreads_count(keep);
+    }
+    if (tid == 0) slot.nkeep = cnt;
+    cl.sync();
+    int off, S;
+    cluster_scan_int(cl, slot, C, r, [](const ClusterSlot& x) { return x.nkeep; }, &off, &S);
+    for (int c0 = eb; c0 < ee; c0 += NT) {
+      const int i = c0 + tid;
+      const int keep = (i < ee && rho * fabs(Z[i]) > tol) ? 1 : 0;
+      int total;
+      const int ex = block_excl_scan<NT>(keep, sm_int, &total);
+      if (keep) SURV[off + ex] = lo + i;
+      off += total;
+    }
+    cluster_sync_mem(cl);
+
+    // 3. run boundaries: speculative walk per warp segment, then parallel rounds
+    {
+      const int NS = C * NW;
+      const int seg = ((S + NS - 1) / NS + 31) & ~31;
+      const int sid = r * NW + warp;
+      const int b = min(S, sid * seg), e = min(S, b + seg);
+      double cW = 0.0, cDW = 0.0;
+      if (b < e) {
+        bool have = false;
+        if (b > 0) {
+          const int pos = SURV[b - 1];
+          const double z = a.Z[pos];
+          cW = z * z;
+          cDW = a.D[pos] * cW;
+          have = true;
+        }
+        run_segment(b, e, SURV, a.D, a.Z, tol2, RFLAG, cW, cDW, have, false);
+      }
+      if (lane == 0) {
+        s_cw[0][warp] = cW;
+        s_cdw[0][warp] = cDW;
+      }
+      cluster_sync_mem(cl);
+      int cur = 0;
+      bool converged = false;
+      for (int round = 0; round <= NS; ++round) {
+        double nW = s_cw[cur][warp], nDW = s_cdw[cur][warp];
+        bool changed = false;
+        if (b < e && sid > 0) {
+          const int pr = (sid - 1) / NW, pw = (sid - 1) % NW;
+          double W = cl.map_shared_rank(&s_cw[cur][0], pr)[pw];
+          double DW = cl.map_shared_rank(&s_cdw[cur][0], pr)[pw];
+          if (run_segment(b, e, SURV, a.D, a.Z, tol2, RFLAG, W, DW, true, true)) {
+            changed = __double_as_longlong(W) != __double_as_longlong(nW) ||
+                      __double_as_longlong(DW) != __double_as_longlong(nDW);
+            nW = W;
+            nDW = DW;
+          }
+        }
+        if (lane == 0) {
+          s_cw[cur ^ 1][warp] = nW;
+          s_cdw[cur ^ 1][warp] = nDW;
+        }
+        const int any = __syncthreads_or(changed ? 1 : 0);
+        if (tid == 0) slot.changed[round & 1] = any;
+        cluster_sync_mem(cl);
+        int anyc = lane < C ? cl.map_shared_rank(&slot, lane)->changed[round & 1] : 0;
+        anyc = __any_sync(0xffffffffu, anyc != 0) ? 1 : 0;
+        cur ^= 1;
+        if (!anyc) {
+          converged = true;
+          break;
+        }
+      }
+      if (!converged && r == 0 && tid == 0) set_status(a.st, TDE_ENOCONV);
+    }
+
+    // 4. emit over this CTA's survivors [sb, se): the carry-in is the run sum from
+    //    the last run start in the CTAs before
+    const int LS = (S + C - 1) / C;
+    const int sb = min(S, r * LS), se = min(S, sb + LS);
+    {
+      int hl = -1, nend = 0;
+      for (int c0 = sb; c0 < se; c0 += NT) {
+        const int k = c0 + tid;
+        bool end = false;
+        if (k < se) {
+          if (RFLAG[k] != 0) hl = k;
+          end = (k == S - 1) || RFLAG[k + 1] != 0;
+        }
+        nend += __syncthreads_count(end ? 1 : 0);
+      }
+      hl = block_max_int<NT>(hl, sm_int);
+      T4 acc{0.0, 0.0, 0.0, 0.0};
+      for (int k = max(hl, sb) + tid; k < se; k += NT) {
+        const int pos = SURV[k] - lo;
+        const double zk = Z[pos], wk = zk * zk;
+        acc = t4_add(acc, T4{wk, D[pos] * wk, zk * RLO[pos], zk * RHI[pos]});
+      }
+      acc.w = block_sum<NT>(acc.w, sm_dbl);
+      acc.dw = block_sum<NT>(acc.dw, sm_dbl);
+      acc.ulo = block_sum<NT>(acc.ulo, sm_dbl);
+      acc.uhi = block_sum<NT>(acc.uhi, sm_dbl);
+      if (tid == 0) {
+        slot.agg = acc;
+        slot.has_head = hl >= 0 ? 1 : 0;
+        slot.nend = nend;
+      }
+    }
+    cl.sync();
+    if (tid == 0) {
+      T4 c{0.0, 0.0, 0.0, 0.0};
+      for (int q = r - 1; q >= 0; --q) {
+        const ClusterSlot* p = cl.map_shared_rank(&slot, q);
+        c = t4_add(p->agg, c);
+        if (p->has_head) break;
+      }
+      s_carry = c;
+    }
+    int K, Ktot;
+    cluster_scan_int(cl, slot, C, r, [](const ClusterSlot& x) { return x.nend; }, &K, &Ktot);
+    __syncthreads();
+    T4 carry = s_carry;
+    double zsq = 0.0;
+    for (int c0 = sb; c0 < se; c0 += NT) {
+      const int k = c0 + tid;
+      const bool valid = k < se;
+      int pos = 0;
+      bool head = true;
+      double Dk = 0.0, zk = 0.0, rl = 0.0, rh = 0.0;
+      T4 own{0.0, 0.0, 0.0, 0.0};
+      if (valid) {
+        pos = SURV[k] - lo;
+        head = RFLAG[k] != 0;
+        Dk = D[pos];
+        zk = Z[pos];
+        rl = RLO[pos];
+        rh = RHI[pos];
+        double wk = zk * zk;
+        own = T4{wk, Dk * wk, zk * rl, zk * rh};
+      }
+      T4 v = own;
+      bool h = head;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        T4 vo = t4_shfl_up(v, o);
+        bool ho = __shfl_up_sync(0xffffffffu, h, o);
+        if (lane >= o) {
+          if (!h) v = t4_add(v, vo);
+          h = h || ho;
+        }
+      }
+      if (lane == 31) {
+        s_agg[warp] = v;
+        s_aggh[warp] = h ? 1 : 0;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        T4 inc = lane < NW ? s_agg[lane] : T4{0.0, 0.0, 0.0, 0.0};
+        bool hh = lane < NW ? s_aggh[lane] != 0 : true;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          T4 vo = t4_shfl_up(inc, o);
+          bool ho = __shfl_up_sync(0xffffffffu, hh, o);
+          if (lane >= o) {
+            if (!hh) inc = t4_add(inc, vo);
+            hh = hh || ho;
+          }
+        }
+        const T4 pv = t4_shfl_up(inc, 1);
+        const bool ph = __shfl_up_sync(0xffffffffu, hh, 1);
+        if (lane < NW) s_pre[lane] = lane == 0 ? carry : (ph ? pv : t4_add(carry, pv));
+      }
+      __syncthreads();
+      if (!h) v = t4_add(v, s_pre[warp]);
+      s_incl[tid] = v;
+      __syncthreads();
+      const T4 prev = (tid > 0) ? s_incl[tid - 1] : carry;
+      bool runend = false;
+      if (valid) runend = (k == S - 1) || RFLAG[k + 1] != 0;
+      int ex_total;
+      int act = block_excl_scan<NT>(runend ? 1 : 0, sm_int, &ex_total);
+      double zact2 = 0.0;
+      if (valid && !head) {
+        double Wp = prev.w, wk = own.w;
+        double c = prev.dw / Wp;
+        double val = (wk * c + Wp * Dk) / (Wp + wk);
+        double sc = 1.0 / sqrt(Wp * (Wp + wk));
+        D[pos] = val;
+        RLO[pos] = (zk * prev.ulo - Wp * rl) * sc;
+        RHI[pos] = (zk * prev.uhi - Wp * rh) * sc;
+        PFLAG[pos] = 2;
+        a.KEEPIDX[lo + pos] = K + act;
+      }
+      if (valid && runend) {
+        a.ACTMAP[lo + k] = K + act;
+        double ad, az, al, ah;
+        if (head) {
+          ad = Dk;
+          az = zk;
+          al = rl;
+          ah = rh;
+        } else {
+          double W = v.w;
+          az = sqrt(W);
+          ad = v.dw / W;
+          double inv = 1.0 / az;
+          al = v.ulo * inv;
+          ah = v.uhi * inv;
+        }
+        int idx = lo + K + act;
+        a.AD[idx] = ad;
+        a.AZ[idx] = az;
+        a.ALO[idx] = al;
+        a.AHI[idx] = ah;
+        zact2 = az * az;
+      }
+      zsq += block_sum<NT>(zact2, sm_dbl);
+      K += ex_total;
+      int last = min(NT - 1, se - 1 - c0);
+      carry = s_incl[last];
+      __syncthreads();
+    }
+    if (tid == 0) slot.zsq = zsq;
+    cluster_sync_mem(cl);
+    K = Ktot;
+    zsq = 0.0;
+    for (int q = 0; q < C; ++q) zsq += cl.map_shared_rank(&slot, q)->zsq;
+
+    // 5. deflated positions of each kind, in position order, over the CTA slices
+    int32_t* ZPOS = a.ZPOS + lo;
+    int32_t* RPOS = a.IDXA + lo;
+    {
+      int nz = 0, nr = 0;
+      for (int c0 = eb; c0 < ee; c0 += NT) {
+        const int i = c0 + tid;
+        const int pf = i < ee ? PFLAG[i] : 0;
+        nz += __syncthreads_count(pf == 1);
+        nr += __syncthreads_count(pf == 2);
+      }
+      if (tid == 0) {
+        slot.nz = nz;
+        slot.nr = nr;
+      }
+    }
+    cl.sync();
+    int FZ, FR, oz, orr;
+    cluster_scan_int(cl, slot, C, r, [](const ClusterSlot& x) { return x.nz; }, &oz, &FZ);
+    cluster_scan_int(cl, slot, C, r, [](const ClusterSlot& x) { return x.nr; }, &orr, &FR);
+    for (int c0 = eb; c0 < ee; c0 += NT) {
+      const int i = c0 + tid;
+      const int pf = i < ee ? PFLAG[i] : 0;
+      const int both = (pf == 1 ? 1 : 0) | (pf == 2 ? (1 << 16) : 0);
+      int total;
+      const int ex = block_excl_scan<NT>(both, sm_int, &total);
+      if (pf == 1) ZPOS[oz + (ex & 0xffff)] = i;
+      if (pf == 2) RPOS[orr + (ex >> 16)] = i;
+      oz += total & 0xffff;
+      orr += total >> 16;
+    }
+    cluster_sync_mem(cl);
+
+    // 6. sort the rotated ones by value if they are out of order (CTA 0)
+    {
+      int bad = 0;
+      for (int k = r * NT + tid; k + 1 < FR; k += C * NT)
+        if (D[RPOS[k]] > D[RPOS[k + 1]]) bad = 1;
+      bad = __syncthreads_or(bad);
+      if (tid == 0) slot.unsorted = bad;
+    }
+    cl.sync();
+    int unsorted = lane < C ? cl.map_shared_rank(&slot, lane)->unsorted : 0;
+    unsorted = __any_sync(0xffffffffu, unsorted != 0) ? 1 : 0;
+    if (unsorted) {
+      if (r == 0) {
+        if (tid == 0) {
+          atomicAdd(&a.st->work[kWorkSorts], 1ull);
+          atomicAdd(&a.st->work[kWorkSortedEntries], (unsigned long long)FR);
+        }
+        for (int k = tid; k < FR; k += NT) a.KEYA[lo + k] = order_key(D[RPOS[k]]);
+        __syncthreads();
+        const int which =
+            block_sort(FR, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);
+        if (tid == 0) slot.which = which;
+      }
+      cluster_sync_mem(cl);
+      if (cl.map_shared_rank(&slot, 0)->which) RPOS = a.IDXB + lo;
+    }
+
+    // 7. merge the two ascending lists after the K active poles
+    for (int k = r * NT + tid; k < FZ; k += C * NT) {
+      const int pos = ZPOS[k];
+      const double x = D[pos];
+      int l = 0, h = FR;
+      while (l < h) {
+        const int md = (l + h) >> 1;
+        if (D[RPOS[md]] < x) l = md + 1; else h = md;
+      }
+      const int dst = lo + K + k + l;
+      a.AD[dst] = x;
+      a.ALO[dst] = RLO[pos];
+      a.AHI[dst] = RHI[pos];
+      a.OUTIDX[lo + pos] = K + k + l;
+    }
+    for (int k = r * NT + tid; k < FR; k += C * NT) {
+      const int pos = RPOS[k];
+      const double x = D[pos];
+      int l = 0, h = FZ;
+      while (l < h) {
+        const int md = (l + h) >> 1;
+        if (D[ZPOS[md]] <= x) l = md + 1; else h = md;
+      }
+      const int dst = lo + K + k + l;
+      a.AD[dst] = x;
+      a.ALO[dst] = RLO[pos];
+      a.AHI[dst] = RHI[pos];
+      a.OUTIDX[lo + pos] = K + k + l;
+    }
+    cluster_sync_mem(cl);  // KEYB / IDXB (sort scratch, RPOS) are reused below
+
+    // 8. single-precision pole copies (k_deflate step 8)
+    const double shift = K > 0 ? 0.5 * (a.AD[lo] + a.AD[lo + K - 1]) : 0.0;
+    {
+      float2* AD32 = reinterpret_cast<float2*>(a.KEYB) + lo;
+      float* AZ32 = reinterpret_cast<float*>(a.IDXB) + lo;
+      for (int k = r * NT + tid; k < K; k += C * NT) {
+        const double x = a.AD[lo + k] - shift;
+        const float hi = __double2float_rn(x);
+        AD32[k] = make_float2(hi, __double2float_rn(x - double(hi)));
+        AZ32[k] = __double2float_rn(a.AZ[lo + k]);
+      }
+    }
+    // 9. root list range and merge state (CTA 0), then the root map
+    const bool big = K >= a.warp_min_k;
+    if (r == 0 && tid == 0) {
+      const int base = K > 0 ? int(atomicAdd(big ? &a.st->root_count_big[a.step]
+                                                 : &a.st->root_count[a.step],
+                                             unsigned(K)))
+                             : 0;
+      MState st;
+      st.K = K;
+      st.base = base;
+      st.rho = rho;
+      st.zsq = zsq;
+      st.big = big ? 1 : 0;
+      st.surv = S;
+      st.shift = shift;
+      a.ms[g] = st;
+      slot.base = base;
+      atomicAdd(&a.st->work[kWorkDeflated], (unsigned long long)(n0 - K));
+      atomicAdd(&a.st->work[kWorkRotations], (unsigned long long)(S - K));
+    }
+    cl.sync();
+    const int base = cl.map_shared_rank(&slot, 0)->base;
+    int32_t* rmap = big ? a.ROOTMAP2 : a.ROOTMAP;
+    for (int j = r * NT + tid; j < K; j += C * NT) rmap[base + j] = int32_t(g);
+    cl.sync();  // the slots are rewritten by the next merge
+  }
+}
+
+// ---------------------------------------------------------------------------
 __global__ void k_place(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
                         const MState* __restrict__ ms, const double* __restrict__ LAMA,
                         const double* __restrict__ ROWLO, const double* __restrict__ ROWHI,
@@ -631,6 +1108,65 @@ void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in,
                                    ws.D, ws.Z, ws.RLO, ws.RHI);
 }
 
+// Cluster size for steps with few large merges: as many CTAs per merge as fill the
+// SMs once (at most 16, the non-portable maximum, if a 16-CTA cluster of
+// 1024-thread CTAs fits this device; 8 otherwise).  0 selects the one-CTA kernels.
+static int deflate_cluster_size(int64_t cnt, int64_t maxsize) {
+  static int cmax = 0;
+  if (cmax == 0) {
+    cmax = 8;
+    if (cudaFuncSetAttribute(k_deflate_cluster<1024>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(1024);
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = 16;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      cfg.attrs = &at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_deflate_cluster<1024>, &cfg) ==
+              cudaSuccess &&
+          nclusters > 0)
+        cmax = 16;
+    }
+    cudaGetLastError();  // a refused query leaves no sticky error
+  }
+  if (maxsize < 1024 || cnt < 1) return 0;
+  int c = 1;
+  while (c < cmax && cnt * (2 * c) <= 148) c *= 2;
+  return c >= 2 ? c : 0;
+}
+
+void launch_deflate(const DeflateArgs& da, int64_t maxsize, cudaStream_t s) {
+  const int64_t cnt = da.cnt;
+  const int c = deflate_cluster_size(cnt, maxsize);
+  if (c > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(cnt * c));
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = unsigned(c);
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_deflate_cluster<1024>, da);
+    return;
+  }
+  const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
+  if (maxsize > 8192)
+    k_deflate<1024><<<def_grid, 1024, 0, s>>>(da);
+  else
+    k_deflate<kNT><<<def_grid, kNT, 0, s>>>(da);
+}
+
 void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
                  LevelState in, LevelState out, bool recompute, const SelArgs* sel,
                  double* rows_inu, const RootsCheckpoint* roots) {
@@ -675,12 +1211,8 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   da.ms = ws.mstate;
   da.st = ws.status;
   da.warp_min_k = plan.tune.warp_min_k;
-  const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
   prof_begin(kKDeflate, s);
-  if (plan.step_maxsize[step] > 8192)
-    k_deflate<1024><<<def_grid, 1024, 0, s>>>(da);
-  else
-    k_deflate<kNT><<<def_grid, kNT, 0, s>>>(da);
+  launch_deflate(da, plan.step_maxsize[step], s);
   prof_end(kKDeflate, s);
   if (sel) {
     prof_begin(kKSel, s);
