@@ -29,7 +29,8 @@ struct RootArgs {
   const uint32_t* count;    // lengths of the two lists (device)
   const uint32_t* count2;
   const double *AD, *AZ, *ALO, *AHI;
-  const float2* AD32;  // alias KEYB: active D as an unevaluated float pair (hi, lo)
+  const float2* AD32;  // alias KEYB: active D minus the merge's midrange as an unevaluated
+                       // float pair (hi, lo)
   const float* AZ32;   // alias IDXB: active z rounded to float
   double* TAU;
   int32_t* ORG;
@@ -65,9 +66,10 @@ struct RootArgs {
 //
 // Two precisions.  On this part an FP64 instruction costs about forty times the
 // issue slots of an FP32 one, so every root starts with a single-precision stage:
-// pole offsets from an unevaluated float pair per pole (D_i = hi + lo, about 48
-// bits, so D_i - D_org keeps its relative accuracy), hardware reciprocal
-// approximations and a compensated sum for w.  It starts at the midpoint of the
+// pole offsets from an unevaluated float pair per pole (D_i - shift = hi + lo with
+// the merge's midrange as shift, about 48 bits, so D_i - D_org keeps its relative
+// accuracy), hardware reciprocal approximations and a compensated sum for w, all
+// in units of the root's interval width so that the sums stay in the float range.  It starts at the midpoint of the
 // interval (whose sign of w chooses the origin, the nearer pole), iterates the
 // third-order model until the step is below 2^-10 |tau| and ends with one sweep at
 // the final tau, which also supplies w'' there.  The FP64 stage starts from that
@@ -78,9 +80,9 @@ struct RootArgs {
 // (2^-18)^3 |tau|), a two-term step below 2^-27 |tau| likewise (order
 // (2^-27)^2 |tau|).  Anything non-finite or a negative fitted weight sends a step
 // to the two-term model.  A root whose interval is narrower than 2^-28 of the
-// pole magnitude (where the float pair cannot resolve the offsets), or whose
-// single-precision stage fails, starts in FP64 at the midpoint and iterates with
-// the two-term model only.  Convergence: |w| below eps times a running bound on the
+// shifted pole magnitude |D - shift| (where the float pair cannot resolve the
+// offsets), or whose single-precision stage fails, starts in FP64 at the midpoint
+// and iterates with the two-term model only.  Convergence: |w| below eps times a running bound on the
 // rounding error of its evaluation, 8 (|psi| + |phi|) + 1/rho' + |tau| (psi' + phi').
 struct SecSums {
   double psi, dpsi, phi, dphi;
@@ -247,41 +249,50 @@ constexpr int kMaxSweeps = 64;
 constexpr int kMaxSweeps32 = 6;
 
 // Single-precision stage for root j, all of it in float, as steps that a driver
-// interleaves with its sweeps (`sw32(org, jl, tau)` evaluates the sums):
+// interleaves with its sweeps (`sw32(org, jl, tau, inv)` evaluates the sums):
 //   s32_begin   applicability and the first point (interval midpoint); the stage is
-//               skipped where the float pair cannot resolve the interval (width
-//               below 2^-28 of the shifted pole magnitude |D - shift|)
+//               skipped where the float copies cannot resolve the interval
+//               (`sw32.resolves`)
 //   s32_first   after the first sweep: the origin (nearer pole) and its bracket
-//   s32_step    one model step; false when the stage stops (no move, non-finite)
+//   s32_step    one model step; false when the stage stops (w at the float
+//               resolution, no move, non-finite)
 //   s32_after   after the sweep at the new point: stop below 2^-10 |tau| or at
 //               kMaxSweeps32 sweeps
 //   s32_finish  on success fills q for the FP64 stage (origin, tau, the whole
 //               interval as bracket) and *hw with w''/2 at tau
+// The stage works in units of S, the power of two at or below the root's interval
+// width (offsets and tau divided by S, w and its sums multiplied by S, so the
+// derivative sums of poles closer than 2^-40 stay inside the float range); inv is
+// 1/S.
 struct Stage32 {
   int org, jl, jr, sweeps;
   bool live;
-  float rhoinv, tau, tlo, thi, lo_int, hi_int, ol, orr, gap;
-  double dorg;
+  float rhoinv, tau, tlo, thi, lo_int, hi_int, ol, orr, gap, inv;
+  double dorg, S;
   Sec32 s;
 };
 
+template <class Sweep32>
 __device__ __forceinline__ bool s32_begin(const double* D, int K, int j, double rho, double zsq,
-                                          double shift, Stage32& st) {
+                                          const Sweep32& sw32, Stage32& st) {
   st.jl = (j < K - 1) ? j : K - 2;
   st.jr = st.jl + 1;
-  const double Dl = D[st.jl], Dr = D[st.jr];
-  const double width = (j < K - 1) ? Dr - Dl : rho * zsq;
-  if (!(width >= 0x1p-28 * fmax(fabs(Dl - shift), fabs(Dr - shift)))) return false;
-  st.rhoinv = float(1.0 / rho);
+  const double width = (j < K - 1) ? D[st.jr] - D[st.jl] : rho * zsq;
+  if (!(width >= 0x1p-90 && width <= 0x1p90) || !sw32.resolves(st.jl, st.jr, j == K - 1, width))
+    return false;
+  const int ex = ilogb(width);
+  st.S = ldexp(1.0, ex);
+  st.inv = ldexpf(1.0f, -ex);
+  st.rhoinv = float(st.S / rho);
   st.sweeps = 0;
   st.live = false;
   if (j < K - 1) {
-    st.gap = float(width);
+    st.gap = float(width / st.S);
     st.org = j;
     st.tau = 0.5f * st.gap;
   } else {
     st.org = K - 1;
-    st.hi_int = float(width);
+    st.hi_int = float(width / st.S);
     st.lo_int = 0.0f;
     st.tau = 0.5f * st.hi_int;
     st.tlo = 0.0f;
@@ -310,14 +321,20 @@ __device__ __forceinline__ void s32_first(const double* D, int K, int j, Stage32
     }
   }
   st.dorg = D[st.org];
-  st.ol = float(D[st.jl] - st.dorg);
-  st.orr = float(D[st.jr] - st.dorg);
+  st.ol = float((D[st.jl] - st.dorg) / st.S);
+  st.orr = float((D[st.jr] - st.dorg) / st.S);
   st.live = true;
 }
 
 __device__ __forceinline__ bool s32_step(Stage32& st, float* eta_out, bool* have_out) {
   const float w = st.rhoinv + st.s.psi + st.s.phi;
   if (!isfinite(w)) {
+    st.live = false;
+    return false;
+  }
+  // w at the resolution of the float sums: tau is as good as this stage gets (a
+  // model step would be below the rounding of tau), stop here with s at tau
+  if (fabsf(w) <= 0x1p-22f * (st.rhoinv + fabsf(st.s.psi) + fabsf(st.s.phi))) {
     st.live = false;
     return false;
   }
@@ -349,6 +366,18 @@ __device__ __forceinline__ void s32_after(Stage32& st, float eta, bool have) {
   if ((have && fabsf(eta) <= 0x1p-10f * fabsf(st.tau)) || st.sweeps >= kMaxSweeps32) st.live = false;
 }
 
+// w''/2 in natural units from its value in the stage's units (S^3 w''/2)
+__device__ __forceinline__ double hw_natural(const Stage32& st, float hws) {
+  const double inv = 1.0 / st.S;
+  return double(hws) * (inv * inv * inv);
+}
+
+// single-precision sweep at the FP64 stage's tau, for w''/2 (natural units)
+template <class Sweep32>
+__device__ __forceinline__ double hw_at(const Sweep32& sw32, const Stage32& st, const SecState& q) {
+  return hw_natural(st, sw32(q.org, q.jl, float(q.tau / st.S), st.inv).hw);
+}
+
 __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, double rho,
                                            const Stage32& st, SecState& q, double* hw) {
   if (!(isfinite(st.rhoinv + st.s.psi + st.s.phi) && isfinite(st.s.hw) && st.tau > st.lo_int &&
@@ -357,9 +386,9 @@ __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, dou
   q.org = st.org;
   q.jl = st.jl;
   q.jr = st.jr;
-  q.tau = double(st.tau);
-  q.tlo = double(st.lo_int);
-  q.thi = double(st.hi_int);
+  q.tau = double(st.tau) * st.S;
+  q.tlo = double(st.lo_int) * st.S;
+  q.thi = double(st.hi_int) * st.S;
   q.rhoinv = 1.0 / rho;
   q.dorg = st.dorg;
   q.zorg2 = Z[st.org] * Z[st.org];
@@ -367,7 +396,7 @@ __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, dou
   q.orr = D[st.jr] - st.dorg;
   q.exact = false;
   q.wprev = 0.0;
-  *hw = double(st.s.hw);
+  *hw = hw_natural(st, st.s.hw);
   return true;
 }
 
@@ -375,7 +404,7 @@ __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, dou
 // ones), *ok = false if capped.  One root per caller (a warp or a thread).
 template <class Sweep, class Sweep32>
 __device__ int secular_root(const double* D, const double* Z, int K, int j, double rho, double zsq,
-                            double shift, Sweep& sweep, Sweep32& sw32, int* org_out,
+                            Sweep& sweep, Sweep32& sw32, int* org_out,
                             double* tau_out, bool* ok, int* n32) {
   *ok = true;
   *n32 = 0;
@@ -388,14 +417,14 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
   double hw = 0.0;
   Stage32 st;
   bool third = false;
-  if (s32_begin(D, K, j, rho, zsq, shift, st)) {
-    st.s = sw32(st.org, st.jl, st.tau);
+  if (s32_begin(D, K, j, rho, zsq, sw32, st)) {
+    st.s = sw32(st.org, st.jl, st.tau, st.inv);
     s32_first(D, K, j, st);
     for (;;) {
       float eta = 0.0f;
       bool have = false;
       if (!s32_step(st, &eta, &have)) break;
-      st.s = sw32(st.org, st.jl, st.tau);
+      st.s = sw32(st.org, st.jl, st.tau, st.inv);
       s32_after(st, eta, have);
       if (!st.live) break;
     }
@@ -417,7 +446,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
       break;
     }
     if (third) {
-      hw = double(sw32(q.org, q.jl, float(q.tau)).hw);
+      hw = hw_at(sw32, st, q);
       ++*n32;
     }
     q.s = sweep(q.dorg, q.tau, q.jl);
@@ -438,7 +467,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
 // secular_root; all 32 lanes must call it together.
 template <class Sweep, class Sweep32>
 __device__ int secular_root_sync(const double* D, const double* Z, int K, int j, double rho,
-                                 double zsq, double shift, bool valid, Sweep& sweep, Sweep32& sw32,
+                                 double zsq, bool valid, Sweep& sweep, Sweep32& sw32,
                                  int* org_out, double* tau_out, bool* ok, int* n32) {
   constexpr unsigned kFull = 0xffffffffu;
   *ok = true;
@@ -446,9 +475,9 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
   const bool act = valid && K > 1;
   Stage32 st;
   st.live = false;
-  const bool in32 = act && s32_begin(D, K, j, rho, zsq, shift, st);
+  const bool in32 = act && s32_begin(D, K, j, rho, zsq, sw32, st);
   if (in32) {
-    st.s = sw32(st.org, st.jl, st.tau);
+    st.s = sw32(st.org, st.jl, st.tau, st.inv);
     s32_first(D, K, j, st);
   }
   for (;;) {
@@ -457,7 +486,7 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
     const bool need = in32 && st.live && s32_step(st, &eta, &have);
     if (!__any_sync(kFull, need)) break;
     if (need) {
-      st.s = sw32(st.org, st.jl, st.tau);
+      st.s = sw32(st.org, st.jl, st.tau, st.inv);
       s32_after(st, eta, have);
     }
   }
@@ -491,7 +520,7 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
     }
     if (!__any_sync(kFull, go)) break;
     if (go && third) {
-      hw = double(sw32(q.org, q.jl, float(q.tau)).hw);
+      hw = hw_at(sw32, st, q);
       ++*n32;
     }
     if (go) {
@@ -652,18 +681,19 @@ __device__ __forceinline__ float rcp_approx32(float x) {
 }
 
 // Terms of poles b + l0, b + l0 + st, ... below e at offset tau from the origin
-// pole ho, in single precision: w = sum z^2/Delta (compensated: c carries the
-// negated low part lost so far), dw = sum z^2/Delta^2, hw = sum z^2/Delta^3.
-// Delta = ((hi_i - hi_o) + (lo_i - lo_o)) - tau: the hi difference is exact for
+// pole ho, in single precision and in units of S = 1 / inv: with Delta the pole's
+// offset divided by S, w = sum z^2/Delta (compensated: c carries the negated low
+// part lost so far), dw = sum z^2/Delta^2, hw = sum z^2/Delta^3, and
+// Delta = ((hi_i - hi_o) + (lo_i - lo_o)) inv - tau: the hi difference is exact for
 // nearby poles, so the offset keeps about 24 bits relative to its own size.
 __device__ __forceinline__ void range32(const float2* __restrict__ H, const float* __restrict__ Z,
                                         int b, int e, int l0, int st, float2 ho, float tau,
-                                        float& w, float& dw, float& hw) {
+                                        float inv, float& w, float& dw, float& hw) {
   float s = 0.f, c = 0.f, d = 0.f, h = 0.f;
   for (int i = b + l0; i < e; i += st) {
     const float2 p = H[i];
     const float z = Z[i];
-    const float del = ((p.x - ho.x) + (p.y - ho.y)) - tau;
+    const float del = fmaf((p.x - ho.x) + (p.y - ho.y), inv, -tau);
     const float r = rcp_approx32(del);
     const float t = z * r;
     const float y = fmaf(z, t, -c);
@@ -678,33 +708,39 @@ __device__ __forceinline__ void range32(const float2* __restrict__ H, const floa
   hw = h;
 }
 
-struct ThreadSweep32 {
+// Float copies of the active poles.  `resolves`: whether they resolve the interval
+// of the given width between poles jl < jr (or, for the last root, above jr): the
+// width must reach 2^-28 of the shifted pole magnitudes |D - shift|.
+struct Copies32 {
   const float2* __restrict__ H;
   const float* __restrict__ Z;
   int K;
-  __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau) const {
+  __device__ __forceinline__ bool resolves(int jl, int jr, bool, double width) const {
+    return width >= 0x1p-28 * double(fmaxf(fabsf(H[jl].x), fabsf(H[jr].x)));
+  }
+};
+
+struct ThreadSweep32 : Copies32 {
+  __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau, float inv) const {
     const float2 ho = H[org];
     Sec32 s;
     float hl, hr;
-    range32(H, Z, 0, jl + 1, 0, 1, ho, tau, s.psi, s.dpsi, hl);
-    range32(H, Z, jl + 1, K, 0, 1, ho, tau, s.phi, s.dphi, hr);
+    range32(H, Z, 0, jl + 1, 0, 1, ho, tau, inv, s.psi, s.dpsi, hl);
+    range32(H, Z, jl + 1, K, 0, 1, ho, tau, inv, s.phi, s.dphi, hr);
     s.hw = hl + hr;
     return s;
   }
 };
 
 template <int G>
-struct GroupSweep32 {
-  const float2* __restrict__ H;
-  const float* __restrict__ Z;
-  int K;
+struct GroupSweep32 : Copies32 {
   int gl;
   unsigned mask;
-  __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau) const {
+  __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau, float inv) const {
     const float2 ho = H[org];
     float p, dp, hl, f, df, hr;
-    range32(H, Z, 0, jl + 1, gl, G, ho, tau, p, dp, hl);
-    range32(H, Z, jl + 1, K, gl, G, ho, tau, f, df, hr);
+    range32(H, Z, 0, jl + 1, gl, G, ho, tau, inv, p, dp, hl);
+    range32(H, Z, jl + 1, K, gl, G, ho, tau, inv, f, df, hr);
     Sec32 s;
     s.psi = group_sum<G>(p, mask);
     s.dpsi = group_sum<G>(dp, mask);
@@ -764,12 +800,12 @@ __global__ void k_secular_thread(RootArgs a) {
     const MState ms = valid ? a.ms[g] : MState{};
     const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
     ThreadSweep sw{a.AD + lo, a.AZ + lo, K};
-    ThreadSweep32 sw32{a.AD32 + lo, a.AZ32 + lo, K};
+    ThreadSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, K}};
     int org = 0, n32 = 0;
     double tau = 0.0;
     bool ok = true;
-    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, ms.shift,
-                                         valid, sw, sw32, &org, &tau, &ok, &n32);
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw,
+                                         sw32, &org, &tau, &ok, &n32);
     if (valid) {
       secular_store(a, lo, j, org, tau, sweeps, K, ok, true);
       tally.add(sweeps, n32, K);
@@ -797,12 +833,12 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
     const MState ms = valid ? a.ms[g] : MState{};
     const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
     GroupSweep<G> sw{a.AD + lo, a.AZ + lo, K, gl, mask};
-    GroupSweep32<G> sw32{a.AD32 + lo, a.AZ32 + lo, K, gl, mask};
+    GroupSweep32<G> sw32{{a.AD32 + lo, a.AZ32 + lo, K}, gl, mask};
     int org = 0, n32 = 0;
     double tau = 0.0;
     bool ok = true;
-    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, ms.shift,
-                                         valid, sw, sw32, &org, &tau, &ok, &n32);
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw,
+                                         sw32, &org, &tau, &ok, &n32);
     if (valid) {
       secular_store(a, lo, j, org, tau, sweeps, K, ok, gl == 0);
       tally.add(sweeps, n32, K);
@@ -841,13 +877,13 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     const MState ms = a.ms[g];
     const int j = rl - ms.base, lo = a.M[g].lo;
     WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane};
-    GroupSweep32<32> sw32{a.AD32 + lo, a.AZ32 + lo, ms.K, lane, 0xffffffffu};
+    GroupSweep32<32> sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, 0xffffffffu};
     int org, n32;
     double tau;
     bool ok;
     const int sweeps =
-        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, ms.shift, sw, sw32, &org, &tau,
-                     &ok, &n32);
+        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok,
+                     &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
     tally.add(sweeps, n32, ms.K);
   }
