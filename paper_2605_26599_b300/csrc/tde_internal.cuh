@@ -278,6 +278,36 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sm, int* total) {
   return before + x - v;
 }
 
+// Block-wide inclusive max-scan of one int per thread (values >= -1; -1 is the
+// identity); *total receives the block's maximum.  All threads of the block must
+// call it.  sm: NT/32 ints.
+template <int NT>
+__device__ __forceinline__ int block_incl_max_scan(int v, int* sm, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x = max(x, y);
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < NT / 32) ? sm[lane] : -1;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w = max(w, y);
+    }
+    if (lane < NT / 32) sm[lane] = w;
+  }
+  __syncthreads();
+  const int before = (warp > 0) ? sm[warp - 1] : -1;
+  *total = sm[NT / 32 - 1];
+  __syncthreads();
+  return max(before, x);
+}
+
 template <int NT>
 __device__ __forceinline__ double block_max(double v, double* sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

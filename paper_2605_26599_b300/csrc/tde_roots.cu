@@ -38,6 +38,9 @@ struct RootArgs {
   double* ZHAT;           // aliases Z
   double *ROWLO, *ROWHI;  // alias RLO, RHI: parent rows of the active columns
   double* DORG;           // alias KEYA: D_org(j) of every active root
+  int32_t* CLF;           // alias IDXA: first pole of each active pole's cluster
+  int32_t* CLL;           // alias ZPOS: at a cluster's first pole, its last (-1: unused)
+  double *CF0, *CF1, *CF2;  // alias RLO, RHI, Z: outside sums of each cluster
   Status* st;
   uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
   int all_merges;           // also build z-hat and rows at root merges (adjoint)
@@ -539,14 +542,64 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
   return sweeps;
 }
 
-// one thread evaluates all K poles
+// Cluster evaluation of the FP64 sums.  Where a root's two bracketing poles lie in
+// one pole cluster [f, l] (a maximal run of poles joined by gaps too narrow for the
+// single-precision stage, found at deflation), the poles outside the cluster are
+// summed once per cluster (k_cluster_far) as the first three Taylor coefficients of
+// each side about the cluster's first pole m = D_f,
+//   c_k = sum_{i outside, one side} z_i^2 / (D_i - m)^(k+1),  k = 0, 1, 2,
+// and a sweep sums only the cluster's own poles exactly, adding the outside ones as
+// c0 + c1 d + c2 d^2 to psi / phi and c1 + 2 c2 d to their derivatives, with
+// d = lambda - m = (D_org - m) + tau (D_org - m is exact: both are cluster poles).
+// A cluster is used only if its span is at most 2^-19 of the distance from m to the
+// nearest outside pole, so the dropped terms stay below 2^-57 of the outside sums,
+// far below the rounding bound of the convergence test.
+struct ClusterFar {
+  int nb, ne;  // poles summed exactly: [nb, ne) (all of them, without outside sums, if !on)
+  bool on;
+  double m, c0l, c1l, c2l, c0r, c1r, c2r;
+  __device__ __forceinline__ void add(SecSums& s, double dorg, double tau) const {
+    const double d = (dorg - m) + tau;
+    s.psi += fma(d, fma(d, c2l, c1l), c0l);
+    s.dpsi += fma(2.0 * d, c2l, c1l);
+    s.phi += fma(d, fma(d, c2r, c1r), c0r);
+    s.dphi += fma(2.0 * d, c2r, c1r);
+  }
+};
+
+__device__ __forceinline__ ClusterFar cluster_far(const RootArgs& a, int lo, int K, int j) {
+  ClusterFar c;
+  c.nb = 0;
+  c.ne = K;
+  c.on = false;
+  c.m = c.c0l = c.c1l = c.c2l = c.c0r = c.c1r = c.c2r = 0.0;
+  if (j >= K - 1) return c;
+  const int f = a.CLF[lo + j];
+  if (a.CLF[lo + j + 1] != f) return c;
+  const int l = a.CLL[lo + f];
+  if (l <= f) return c;
+  c.nb = f;
+  c.ne = l + 1;
+  c.on = true;
+  c.m = a.AD[lo + f];
+  c.c0l = a.CF0[lo + f];
+  c.c1l = a.CF0[lo + f + 1];
+  c.c2l = a.CF1[lo + f];
+  c.c0r = a.CF1[lo + f + 1];
+  c.c1r = a.CF2[lo + f];
+  c.c2r = a.CF2[lo + f + 1];
+  return c;
+}
+
+// one thread evaluates all K poles (or a cluster's poles and its outside sums)
 struct ThreadSweep {
   const double* __restrict__ D;
   const double* __restrict__ Z;
   int K;
+  ClusterFar cf;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
     SecSums s{0.0, 0.0, 0.0, 0.0};
-    for (int i = 0; i < K; ++i) {
+    for (int i = cf.nb; i < cf.ne; ++i) {
       const double zi = Z[i];
       const double t = zi * rcp_refined((D[i] - dorg) - tau);
       const bool left = i <= jl;
@@ -557,6 +610,7 @@ struct ThreadSweep {
       s.phi = fma(zr, t, s.phi);
       s.dphi = fma(tr, t, s.dphi);
     }
+    if (cf.on) cf.add(s, dorg, tau);
     return s;
   }
 };
@@ -605,15 +659,17 @@ struct WarpSweep {
   const double* __restrict__ Z;
   int K;
   int lane;
+  ClusterFar cf;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
     double p, dp, f, df;
-    lane_sums(D, Z, 0, jl + 1, lane, dorg, tau, p, dp);
-    lane_sums(D, Z, jl + 1, K, lane, dorg, tau, f, df);
+    lane_sums(D, Z, cf.nb, jl + 1, lane, dorg, tau, p, dp);
+    lane_sums(D, Z, jl + 1, cf.ne, lane, dorg, tau, f, df);
     SecSums s;
     s.psi = warp_sum(p);
     s.dpsi = warp_sum(dp);
     s.phi = warp_sum(f);
     s.dphi = warp_sum(df);
+    if (cf.on) cf.add(s, dorg, tau);
     return s;
   }
 };
@@ -660,15 +716,17 @@ struct GroupSweep {
   int K;
   int gl;
   unsigned mask;
+  ClusterFar cf;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
     double p, dp, f, df;
-    group_lane_sums<G>(D, Z, 0, jl + 1, gl, dorg, tau, p, dp);
-    group_lane_sums<G>(D, Z, jl + 1, K, gl, dorg, tau, f, df);
+    group_lane_sums<G>(D, Z, cf.nb, jl + 1, gl, dorg, tau, p, dp);
+    group_lane_sums<G>(D, Z, jl + 1, cf.ne, gl, dorg, tau, f, df);
     SecSums s;
     s.psi = group_sum<G>(p, mask);
     s.dpsi = group_sum<G>(dp, mask);
     s.phi = group_sum<G>(f, mask);
     s.dphi = group_sum<G>(df, mask);
+    if (cf.on) cf.add(s, dorg, tau);
     return s;
   }
 };
@@ -784,6 +842,74 @@ struct SecTally {
   }
 };
 
+// Outside sums of every pole cluster of the step (ClusterFar), one warp per
+// cluster: warps walk the step's two root lists 32 roots at a time and take the
+// roots that start a cluster of two or more poles.  A cluster too wide for the
+// expansion is marked unused (CLL = -1) and its roots sum all poles.
+__global__ void __launch_bounds__(128) k_cluster_far(RootArgs a) {
+  const uint32_t nbig = *a.count2, total = nbig + *a.count;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
+    const uint32_t r = base + lane;
+    int g = 0, j = 0;
+    bool head = false;
+    if (r < total) {
+      const int rl = int(r < nbig ? r : r - nbig);
+      g = r < nbig ? a.ROOTMAP2[r] : a.ROOTMAP[r - nbig];
+      const MState ms = a.ms[g];
+      j = rl - ms.base;
+      const int lo = a.M[g].lo;
+      head = j < ms.K - 1 && a.CLF[lo + j] == j && a.CLF[lo + j + 1] == j;
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int gg = __shfl_sync(0xffffffffu, g, src), f = __shfl_sync(0xffffffffu, j, src);
+      const int lo = a.M[gg].lo, K = a.ms[gg].K;
+      const double* D = a.AD + lo;
+      const double* Z = a.AZ + lo;
+      const int l = a.CLL[lo + f];
+      const double m = D[f];
+      double dist = INFINITY;
+      if (f > 0) dist = m - D[f - 1];
+      if (l < K - 1) dist = fmin(dist, D[l + 1] - m);
+      __syncwarp();
+      if (!(D[l] - m <= 0x1p-19 * dist)) {
+        if (lane == 0) a.CLL[lo + f] = -1;
+        continue;
+      }
+      double c[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) c[q] = 0.0;
+      for (int i = lane; i < f; i += 32) {
+        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
+        c[0] = fma(Z[i], t, c[0]);
+        c[1] = fma(t, t, c[1]);
+        c[2] = fma(t * t, r0, c[2]);
+      }
+      for (int i = l + 1 + lane; i < K; i += 32) {
+        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
+        c[3] = fma(Z[i], t, c[3]);
+        c[4] = fma(t, t, c[4]);
+        c[5] = fma(t * t, r0, c[5]);
+      }
+#pragma unroll
+      for (int q = 0; q < 6; ++q) c[q] = warp_sum(c[q]);
+      if (lane == 0) {
+        a.CF0[lo + f] = c[0];
+        a.CF0[lo + f + 1] = c[1];
+        a.CF1[lo + f] = c[2];
+        a.CF1[lo + f + 1] = c[3];
+        a.CF2[lo + f] = c[4];
+        a.CF2[lo + f + 1] = c[5];
+      }
+    }
+  }
+}
+
 // One thread per root.  The loop over roots advances a whole warp at a time (32
 // consecutive roots), which keeps every lane in step for the warp votes of
 // secular_root_sync.
@@ -799,7 +925,7 @@ __global__ void k_secular_thread(RootArgs a) {
     const int g = valid ? a.ROOTMAP[r] : 0;
     const MState ms = valid ? a.ms[g] : MState{};
     const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
-    ThreadSweep sw{a.AD + lo, a.AZ + lo, K};
+    ThreadSweep sw{a.AD + lo, a.AZ + lo, K, cluster_far(a, lo, K, valid ? j : K)};
     ThreadSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, K}};
     int org = 0, n32 = 0;
     double tau = 0.0;
@@ -832,7 +958,7 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
     const int g = valid ? a.ROOTMAP[r] : 0;
     const MState ms = valid ? a.ms[g] : MState{};
     const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
-    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, K, gl, mask};
+    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, K, gl, mask, cluster_far(a, lo, K, valid ? j : K)};
     GroupSweep32<G> sw32{{a.AD32 + lo, a.AZ32 + lo, K}, gl, mask};
     int org = 0, n32 = 0;
     double tau = 0.0;
@@ -866,7 +992,10 @@ __device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, in
 }
 
 // Roots differ in cost (one to several sweeps in each precision), so warps claim
-// them one at a time instead of a fixed stride, which would leave a tail.
+// them one at a time instead of a fixed stride, which would leave a tail.  Within a
+// merge the claims alternate between the two ends of the spectrum and move inward:
+// the costly roots (narrow gaps, many sweeps) sit at the ends, and a costly root
+// claimed last would run alone on one SM sub-partition while the others idle.
 __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
@@ -875,8 +1004,9 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
     const MState ms = a.ms[g];
-    const int j = rl - ms.base, lo = a.M[g].lo;
-    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane};
+    const int q = rl - ms.base, lo = a.M[g].lo;
+    const int j = (q & 1) ? ms.K - 1 - (q >> 1) : (q >> 1);
+    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, cluster_far(a, lo, ms.K, j)};
     GroupSweep32<32> sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, 0xffffffffu};
     int org, n32;
     double tau;
@@ -1164,6 +1294,11 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.AHI = ws.AHI;
   ra.AD32 = reinterpret_cast<const float2*>(ws.KEYB);
   ra.AZ32 = reinterpret_cast<const float*>(ws.IDXB);
+  ra.CLF = ws.IDXA;
+  ra.CLL = ws.ZPOS;
+  ra.CF0 = ws.RLO;
+  ra.CF1 = ws.RHI;
+  ra.CF2 = ws.Z;
   ra.TAU = ws.TAU;
   ra.ORG = ws.ORG;
   ra.LAMA = ws.D;
@@ -1192,6 +1327,8 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
                                           reinterpret_cast<double*>(ws.KEYA), ws.D);
     launches = 1;
   } else {
+  k_cluster_far<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 4)), 128, 0, s>>>(ra);
+  ++launches;
   switch (G) {
     case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
     case 4: k_secular_group<4><<<ggrid, 128, 0, s>>>(ra); break;
