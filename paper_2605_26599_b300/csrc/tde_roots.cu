@@ -553,7 +553,8 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
 // d = lambda - m = (D_org - m) + tau (D_org - m is exact: both are cluster poles).
 // A cluster is used only if its span is at most 2^-19 of the distance from m to the
 // nearest outside pole, so the dropped terms stay below 2^-57 of the outside sums,
-// far below the rounding bound of the convergence test.
+// far below the rounding bound of the convergence test.  Only the warp-per-root
+// kernel (large K, where the saving is) evaluates clusters this way.
 struct ClusterFar {
   int nb, ne;  // poles summed exactly: [nb, ne) (all of them, without outside sums, if !on)
   bool on;
@@ -591,15 +592,14 @@ __device__ __forceinline__ ClusterFar cluster_far(const RootArgs& a, int lo, int
   return c;
 }
 
-// one thread evaluates all K poles (or a cluster's poles and its outside sums)
+// one thread evaluates all K poles
 struct ThreadSweep {
   const double* __restrict__ D;
   const double* __restrict__ Z;
   int K;
-  ClusterFar cf;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
     SecSums s{0.0, 0.0, 0.0, 0.0};
-    for (int i = cf.nb; i < cf.ne; ++i) {
+    for (int i = 0; i < K; ++i) {
       const double zi = Z[i];
       const double t = zi * rcp_refined((D[i] - dorg) - tau);
       const bool left = i <= jl;
@@ -610,7 +610,6 @@ struct ThreadSweep {
       s.phi = fma(zr, t, s.phi);
       s.dphi = fma(tr, t, s.dphi);
     }
-    if (cf.on) cf.add(s, dorg, tau);
     return s;
   }
 };
@@ -716,17 +715,15 @@ struct GroupSweep {
   int K;
   int gl;
   unsigned mask;
-  ClusterFar cf;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
     double p, dp, f, df;
-    group_lane_sums<G>(D, Z, cf.nb, jl + 1, gl, dorg, tau, p, dp);
-    group_lane_sums<G>(D, Z, jl + 1, cf.ne, gl, dorg, tau, f, df);
+    group_lane_sums<G>(D, Z, 0, jl + 1, gl, dorg, tau, p, dp);
+    group_lane_sums<G>(D, Z, jl + 1, K, gl, dorg, tau, f, df);
     SecSums s;
     s.psi = group_sum<G>(p, mask);
     s.dpsi = group_sum<G>(dp, mask);
     s.phi = group_sum<G>(f, mask);
     s.dphi = group_sum<G>(df, mask);
-    if (cf.on) cf.add(s, dorg, tau);
     return s;
   }
 };
@@ -925,7 +922,7 @@ __global__ void k_secular_thread(RootArgs a) {
     const int g = valid ? a.ROOTMAP[r] : 0;
     const MState ms = valid ? a.ms[g] : MState{};
     const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
-    ThreadSweep sw{a.AD + lo, a.AZ + lo, K, cluster_far(a, lo, K, valid ? j : K)};
+    ThreadSweep sw{a.AD + lo, a.AZ + lo, K};
     ThreadSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, K}};
     int org = 0, n32 = 0;
     double tau = 0.0;
@@ -958,7 +955,7 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
     const int g = valid ? a.ROOTMAP[r] : 0;
     const MState ms = valid ? a.ms[g] : MState{};
     const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
-    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, K, gl, mask, cluster_far(a, lo, K, valid ? j : K)};
+    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, K, gl, mask};
     GroupSweep32<G> sw32{{a.AD32 + lo, a.AZ32 + lo, K}, gl, mask};
     int org = 0, n32 = 0;
     double tau = 0.0;
