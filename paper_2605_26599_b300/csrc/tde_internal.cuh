@@ -308,6 +308,10 @@ __device__ __forceinline__ int block_incl_max_scan(int v, int* sm, int* total) {
   return max(before, x);
 }
 
+// Block-wide max / sum of one double per thread, returned to every thread.  The
+// warp partials are combined by warp 0 alone and broadcast: FP64 work done by every
+// thread of a large block would cost the SM's FP64 pipe once per thread.  All
+// threads must call them.  sm: NT/32 doubles.
 template <int NT>
 __device__ __forceinline__ double block_max(double v, double* sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -315,8 +319,14 @@ __device__ __forceinline__ double block_max(double v, double* sm) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if (lane == 0) sm[warp] = v;
   __syncthreads();
-  double r = sm[0];
-  for (int w = 1; w < NT / 32; ++w) r = fmax(r, sm[w]);
+  if (warp == 0) {
+    double x = sm[lane < NT / 32 ? lane : 0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) sm[0] = x;
+  }
+  __syncthreads();
+  const double r = sm[0];
   __syncthreads();
   return r;
 }
@@ -328,8 +338,14 @@ __device__ __forceinline__ double block_sum(double v, double* sm) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane == 0) sm[warp] = v;
   __syncthreads();
-  double r = sm[0];
-  for (int w = 1; w < NT / 32; ++w) r += sm[w];
+  if (warp == 0) {
+    double x = lane < NT / 32 ? sm[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sm[0] = x;
+  }
+  __syncthreads();
+  const double r = sm[0];
   __syncthreads();
   return r;
 }

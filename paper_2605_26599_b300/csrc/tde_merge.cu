@@ -91,6 +91,10 @@ __device__ __forceinline__ T4 t4_add(const T4& a, const T4& b) {
 __device__ __forceinline__ T4 t4_shfl_up(const T4& v, int o) {
   return T4{shfl_up_d(v.w, o), shfl_up_d(v.dw, o), shfl_up_d(v.ulo, o), shfl_up_d(v.uhi, o)};
 }
+__device__ __forceinline__ T4 t4_shfl_xor(const T4& v, int o) {
+  return T4{__shfl_xor_sync(0xffffffffu, v.w, o), __shfl_xor_sync(0xffffffffu, v.dw, o),
+            __shfl_xor_sync(0xffffffffu, v.ulo, o), __shfl_xor_sync(0xffffffffu, v.uhi, o)};
+}
 
 // Run boundaries of survivors [begin, end) (one warp).  The sequential rule -- walk
 // the survivors in ascending order and let each one join the current run if the
@@ -650,11 +654,10 @@ struct ClusterSlot {
   int changed[2];
 };
 
-// Cluster barrier after making this thread's global writes visible device-wide.
-__device__ __forceinline__ void cluster_sync_mem(cg::cluster_group& cl) {
-  __threadfence();
-  cl.sync();
-}
+// Cluster barrier ordering this thread's global writes before the other CTAs' reads
+// (the barrier's arrive has release and its wait acquire semantics at cluster
+// scope, which covers global memory).
+__device__ __forceinline__ void cluster_sync_mem(cg::cluster_group& cl) { cl.sync(); }
 
 // Sum of an int field over the ranks before r and over all C ranks, computed by
 // every warp on its own (lane q reads rank q).
@@ -679,8 +682,7 @@ __device__ __forceinline__ int block_max_int(int v, int* sm) {
   v = __reduce_max_sync(0xffffffffu, v);
   if (lane == 0) sm[warp] = v;
   __syncthreads();
-  int r = sm[0];
-  for (int w = 1; w < NT / 32; ++w) r = max(r, sm[w]);
+  const int r = __reduce_max_sync(0xffffffffu, sm[lane < NT / 32 ? lane : 0]);
   __syncthreads();
   return r;
 }
@@ -835,10 +837,16 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
         const double zk = Z[pos], wk = zk * zk;
         acc = t4_add(acc, T4{wk, D[pos] * wk, zk * RLO[pos], zk * RHI[pos]});
       }
-      acc.w = block_sum<NT>(acc.w, sm_dbl);
-      acc.dw = block_sum<NT>(acc.dw, sm_dbl);
-      acc.ulo = block_sum<NT>(acc.ulo, sm_dbl);
-      acc.uhi = block_sum<NT>(acc.uhi, sm_dbl);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = t4_add(acc, t4_shfl_xor(acc, o));
+      if (lane == 0) s_agg[warp] = acc;
+      __syncthreads();
+      if (warp == 0) {
+        T4 x = lane < NW ? s_agg[lane] : T4{0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x = t4_add(x, t4_shfl_xor(x, o));
+        acc = x;
+      }
       if (tid == 0) {
         slot.agg = acc;
         slot.has_head = hl >= 0 ? 1 : 0;
@@ -879,13 +887,15 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
       }
       T4 v = own;
       bool h = head;
+      if (c0 + warp * 32 < se) {  // warps past the slice hold no survivor
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        T4 vo = t4_shfl_up(v, o);
-        bool ho = __shfl_up_sync(0xffffffffu, h, o);
-        if (lane >= o) {
-          if (!h) v = t4_add(v, vo);
-          h = h || ho;
+        for (int o = 1; o < 32; o <<= 1) {
+          T4 vo = t4_shfl_up(v, o);
+          bool ho = __shfl_up_sync(0xffffffffu, h, o);
+          if (lane >= o) {
+            if (!h) v = t4_add(v, vo);
+            h = h || ho;
+          }
         }
       }
       if (lane == 31) {
@@ -962,8 +972,10 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
     if (tid == 0) slot.zsq = zsq;
     cluster_sync_mem(cl);
     K = Ktot;
-    zsq = 0.0;
-    for (int q = 0; q < C; ++q) zsq += cl.map_shared_rank(&slot, q)->zsq;
+    if (r == 0 && tid == 0) {  // only the thread writing the merge state needs it
+      zsq = 0.0;
+      for (int q = 0; q < C; ++q) zsq += cl.map_shared_rank(&slot, q)->zsq;
+    }
 
     // 5. deflated positions of each kind, in position order, over the CTA slices
     int32_t* ZPOS = a.ZPOS + lo;
@@ -1164,33 +1176,36 @@ void launch_form(const Plan& plan, const Workspace& ws, int step, LevelState in,
 // SMs once (at most 16, the non-portable maximum, if a 16-CTA cluster of
 // 1024-thread CTAs fits this device; 8 otherwise).  0 selects the one-CTA kernels.
 static int deflate_cluster_size(int64_t cnt, int64_t maxsize) {
-  static int cmax = 0;
-  if (cmax == 0) {
-    cmax = 8;
-    if (cudaFuncSetAttribute(k_deflate_cluster<1024>,
-                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+  // fit[k]: how many clusters of 2^k CTAs this device runs at once (queried once)
+  static int fit[5] = {-1, 0, 0, 0, 0};
+  if (fit[0] < 0) {
+    fit[0] = 0;
+    const bool np = cudaFuncSetAttribute(k_deflate_cluster<1024>,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                         1) == cudaSuccess;
+    for (int k = 1; k <= 4; ++k) {
+      if (k == 4 && !np) break;
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(16);
+      cfg.gridDim = dim3(1u << k);
       cfg.blockDim = dim3(1024);
       cudaLaunchAttribute at;
       at.id = cudaLaunchAttributeClusterDimension;
-      at.val.clusterDim.x = 16;
+      at.val.clusterDim.x = 1u << k;
       at.val.clusterDim.y = 1;
       at.val.clusterDim.z = 1;
       cfg.attrs = &at;
       cfg.numAttrs = 1;
-      int nclusters = 0;
-      if (cudaOccupancyMaxActiveClusters(&nclusters, k_deflate_cluster<1024>, &cfg) ==
-              cudaSuccess &&
-          nclusters > 0)
-        cmax = 16;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_deflate_cluster<1024>, &cfg) == cudaSuccess)
+        fit[k] = n;
     }
     cudaGetLastError();  // a refused query leaves no sticky error
   }
   if (maxsize < 1024 || cnt < 1) return 0;
-  int c = 1;
-  while (c < cmax && cnt * (2 * c) <= 148) c *= 2;
-  return c >= 2 ? c : 0;
+  // the largest cluster size whose clusters for all cnt merges run in one wave
+  for (int k = 4; k >= 1; --k)
+    if (fit[k] >= cnt) return 1 << k;
+  return 0;
 }
 
 void launch_deflate(const DeflateArgs& da, int64_t maxsize, cudaStream_t s) {

@@ -839,33 +839,37 @@ struct SecTally {
   }
 };
 
-// Outside sums of every pole cluster of the step (ClusterFar), one warp per
-// cluster: warps walk the step's two root lists 32 roots at a time and take the
-// roots that start a cluster of two or more poles.  A cluster too wide for the
-// expansion is marked unused (CLL = -1) and its roots sum all poles.
+// Outside sums of every pole cluster of the step (ClusterFar), one block per
+// cluster: blocks walk the step's two root lists 128 roots at a time and take, one
+// after the other, the roots of the chunk that start a cluster of two or more
+// poles.  A cluster too wide for the expansion is marked unused (CLL = -1) and its
+// roots sum all poles.
 __global__ void __launch_bounds__(128) k_cluster_far(RootArgs a) {
+  __shared__ int s_head[128][2];
+  __shared__ int s_n;
+  __shared__ double s_red[4][6];
   const uint32_t nbig = *a.count2, total = nbig + *a.count;
-  const int lane = threadIdx.x & 31;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
-    const uint32_t r = base + lane;
-    int g = 0, j = 0;
-    bool head = false;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (uint32_t base = blockIdx.x * 128u; base < total; base += gridDim.x * 128u) {
+    if (tid == 0) s_n = 0;
+    __syncthreads();
+    const uint32_t r = base + tid;
     if (r < total) {
       const int rl = int(r < nbig ? r : r - nbig);
-      g = r < nbig ? a.ROOTMAP2[r] : a.ROOTMAP[r - nbig];
+      const int g = r < nbig ? a.ROOTMAP2[r] : a.ROOTMAP[r - nbig];
       const MState ms = a.ms[g];
-      j = rl - ms.base;
-      const int lo = a.M[g].lo;
-      head = j < ms.K - 1 && a.CLF[lo + j] == j && a.CLF[lo + j + 1] == j;
+      const int j = rl - ms.base, lo = a.M[g].lo;
+      if (j < ms.K - 1 && a.CLF[lo + j] == j && a.CLF[lo + j + 1] == j) {
+        const int q = atomicAdd(&s_n, 1);
+        s_head[q][0] = g;
+        s_head[q][1] = j;
+      }
     }
-    unsigned hm = __ballot_sync(0xffffffffu, head);
-    while (hm) {
-      const int src = __ffs(hm) - 1;
-      hm &= hm - 1;
-      const int gg = __shfl_sync(0xffffffffu, g, src), f = __shfl_sync(0xffffffffu, j, src);
-      const int lo = a.M[gg].lo, K = a.ms[gg].K;
+    __syncthreads();
+    const int nh = s_n;
+    for (int h = 0; h < nh; ++h) {
+      const int g = s_head[h][0], f = s_head[h][1];
+      const int lo = a.M[g].lo, K = a.ms[g].K;
       const double* D = a.AD + lo;
       const double* Z = a.AZ + lo;
       const int l = a.CLL[lo + f];
@@ -873,36 +877,44 @@ __global__ void __launch_bounds__(128) k_cluster_far(RootArgs a) {
       double dist = INFINITY;
       if (f > 0) dist = m - D[f - 1];
       if (l < K - 1) dist = fmin(dist, D[l + 1] - m);
-      __syncwarp();
-      if (!(D[l] - m <= 0x1p-19 * dist)) {
-        if (lane == 0) a.CLL[lo + f] = -1;
-        continue;
-      }
+      const bool ok = D[l] - m <= 0x1p-19 * dist;
       double c[6];
 #pragma unroll
       for (int q = 0; q < 6; ++q) c[q] = 0.0;
-      for (int i = lane; i < f; i += 32) {
-        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
-        c[0] = fma(Z[i], t, c[0]);
-        c[1] = fma(t, t, c[1]);
-        c[2] = fma(t * t, r0, c[2]);
-      }
-      for (int i = l + 1 + lane; i < K; i += 32) {
-        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
-        c[3] = fma(Z[i], t, c[3]);
-        c[4] = fma(t, t, c[4]);
-        c[5] = fma(t * t, r0, c[5]);
-      }
+      if (ok) {
+        for (int i = tid; i < f; i += 128) {
+          const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
+          c[0] = fma(Z[i], t, c[0]);
+          c[1] = fma(t, t, c[1]);
+          c[2] = fma(t * t, r0, c[2]);
+        }
+        for (int i = l + 1 + tid; i < K; i += 128) {
+          const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
+          c[3] = fma(Z[i], t, c[3]);
+          c[4] = fma(t, t, c[4]);
+          c[5] = fma(t * t, r0, c[5]);
+        }
 #pragma unroll
-      for (int q = 0; q < 6; ++q) c[q] = warp_sum(c[q]);
-      if (lane == 0) {
-        a.CF0[lo + f] = c[0];
-        a.CF0[lo + f + 1] = c[1];
-        a.CF1[lo + f] = c[2];
-        a.CF1[lo + f + 1] = c[3];
-        a.CF2[lo + f] = c[4];
-        a.CF2[lo + f + 1] = c[5];
+        for (int q = 0; q < 6; ++q) c[q] = warp_sum(c[q]);
+        if (lane == 0)
+#pragma unroll
+          for (int q = 0; q < 6; ++q) s_red[warp][q] = c[q];
       }
+      __syncthreads();
+      if (tid == 0) {
+        if (ok) {
+          for (int q = 0; q < 6; ++q) c[q] = (s_red[0][q] + s_red[1][q]) + (s_red[2][q] + s_red[3][q]);
+          a.CF0[lo + f] = c[0];
+          a.CF0[lo + f + 1] = c[1];
+          a.CF1[lo + f] = c[2];
+          a.CF1[lo + f + 1] = c[3];
+          a.CF2[lo + f] = c[4];
+          a.CF2[lo + f + 1] = c[5];
+        } else {
+          a.CLL[lo + f] = -1;
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -1324,7 +1336,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
                                           reinterpret_cast<double*>(ws.KEYA), ws.D);
     launches = 1;
   } else {
-  k_cluster_far<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 4)), 128, 0, s>>>(ra);
+  k_cluster_far<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
   ++launches;
   switch (G) {
     case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
