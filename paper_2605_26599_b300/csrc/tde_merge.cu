@@ -356,8 +356,9 @@ __device__ int write_clusters(const DeflateArgs& a, int lo, int K, int kb, int k
   return carry;
 }
 
-// One CTA of NT threads per merge: 256, or 1024 for steps with merges above
-// 8192 rows, where a single CTA walks the whole merge in NT-row chunks.
+// One CTA of NT threads per merge: 64 for steps whose merges have at most 64 rows,
+// 256 up to 8192 rows and 1024 above (where steps with few merges take the
+// cluster kernel instead); a CTA walks its merge in NT-row chunks.
 template <int NT>
 __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
   __shared__ int sm_int[NT / 32];
@@ -433,16 +434,18 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
         double wk = zk * zk;
         own = T4{wk, Dk * wk, zk * rl, zk * rh};
       }
-      // block segmented inclusive scan with carry-in
+      // block segmented inclusive scan with carry-in (warps past S hold no survivor)
       T4 v = own;
       bool h = head;
+      if (c0 + warp * 32 < S) {
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        T4 vo = t4_shfl_up(v, o);
-        bool ho = __shfl_up_sync(0xffffffffu, h, o);
-        if (lane >= o) {
-          if (!h) v = t4_add(v, vo);
-          h = h || ho;
+        for (int o = 1; o < 32; o <<= 1) {
+          T4 vo = t4_shfl_up(v, o);
+          bool ho = __shfl_up_sync(0xffffffffu, h, o);
+          if (lane >= o) {
+            if (!h) v = t4_add(v, vo);
+            h = h || ho;
+          }
         }
       }
       if (lane == 31) {
@@ -1227,11 +1230,12 @@ void launch_deflate(const DeflateArgs& da, int64_t maxsize, cudaStream_t s) {
     cudaLaunchKernelEx(&cfg, k_deflate_cluster<1024>, da);
     return;
   }
-  const int def_grid = int(std::min<int64_t>(cnt, 148 * 8));
   if (maxsize > 8192)
-    k_deflate<1024><<<def_grid, 1024, 0, s>>>(da);
+    k_deflate<1024><<<int(std::min<int64_t>(cnt, 148 * 8)), 1024, 0, s>>>(da);
+  else if (maxsize > 64)
+    k_deflate<kNT><<<int(std::min<int64_t>(cnt, 148 * 8)), kNT, 0, s>>>(da);
   else
-    k_deflate<kNT><<<def_grid, kNT, 0, s>>>(da);
+    k_deflate<64><<<int(std::min<int64_t>(cnt, 148 * 32)), 64, 0, s>>>(da);
 }
 
 void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda, cudaStream_t s,
