@@ -839,24 +839,42 @@ struct SecTally {
   }
 };
 
-// Outside sums of every pole cluster of the step (ClusterFar), one block per
-// cluster: blocks walk the step's two root lists 128 roots at a time and take, one
-// after the other, the roots of the chunk that start a cluster of two or more
-// poles.  A cluster too wide for the expansion is marked unused (CLL = -1) and its
-// roots sum all poles.
+// Root r of the warp kernels' list: the large-K list, then the small-K list when
+// that one is too short for the thread kernels.
+__device__ __forceinline__ uint32_t warp_list_total(const RootArgs& a) {
+  const uint32_t small = *a.count;
+  return *a.count2 + (small < a.small_list_min ? small : 0u);
+}
+// Merge of entry r of that combined list; *in_list receives r's index within its
+// own list, which is what a merge's `base` refers to.
+__device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, int* in_list) {
+  const uint32_t nb = *a.count2;
+  if (r < nb) {
+    *in_list = int(r);
+    return a.ROOTMAP2[r];
+  }
+  *in_list = int(r - nb);
+  return a.ROOTMAP[r - nb];
+}
+
+// Outside sums of the pole clusters of the merges whose roots k_secular_warp
+// solves (ClusterFar), one block per cluster: blocks walk that kernel's root list
+// 128 roots at a time and take, one after the other, the roots of the chunk that
+// start a cluster of two or more poles.  A cluster too wide for the expansion is
+// marked unused (CLL = -1) and its roots sum all poles.
 __global__ void __launch_bounds__(128) k_cluster_far(RootArgs a) {
   __shared__ int s_head[128][2];
   __shared__ int s_n;
   __shared__ double s_red[4][6];
-  const uint32_t nbig = *a.count2, total = nbig + *a.count;
+  const uint32_t total = warp_list_total(a);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint32_t base = blockIdx.x * 128u; base < total; base += gridDim.x * 128u) {
     if (tid == 0) s_n = 0;
     __syncthreads();
     const uint32_t r = base + tid;
     if (r < total) {
-      const int rl = int(r < nbig ? r : r - nbig);
-      const int g = r < nbig ? a.ROOTMAP2[r] : a.ROOTMAP[r - nbig];
+      int rl;
+      const int g = warp_list_merge(a, r, &rl);
       const MState ms = a.ms[g];
       const int j = rl - ms.base, lo = a.M[g].lo;
       if (j < ms.K - 1 && a.CLF[lo + j] == j && a.CLF[lo + j + 1] == j) {
@@ -980,24 +998,6 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
     }
   }
   if (gl == 0) tally.flush(a.st);
-}
-
-// Root r of the warp kernels' list: the large-K list, then the small-K list when
-// that one is too short for the thread kernels.
-__device__ __forceinline__ uint32_t warp_list_total(const RootArgs& a) {
-  const uint32_t small = *a.count;
-  return *a.count2 + (small < a.small_list_min ? small : 0u);
-}
-// Merge of entry r of that combined list; *in_list receives r's index within its
-// own list, which is what a merge's `base` refers to.
-__device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, int* in_list) {
-  const uint32_t nb = *a.count2;
-  if (r < nb) {
-    *in_list = int(r);
-    return a.ROOTMAP2[r];
-  }
-  *in_list = int(r - nb);
-  return a.ROOTMAP[r - nb];
 }
 
 // Roots differ in cost (one to several sweeps in each precision), so warps claim
