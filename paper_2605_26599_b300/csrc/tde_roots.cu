@@ -41,6 +41,7 @@ struct RootArgs {
   int32_t* CLF;           // alias IDXA: first pole of each active pole's cluster
   int32_t* CLL;           // alias ZPOS: at a cluster's first pole, its last (-1: unused)
   double *CF0, *CF1, *CF2;  // alias RLO, RHI, Z: outside sums of each cluster
+  float* CF3;               // alias SEG: their highest-order terms, times span^3
   Status* st;
   uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
   int all_merges;           // also build z-hat and rows at root merges (adjoint)
@@ -544,27 +545,56 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
 
 // Cluster evaluation of the FP64 sums.  Where a root's two bracketing poles lie in
 // one pole cluster [f, l] (a maximal run of poles joined by gaps too narrow for the
-// single-precision stage, found at deflation), the poles outside the cluster are
-// summed once per cluster (k_cluster_far) as the first three Taylor coefficients of
-// each side about the cluster's first pole m = D_f,
-//   c_k = sum_{i outside, one side} z_i^2 / (D_i - m)^(k+1),  k = 0, 1, 2,
-// and a sweep sums only the cluster's own poles exactly, adding the outside ones as
-// c0 + c1 d + c2 d^2 to psi / phi and c1 + 2 c2 d to their derivatives, with
-// d = lambda - m = (D_org - m) + tau (D_org - m is exact: both are cluster poles).
-// A cluster is used only if its span is at most 2^-19 of the distance from m to the
-// nearest outside pole, so the dropped terms stay below 2^-57 of the outside sums,
-// far below the rounding bound of the convergence test.  Only the warp-per-root
-// kernel (large K, where the saving is) evaluates clusters this way.
+// single-precision stage, found at deflation), the sums split at a near range
+// [F, L] containing the cluster: its poles are summed exactly at every sweep, the
+// poles outside it once per cluster (k_cluster_far), as the first four Taylor
+// coefficients of each side about the cluster's first pole m = D_f,
+//   c_k = sum_{i outside [F, L], one side} z_i^2 / (D_i - m)^(k+1),  k = 0..3
+// (c3, whose term only has to be roughly right, kept as a float times span^3),
+// which a sweep adds as c0 + c1 d + c2 d^2 + c3 d^3 to psi / phi and
+// c1 + 2 c2 d + 3 c3 d^2 to their derivatives, with d = lambda - m =
+// (D_org - m) + tau (D_org - m is exact: both are cluster poles).  The near range
+// starts as the cluster and takes in whole neighbouring clusters (at most four
+// times) until the cluster's span is at most 2^-15 of the distance from m to the
+// nearest pole outside; otherwise the cluster is not used.  The dropped terms then
+// stay below 2^-60 of the outside sums, far below the rounding bound of the
+// convergence test.  Only the warp-per-root kernel (large K, where the saving is)
+// evaluates clusters this way.
+__device__ __forceinline__ bool cluster_extent(const double* __restrict__ D,
+                                               const int32_t* __restrict__ CLF,
+                                               const int32_t* __restrict__ CLL, int K, int f,
+                                               int* F, int* L) {
+  const int l = CLL[f];
+  const double m = D[f], span = D[l] - m;
+  int lo = f, hi = l;
+  for (int it = 0; it <= 4; ++it) {
+    const double dl = lo > 0 ? m - D[lo - 1] : INFINITY;
+    const double dr = hi < K - 1 ? D[hi + 1] - m : INFINITY;
+    const double dist = fmin(dl, dr);
+    if (span <= 0x1p-15 * dist) {
+      *F = lo;
+      *L = hi;
+      return true;
+    }
+    if (it == 4) break;
+    if (dl < dr)
+      lo = CLF[lo - 1];
+    else
+      hi = CLL[hi + 1];  // pole hi + 1 starts the next cluster (the gap before it is wide)
+  }
+  return false;
+}
+
 struct ClusterFar {
   int nb, ne;  // poles summed exactly: [nb, ne) (all of them, without outside sums, if !on)
   bool on;
-  double m, c0l, c1l, c2l, c0r, c1r, c2r;
+  double m, c0l, c1l, c2l, c3l, c0r, c1r, c2r, c3r;
   __device__ __forceinline__ void add(SecSums& s, double dorg, double tau) const {
     const double d = (dorg - m) + tau;
-    s.psi += fma(d, fma(d, c2l, c1l), c0l);
-    s.dpsi += fma(2.0 * d, c2l, c1l);
-    s.phi += fma(d, fma(d, c2r, c1r), c0r);
-    s.dphi += fma(2.0 * d, c2r, c1r);
+    s.psi += fma(d, fma(d, fma(d, c3l, c2l), c1l), c0l);
+    s.dpsi += fma(d, fma(3.0 * d, c3l, 2.0 * c2l), c1l);
+    s.phi += fma(d, fma(d, fma(d, c3r, c2r), c1r), c0r);
+    s.dphi += fma(d, fma(3.0 * d, c3r, 2.0 * c2r), c1r);
   }
 };
 
@@ -573,22 +603,25 @@ __device__ __forceinline__ ClusterFar cluster_far(const RootArgs& a, int lo, int
   c.nb = 0;
   c.ne = K;
   c.on = false;
-  c.m = c.c0l = c.c1l = c.c2l = c.c0r = c.c1r = c.c2r = 0.0;
+  c.m = c.c0l = c.c1l = c.c2l = c.c3l = c.c0r = c.c1r = c.c2r = c.c3r = 0.0;
   if (j >= K - 1) return c;
   const int f = a.CLF[lo + j];
   if (a.CLF[lo + j + 1] != f) return c;
-  const int l = a.CLL[lo + f];
-  if (l <= f) return c;
-  c.nb = f;
-  c.ne = l + 1;
+  int F, L;
+  if (!cluster_extent(a.AD + lo, a.CLF + lo, a.CLL + lo, K, f, &F, &L)) return c;
+  c.nb = F;
+  c.ne = L + 1;
   c.on = true;
   c.m = a.AD[lo + f];
   c.c0l = a.CF0[lo + f];
   c.c1l = a.CF0[lo + f + 1];
   c.c2l = a.CF1[lo + f];
+  const double sp = a.AD[lo + a.CLL[lo + f]] - c.m, sp3 = sp * sp * sp;
+  c.c3l = double(a.CF3[lo + f]) / sp3;
   c.c0r = a.CF1[lo + f + 1];
   c.c1r = a.CF2[lo + f];
   c.c2r = a.CF2[lo + f + 1];
+  c.c3r = double(a.CF3[lo + f + 1]) / sp3;
   return c;
 }
 
@@ -860,12 +893,12 @@ __device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, in
 // Outside sums of the pole clusters of the merges whose roots k_secular_warp
 // solves (ClusterFar), one block per cluster: blocks walk that kernel's root list
 // 128 roots at a time and take, one after the other, the roots of the chunk that
-// start a cluster of two or more poles.  A cluster too wide for the expansion is
-// marked unused (CLL = -1) and its roots sum all poles.
+// start a cluster of two or more poles (clusters without a valid near range,
+// cluster_extent, are skipped: their roots sum all poles).
 __global__ void __launch_bounds__(128) k_cluster_far(RootArgs a) {
   __shared__ int s_head[128][2];
   __shared__ int s_n;
-  __shared__ double s_red[4][6];
+  __shared__ double s_red[4][8];
   const uint32_t total = warp_list_total(a);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (uint32_t base = blockIdx.x * 128u; base < total; base += gridDim.x * 128u) {
@@ -890,47 +923,43 @@ __global__ void __launch_bounds__(128) k_cluster_far(RootArgs a) {
       const int lo = a.M[g].lo, K = a.ms[g].K;
       const double* D = a.AD + lo;
       const double* Z = a.AZ + lo;
-      const int l = a.CLL[lo + f];
+      int F, L;
+      if (!cluster_extent(D, a.CLF + lo, a.CLL + lo, K, f, &F, &L)) continue;
       const double m = D[f];
-      double dist = INFINITY;
-      if (f > 0) dist = m - D[f - 1];
-      if (l < K - 1) dist = fmin(dist, D[l + 1] - m);
-      const bool ok = D[l] - m <= 0x1p-19 * dist;
-      double c[6];
+      double c[8];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) c[q] = 0.0;
-      if (ok) {
-        for (int i = tid; i < f; i += 128) {
-          const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
-          c[0] = fma(Z[i], t, c[0]);
-          c[1] = fma(t, t, c[1]);
-          c[2] = fma(t * t, r0, c[2]);
-        }
-        for (int i = l + 1 + tid; i < K; i += 128) {
-          const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0;
-          c[3] = fma(Z[i], t, c[3]);
-          c[4] = fma(t, t, c[4]);
-          c[5] = fma(t * t, r0, c[5]);
-        }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) c[q] = warp_sum(c[q]);
-        if (lane == 0)
-#pragma unroll
-          for (int q = 0; q < 6; ++q) s_red[warp][q] = c[q];
+      for (int q = 0; q < 8; ++q) c[q] = 0.0;
+      for (int i = tid; i < F; i += 128) {
+        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0, u = t * r0;
+        c[0] = fma(Z[i], t, c[0]);
+        c[1] = fma(t, t, c[1]);
+        c[2] = fma(t, u, c[2]);
+        c[3] = fma(u, u, c[3]);
       }
+      for (int i = L + 1 + tid; i < K; i += 128) {
+        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0, u = t * r0;
+        c[4] = fma(Z[i], t, c[4]);
+        c[5] = fma(t, t, c[5]);
+        c[6] = fma(t, u, c[6]);
+        c[7] = fma(u, u, c[7]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) c[q] = warp_sum(c[q]);
+      if (lane == 0)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s_red[warp][q] = c[q];
       __syncthreads();
       if (tid == 0) {
-        if (ok) {
-          for (int q = 0; q < 6; ++q) c[q] = (s_red[0][q] + s_red[1][q]) + (s_red[2][q] + s_red[3][q]);
-          a.CF0[lo + f] = c[0];
-          a.CF0[lo + f + 1] = c[1];
-          a.CF1[lo + f] = c[2];
-          a.CF1[lo + f + 1] = c[3];
-          a.CF2[lo + f] = c[4];
-          a.CF2[lo + f + 1] = c[5];
-        } else {
-          a.CLL[lo + f] = -1;
-        }
+        for (int q = 0; q < 8; ++q) c[q] = (s_red[0][q] + s_red[1][q]) + (s_red[2][q] + s_red[3][q]);
+        a.CF0[lo + f] = c[0];
+        a.CF0[lo + f + 1] = c[1];
+        a.CF1[lo + f] = c[2];
+        const double sp = D[a.CLL[lo + f]] - m, sp3 = sp * sp * sp;  // c3 sp^3 <= c0
+        a.CF3[lo + f] = float(c[3] * sp3);
+        a.CF1[lo + f + 1] = c[4];
+        a.CF2[lo + f] = c[5];
+        a.CF2[lo + f + 1] = c[6];
+        a.CF3[lo + f + 1] = float(c[7] * sp3);
       }
       __syncthreads();
     }
@@ -1308,6 +1337,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.CF0 = ws.RLO;
   ra.CF1 = ws.RHI;
   ra.CF2 = ws.Z;
+  ra.CF3 = reinterpret_cast<float*>(ws.SEG);
   ra.TAU = ws.TAU;
   ra.ORG = ws.ORG;
   ra.LAMA = ws.D;
