@@ -169,10 +169,12 @@ int tde_measure_fp64_peak(double* fma_per_s);
 
 /* Launch-shape tuning for subsequent calls on this thread (0 restores a default):
  *   warp_min_k      merges whose active rank reaches this solve one warp per root
- *                   (default 512), smaller ones one thread per root;
+ *                   (default 256), smaller ones one thread per root;
  *   small_list_min  a step with fewer small-merge roots than this hands them to the
  *                   warp-per-root kernels too (default 18944 = 148 SMs x 4 warps x 32).
- * The eigenvalues do not depend on these; only the time does. */
+ * They change the time, and the eigenvalues only at the level of rounding (the
+ * kernels sum in different orders, and only the warp-per-root kernel uses the
+ * cluster expansion of the secular sums). */
 int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min);
 /* out[0] = warp_min_k, out[1] = small_list_min of this thread. */
 int tde_get_tuning(int32_t* out);

@@ -140,7 +140,7 @@ def autotune(offsets, d, e, leaves=DEFAULT_LEAVES, warp_min_ks=DEFAULT_WARP_MIN_
         trials.append({"leaf": leaf, "warp_min_k": wmk, "ms": ms})
         return ms
 
-    default_wmk = 512
+    default_wmk = 256  # the library's default
     best_leaf = min(leaves, key=lambda lf: trial(lf, default_wmk))
     best_wmk = min(warp_min_ks, key=lambda w: trial(best_leaf, w) if w != default_wmk else
                    next(t["ms"] for t in trials if t["leaf"] == best_leaf and t["warp_min_k"] == w))

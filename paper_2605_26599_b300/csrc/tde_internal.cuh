@@ -58,7 +58,7 @@ struct MState {
 //   small_list_min  below this many small-K roots in a step the thread-per-root
 //                   kernels would leave SMs idle, so the warp kernels take them too
 struct Tuning {
-  int32_t warp_min_k = 512;
+  int32_t warp_min_k = 256;
   int32_t small_list_min = 148 * 4 * 32;
 };
 Tuning& thread_tuning();
