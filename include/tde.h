@@ -176,6 +176,15 @@ int tde_measure_fp64_peak(double* fma_per_s);
  * kernels sum in different orders, and only the warp-per-root kernel uses the
  * cluster expansion of the secular sums). */
 int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min);
+
+/* Threshold of the secular solver's block expansion for subsequent calls on this
+ * thread: FP64 sweeps of merges whose active rank K reaches min_k (and that the
+ * warp-per-root kernel solves) sum the poles of distant 128-pole blocks through a
+ * 27-term series of the block's moments instead of term by term (series error
+ * below 2^-53 of the block's terms).  min_k = 0 restores the default (2048); any
+ * other value below 256 is TDE_EINVAL; a value above every K turns the expansion
+ * off.  *previous (if not NULL) receives the value in force before the call. */
+int tde_set_multipole(int32_t min_k, int32_t* previous);
 /* out[0] = warp_min_k, out[1] = small_list_min of this thread. */
 int tde_get_tuning(int32_t* out);
 
@@ -210,14 +219,16 @@ int tde_profile_collect(int nids, double* ms, int64_t* launches);
 int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launches);
 
 /* Copies the workspace's device work counters (synchronises `stream`):
- * out[0] FP64 secular pole sweeps x K summed over roots (pair-evaluations),
+ * out[0] pole terms summed exactly in FP64 secular sweeps (K per sweep of a root,
+ * fewer where the block expansion takes distant blocks through their series),
  * out[1] FP64 secular sweeps, out[2] Lowner pairs, out[3] boundary-row pairs,
  * out[4] roots solved, out[5] deflated eigenvalues, out[6] close-pole rotations,
  * out[7] leaf plane rotations, out[8] merges whose rotated deflated eigenvalues
  * needed sorting, out[9] entries sorted, out[10] single-precision secular pole
  * sweeps x K, out[11] single-precision secular sweeps, out[12] requested-row
  * updates as (pole, root, row) triples, out[13] their (pole, root) sweeps (one per
- * group of up to four rows of a merge).  n <= 16 entries are copied.  The counters are
+ * group of up to four rows of a merge), out[14] pole blocks taken through their
+ * series in FP64 secular sweeps.  n <= 16 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 

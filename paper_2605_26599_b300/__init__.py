@@ -255,6 +255,15 @@ def set_tuning(warp_min_k: int = 0, small_list_min: int = 0) -> None:
     _lib.check("tde_set_tuning", _lib.load().tde_set_tuning(int(warp_min_k), int(small_list_min)))
 
 
+def set_multipole(min_k: int = 0) -> int:
+    """Threshold K of the secular solver's block expansion for later calls on this
+    thread (0 = default 2048; a value above every K turns it off).  Returns the
+    previous threshold."""
+    prev = ctypes.c_int32()
+    _lib.check("tde_set_multipole", _lib.load().tde_set_multipole(int(min_k), ctypes.byref(prev)))
+    return int(prev.value)
+
+
 def get_tuning() -> dict:
     out = (ctypes.c_int32 * 2)()
     _lib.check("tde_get_tuning", _lib.load().tde_get_tuning(out))

@@ -27,7 +27,8 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
            "tde_eigvals_noalloc", "tde_plan_query", "tde_check_reciprocal",
            "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning",
            "tde_eigvals_backward_workspace", "tde_eigvals_backward", "tde_eigvecs_rows_workspace",
-           "tde_eigvecs_rows", "tde_dense_eigvals_workspace", "tde_dense_eigvals")
+           "tde_eigvecs_rows", "tde_dense_eigvals_workspace", "tde_dense_eigvals",
+           "tde_set_multipole")
 
 MAX_SEL_ROWS = 1024  # TDE_MAX_SEL_ROWS
 
@@ -35,7 +36,7 @@ KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner
                 "sel", "sel_rows")
 WORK_NAMES = ("secular_pairs", "secular_sweeps", "lowner_pairs", "rows_pairs", "roots", "deflated",
               "rotations", "leaf_rotations", "sorts", "sorted_entries", "secular32_pairs",
-              "secular32_sweeps", "sel_row_pairs", "sel_sweep_pairs")
+              "secular32_sweeps", "sel_row_pairs", "sel_sweep_pairs", "secular_far_blocks")
 
 
 class TdeError(RuntimeError):
@@ -83,6 +84,7 @@ def load() -> ctypes.CDLL:
     lib.tde_eigvals_backward_workspace.argtypes = [i64, vp, i32, szp]
     lib.tde_eigvals_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.tde_get_tuning.argtypes = [ctypes.POINTER(ctypes.c_int32)]
+    lib.tde_set_multipole.argtypes = [i32, ctypes.POINTER(ctypes.c_int32)]
     lib.tde_profile_collect_steps.argtypes = [ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_double),
                                               ctypes.POINTER(ctypes.c_int64)]

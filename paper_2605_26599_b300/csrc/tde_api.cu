@@ -269,10 +269,16 @@ int64_t tde_last_launch_count(void) { return g_launches; }
 
 int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min) {
   if (warp_min_k < 0 || small_list_min < 0) return TDE_EINVAL;
-  Tuning t;
-  if (warp_min_k > 0) t.warp_min_k = warp_min_k;
-  if (small_list_min > 0) t.small_list_min = small_list_min;
-  g_tuning = t;
+  const Tuning d;
+  g_tuning.warp_min_k = warp_min_k > 0 ? warp_min_k : d.warp_min_k;
+  g_tuning.small_list_min = small_list_min > 0 ? small_list_min : d.small_list_min;
+  return TDE_OK;
+}
+
+int tde_set_multipole(int32_t min_k, int32_t* previous) {
+  if (min_k != 0 && min_k < 256) return TDE_EINVAL;
+  if (previous != nullptr) *previous = g_tuning.multipole_min_k;
+  g_tuning.multipole_min_k = min_k > 0 ? min_k : Tuning{}.multipole_min_k;
   return TDE_OK;
 }
 

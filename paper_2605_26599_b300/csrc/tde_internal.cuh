@@ -60,6 +60,7 @@ struct MState {
 struct Tuning {
   int32_t warp_min_k = 256;
   int32_t small_list_min = 148 * 4 * 32;
+  int32_t multipole_min_k = 2048;  // secular block expansion for merges with K >= this
 };
 Tuning& thread_tuning();
 
@@ -73,7 +74,8 @@ constexpr uint32_t kMatMask = 0x1fffffffu;
 
 // Work counters accumulated on the device by every call (reset per call):
 enum WorkCounter {
-  kWorkSecularPairs = 0,  // sum over roots of K x (number of pole sweeps)
+  kWorkSecularPairs = 0,  // pole terms summed exactly in FP64 sweeps (K per sweep without
+                          // the block expansion)
   kWorkSecularSweeps,     // sum over roots of the number of pole sweeps
   kWorkLownerPairs,       // sum over non-root merges of K^2
   kWorkRowsPairs,         // sum over non-root merges of K^2
@@ -87,6 +89,7 @@ enum WorkCounter {
   kWorkSecular32Sweeps,   // sum over roots of the number of single-precision pole sweeps
   kWorkSelRowPairs,       // requested-row updates: (pole, root, requested row) triples
   kWorkSelSweepPairs,     // requested-row updates: (pole, root) pairs per sweep of up to four rows
+  kWorkSecularFarBlocks,  // pole blocks taken through their series in FP64 sweeps
   kNumWork
 };
 
@@ -276,36 +279,6 @@ __device__ __forceinline__ int block_excl_scan(int v, int* sm, int* total) {
   *total = sm[NT / 32 - 1];
   __syncthreads();
   return before + x - v;
-}
-
-// Block-wide inclusive max-scan of one int per thread (values >= -1; -1 is the
-// identity); *total receives the block's maximum.  All threads of the block must
-// call it.  sm: NT/32 ints.
-template <int NT>
-__device__ __forceinline__ int block_incl_max_scan(int v, int* sm, int* total) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x = max(x, y);
-  }
-  if (lane == 31) sm[warp] = x;
-  __syncthreads();
-  if (warp == 0) {
-    int w = (lane < NT / 32) ? sm[lane] : -1;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w = max(w, y);
-    }
-    if (lane < NT / 32) sm[lane] = w;
-  }
-  __syncthreads();
-  const int before = (warp > 0) ? sm[warp - 1] : -1;
-  *total = sm[NT / 32 - 1];
-  __syncthreads();
-  return max(before, x);
 }
 
 // Block-wide max / sum of one double per thread, returned to every thread.  The

@@ -319,42 +319,6 @@ struct DeflateArgs {
   int32_t warp_min_k;
 };
 
-// Pole clusters of the active poles [kb, ke) of the merge at lo, for the secular
-// solver's cluster evaluation: a gap D_{k+1} - D_k is narrow when it is below 2^-28
-// of max(|D_k - shift|, |D_{k+1} - shift|) (the gaps the single-precision stage
-// cannot resolve), and a cluster is a maximal run of poles joined by narrow gaps.
-// CLF[k] (alias IDXA) receives the first pole of k's cluster; CLL[f] (alias ZPOS)
-// the last pole of the cluster starting at f.  `carry` is the cluster start of pole
-// kb - 1 (or -1); returns that of pole ke - 1.  Whole block.
-__device__ __forceinline__ bool narrow_gap(const double* AD, int k, double shift) {
-  const double a = AD[k], b = AD[k + 1];
-  return b - a < 0x1p-28 * fmax(fabs(a - shift), fabs(b - shift));
-}
-
-template <int NT>
-__device__ int write_clusters(const DeflateArgs& a, int lo, int K, int kb, int ke, double shift,
-                              int carry, int* sm_int) {
-  const double* AD = a.AD + lo;
-  int32_t* CLF = a.IDXA + lo;
-  int32_t* CLL = a.ZPOS + lo;
-  for (int c0 = kb; c0 < ke; c0 += NT) {
-    const int k = c0 + threadIdx.x;
-    int h = -1;
-    bool tail = false;
-    if (k < ke) {
-      if (k == 0 || !narrow_gap(AD, k - 1, shift)) h = k;
-      tail = k == K - 1 || !narrow_gap(AD, k, shift);
-    }
-    int chunk;
-    h = max(block_incl_max_scan<NT>(h, sm_int, &chunk), carry);
-    if (k < ke) {
-      CLF[k] = h;
-      if (tail) CLL[h] = k;
-    }
-    carry = max(carry, chunk);
-  }
-  return carry;
-}
 
 // One CTA of NT threads per merge: 64 for steps whose merges have at most 64 rows,
 // 256 up to 8192 rows and 1024 above (where steps with few merges take the
@@ -602,7 +566,6 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
         AZ32[k] = __double2float_rn(a.AZ[lo + k]);
       }
     }
-    write_clusters<NT>(a, lo, K, 0, K, shift, -1, sm_int);
     // 9. roots of this merge get a contiguous range of one of the step's two root
     //    lists: merges with K >= warp_min_k are solved one warp per root
     __shared__ int s_base;
@@ -653,7 +616,7 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
 struct ClusterSlot {
   double zmax, zsq;
   T4 agg;
-  int nkeep, nend, has_head, nz, nr, unsorted, which, base, hmax;
+  int nkeep, nend, has_head, nz, nr, unsorted, which, base;
   int changed[2];
 };
 
@@ -1082,20 +1045,6 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
         AD32[k] = make_float2(hi, __double2float_rn(x - double(hi)));
         AZ32[k] = __double2float_rn(a.AZ[lo + k]);
       }
-    }
-    {  // pole clusters over the CTA slices; the cluster start carried into a slice is
-       // the last cluster start of the slices before
-      const int LK = (K + C - 1) / C;
-      const int kb = min(K, r * LK), ke = min(K, kb + LK);
-      int hmax = -1;
-      for (int k = kb + tid; k < ke; k += NT)
-        if (k == 0 || !narrow_gap(a.AD + lo, k - 1, shift)) hmax = k;
-      hmax = block_max_int<NT>(hmax, sm_int);
-      if (tid == 0) slot.hmax = hmax;
-      cl.sync();
-      int carry = lane < r ? cl.map_shared_rank(&slot, lane)->hmax : -1;
-      carry = __reduce_max_sync(0xffffffffu, carry);
-      write_clusters<NT>(a, lo, K, kb, ke, shift, carry, sm_int);
     }
     // 9. root list range and merge state (CTA 0), then the root map
     const bool big = K >= a.warp_min_k;

@@ -38,10 +38,8 @@ struct RootArgs {
   double* ZHAT;           // aliases Z
   double *ROWLO, *ROWHI;  // alias RLO, RHI: parent rows of the active columns
   double* DORG;           // alias KEYA: D_org(j) of every active root
-  int32_t* CLF;           // alias IDXA: first pole of each active pole's cluster
-  int32_t* CLL;           // alias ZPOS: at a cluster's first pole, its last (-1: unused)
-  double *CF0, *CF1, *CF2;  // alias RLO, RHI, Z: outside sums of each cluster
-  float* CF3;               // alias SEG: their highest-order terms, times span^3
+  double* MPD;            // alias Z: pole-block centres, radii and moments (BlockFar)
+  int32_t mp_min_k;       // merges with K >= this use the block expansion
   Status* st;
   uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
   int all_merges;           // also build z-hat and rows at root merges (adjoint)
@@ -543,86 +541,28 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
   return sweeps;
 }
 
-// Cluster evaluation of the FP64 sums.  Where a root's two bracketing poles lie in
-// one pole cluster [f, l] (a maximal run of poles joined by gaps too narrow for the
-// single-precision stage, found at deflation), the sums split at a near range
-// [F, L] containing the cluster: its poles are summed exactly at every sweep, the
-// poles outside it once per cluster (k_cluster_far), as the first four Taylor
-// coefficients of each side about the cluster's first pole m = D_f,
-//   c_k = sum_{i outside [F, L], one side} z_i^2 / (D_i - m)^(k+1),  k = 0..3
-// (c3, whose term only has to be roughly right, kept as a float times span^3),
-// which a sweep adds as c0 + c1 d + c2 d^2 + c3 d^3 to psi / phi and
-// c1 + 2 c2 d + 3 c3 d^2 to their derivatives, with d = lambda - m =
-// (D_org - m) + tau (D_org - m is exact: both are cluster poles).  The near range
-// starts as the cluster and takes in whole neighbouring clusters (at most four
-// times) until the cluster's span is at most 2^-15 of the distance from m to the
-// nearest pole outside; otherwise the cluster is not used.  The dropped terms then
-// stay below 2^-60 of the outside sums, far below the rounding bound of the
-// convergence test.  Only the warp-per-root kernel (large K, where the saving is)
-// evaluates clusters this way.
-__device__ __forceinline__ bool cluster_extent(const double* __restrict__ D,
-                                               const int32_t* __restrict__ CLF,
-                                               const int32_t* __restrict__ CLL, int K, int f,
-                                               int* F, int* L) {
-  const int l = CLL[f];
-  const double m = D[f], span = D[l] - m;
-  int lo = f, hi = l;
-  for (int it = 0; it <= 4; ++it) {
-    const double dl = lo > 0 ? m - D[lo - 1] : INFINITY;
-    const double dr = hi < K - 1 ? D[hi + 1] - m : INFINITY;
-    const double dist = fmin(dl, dr);
-    if (span <= 0x1p-15 * dist) {
-      *F = lo;
-      *L = hi;
-      return true;
-    }
-    if (it == 4) break;
-    if (dl < dr)
-      lo = CLF[lo - 1];
-    else
-      hi = CLL[hi + 1];  // pole hi + 1 starts the next cluster (the gap before it is wide)
-  }
-  return false;
-}
+// Block expansion of the FP64 sums (merges with K >= mp_min_k, warp-per-root
+// kernel).  The K poles are cut into nb = K / 128 blocks of consecutive poles (the
+// last one takes the remainder).  Per block, k_block_moments stores its centre m,
+// its radius r (largest |D_i - m|) and the moments
+//   M_k = sum_{i in block} z_i^2 (D_i - m)^k,   k = 0 .. 26,
+// so that for lambda outside the block, with t = 1 / (m - lambda),
+//   sum z_i^2 / (D_i - lambda)   = t   sum_k M_k (-t)^k,
+//   sum z_i^2 / (D_i - lambda)^2 = t^2 sum_k (k + 1) M_k (-t)^k.
+// A sweep takes a block through these series when r <= |m - lambda| / 4: the
+// dropped terms are then below 4^-27 (4/3)^2 < 2^-53 of the block's own
+// sum_i |z_i^2 / (D_i - lambda)|, under the rounding bound of the convergence test.
+// Every other block (the root's own and its neighbours) is summed exactly.  The
+// block lies wholly on one side of lambda, so it adds to psi or phi as a whole.
+// m - lambda is formed as (m - D_org) - tau, like every Delta.
+constexpr int kMpBlock = 128;  // poles per block
+constexpr int kMpTerms = 27;   // series terms
+constexpr int kMpFields = 2 + 2 * kMpTerms;  // m, r, M_k, (k + 1) M_k
 
-struct ClusterFar {
-  int nb, ne;  // poles summed exactly: [nb, ne) (all of them, without outside sums, if !on)
-  bool on;
-  double m, c0l, c1l, c2l, c3l, c0r, c1r, c2r, c3r;
-  __device__ __forceinline__ void add(SecSums& s, double dorg, double tau) const {
-    const double d = (dorg - m) + tau;
-    s.psi += fma(d, fma(d, fma(d, c3l, c2l), c1l), c0l);
-    s.dpsi += fma(d, fma(3.0 * d, c3l, 2.0 * c2l), c1l);
-    s.phi += fma(d, fma(d, fma(d, c3r, c2r), c1r), c0r);
-    s.dphi += fma(d, fma(3.0 * d, c3r, 2.0 * c2r), c1r);
-  }
-};
-
-__device__ __forceinline__ ClusterFar cluster_far(const RootArgs& a, int lo, int K, int j) {
-  ClusterFar c;
-  c.nb = 0;
-  c.ne = K;
-  c.on = false;
-  c.m = c.c0l = c.c1l = c.c2l = c.c3l = c.c0r = c.c1r = c.c2r = c.c3r = 0.0;
-  if (j >= K - 1) return c;
-  const int f = a.CLF[lo + j];
-  if (a.CLF[lo + j + 1] != f) return c;
-  int F, L;
-  if (!cluster_extent(a.AD + lo, a.CLF + lo, a.CLL + lo, K, f, &F, &L)) return c;
-  c.nb = F;
-  c.ne = L + 1;
-  c.on = true;
-  c.m = a.AD[lo + f];
-  c.c0l = a.CF0[lo + f];
-  c.c1l = a.CF0[lo + f + 1];
-  c.c2l = a.CF1[lo + f];
-  const double sp = a.AD[lo + a.CLL[lo + f]] - c.m, sp3 = sp * sp * sp;
-  c.c3l = double(a.CF3[lo + f]) / sp3;
-  c.c0r = a.CF1[lo + f + 1];
-  c.c1r = a.CF2[lo + f];
-  c.c2r = a.CF2[lo + f + 1];
-  c.c3r = double(a.CF3[lo + f + 1]) / sp3;
-  return c;
+// Block data of the merge at lo lives coefficient-major in MPD + lo: field q of
+// block b at [q * nb + b] (56 nb <= K entries, inside the merge's rows).
+__device__ __forceinline__ int mp_blocks(int K, int mp_min_k) {
+  return K >= mp_min_k ? K / kMpBlock : 0;
 }
 
 // one thread evaluates all K poles
@@ -686,22 +626,73 @@ __device__ __forceinline__ void lane_sums(const double* __restrict__ D, const do
   dsum = (d0 + d1) + (d2 + d3);
 }
 
+// All 32 lanes sum one root.  With nb > 0 (block expansion) lane l takes blocks
+// l, l + 32, ...: a far block through its series, and the near blocks found in
+// each round of 32 are summed exactly by the whole warp.  `pairs` and `blocks`
+// count the exact pole terms and the series evaluations (work counters).
 struct WarpSweep {
   const double* __restrict__ D;
   const double* __restrict__ Z;
   int K;
   int lane;
-  ClusterFar cf;
+  int nb;
+  const double* __restrict__ MP;
+  mutable unsigned long long pairs;
+  mutable unsigned blocks;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
-    double p, dp, f, df;
-    lane_sums(D, Z, cf.nb, jl + 1, lane, dorg, tau, p, dp);
-    lane_sums(D, Z, jl + 1, cf.ne, lane, dorg, tau, f, df);
+    double p = 0.0, dp = 0.0, f = 0.0, df = 0.0;
+    if (nb == 0) {
+      lane_sums(D, Z, 0, jl + 1, lane, dorg, tau, p, dp);
+      lane_sums(D, Z, jl + 1, K, lane, dorg, tau, f, df);
+      pairs += unsigned(K);
+    } else {
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        bool near = false;
+        if (b < nb) {
+          const double dm = (MP[b] - dorg) - tau;  // m - lambda
+          if (MP[nb + b] <= 0.25 * fabs(dm)) {
+            const double t = rcp_refined(dm), u = -t;
+            double val = MP[(1 + kMpTerms) * nb + b], der = MP[(1 + 2 * kMpTerms) * nb + b];
+#pragma unroll
+            for (int k = kMpTerms - 2; k >= 0; --k) {
+              val = fma(val, u, MP[(2 + k) * nb + b]);
+              der = fma(der, u, MP[(2 + kMpTerms + k) * nb + b]);
+            }
+            if (dm > 0.0) {
+              f = fma(t, val, f);
+              df = fma(t * t, der, df);
+            } else {
+              p = fma(t, val, p);
+              dp = fma(t * t, der, dp);
+            }
+          } else {
+            near = true;
+          }
+        }
+        unsigned nm = __ballot_sync(0xffffffffu, near);
+        blocks += unsigned(min(32, nb - b0) - __popc(nm));
+        while (nm) {
+          const int bb = b0 + __ffs(nm) - 1;
+          nm &= nm - 1;
+          const int i0 = bb * kMpBlock, i1 = (bb == nb - 1) ? K : i0 + kMpBlock;
+          const int mid = min(max(jl + 1, i0), i1);
+          double a, da;
+          lane_sums(D, Z, i0, mid, lane, dorg, tau, a, da);
+          p += a;
+          dp += da;
+          lane_sums(D, Z, mid, i1, lane, dorg, tau, a, da);
+          f += a;
+          df += da;
+          pairs += unsigned(i1 - i0);
+        }
+      }
+    }
     SecSums s;
     s.psi = warp_sum(p);
     s.dpsi = warp_sum(dp);
     s.phi = warp_sum(f);
     s.dphi = warp_sum(df);
-    if (cf.on) cf.add(s, dorg, tau);
     return s;
   }
 };
@@ -854,9 +845,16 @@ __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, 
 
 // per-thread tallies of the device work counters, flushed once per thread
 struct SecTally {
-  unsigned pairs = 0, sweeps = 0, pairs32 = 0, sweeps32 = 0, roots = 0;
+  unsigned long long pairs = 0;
+  unsigned sweeps = 0, pairs32 = 0, sweeps32 = 0, roots = 0, blocks = 0;
   __device__ __forceinline__ void add(int n64, int n32, int K) {
-    pairs += unsigned(n64) * unsigned(K);
+    add_counted((unsigned long long)n64 * unsigned(K), 0u, n64, n32, K);
+  }
+  // FP64 work given as exact pole terms and block series evaluations
+  __device__ __forceinline__ void add_counted(unsigned long long exact, unsigned nblocks, int n64,
+                                              int n32, int K) {
+    pairs += exact;
+    blocks += nblocks;
     sweeps += unsigned(n64);
     pairs32 += unsigned(n32) * unsigned(K);
     sweeps32 += unsigned(n32);
@@ -864,7 +862,8 @@ struct SecTally {
   }
   __device__ __forceinline__ void flush(Status* st) const {
     if (!roots) return;
-    atomicAdd(&st->work[kWorkSecularPairs], (unsigned long long)pairs);
+    atomicAdd(&st->work[kWorkSecularPairs], pairs);
+    if (blocks) atomicAdd(&st->work[kWorkSecularFarBlocks], (unsigned long long)blocks);
     atomicAdd(&st->work[kWorkSecularSweeps], (unsigned long long)sweeps);
     atomicAdd(&st->work[kWorkSecular32Pairs], (unsigned long long)pairs32);
     atomicAdd(&st->work[kWorkSecular32Sweeps], (unsigned long long)sweeps32);
@@ -890,78 +889,64 @@ __device__ __forceinline__ int warp_list_merge(const RootArgs& a, uint32_t r, in
   return a.ROOTMAP[r - nb];
 }
 
-// Outside sums of the pole clusters of the merges whose roots k_secular_warp
-// solves (ClusterFar), one block per cluster: blocks walk that kernel's root list
-// 128 roots at a time and take, one after the other, the roots of the chunk that
-// start a cluster of two or more poles (clusters without a valid near range,
-// cluster_extent, are skipped: their roots sum all poles).
-__global__ void __launch_bounds__(128) k_cluster_far(RootArgs a) {
-  __shared__ int s_head[128][2];
-  __shared__ int s_n;
-  __shared__ double s_red[4][8];
+// Block centres, radii and moments (BlockFar) of the merges whose roots
+// k_secular_warp solves and whose K reaches mp_min_k, one warp per block: warps
+// walk that kernel's root list 32 roots at a time, and root j = 128 b stands for
+// block b.
+__global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
   const uint32_t total = warp_list_total(a);
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (uint32_t base = blockIdx.x * 128u; base < total; base += gridDim.x * 128u) {
-    if (tid == 0) s_n = 0;
-    __syncthreads();
-    const uint32_t r = base + tid;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
+    const uint32_t r = base + lane;
+    int g = 0, j = 0, nb = 0;
+    bool head = false;
     if (r < total) {
       int rl;
-      const int g = warp_list_merge(a, r, &rl);
+      g = warp_list_merge(a, r, &rl);
       const MState ms = a.ms[g];
-      const int j = rl - ms.base, lo = a.M[g].lo;
-      if (j < ms.K - 1 && a.CLF[lo + j] == j && a.CLF[lo + j + 1] == j) {
-        const int q = atomicAdd(&s_n, 1);
-        s_head[q][0] = g;
-        s_head[q][1] = j;
-      }
+      j = rl - ms.base;
+      nb = mp_blocks(ms.K, a.mp_min_k);
+      head = nb > 0 && (j % kMpBlock) == 0 && j / kMpBlock < nb;
     }
-    __syncthreads();
-    const int nh = s_n;
-    for (int h = 0; h < nh; ++h) {
-      const int g = s_head[h][0], f = s_head[h][1];
-      const int lo = a.M[g].lo, K = a.ms[g].K;
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int gg = __shfl_sync(0xffffffffu, g, src), b = __shfl_sync(0xffffffffu, j, src) / kMpBlock;
+      const int nbb = __shfl_sync(0xffffffffu, nb, src);
+      const int lo = a.M[gg].lo, K = a.ms[gg].K;
       const double* D = a.AD + lo;
       const double* Z = a.AZ + lo;
-      int F, L;
-      if (!cluster_extent(D, a.CLF + lo, a.CLL + lo, K, f, &F, &L)) continue;
-      const double m = D[f];
-      double c[8];
+      const int i0 = b * kMpBlock, i1 = (b == nbb - 1) ? K : i0 + kMpBlock;
+      const double m = 0.5 * (D[i0] + D[i1 - 1]);
+      const double rad = fmax(m - D[i0], D[i1 - 1] - m);
+      double mo[kMpTerms];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) c[q] = 0.0;
-      for (int i = tid; i < F; i += 128) {
-        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0, u = t * r0;
-        c[0] = fma(Z[i], t, c[0]);
-        c[1] = fma(t, t, c[1]);
-        c[2] = fma(t, u, c[2]);
-        c[3] = fma(u, u, c[3]);
-      }
-      for (int i = L + 1 + tid; i < K; i += 128) {
-        const double r0 = rcp_refined(D[i] - m), t = Z[i] * r0, u = t * r0;
-        c[4] = fma(Z[i], t, c[4]);
-        c[5] = fma(t, t, c[5]);
-        c[6] = fma(t, u, c[6]);
-        c[7] = fma(u, u, c[7]);
+      for (int k = 0; k < kMpTerms; ++k) mo[k] = 0.0;
+      for (int i = i0 + lane; i < i1; i += 32) {
+        const double y = D[i] - m;
+        double pw = Z[i] * Z[i];
+#pragma unroll
+        for (int k = 0; k < kMpTerms; ++k) {
+          mo[k] += pw;
+          pw *= y;
+        }
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) c[q] = warp_sum(c[q]);
-      if (lane == 0)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) s_red[warp][q] = c[q];
-      __syncthreads();
-      if (tid == 0) {
-        for (int q = 0; q < 8; ++q) c[q] = (s_red[0][q] + s_red[1][q]) + (s_red[2][q] + s_red[3][q]);
-        a.CF0[lo + f] = c[0];
-        a.CF0[lo + f + 1] = c[1];
-        a.CF1[lo + f] = c[2];
-        const double sp = D[a.CLL[lo + f]] - m, sp3 = sp * sp * sp;  // c3 sp^3 <= c0
-        a.CF3[lo + f] = float(c[3] * sp3);
-        a.CF1[lo + f + 1] = c[4];
-        a.CF2[lo + f] = c[5];
-        a.CF2[lo + f + 1] = c[6];
-        a.CF3[lo + f + 1] = float(c[7] * sp3);
+      for (int k = 0; k < kMpTerms; ++k) mo[k] = warp_sum(mo[k]);
+      double* MP = a.MPD + lo;
+      if (lane == 0) {
+        MP[b] = m;
+        MP[nbb + b] = rad;
       }
-      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < kMpTerms; ++k)
+        if (lane == (k & 31)) {
+          MP[(2 + k) * nbb + b] = mo[k];
+          MP[(2 + kMpTerms + k) * nbb + b] = double(k + 1) * mo[k];
+        }
     }
   }
 }
@@ -1044,7 +1029,8 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     const MState ms = a.ms[g];
     const int q = rl - ms.base, lo = a.M[g].lo;
     const int j = (q & 1) ? ms.K - 1 - (q >> 1) : (q >> 1);
-    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, cluster_far(a, lo, ms.K, j)};
+    const int nb = mp_blocks(ms.K, a.mp_min_k);
+    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, 0ull, 0u};
     GroupSweep32<32> sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, 0xffffffffu};
     int org, n32;
     double tau;
@@ -1053,7 +1039,7 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
         secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok,
                      &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
-    tally.add(sweeps, n32, ms.K);
+    tally.add_counted(sw.pairs, sw.blocks, sweeps, n32, ms.K);
   }
   if (lane == 0) tally.flush(a.st);
   claim_finish_block(a.st);
@@ -1332,12 +1318,8 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.AHI = ws.AHI;
   ra.AD32 = reinterpret_cast<const float2*>(ws.KEYB);
   ra.AZ32 = reinterpret_cast<const float*>(ws.IDXB);
-  ra.CLF = ws.IDXA;
-  ra.CLL = ws.ZPOS;
-  ra.CF0 = ws.RLO;
-  ra.CF1 = ws.RHI;
-  ra.CF2 = ws.Z;
-  ra.CF3 = reinterpret_cast<float*>(ws.SEG);
+  ra.MPD = ws.Z;
+  ra.mp_min_k = plan.tune.multipole_min_k;
   ra.TAU = ws.TAU;
   ra.ORG = ws.ORG;
   ra.LAMA = ws.D;
@@ -1366,8 +1348,10 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
                                           reinterpret_cast<double*>(ws.KEYA), ws.D);
     launches = 1;
   } else {
-  k_cluster_far<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
-  ++launches;
+  if (plan.step_maxsize[step] >= ra.mp_min_k) {
+    k_block_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+    ++launches;
+  }
   switch (G) {
     case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
     case 4: k_secular_group<4><<<ggrid, 128, 0, s>>>(ra); break;

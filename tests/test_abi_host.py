@@ -125,6 +125,22 @@ def test_argument_validation_without_device_work():
     assert lib.tde_eigvecs_rows(10, fake, fake, 3, fake, fake, fake, 0, fake, 64, None) == _lib.TDE_EWORKSPACE
 
 
+def test_multipole_threshold_rules():
+    lib = _lib.load()
+    prev = ctypes.c_int32()
+    assert lib.tde_set_multipole(100, ctypes.byref(prev)) == _lib.TDE_EINVAL
+    assert lib.tde_set_multipole(-1, None) == _lib.TDE_EINVAL
+    assert lib.tde_set_multipole(0, ctypes.byref(prev)) == _lib.TDE_OK
+    default = prev.value
+    assert lib.tde_set_multipole(4096, ctypes.byref(prev)) == _lib.TDE_OK
+    assert lib.tde_set_multipole(0, ctypes.byref(prev)) == _lib.TDE_OK and prev.value == 4096
+    assert lib.tde_set_multipole(default, None) == _lib.TDE_OK
+    # tde_set_tuning leaves the threshold alone
+    assert lib.tde_set_multipole(8192, None) == _lib.TDE_OK
+    assert lib.tde_set_tuning(0, 0) == _lib.TDE_OK
+    assert lib.tde_set_multipole(0, ctypes.byref(prev)) == _lib.TDE_OK and prev.value == 8192
+
+
 def test_python_binding_refuses_cpu_tensors():
     import torch
 
