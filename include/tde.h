@@ -181,7 +181,8 @@ int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min);
  * thread: FP64 sweeps of merges whose active rank K reaches min_k (and that the
  * warp-per-root kernel solves) sum the poles of distant 128-pole blocks through a
  * 27-term series of the block's moments instead of term by term (series error
- * below 2^-53 of the block's terms).  min_k = 0 restores the default (2048); any
+ * below 2^-53 of the block's terms), and so do the boundary-row sums of those
+ * merges (32 terms, below 2^-58).  min_k = 0 restores the default (2048); any
  * other value below 256 is TDE_EINVAL; a value above every K turns the expansion
  * off.  *previous (if not NULL) receives the value in force before the call. */
 int tde_set_multipole(int32_t min_k, int32_t* previous);
@@ -221,14 +222,16 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
 /* Copies the workspace's device work counters (synchronises `stream`):
  * out[0] pole terms summed exactly in FP64 secular sweeps (K per sweep of a root,
  * fewer where the block expansion takes distant blocks through their series),
- * out[1] FP64 secular sweeps, out[2] Lowner pairs, out[3] boundary-row pairs,
+ * out[1] FP64 secular sweeps, out[2] Lowner pairs, out[3] boundary-row terms summed
+ * exactly (K per root without the block expansion),
  * out[4] roots solved, out[5] deflated eigenvalues, out[6] close-pole rotations,
  * out[7] leaf plane rotations, out[8] merges whose rotated deflated eigenvalues
  * needed sorting, out[9] entries sorted, out[10] single-precision secular pole
  * sweeps x K, out[11] single-precision secular sweeps, out[12] requested-row
  * updates as (pole, root, row) triples, out[13] their (pole, root) sweeps (one per
  * group of up to four rows of a merge), out[14] pole blocks taken through their
- * series in FP64 secular sweeps.  n <= 16 entries are copied.  The counters are
+ * series in FP64 secular sweeps, out[15] pole blocks taken through their series in
+ * the boundary-row sums.  n <= 16 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 

@@ -78,7 +78,8 @@ enum WorkCounter {
                           // the block expansion)
   kWorkSecularSweeps,     // sum over roots of the number of pole sweeps
   kWorkLownerPairs,       // sum over non-root merges of K^2
-  kWorkRowsPairs,         // sum over non-root merges of K^2
+  kWorkRowsPairs,         // (pole, root) terms of the row sums summed exactly (K^2 per
+                          // non-root merge without the block expansion)
   kWorkRoots,             // roots solved
   kWorkDeflated,          // eigenvalues deflated (small z or rotation)
   kWorkRotations,         // close-pole rotations
@@ -90,6 +91,7 @@ enum WorkCounter {
   kWorkSelRowPairs,       // requested-row updates: (pole, root, requested row) triples
   kWorkSelSweepPairs,     // requested-row updates: (pole, root) pairs per sweep of up to four rows
   kWorkSecularFarBlocks,  // pole blocks taken through their series in FP64 sweeps
+  kWorkRowsFarBlocks,     // pole blocks taken through their series in the row sums
   kNumWork
 };
 

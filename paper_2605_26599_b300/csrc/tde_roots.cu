@@ -38,7 +38,8 @@ struct RootArgs {
   double* ZHAT;           // aliases Z
   double *ROWLO, *ROWHI;  // alias RLO, RHI: parent rows of the active columns
   double* DORG;           // alias KEYA: D_org(j) of every active root
-  double* MPD;            // alias Z: pole-block centres, radii and moments (BlockFar)
+  double* MPD;            // alias Z: pole-block centres, radii and moments (secular)
+  double* MPR;            // alias KEYB: the same for the boundary rows (after Löwner)
   int32_t mp_min_k;       // merges with K >= this use the block expansion
   Status* st;
   uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
@@ -1249,12 +1250,135 @@ __device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* 
   sho = (MODE & 2) ? warp_sum(sh + shb) : 0.0;
 }
 
+// Block expansion of the row sums (merges with K >= mp_min_k): with the blocks of
+// the secular expansion and t = 1 / (m - lambda_j), a block far from lambda_j
+// (r <= |m - lambda_j| / 4) adds
+//   t^2 sum_k (k + 1) A_k (-t)^k  to  sum zhat_i^2 / Delta_ij^2,   A_k = sum zhat^2 y^k,
+//   t   sum_k L_k (-t)^k          to  sum ALO_i zhat_i / Delta_ij,  L_k = sum zhat ALO y^k,
+//   t   sum_k H_k (-t)^k          to  sum AHI_i zhat_i / Delta_ij,  H_k = sum zhat AHI y^k,
+// y = D_i - m, with 32 terms: the dropped part stays below 2^-58 of the sum of the
+// block's |terms| for the squared kernel and below 2^-60 for the others.
+constexpr int kMrTerms = 32;
+constexpr int kMrFields = 2 + 3 * kMrTerms;  // m, r, (k + 1) A_k, L_k, H_k
+
+// Moments of the row sums, one warp per block (found as in k_block_moments).
+__global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
+  const uint32_t total = warp_list_total(a);
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
+    const uint32_t r = base + lane;
+    int g = 0, j = 0, nb = 0;
+    bool head = false;
+    if (r < total) {
+      int rl;
+      g = warp_list_merge(a, r, &rl);
+      const Merge m = a.M[g];
+      const MState ms = a.ms[g];
+      j = rl - ms.base;
+      nb = ((uint32_t(m.info) & kRootBit) && !a.all_merges) ? 0 : mp_blocks(ms.K, a.mp_min_k);
+      head = nb > 0 && (j % kMpBlock) == 0 && j / kMpBlock < nb;
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int gg = __shfl_sync(0xffffffffu, g, src), b = __shfl_sync(0xffffffffu, j, src) / kMpBlock;
+      const int nbb = __shfl_sync(0xffffffffu, nb, src);
+      const int lo = a.M[gg].lo, K = a.ms[gg].K;
+      const double* D = a.AD + lo;
+      const double* ZH = a.ZHAT + lo;
+      const int i0 = b * kMpBlock, i1 = (b == nbb - 1) ? K : i0 + kMpBlock;
+      const double m = 0.5 * (D[i0] + D[i1 - 1]);
+      double* MP = a.MPR + lo;
+      if (lane == 0) {
+        MP[b] = m;
+        MP[nbb + b] = fmax(m - D[i0], D[i1 - 1] - m);
+      }
+      for (int which = 0; which < 3; ++which) {  // zhat^2 (stored times k + 1), zhat ALO, zhat AHI
+        const double* W = which == 1 ? a.ALO + lo : a.AHI + lo;
+        double mo[kMrTerms];
+#pragma unroll
+        for (int k = 0; k < kMrTerms; ++k) mo[k] = 0.0;
+        for (int i = i0 + lane; i < i1; i += 32) {
+          const double y = D[i] - m;
+          double pw = ZH[i] * (which == 0 ? ZH[i] : W[i]);
+#pragma unroll
+          for (int k = 0; k < kMrTerms; ++k) {
+            mo[k] += pw;
+            pw *= y;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kMrTerms; ++k) {
+          const double v = warp_sum(mo[k]);
+          if (lane == (k & 31)) MP[(2 + which * kMrTerms + k) * nbb + b] = which == 0 ? double(k + 1) * v : v;
+        }
+      }
+    }
+  }
+}
+
+// Row sums of one root with the block expansion (all 32 lanes): far blocks one per
+// lane through their series, near blocks term by term by the whole warp.
+template <int MODE>
+__device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const double* ZH,
+                                                       const double* AL, const double* AH, int K,
+                                                       int nb, const double* __restrict__ MP,
+                                                       int lane, double dorg, double tau,
+                                                       double& s2o, double& slo, double& sho,
+                                                       unsigned& exact, unsigned& series) {
+  double s2 = 0.0, sl = 0.0, sh = 0.0;
+  for (int b0 = 0; b0 < nb; b0 += 32) {
+    const int b = b0 + lane;
+    bool near = false;
+    if (b < nb) {
+      const double dm = (MP[b] - dorg) - tau;  // m - lambda
+      if (MP[nb + b] <= 0.25 * fabs(dm)) {
+        const double t = rcp_refined(dm), u = -t;
+        double va = MP[(1 + kMrTerms) * nb + b];
+        double vl = (MODE & 1) ? MP[(1 + 2 * kMrTerms) * nb + b] : 0.0;
+        double vh = (MODE & 2) ? MP[(1 + 3 * kMrTerms) * nb + b] : 0.0;
+#pragma unroll
+        for (int k = kMrTerms - 2; k >= 0; --k) {
+          va = fma(va, u, MP[(2 + k) * nb + b]);
+          if (MODE & 1) vl = fma(vl, u, MP[(2 + kMrTerms + k) * nb + b]);
+          if (MODE & 2) vh = fma(vh, u, MP[(2 + 2 * kMrTerms + k) * nb + b]);
+        }
+        s2 = fma(t * t, va, s2);
+        if (MODE & 1) sl = fma(t, vl, sl);
+        if (MODE & 2) sh = fma(t, vh, sh);
+      } else {
+        near = true;
+      }
+    }
+    unsigned nm = __ballot_sync(0xffffffffu, near);
+    series += unsigned(min(32, nb - b0) - __popc(nm));
+    while (nm) {
+      const int bb = b0 + __ffs(nm) - 1;
+      nm &= nm - 1;
+      const int i0 = bb * kMpBlock, i1 = (bb == nb - 1) ? K : i0 + kMpBlock;
+      for (int i = i0 + lane; i < i1; i += 32) {
+        const double t0 = ZH[i] * rcp_refined((AD[i] - dorg) - tau);
+        s2 = fma(t0, t0, s2);
+        if (MODE & 1) sl = fma(AL[i], t0, sl);
+        if (MODE & 2) sh = fma(AH[i], t0, sh);
+      }
+      exact += unsigned(i1 - i0);
+    }
+  }
+  s2o = warp_sum(s2);
+  slo = (MODE & 1) ? warp_sum(sl) : 0.0;
+  sho = (MODE & 2) ? warp_sum(sh) : 0.0;
+}
+
 __global__ void k_rows_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned pairs = 0;
+  unsigned pairs = 0, series = 0;
   for (uint32_t r = warp; r < total; r += nwarps) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
@@ -1269,10 +1393,21 @@ __global__ void k_rows_warp(RootArgs a) {
     const double dorg = a.DORG[lo + j];
     const double tau = a.TAU[lo + j];
     double s2, sl, sh;
-    switch (rows_mode(a, m)) {
-      case 1: rows_warp_sweep<1>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
-      case 2: rows_warp_sweep<2>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
-      default: rows_warp_sweep<3>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
+    const int nb = mp_blocks(K, a.mp_min_k);
+    if (nb > 0) {
+      const double* MP = a.MPR + lo;
+      switch (rows_mode(a, m)) {
+        case 1: rows_warp_sweep_blocks<1>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series); break;
+        case 2: rows_warp_sweep_blocks<2>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series); break;
+        default: rows_warp_sweep_blocks<3>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series); break;
+      }
+    } else {
+      switch (rows_mode(a, m)) {
+        case 1: rows_warp_sweep<1>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
+        case 2: rows_warp_sweep<2>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
+        default: rows_warp_sweep<3>(AD, ZH, AL, AH, K, lane, dorg, tau, s2, sl, sh); break;
+      }
+      pairs += unsigned(K);
     }
     if (lane == 0) {
       const double inv = 1.0 / sqrt(s2);
@@ -1280,9 +1415,9 @@ __global__ void k_rows_warp(RootArgs a) {
       a.ROWLO[lo + j] = sl * inv;
       a.ROWHI[lo + j] = sh * inv;
     }
-    pairs += unsigned(K);
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkRowsPairs], (unsigned long long)pairs);
+  if (lane == 0 && series) atomicAdd(&a.st->work[kWorkRowsFarBlocks], (unsigned long long)series);
 }
 
 // Restores the saved roots of one step: tau, D_org and lambda = D_org + tau (the
@@ -1319,6 +1454,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   ra.AD32 = reinterpret_cast<const float2*>(ws.KEYB);
   ra.AZ32 = reinterpret_cast<const float*>(ws.IDXB);
   ra.MPD = ws.Z;
+  ra.MPR = reinterpret_cast<double*>(ws.KEYB);
   ra.mp_min_k = plan.tune.multipole_min_k;
   ra.TAU = ws.TAU;
   ra.ORG = ws.ORG;
@@ -1367,6 +1503,10 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
     k_lowner_warp<<<wgrid, 128, 0, s>>>(ra);
     prof_end(kKLowner, s);
     prof_begin(kKRows, s);
+    if (plan.step_maxsize[step] >= ra.mp_min_k) {
+      k_rows_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+      ++launches;
+    }
     k_rows_thread<<<tgrid, 128, 0, s>>>(ra);
     k_rows_warp<<<wgrid, 128, 0, s>>>(ra);
     prof_end(kKRows, s);
