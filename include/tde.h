@@ -182,7 +182,8 @@ int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min);
  * warp-per-root kernel solves) sum the poles of distant 128-pole blocks through a
  * 27-term series of the block's moments instead of term by term (series error
  * below 2^-53 of the block's terms), and so do the boundary-row sums of those
- * merges (32 terms, below 2^-58).  min_k = 0 restores the default (2048); any
+ * merges (32 terms, below 2^-58) and the Lowner products in log form (27 terms,
+ * below 2^-55 absolute in the log).  min_k = 0 restores the default (2048); any
  * other value below 256 is TDE_EINVAL; a value above every K turns the expansion
  * off.  *previous (if not NULL) receives the value in force before the call. */
 int tde_set_multipole(int32_t min_k, int32_t* previous);
@@ -222,7 +223,8 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
 /* Copies the workspace's device work counters (synchronises `stream`):
  * out[0] pole terms summed exactly in FP64 secular sweeps (K per sweep of a root,
  * fewer where the block expansion takes distant blocks through their series),
- * out[1] FP64 secular sweeps, out[2] Lowner pairs, out[3] boundary-row terms summed
+ * out[1] FP64 secular sweeps, out[2] Lowner factors multiplied directly (K per
+ * pole without the block expansion), out[3] boundary-row terms summed
  * exactly (K per root without the block expansion),
  * out[4] roots solved, out[5] deflated eigenvalues, out[6] close-pole rotations,
  * out[7] leaf plane rotations, out[8] merges whose rotated deflated eigenvalues
@@ -231,7 +233,8 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
  * updates as (pole, root, row) triples, out[13] their (pole, root) sweeps (one per
  * group of up to four rows of a merge), out[14] pole blocks taken through their
  * series in FP64 secular sweeps, out[15] pole blocks taken through their series in
- * the boundary-row sums.  n <= 16 entries are copied.  The counters are
+ * the boundary-row sums, out[16] pair blocks taken through their series in the
+ * Lowner products.  n <= 17 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 

@@ -343,7 +343,7 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
 }
 
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n) {
-  if (ws == nullptr || out == nullptr || n < 0 || n > 16) return TDE_EINVAL;
+  if (ws == nullptr || out == nullptr || n < 0 || n > kNumWork) return TDE_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Status* st = static_cast<const Status*>(ws);
   if (cudaMemcpyAsync(out, st->work, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost, s) !=

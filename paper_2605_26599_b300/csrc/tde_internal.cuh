@@ -77,7 +77,8 @@ enum WorkCounter {
   kWorkSecularPairs = 0,  // pole terms summed exactly in FP64 sweeps (K per sweep without
                           // the block expansion)
   kWorkSecularSweeps,     // sum over roots of the number of pole sweeps
-  kWorkLownerPairs,       // sum over non-root merges of K^2
+  kWorkLownerPairs,       // Löwner factors multiplied directly (K^2 per non-root merge
+                          // without the block expansion)
   kWorkRowsPairs,         // (pole, root) terms of the row sums summed exactly (K^2 per
                           // non-root merge without the block expansion)
   kWorkRoots,             // roots solved
@@ -92,6 +93,7 @@ enum WorkCounter {
   kWorkSelSweepPairs,     // requested-row updates: (pole, root) pairs per sweep of up to four rows
   kWorkSecularFarBlocks,  // pole blocks taken through their series in FP64 sweeps
   kWorkRowsFarBlocks,     // pole blocks taken through their series in the row sums
+  kWorkLownerFarBlocks,   // pair blocks taken through their series in the Löwner products
   kNumWork
 };
 
@@ -102,7 +104,7 @@ struct Status {
   int32_t pad[29];
   uint32_t root_count[kMaxSteps];      // roots of small-K merges per step
   uint32_t root_count_big[kMaxSteps];  // roots of merges with K >= warp_min_k
-  unsigned long long work[16];
+  unsigned long long work[kNumWork];
 };
 
 // Kernel classes timed by the optional per-launch event profiler.

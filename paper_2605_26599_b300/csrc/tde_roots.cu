@@ -39,7 +39,8 @@ struct RootArgs {
   double *ROWLO, *ROWHI;  // alias RLO, RHI: parent rows of the active columns
   double* DORG;           // alias KEYA: D_org(j) of every active root
   double* MPD;            // alias Z: pole-block centres, radii and moments (secular)
-  double* MPR;            // alias KEYB: the same for the boundary rows (after Löwner)
+  double* MPR;            // alias KEYB: Löwner's pair-block moments, then (after Löwner)
+                          // the boundary rows' block moments
   int32_t mp_min_k;       // merges with K >= this use the block expansion
   Status* st;
   uint32_t small_list_min;  // shorter small-K lists go to the warp kernels
@@ -559,6 +560,7 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
 constexpr int kMpBlock = 128;  // poles per block
 constexpr int kMpTerms = 27;   // series terms
 constexpr int kMpFields = 2 + 2 * kMpTerms;  // m, r, M_k, (k + 1) M_k
+static_assert(kMpFields <= kMpBlock, "block data must fit the merge's rows (fields x K / 128 <= K)");
 
 // Block data of the merge at lo lives coefficient-major in MPD + lo: field q of
 // block b at [q * nb + b] (56 nb <= K entries, inside the merge's rows).
@@ -1091,9 +1093,10 @@ __device__ __forceinline__ void lowner_pair(const double* AD, const double* DORG
 }
 
 __device__ __forceinline__ void lowner_store(const RootArgs& a, int lo, int i, double Di, int K,
-                                             double rho, MantExp num, MantExp den) {
+                                             double rho, MantExp num, MantExp den,
+                                             double slog = 0.0) {
   const double last = ((a.DORG[lo + K - 1] - Di) + a.TAU[lo + K - 1]) / rho;
-  const double z2 = me_ratio(num, den) * last;
+  const double z2 = me_ratio(num, den) * last * (slog != 0.0 ? exp(slog) : 1.0);
   a.ZHAT[lo + i] = copysign(sqrt(fmax(z2, 0.0)), a.AZ[lo + i]);
 }
 
@@ -1126,12 +1129,95 @@ __global__ void k_lowner_thread(RootArgs a) {
   }
 }
 
+// Block expansion of the Löwner products (merges with K >= mp_min_k).  In log form
+// zhat_i^2 = (lambda_K - D_i) / rho' exp(sum_j log f_j), f_j = (lambda_j - D_i) /
+// (P_j - D_i) with P_j = D_j for j < i and D_{j+1} for j >= i.  The K - 1 pairs
+// are cut into the blocks of the secular expansion (pairs j in [128 b, 128 b +
+// 128), the last block up to K - 1); block b spans [D_b0, D_b1] around its centre
+// m with radius r.  For D_i far from it (r <= |D_i - m| / 4) its pairs sum to
+//   sum_j log f_j = -sum_{k>=1} (G_k / k) w^k,  w = 1 / (D_i - m),
+//   G_k = sum_j (lambda_j - m)^k - (P_j - m)^k = sum_j a_j h_{k-1}(lambda_j - m, P_j - m),
+// a_j = lambda_j - P_j and h the complete homogeneous sum, so G_k carries no
+// cancellation; the block lies wholly on one side of D_i, so P_j = D_j (left, set
+// L) or D_{j+1} (right, set R) for all its pairs.  With 27 terms the dropped part
+// is below 2^-55 of sum_j |a_j| / |D_i - m| <= 1 (absolute, in the log), and the
+// far blocks' sum enters zhat^2 through one exp.  Near blocks multiply their
+// factors directly.
+constexpr int kMlTerms = 27;
+constexpr int kMlFields = 2 + 2 * kMlTerms;  // m, r, G^L_k / k, G^R_k / k
+static_assert(kMlFields <= kMpBlock, "block data must fit the merge's rows");
+
+__device__ __forceinline__ int lowner_block_end(int b, int nb, int K) {
+  return b == nb - 1 ? K - 1 : (b + 1) * kMpBlock;
+}
+
+__global__ void __launch_bounds__(128) k_lowner_moments(RootArgs a) {
+  const uint32_t total = warp_list_total(a);
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
+    const uint32_t r = base + lane;
+    int g = 0, j = 0, nb = 0;
+    bool head = false;
+    if (r < total) {
+      int rl;
+      g = warp_list_merge(a, r, &rl);
+      const Merge m = a.M[g];
+      const MState ms = a.ms[g];
+      j = rl - ms.base;
+      nb = ((uint32_t(m.info) & kRootBit) && !a.all_merges) ? 0 : mp_blocks(ms.K, a.mp_min_k);
+      head = nb > 0 && (j % kMpBlock) == 0 && j / kMpBlock < nb;
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int gg = __shfl_sync(0xffffffffu, g, src), b = __shfl_sync(0xffffffffu, j, src) / kMpBlock;
+      const int nbb = __shfl_sync(0xffffffffu, nb, src);
+      const int lo = a.M[gg].lo, K = a.ms[gg].K;
+      const double* D = a.AD + lo;
+      const double* DORG = a.DORG + lo;
+      const double* TAU = a.TAU + lo;
+      const int j0 = b * kMpBlock, j1 = lowner_block_end(b, nbb, K);
+      const double m = 0.5 * (D[j0] + D[j1]);
+      double* MP = a.MPR + lo;
+      if (lane == 0) {
+        MP[b] = m;
+        MP[nbb + b] = fmax(m - D[j0], D[j1] - m);
+      }
+      for (int side = 0; side < 2; ++side) {  // L: partner D_j, R: partner D_{j+1}
+        double gk[kMlTerms];
+#pragma unroll
+        for (int k = 0; k < kMlTerms; ++k) gk[k] = 0.0;
+        for (int jj = j0 + lane; jj < j1; jj += 32) {
+          const double P = D[jj + side];
+          const double u = (DORG[jj] - m) + TAU[jj], v = P - m;
+          const double aj = (DORG[jj] - P) + TAU[jj];
+          double h = 1.0, vk = 1.0;
+#pragma unroll
+          for (int k = 0; k < kMlTerms; ++k) {  // G_{k+1} += a h_k
+            gk[k] = fma(aj, h, gk[k]);
+            vk *= v;
+            h = fma(u, h, vk);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kMlTerms; ++k) {
+          const double s = warp_sum(gk[k]);
+          if (lane == (k & 31)) MP[(2 + side * kMlTerms + k) * nbb + b] = s / double(k + 1);
+        }
+      }
+    }
+  }
+}
+
 __global__ void k_lowner_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  unsigned pairs = 0;
+  unsigned pairs = 0, series = 0;
   for (uint32_t r = warp; r < total; r += nwarps) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
@@ -1144,16 +1230,52 @@ __global__ void k_lowner_warp(RootArgs a) {
     const double* TAU = a.TAU + lo;
     const double Di = AD[i];
     MantExp num{1.0, 0}, den{1.0, 0};
-    int j = lane;
-    for (; j + 7 * 32 < K - 1; j += 8 * 32) {
+    double slog = 0.0;  // far blocks' log sum (block expansion)
+    const int nb = mp_blocks(K, a.mp_min_k);
+    if (nb == 0) {
+      int j = lane;
+      for (; j + 7 * 32 < K - 1; j += 8 * 32) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) lowner_pair(AD, DORG, TAU, i, Di, j + 32 * u, num.m, den.m);
+        for (int u = 0; u < 8; ++u) lowner_pair(AD, DORG, TAU, i, Di, j + 32 * u, num.m, den.m);
+        me_renorm(num);
+        me_renorm(den);
+      }
+      for (; j < K - 1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
       me_renorm(num);
       me_renorm(den);
+      pairs += unsigned(K);
+    } else {
+      const double* MP = a.MPR + lo;
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        bool near = false;
+        if (b < nb) {
+          const double dm = Di - MP[b];
+          if (MP[nb + b] <= 0.25 * fabs(dm)) {
+            const double w = rcp_refined(dm);
+            const double* c = MP + (2 + (dm < 0.0 ? kMlTerms : 0)) * nb + b;  // right of D_i: R
+            double val = c[(kMlTerms - 1) * nb];
+#pragma unroll
+            for (int k = kMlTerms - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
+            slog = fma(-w, val, slog);
+          } else {
+            near = true;
+          }
+        }
+        unsigned nm = __ballot_sync(0xffffffffu, near);
+        series += unsigned(min(32, nb - b0) - __popc(nm));
+        while (nm) {
+          const int bb = b0 + __ffs(nm) - 1;
+          nm &= nm - 1;
+          const int j0 = bb * kMpBlock, j1 = lowner_block_end(bb, nb, K);
+          for (int j = j0 + lane; j < j1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
+          me_renorm(num);  // at most four factors per lane since the last renormalisation
+          me_renorm(den);
+          pairs += unsigned(j1 - j0);
+        }
+      }
+      slog = warp_sum(slog);
     }
-    for (; j < K - 1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
-    me_renorm(num);
-    me_renorm(den);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       MantExp pn{__shfl_xor_sync(0xffffffffu, num.m, o), __shfl_xor_sync(0xffffffffu, num.e, o)};
@@ -1161,10 +1283,10 @@ __global__ void k_lowner_warp(RootArgs a) {
       me_mul(num, pn);
       me_mul(den, pd);
     }
-    if (lane == 0) lowner_store(a, lo, i, Di, K, ms.rho, num, den);
-    pairs += unsigned(K);
+    if (lane == 0) lowner_store(a, lo, i, Di, K, ms.rho, num, den, slog);
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkLownerPairs], (unsigned long long)pairs);
+  if (lane == 0 && series) atomicAdd(&a.st->work[kWorkLownerFarBlocks], (unsigned long long)series);
 }
 
 // ---------------------------------------------------------------------------
@@ -1260,6 +1382,7 @@ __device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* 
 // block's |terms| for the squared kernel and below 2^-60 for the others.
 constexpr int kMrTerms = 32;
 constexpr int kMrFields = 2 + 3 * kMrTerms;  // m, r, (k + 1) A_k, L_k, H_k
+static_assert(kMrFields <= kMpBlock, "block data must fit the merge's rows");
 
 // Moments of the row sums, one warp per block (found as in k_block_moments).
 __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
@@ -1499,6 +1622,10 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   prof_end(kKSecular, s);
   if (plan.step_has_nonroot[step] || all_merges) {
     prof_begin(kKLowner, s);
+    if (plan.step_maxsize[step] >= ra.mp_min_k) {
+      k_lowner_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+      ++launches;
+    }
     k_lowner_thread<<<tgrid, 128, 0, s>>>(ra);
     k_lowner_warp<<<wgrid, 128, 0, s>>>(ra);
     prof_end(kKLowner, s);
