@@ -107,3 +107,75 @@ def test_expansion_counts_and_default(tde):
     assert work["secular_far_blocks"] > 0 and work_exact["secular_far_blocks"] == 0
     assert work["secular_pairs"] < work_exact["secular_pairs"]
     assert np.abs(lam - lam_exact).max() <= 16 * EPS * oracle.norm1(d, e)
+
+
+def forced(tde):
+    """Context: expansion from K = 256 on, warp-per-root kernel from K = 256 on."""
+    import contextlib
+
+    @contextlib.contextmanager
+    def ctx():
+        saved = tde.get_tuning()
+        prev = tde.set_multipole(256)
+        try:
+            tde.set_tuning(warp_min_k=256, small_list_min=1)
+            yield
+        finally:
+            tde.set_tuning(**saved)
+            tde.set_multipole(prev)
+
+    return ctx()
+
+
+@pytest.mark.parametrize("name", ["toeplitz", "uniform11", "normal", "paper_clustered"])
+@pytest.mark.parametrize("n", [1000, 2000])
+def test_requested_rows_with_expansion(tde, name, n):
+    # eigenvector rows from the boundary-row state of merges that use all three
+    # expansions (secular sums, Löwner products, row sums): orthonormal, reproducing
+    # T's principal block, and equal (per column, up to sign) to dense eigh
+    import torch
+
+    d, e = fam(name, n)
+    rng = np.random.default_rng(n)
+    rows = [0, n - 1, n // 2, n // 2 - 1] + list(rng.integers(0, n, size=4))
+    r = torch.tensor(np.asarray(rows, dtype=np.int64)).cuda()
+    with forced(tde):
+        lam, q = tde.eigvecs_rows(torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda(), r, leaf=8)
+    lam, q = lam.cpu().numpy(), q.cpu().numpy()
+    nrm = max(1.0, oracle.norm1(d, e))
+    tol = 64 * n * EPS
+    same = (np.asarray(rows)[:, None] == np.asarray(rows)[None, :]).astype(np.float64)
+    assert np.abs(q @ q.T - same).max() <= tol
+    assert np.abs((q * lam) @ q.T - oracle.principal_block(d, e, rows)).max() <= tol * nrm
+    lam_ref, qref = oracle.eigvec_rows(d, e, rows)
+    assert np.abs(lam - lam_ref).max() <= 8 * n * EPS * nrm
+    gaps = np.full(n, np.inf)
+    dl = np.diff(lam_ref)
+    gaps[:-1] = np.minimum(gaps[:-1], dl)
+    gaps[1:] = np.minimum(gaps[1:], dl)
+    sign = np.where(np.sum(q * qref, axis=0) >= 0, 1.0, -1.0)
+    err = np.abs(q - qref * sign).max(axis=0)
+    bound = 1e-13 + 64 * n * EPS * nrm / np.maximum(gaps, 1e-300)
+    assert np.all(err <= bound)
+
+
+@pytest.mark.parametrize("name", ["toeplitz", "uniform11", "normal"])
+def test_gradient_with_expansion(tde, name):
+    # the adjoint's forward and reverse passes use the expansions at every merge
+    # (including root merges) from K = 256 on; the gradient of sum w lambda^2 matches
+    # the dense-eigh oracle gradient
+    import torch
+
+    n = 1536
+    d, e = fam(name, n)
+    w = np.random.default_rng(7).uniform(0, 1, n)
+    dt = torch.from_numpy(d).cuda()
+    et = torch.from_numpy(np.concatenate([e, [0.0]])).cuda()
+    with forced(tde):
+        lam = tde.eigvals(dt, et, leaf=8)
+        gl = 2.0 * torch.from_numpy(w).cuda() * lam
+        _, gd, ge = tde.eigvals_backward(dt, et, gl, leaf=8)
+    rd, re_ = oracle.grad_dense(d, e, w)
+    gd, ge = gd.cpu().numpy(), ge.cpu().numpy()[: n - 1]
+    assert np.max(np.abs(gd - rd)) <= 1e-8 * np.max(np.abs(rd))
+    assert np.max(np.abs(ge - re_)) <= 1e-8 * np.max(np.abs(re_))
