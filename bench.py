@@ -46,21 +46,30 @@ METRIC = "FP64 tridiag eigvals/s (n=64K)"
 UNIT = "eigvals/s"
 FAMILIES = ("a_uniform11", "b_toeplitz", "c_wilkinson", "d_glued_wilkinson")
 
-# Algorithmic FP64 operations per unit of device work (add, mul, division each one
-# flop, a fused multiply-add two):
-#   secular, per pole per sweep:  Delta = (D_i - D_org) - tau (2), t = z / Delta (1),
-#                                 z t (1), accumulate (1), t t (1), accumulate (1)
-#   Lowner, per pair:             numerator (2), denominator (1), ratio (1), product (1)
-#   rows, per pair:               Delta (2), zhat / Delta (1), t^2 + acc (2), two row FMAs (4)
-# Algorithmic work per (pole, root) pair, in FP64 operations with an add, multiply,
-# fused multiply-add, reciprocal or division each counted once: per secular sweep
-# 1 reciprocal + 4 (Delta, z^2 t, the psi and psi' sums); Lowner 1 division + 2;
-# boundary rows 1 reciprocal + 6 (Delta, zhat t, t^2, low row, high row, norm).
-OPS_PER_UNIT = {"secular": 5, "lowner": 3, "rows": 7}
+# Algorithmic work in FP64 operations, an add, multiply, fused multiply-add,
+# reciprocal or division each counted once.  Per (pole, root) pair summed or
+# multiplied term by term: secular sweep 1 reciprocal + 4 (Delta, z^2 t, the psi and
+# psi' sums); Lowner 1 division + 2; boundary rows 1 reciprocal + 6 (Delta, zhat t,
+# t^2, low row, high row, norm).  Per far block taken through its series (block
+# expansion of large merges): secular 58 (m - lambda 2, reciprocal 1, two 27-term
+# Horner chains 52, three to accumulate); Lowner 29 (D_i - m, reciprocal, a 27-term
+# chain 26, accumulate); boundary rows 34 per series (a 32-term chain 31, its
+# accumulate, and its share of m - lambda, the reciprocal and t^2).
+OPS = {  # stage: (ops per exact pair, pair counter, ops per series unit, series counter)
+    "secular": (5, "secular_pairs", 58, "secular_far_blocks"),
+    "lowner": (3, "lowner_pairs", 29, "lowner_far_blocks"),
+    "rows": (7, "rows_pairs", 34, "rows_far_series"),
+}
+OPS_PER_UNIT = {k: {"per_pair": v[0], "per_series": v[2]} for k, v in OPS.items()}
 # nominal FP64 rate of the part (1.25 TFLOP/s, an FMA counting two), in operations per
 # second with an FMA counting one: 148 SMs x 2.032 GHz x about 2.08 FMA per SM clock
 NOMINAL_FP64_OPS = 0.625e12
-WORK_OF = {"secular": "secular_pairs", "lowner": "lowner_pairs", "rows": "rows_pairs"}
+
+
+def stage_ops(stage: str, work: dict) -> int:
+    """Algorithmic FP64 operations of one stage from the device work counters."""
+    pp, pc, ps, sc = OPS[stage]
+    return pp * work[pc] + ps * work[sc]
 
 
 def family_inputs(n: int):
@@ -307,8 +316,8 @@ def run_ours(args, rank: int, world: int, dist) -> None:
 
     # device work of one step (identical every step)
     work = {k: 0 for k in ("secular_pairs", "secular32_pairs", "lowner_pairs", "rows_pairs", "secular_sweeps",
-                           "secular32_sweeps", "roots",
-                           "deflated", "rotations", "leaf_rotations")}
+                           "secular32_sweeps", "roots", "deflated", "rotations", "leaf_rotations",
+                           "secular_far_blocks", "lowner_far_blocks", "rows_far_series")}
     per_family_work = {}
     for name in FAMILIES:
         w = tde.read_work(wss[name])
@@ -353,12 +362,14 @@ def run_ours(args, rank: int, world: int, dist) -> None:
                            "MEASURED_PEAKS.json carries no FP64 figure",
             "peak_nominal": NOMINAL_FP64_OPS / 1e12,
             "ops_per_unit": OPS_PER_UNIT}
-    if dominant in OPS_PER_UNIT:
-        ops = OPS_PER_UNIT[dominant] * work[WORK_OF[dominant]]
+    if dominant in OPS:
+        ops = stage_ops(dominant, work)
         achieved = ops / (ktimes[dominant] * 1e-3) / 1e12
         roof.update({"achieved": achieved, "frac": achieved / peak_tops,
                      "frac_nominal": achieved / (NOMINAL_FP64_OPS / 1e12),
-                     "algorithmic_ops_per_step": ops, "units_per_step": work[WORK_OF[dominant]],
+                     "algorithmic_ops_per_step": ops,
+                     "units_per_step": {"exact_pairs": work[OPS[dominant][1]],
+                                        "series": work[OPS[dominant][3]]},
                      "launches_per_step": klaunch[dominant],
                      "avg_launch_ms": ktimes[dominant] / max(klaunch[dominant], 1)})
     else:
@@ -366,9 +377,9 @@ def run_ours(args, rank: int, world: int, dist) -> None:
                      "note": f"dominant kernel {dominant} is not an FP64 pair kernel"})
     roof["traffic"] = load_traffic(dominant)
     kernel_rates = {}
-    for k in OPS_PER_UNIT:
+    for k in OPS:
         if ktimes.get(k, 0) > 0:
-            ops = OPS_PER_UNIT[k] * work[WORK_OF[k]]
+            ops = stage_ops(k, work)
             kernel_rates[k] = {"ms_per_step": ktimes[k], "tops": ops / (ktimes[k] * 1e-3) / 1e12,
                                "frac_of_peak": ops / (ktimes[k] * 1e-3) / 1e12 / peak_tops}
 

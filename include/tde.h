@@ -232,8 +232,8 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
  * sweeps x K, out[11] single-precision secular sweeps, out[12] requested-row
  * updates as (pole, root, row) triples, out[13] their (pole, root) sweeps (one per
  * group of up to four rows of a merge), out[14] pole blocks taken through their
- * series in FP64 secular sweeps, out[15] pole blocks taken through their series in
- * the boundary-row sums, out[16] pair blocks taken through their series in the
+ * series in FP64 secular sweeps, out[15] series evaluated for the boundary-row sums
+ * (two or three per far pole block), out[16] pair blocks taken through their series in the
  * Lowner products.  n <= 17 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);

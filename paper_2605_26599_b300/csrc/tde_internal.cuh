@@ -92,7 +92,8 @@ enum WorkCounter {
   kWorkSelRowPairs,       // requested-row updates: (pole, root, requested row) triples
   kWorkSelSweepPairs,     // requested-row updates: (pole, root) pairs per sweep of up to four rows
   kWorkSecularFarBlocks,  // pole blocks taken through their series in FP64 sweeps
-  kWorkRowsFarBlocks,     // pole blocks taken through their series in the row sums
+  kWorkRowsFarSeries,     // series evaluated for the row sums (two or three per far block:
+                          // the norm and the rows the merge needs)
   kWorkLownerFarBlocks,   // pair blocks taken through their series in the Löwner products
   kNumWork
 };

@@ -1477,7 +1477,7 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
       }
     }
     unsigned nm = __ballot_sync(0xffffffffu, near);
-    series += unsigned(min(32, nb - b0) - __popc(nm));
+    series += unsigned(min(32, nb - b0) - __popc(nm)) * (MODE == 3 ? 3u : 2u);  // chains
     while (nm) {
       const int bb = b0 + __ffs(nm) - 1;
       nm &= nm - 1;
@@ -1540,7 +1540,7 @@ __global__ void k_rows_warp(RootArgs a) {
     }
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkRowsPairs], (unsigned long long)pairs);
-  if (lane == 0 && series) atomicAdd(&a.st->work[kWorkRowsFarBlocks], (unsigned long long)series);
+  if (lane == 0 && series) atomicAdd(&a.st->work[kWorkRowsFarSeries], (unsigned long long)series);
 }
 
 // Restores the saved roots of one step: tau, D_org and lambda = D_org + tau (the
