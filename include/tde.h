@@ -183,7 +183,7 @@ int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min);
  * 27-term series of the block's moments instead of term by term (series error
  * below 2^-53 of the block's terms), and so do the boundary-row sums of those
  * merges (32 terms, below 2^-58) and the Lowner products in log form (27 terms,
- * below 2^-55 absolute in the log).  min_k = 0 restores the default (2048); any
+ * below 2^-55 absolute in the log).  min_k = 0 restores the default (1024); any
  * other value below 256 is TDE_EINVAL; a value above every K turns the expansion
  * off.  *previous (if not NULL) receives the value in force before the call. */
 int tde_set_multipole(int32_t min_k, int32_t* previous);

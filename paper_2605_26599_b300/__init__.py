@@ -257,7 +257,7 @@ def set_tuning(warp_min_k: int = 0, small_list_min: int = 0) -> None:
 
 def set_multipole(min_k: int = 0) -> int:
     """Threshold K of the secular solver's block expansion for later calls on this
-    thread (0 = default 2048; a value above every K turns it off).  Returns the
+    thread (0 = default 1024; a value above every K turns it off).  Returns the
     previous threshold."""
     prev = ctypes.c_int32()
     _lib.check("tde_set_multipole", _lib.load().tde_set_multipole(int(min_k), ctypes.byref(prev)))

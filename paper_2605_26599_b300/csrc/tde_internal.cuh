@@ -60,7 +60,7 @@ struct MState {
 struct Tuning {
   int32_t warp_min_k = 256;
   int32_t small_list_min = 148 * 4 * 32;
-  int32_t multipole_min_k = 2048;  // secular block expansion for merges with K >= this
+  int32_t multipole_min_k = 1024;  // block expansions for merges with K >= this
 };
 Tuning& thread_tuning();
 
