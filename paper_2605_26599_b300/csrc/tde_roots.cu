@@ -554,11 +554,14 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
 // A sweep takes a block through these series when r <= |m - lambda| / 4: the
 // dropped terms are then below 4^-27 (4/3)^2 < 2^-53 of the block's own
 // sum_i |z_i^2 / (D_i - lambda)|, under the rounding bound of the convergence test.
+// A round of 32 blocks all within r <= |m - lambda| / 16 stops after 14 terms
+// (16^-14 = 2^-56).
 // Every other block (the root's own and its neighbours) is summed exactly.  The
 // block lies wholly on one side of lambda, so it adds to psi or phi as a whole.
 // m - lambda is formed as (m - D_org) - tau, like every Delta.
 constexpr int kMpBlock = 128;  // poles per block
-constexpr int kMpTerms = 27;   // series terms
+constexpr int kMpTerms = 27;   // series terms (radius <= 1/4 of the distance)
+constexpr int kMpShort = 14;   // enough when radius <= 1/16 of the distance (16^-14 = 2^-56)
 constexpr int kMpFields = 2 + 2 * kMpTerms;  // m, r, M_k, (k + 1) M_k
 static_assert(kMpFields <= kMpBlock, "block data must fit the merge's rows (fields x K / 128 <= K)");
 
@@ -652,15 +655,30 @@ struct WarpSweep {
       for (int b0 = 0; b0 < nb; b0 += 32) {
         const int b = b0 + lane;
         bool near = false;
+        // every block of this round at most 1/16 of its distance wide: 14 terms do
+        const bool short_series = __all_sync(
+            0xffffffffu, b >= nb || MP[nb + b] <= 0.0625 * fabs((MP[b] - dorg) - tau));
         if (b < nb) {
           const double dm = (MP[b] - dorg) - tau;  // m - lambda
           if (MP[nb + b] <= 0.25 * fabs(dm)) {
             const double t = rcp_refined(dm), u = -t;
-            double val = MP[(1 + kMpTerms) * nb + b], der = MP[(1 + 2 * kMpTerms) * nb + b];
+            double val, der;
+            if (short_series) {
+              val = MP[(1 + kMpShort) * nb + b];
+              der = MP[(1 + kMpTerms + kMpShort) * nb + b];
 #pragma unroll
-            for (int k = kMpTerms - 2; k >= 0; --k) {
-              val = fma(val, u, MP[(2 + k) * nb + b]);
-              der = fma(der, u, MP[(2 + kMpTerms + k) * nb + b]);
+              for (int k = kMpShort - 2; k >= 0; --k) {
+                val = fma(val, u, MP[(2 + k) * nb + b]);
+                der = fma(der, u, MP[(2 + kMpTerms + k) * nb + b]);
+              }
+            } else {
+              val = MP[(1 + kMpTerms) * nb + b];
+              der = MP[(1 + 2 * kMpTerms) * nb + b];
+#pragma unroll
+              for (int k = kMpTerms - 2; k >= 0; --k) {
+                val = fma(val, u, MP[(2 + k) * nb + b]);
+                der = fma(der, u, MP[(2 + kMpTerms + k) * nb + b]);
+              }
             }
             if (dm > 0.0) {
               f = fma(t, val, f);
@@ -1249,14 +1267,23 @@ __global__ void k_lowner_warp(RootArgs a) {
       for (int b0 = 0; b0 < nb; b0 += 32) {
         const int b = b0 + lane;
         bool near = false;
+        const bool short_series =
+            __all_sync(0xffffffffu, b >= nb || MP[nb + b] <= 0.0625 * fabs(Di - MP[b]));
         if (b < nb) {
           const double dm = Di - MP[b];
           if (MP[nb + b] <= 0.25 * fabs(dm)) {
             const double w = rcp_refined(dm);
             const double* c = MP + (2 + (dm < 0.0 ? kMlTerms : 0)) * nb + b;  // right of D_i: R
-            double val = c[(kMlTerms - 1) * nb];
+            double val;
+            if (short_series) {
+              val = c[(kMpShort - 1) * nb];
 #pragma unroll
-            for (int k = kMlTerms - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
+              for (int k = kMpShort - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
+            } else {
+              val = c[(kMlTerms - 1) * nb];
+#pragma unroll
+              for (int k = kMlTerms - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
+            }
             slog = fma(-w, val, slog);
           } else {
             near = true;
@@ -1381,6 +1408,7 @@ __device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* 
 // y = D_i - m, with 32 terms: the dropped part stays below 2^-58 of the sum of the
 // block's |terms| for the squared kernel and below 2^-60 for the others.
 constexpr int kMrTerms = 32;
+constexpr int kMrShort = 16;  // radius <= 1/16 of the distance: 17 x 16^-16 < 2^-59
 constexpr int kMrFields = 2 + 3 * kMrTerms;  // m, r, (k + 1) A_k, L_k, H_k
 static_assert(kMrFields <= kMpBlock, "block data must fit the merge's rows");
 
@@ -1456,18 +1484,33 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
   for (int b0 = 0; b0 < nb; b0 += 32) {
     const int b = b0 + lane;
     bool near = false;
+    const bool short_series = __all_sync(
+        0xffffffffu, b >= nb || MP[nb + b] <= 0.0625 * fabs((MP[b] - dorg) - tau));
     if (b < nb) {
       const double dm = (MP[b] - dorg) - tau;  // m - lambda
       if (MP[nb + b] <= 0.25 * fabs(dm)) {
         const double t = rcp_refined(dm), u = -t;
-        double va = MP[(1 + kMrTerms) * nb + b];
-        double vl = (MODE & 1) ? MP[(1 + 2 * kMrTerms) * nb + b] : 0.0;
-        double vh = (MODE & 2) ? MP[(1 + 3 * kMrTerms) * nb + b] : 0.0;
+        double va, vl = 0.0, vh = 0.0;
+        if (short_series) {
+          va = MP[(1 + kMrShort) * nb + b];
+          if (MODE & 1) vl = MP[(1 + kMrTerms + kMrShort) * nb + b];
+          if (MODE & 2) vh = MP[(1 + 2 * kMrTerms + kMrShort) * nb + b];
 #pragma unroll
-        for (int k = kMrTerms - 2; k >= 0; --k) {
-          va = fma(va, u, MP[(2 + k) * nb + b]);
-          if (MODE & 1) vl = fma(vl, u, MP[(2 + kMrTerms + k) * nb + b]);
-          if (MODE & 2) vh = fma(vh, u, MP[(2 + 2 * kMrTerms + k) * nb + b]);
+          for (int k = kMrShort - 2; k >= 0; --k) {
+            va = fma(va, u, MP[(2 + k) * nb + b]);
+            if (MODE & 1) vl = fma(vl, u, MP[(2 + kMrTerms + k) * nb + b]);
+            if (MODE & 2) vh = fma(vh, u, MP[(2 + 2 * kMrTerms + k) * nb + b]);
+          }
+        } else {
+          va = MP[(1 + kMrTerms) * nb + b];
+          if (MODE & 1) vl = MP[(1 + 2 * kMrTerms) * nb + b];
+          if (MODE & 2) vh = MP[(1 + 3 * kMrTerms) * nb + b];
+#pragma unroll
+          for (int k = kMrTerms - 2; k >= 0; --k) {
+            va = fma(va, u, MP[(2 + k) * nb + b]);
+            if (MODE & 1) vl = fma(vl, u, MP[(2 + kMrTerms + k) * nb + b]);
+            if (MODE & 2) vh = fma(vh, u, MP[(2 + 2 * kMrTerms + k) * nb + b]);
+          }
         }
         s2 = fma(t * t, va, s2);
         if (MODE & 1) sl = fma(t, vl, sl);
