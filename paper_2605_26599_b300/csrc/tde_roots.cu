@@ -565,6 +565,20 @@ constexpr int kMpShort = 14;   // enough when radius <= 1/16 of the distance (16
 constexpr int kMpFields = 2 + 2 * kMpTerms;  // m, r, M_k, (k + 1) M_k
 static_assert(kMpFields <= kMpBlock, "block data must fit the merge's rows (fields x K / 128 <= K)");
 
+// The single-precision stage uses the same blocks, with float data placed after the
+// FP64 data (field q of block b at BF[q nb + b], BF = (float*)(MPD + lo + 56 nb)):
+// the centre minus the merge's midrange as a float pair, the radius, and the
+// normalised moments M'_k = sum z_i^2 ((D_i - m) / r)^k, k < 14, times 1, k + 1
+// and (k + 1)(k + 2) / 2.  In the stage's units (offsets / S, sums x S) a far block
+// with d = (m - lambda) / S and x = -(r / S) / d adds
+//   w: (1/d) sum M'_k x^k,  w': (1/d)^2 sum (k + 1) M'_k x^k,
+//   w''/2: (1/d)^3 sum (k + 1)(k + 2)/2 M'_k x^k,
+// |x| <= 1/4, so 14 terms leave less than 2^-27 of the block's terms, under the
+// rounding of the float sums.  The normalisation keeps every float in range.
+constexpr int kMfTerms = 14;
+constexpr int kMfFields = 3 + 3 * kMfTerms;  // centre hi, lo, radius, three series
+static_assert(2 * kMpFields + kMfFields <= 2 * kMpBlock, "both block data sets fit the merge's rows");
+
 // Block data of the merge at lo lives coefficient-major in MPD + lo: field q of
 // block b at [q * nb + b] (56 nb <= K entries, inside the merge's rows).
 __device__ __forceinline__ int mp_blocks(int K, int mp_min_k) {
@@ -851,6 +865,80 @@ struct GroupSweep32 : Copies32 {
   }
 };
 
+// Single-precision sums of the warp kernel (all 32 lanes on one root).  With nb > 0
+// lane l takes blocks l, l + 32, ...: far blocks through their float series, near
+// blocks term by term by the whole warp.
+struct WarpSweep32 : Copies32 {
+  int lane;
+  int nb;
+  const float* __restrict__ BF;
+  __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau, float inv) const {
+    const float2 ho = H[org];
+    float p = 0.f, dp = 0.f, f = 0.f, df = 0.f, h = 0.f;
+    if (nb == 0) {
+      float hl, hr;
+      range32(H, Z, 0, jl + 1, lane, 32, ho, tau, inv, p, dp, hl);
+      range32(H, Z, jl + 1, K, lane, 32, ho, tau, inv, f, df, hr);
+      h = hl + hr;
+    } else {
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int b = b0 + lane;
+        bool near = false;
+        if (b < nb) {
+          const float d = fmaf((BF[b] - ho.x) + (BF[nb + b] - ho.y), inv, -tau);
+          const float rs = BF[2 * nb + b] * inv;
+          if (rs <= 0.25f * fabsf(d)) {
+            const float q = rcp_approx32(d), x = -rs * q;
+            const float* A = BF + 3 * nb + b;
+            float va = A[(kMfTerms - 1) * nb], vb = A[(2 * kMfTerms - 1) * nb],
+                  vc = A[(3 * kMfTerms - 1) * nb];
+#pragma unroll
+            for (int k = kMfTerms - 2; k >= 0; --k) {
+              va = fmaf(va, x, A[k * nb]);
+              vb = fmaf(vb, x, A[(kMfTerms + k) * nb]);
+              vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
+            }
+            const float q2 = q * q;
+            if (d > 0.f) {
+              f = fmaf(q, va, f);
+              df = fmaf(q2, vb, df);
+            } else {
+              p = fmaf(q, va, p);
+              dp = fmaf(q2, vb, dp);
+            }
+            h = fmaf(q2 * q, vc, h);
+          } else {
+            near = true;
+          }
+        }
+        unsigned nm = __ballot_sync(0xffffffffu, near);
+        while (nm) {
+          const int bb = b0 + __ffs(nm) - 1;
+          nm &= nm - 1;
+          const int i0 = bb * kMpBlock, i1 = (bb == nb - 1) ? K : i0 + kMpBlock;
+          const int mid = min(max(jl + 1, i0), i1);
+          float w, dw, hw;
+          range32(H, Z, i0, mid, lane, 32, ho, tau, inv, w, dw, hw);
+          p += w;
+          dp += dw;
+          h += hw;
+          range32(H, Z, mid, i1, lane, 32, ho, tau, inv, w, dw, hw);
+          f += w;
+          df += dw;
+          h += hw;
+        }
+      }
+    }
+    Sec32 s;
+    s.psi = group_sum<32>(p, 0xffffffffu);
+    s.dpsi = group_sum<32>(dp, 0xffffffffu);
+    s.phi = group_sum<32>(f, 0xffffffffu);
+    s.dphi = group_sum<32>(df, 0xffffffffu);
+    s.hw = group_sum<32>(h, 0xffffffffu);
+    return s;
+  }
+};
+
 // ---- kernels ------------------------------------------------------------------
 __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, int org, double tau,
                                               int sweeps, int K, bool ok, bool leader) {
@@ -943,30 +1031,54 @@ __global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
       const int i0 = b * kMpBlock, i1 = (b == nbb - 1) ? K : i0 + kMpBlock;
       const double m = 0.5 * (D[i0] + D[i1 - 1]);
       const double rad = fmax(m - D[i0], D[i1 - 1] - m);
-      double mo[kMpTerms];
+      double mo[kMpTerms], mf[kMfTerms];
 #pragma unroll
       for (int k = 0; k < kMpTerms; ++k) mo[k] = 0.0;
+#pragma unroll
+      for (int k = 0; k < kMfTerms; ++k) mf[k] = 0.0;
+      const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
       for (int i = i0 + lane; i < i1; i += 32) {
-        const double y = D[i] - m;
-        double pw = Z[i] * Z[i];
+        const double y = D[i] - m, w = Z[i] * Z[i];
+        double pw = w, pn = w;
 #pragma unroll
         for (int k = 0; k < kMpTerms; ++k) {
           mo[k] += pw;
           pw *= y;
         }
+#pragma unroll
+        for (int k = 0; k < kMfTerms; ++k) {  // normalised: ((D_i - m) / r)^k
+          mf[k] += pn;
+          pn *= y * rinv;
+        }
       }
 #pragma unroll
       for (int k = 0; k < kMpTerms; ++k) mo[k] = warp_sum(mo[k]);
+#pragma unroll
+      for (int k = 0; k < kMfTerms; ++k) mf[k] = warp_sum(mf[k]);
       double* MP = a.MPD + lo;
+      float* BF = reinterpret_cast<float*>(MP + kMpFields * nbb);
       if (lane == 0) {
         MP[b] = m;
         MP[nbb + b] = rad;
+        const double c = m - a.ms[gg].shift;
+        const float ch = __double2float_rn(c);
+        BF[b] = ch;
+        BF[nbb + b] = __double2float_rn(c - double(ch));
+        BF[2 * nbb + b] = __double2float_rn(rad);
       }
 #pragma unroll
       for (int k = 0; k < kMpTerms; ++k)
         if (lane == (k & 31)) {
           MP[(2 + k) * nbb + b] = mo[k];
           MP[(2 + kMpTerms + k) * nbb + b] = double(k + 1) * mo[k];
+        }
+#pragma unroll
+      for (int k = 0; k < kMfTerms; ++k)
+        if (lane == ((k + 16) & 31)) {
+          BF[(3 + k) * nbb + b] = __double2float_rn(mf[k]);
+          BF[(3 + kMfTerms + k) * nbb + b] = __double2float_rn(double(k + 1) * mf[k]);
+          BF[(3 + 2 * kMfTerms + k) * nbb + b] =
+              __double2float_rn(0.5 * double((k + 1) * (k + 2)) * mf[k]);
         }
     }
   }
@@ -1052,7 +1164,8 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     const int j = (q & 1) ? ms.K - 1 - (q >> 1) : (q >> 1);
     const int nb = mp_blocks(ms.K, a.mp_min_k);
     WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, 0ull, 0u};
-    GroupSweep32<32> sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, 0xffffffffu};
+    WarpSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, nb,
+                     reinterpret_cast<const float*>(a.MPD + lo + kMpFields * nb)};
     int org, n32;
     double tau;
     bool ok;
