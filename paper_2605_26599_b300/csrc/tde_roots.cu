@@ -547,35 +547,62 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
 // kernel).  The K poles are cut into nb = K / 128 blocks of consecutive poles (the
 // last one takes the remainder).  Per block, k_block_moments stores its centre m,
 // its radius r (largest |D_i - m|) and the moments
-//   M_k = sum_{i in block} z_i^2 (D_i - m)^k,   k = 0 .. 26,
+//   M_k = sum_{i in block} z_i^2 (D_i - m)^k,
 // so that for lambda outside the block, with t = 1 / (m - lambda),
 //   sum z_i^2 / (D_i - lambda)   = t   sum_k M_k (-t)^k,
-//   sum z_i^2 / (D_i - lambda)^2 = t^2 sum_k (k + 1) M_k (-t)^k.
-// A sweep takes a block through these series when r <= |m - lambda| / 4: the
-// dropped terms are then below 4^-27 (4/3)^2 < 2^-53 of the block's own
-// sum_i |z_i^2 / (D_i - lambda)|, under the rounding bound of the convergence test.
-// A round of 32 blocks all within r <= |m - lambda| / 16 stops after 14 terms
-// (16^-14 = 2^-56).
+//   sum z_i^2 / (D_i - lambda)^2 = t^2 sum_k (k + 1) M_k (-t)^k
+// (k = 0 .. 34).
+// A sweep takes a block through these series when r <= |m - lambda| / 3: with 35
+// terms the dropped part is below 3^-35 (1 + 1/3) / (1 - 1/3) < 2^-54 of the
+// block's own sum_i |z_i^2 / (D_i - lambda)|, under the rounding bound of the
+// convergence test.  A round of 32 blocks all within 1/4 of their distance stops
+// after 27 terms (4^-27 (5/3) < 2^-53), all within 1/16 after 14 (16^-14 = 2^-56).
 // Every other block (the root's own and its neighbours) is summed exactly.  The
 // block lies wholly on one side of lambda, so it adds to psi or phi as a whole.
 // m - lambda is formed as (m - D_org) - tau, like every Delta.
 constexpr int kMpBlock = 128;  // poles per block
-constexpr int kMpTerms = 27;   // series terms (radius <= 1/4 of the distance)
+constexpr int kMpTerms = 35;   // series terms (radius <= 1/3 of the distance)
+constexpr int kMpMid = 27;     // enough when radius <= 1/4 of the distance
 constexpr int kMpShort = 14;   // enough when radius <= 1/16 of the distance (16^-14 = 2^-56)
 constexpr int kMpFields = 2 + 2 * kMpTerms;  // m, r, M_k, (k + 1) M_k
+
+// Series tier of a round of 32 blocks (warp vote over the lanes whose block, of
+// radius r at distance dist, is far): 0 if all of them are within 1/16 of their
+// distance, 1 if within 1/4, else 2.
+__device__ __forceinline__ int series_tier(double r, double dist, bool far) {
+  if (__all_sync(0xffffffffu, !far || 16.0 * r <= dist)) return 0;
+  if (__all_sync(0xffffffffu, !far || 4.0 * r <= dist)) return 1;
+  return 2;
+}
+
+// Horner evaluation of two interleaved series of N terms, coefficient-major data
+// (the first series' coefficient k at c0[k * nb], the second's at c1[k * nb])
+template <int N>
+__device__ __forceinline__ void horner2(const double* c0, const double* c1, int nb, double u,
+                                        double& v0, double& v1) {
+  v0 = c0[(N - 1) * nb];
+  v1 = c1[(N - 1) * nb];
+#pragma unroll
+  for (int k = N - 2; k >= 0; --k) {
+    v0 = fma(v0, u, c0[k * nb]);
+    v1 = fma(v1, u, c1[k * nb]);
+  }
+}
 static_assert(kMpFields <= kMpBlock, "block data must fit the merge's rows (fields x K / 128 <= K)");
 
 // The single-precision stage uses the same blocks, with float data placed after the
 // FP64 data (field q of block b at BF[q nb + b], BF = (float*)(MPD + lo + 56 nb)):
 // the centre minus the merge's midrange as a float pair, the radius, and the
-// normalised moments M'_k = sum z_i^2 ((D_i - m) / r)^k, k < 14, times 1, k + 1
+// normalised moments M'_k = sum z_i^2 ((D_i - m) / r)^k, k < 18, times 1, k + 1
 // and (k + 1)(k + 2) / 2.  In the stage's units (offsets / S, sums x S) a far block
 // with d = (m - lambda) / S and x = -(r / S) / d adds
 //   w: (1/d) sum M'_k x^k,  w': (1/d)^2 sum (k + 1) M'_k x^k,
 //   w''/2: (1/d)^3 sum (k + 1)(k + 2)/2 M'_k x^k,
-// |x| <= 1/4, so 14 terms leave less than 2^-27 of the block's terms, under the
-// rounding of the float sums.  The normalisation keeps every float in range.
-constexpr int kMfTerms = 14;
+// far blocks (|x| <= 1/3) take 18 terms, rounds within 1/16 10: the dropped part
+// stays below 2^-27 of the block's terms, under the rounding of the float sums.
+// The normalisation keeps every float in range.
+constexpr int kMfTerms = 18;  // radius <= 1/3: 3^-18 x 2 < 2^-27
+constexpr int kMfShort = 10;  // radius <= 1/16: 16^-10 = 2^-40
 constexpr int kMfFields = 3 + 3 * kMfTerms;  // centre hi, lo, radius, three series
 static_assert(2 * kMpFields + kMfFields <= 2 * kMpBlock, "both block data sets fit the merge's rows");
 
@@ -669,31 +696,22 @@ struct WarpSweep {
       for (int b0 = 0; b0 < nb; b0 += 32) {
         const int b = b0 + lane;
         bool near = false;
-        // every block of this round at most 1/16 of its distance wide: 14 terms do
-        const bool short_series = __all_sync(
-            0xffffffffu, b >= nb || MP[nb + b] <= 0.0625 * fabs((MP[b] - dorg) - tau));
+        const double dm = b < nb ? (MP[b] - dorg) - tau : 1.0;  // m - lambda
+        const double rb = b < nb ? MP[nb + b] : 0.0;
+        const bool far = b < nb && 3.0 * rb <= fabs(dm);
+        const int tier = series_tier(rb, fabs(dm), far);
         if (b < nb) {
-          const double dm = (MP[b] - dorg) - tau;  // m - lambda
-          if (MP[nb + b] <= 0.25 * fabs(dm)) {
+          if (far) {
             const double t = rcp_refined(dm), u = -t;
+            const double* c0 = MP + 2 * nb + b;
+            const double* c1 = MP + (2 + kMpTerms) * nb + b;
             double val, der;
-            if (short_series) {
-              val = MP[(1 + kMpShort) * nb + b];
-              der = MP[(1 + kMpTerms + kMpShort) * nb + b];
-#pragma unroll
-              for (int k = kMpShort - 2; k >= 0; --k) {
-                val = fma(val, u, MP[(2 + k) * nb + b]);
-                der = fma(der, u, MP[(2 + kMpTerms + k) * nb + b]);
-              }
-            } else {
-              val = MP[(1 + kMpTerms) * nb + b];
-              der = MP[(1 + 2 * kMpTerms) * nb + b];
-#pragma unroll
-              for (int k = kMpTerms - 2; k >= 0; --k) {
-                val = fma(val, u, MP[(2 + k) * nb + b]);
-                der = fma(der, u, MP[(2 + kMpTerms + k) * nb + b]);
-              }
-            }
+            if (tier == 0)
+              horner2<kMpShort>(c0, c1, nb, u, val, der);
+            else if (tier == 1)
+              horner2<kMpMid>(c0, c1, nb, u, val, der);
+            else
+              horner2<kMpTerms>(c0, c1, nb, u, val, der);
             if (dm > 0.0) {
               f = fma(t, val, f);
               df = fma(t * t, der, df);
@@ -884,19 +902,35 @@ struct WarpSweep32 : Copies32 {
       for (int b0 = 0; b0 < nb; b0 += 32) {
         const int b = b0 + lane;
         bool near = false;
+        const float d = b < nb ? fmaf((BF[b] - ho.x) + (BF[nb + b] - ho.y), inv, -tau) : 1.f;
+        const float rs = b < nb ? BF[2 * nb + b] * inv : 0.f;
+        const bool far = b < nb && 3.f * rs <= fabsf(d);
+        const bool tail = __all_sync(0xffffffffu, !far || 16.f * rs <= fabsf(d));
         if (b < nb) {
-          const float d = fmaf((BF[b] - ho.x) + (BF[nb + b] - ho.y), inv, -tau);
-          const float rs = BF[2 * nb + b] * inv;
-          if (rs <= 0.25f * fabsf(d)) {
+          if (far) {
             const float q = rcp_approx32(d), x = -rs * q;
             const float* A = BF + 3 * nb + b;
-            float va = A[(kMfTerms - 1) * nb], vb = A[(2 * kMfTerms - 1) * nb],
-                  vc = A[(3 * kMfTerms - 1) * nb];
+            float va, vb, vc;
+            if (tail) {
+              va = A[(kMfShort - 1) * nb];
+              vb = A[(kMfTerms + kMfShort - 1) * nb];
+              vc = A[(2 * kMfTerms + kMfShort - 1) * nb];
 #pragma unroll
-            for (int k = kMfTerms - 2; k >= 0; --k) {
-              va = fmaf(va, x, A[k * nb]);
-              vb = fmaf(vb, x, A[(kMfTerms + k) * nb]);
-              vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
+              for (int k = kMfShort - 2; k >= 0; --k) {
+                va = fmaf(va, x, A[k * nb]);
+                vb = fmaf(vb, x, A[(kMfTerms + k) * nb]);
+                vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
+              }
+            } else {
+              va = A[(kMfTerms - 1) * nb];
+              vb = A[(2 * kMfTerms - 1) * nb];
+              vc = A[(3 * kMfTerms - 1) * nb];
+#pragma unroll
+              for (int k = kMfTerms - 2; k >= 0; --k) {
+                va = fmaf(va, x, A[k * nb]);
+                vb = fmaf(vb, x, A[(kMfTerms + k) * nb]);
+                vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
+              }
             }
             const float q2 = q * q;
             if (d > 0.f) {
@@ -1270,11 +1304,12 @@ __global__ void k_lowner_thread(RootArgs a) {
 //   G_k = sum_j (lambda_j - m)^k - (P_j - m)^k = sum_j a_j h_{k-1}(lambda_j - m, P_j - m),
 // a_j = lambda_j - P_j and h the complete homogeneous sum, so G_k carries no
 // cancellation; the block lies wholly on one side of D_i, so P_j = D_j (left, set
-// L) or D_{j+1} (right, set R) for all its pairs.  With 27 terms the dropped part
-// is below 2^-55 of sum_j |a_j| / |D_i - m| <= 1 (absolute, in the log), and the
-// far blocks' sum enters zhat^2 through one exp.  Near blocks multiply their
-// factors directly.
-constexpr int kMlTerms = 27;
+// L) or D_{j+1} (right, set R) for all its pairs.  A block is far when
+// r <= |D_i - m| / 3; with 35 terms (27 for rounds within 1/4, 14 within 1/16) the
+// dropped part is below 2^-53 of sum_j |a_j| / |D_i - m| <= 1 (absolute, in the
+// log), and the far blocks' sum enters zhat^2 through one exp.  Near blocks
+// multiply their factors directly.
+constexpr int kMlTerms = 35;  // far: radius <= 1/3 of the distance; 27 within 1/4, 14 within 1/16
 constexpr int kMlFields = 2 + 2 * kMlTerms;  // m, r, G^L_k / k, G^R_k / k
 static_assert(kMlFields <= kMpBlock, "block data must fit the merge's rows");
 
@@ -1380,20 +1415,23 @@ __global__ void k_lowner_warp(RootArgs a) {
       for (int b0 = 0; b0 < nb; b0 += 32) {
         const int b = b0 + lane;
         bool near = false;
-        const bool short_series =
-            __all_sync(0xffffffffu, b >= nb || MP[nb + b] <= 0.0625 * fabs(Di - MP[b]));
+        const double dm = b < nb ? Di - MP[b] : 1.0;
+        const double rb = b < nb ? MP[nb + b] : 0.0;
+        const bool far = b < nb && 3.0 * rb <= fabs(dm);
+        const int tier = series_tier(rb, fabs(dm), far);
         if (b < nb) {
-          const double dm = Di - MP[b];
-          if (MP[nb + b] <= 0.25 * fabs(dm)) {
+          if (far) {
             const double w = rcp_refined(dm);
             const double* c = MP + (2 + (dm < 0.0 ? kMlTerms : 0)) * nb + b;  // right of D_i: R
-            double val;
-            if (short_series) {
-              val = c[(kMpShort - 1) * nb];
+            const int nt = tier == 0 ? kMpShort : (tier == 1 ? kMpMid : kMlTerms);
+            double val = c[(nt - 1) * nb];
+            if (tier == 0) {
 #pragma unroll
               for (int k = kMpShort - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
+            } else if (tier == 1) {
+#pragma unroll
+              for (int k = kMpMid - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
             } else {
-              val = c[(kMlTerms - 1) * nb];
 #pragma unroll
               for (int k = kMlTerms - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
             }
@@ -1514,13 +1552,15 @@ __device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* 
 
 // Block expansion of the row sums (merges with K >= mp_min_k): with the blocks of
 // the secular expansion and t = 1 / (m - lambda_j), a block far from lambda_j
-// (r <= |m - lambda_j| / 4) adds
+// (r <= |m - lambda_j| / 3) adds
 //   t^2 sum_k (k + 1) A_k (-t)^k  to  sum zhat_i^2 / Delta_ij^2,   A_k = sum zhat^2 y^k,
 //   t   sum_k L_k (-t)^k          to  sum ALO_i zhat_i / Delta_ij,  L_k = sum zhat ALO y^k,
 //   t   sum_k H_k (-t)^k          to  sum AHI_i zhat_i / Delta_ij,  H_k = sum zhat AHI y^k,
-// y = D_i - m, with 32 terms: the dropped part stays below 2^-58 of the sum of the
-// block's |terms| for the squared kernel and below 2^-60 for the others.
-constexpr int kMrTerms = 32;
+// y = D_i - m, with 40 terms (32 for rounds within 1/4 of their distance, 16 within
+// 1/16): the dropped part stays below 2^-55 of the sum of the block's |terms| for
+// the squared kernel and below 2^-60 for the others.
+constexpr int kMrTerms = 40;  // far: radius <= 1/3 of the distance
+constexpr int kMrMid = 32;    // radius <= 1/4
 constexpr int kMrShort = 16;  // radius <= 1/16 of the distance: 17 x 16^-16 < 2^-59
 constexpr int kMrFields = 2 + 3 * kMrTerms;  // m, r, (k + 1) A_k, L_k, H_k
 static_assert(kMrFields <= kMpBlock, "block data must fit the merge's rows");
@@ -1584,6 +1624,22 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
   }
 }
 
+// the row sums' series of one far block, N terms (coefficient-major block data)
+template <int MODE, int N>
+__device__ __forceinline__ void rows_horner(const double* __restrict__ MP, int nb, int b, double u,
+                                            double& va, double& vl, double& vh) {
+  const double* A = MP + 2 * nb + b;
+  va = A[(N - 1) * nb];
+  if (MODE & 1) vl = A[(kMrTerms + N - 1) * nb];
+  if (MODE & 2) vh = A[(2 * kMrTerms + N - 1) * nb];
+#pragma unroll
+  for (int k = N - 2; k >= 0; --k) {
+    va = fma(va, u, A[k * nb]);
+    if (MODE & 1) vl = fma(vl, u, A[(kMrTerms + k) * nb]);
+    if (MODE & 2) vh = fma(vh, u, A[(2 * kMrTerms + k) * nb]);
+  }
+}
+
 // Row sums of one root with the block expansion (all 32 lanes): far blocks one per
 // lane through their series, near blocks term by term by the whole warp.
 template <int MODE>
@@ -1597,34 +1653,20 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
   for (int b0 = 0; b0 < nb; b0 += 32) {
     const int b = b0 + lane;
     bool near = false;
-    const bool short_series = __all_sync(
-        0xffffffffu, b >= nb || MP[nb + b] <= 0.0625 * fabs((MP[b] - dorg) - tau));
+    const double dm = b < nb ? (MP[b] - dorg) - tau : 1.0;  // m - lambda
+    const double rb = b < nb ? MP[nb + b] : 0.0;
+    const bool far = b < nb && 3.0 * rb <= fabs(dm);
+    const int tier = series_tier(rb, fabs(dm), far);
     if (b < nb) {
-      const double dm = (MP[b] - dorg) - tau;  // m - lambda
-      if (MP[nb + b] <= 0.25 * fabs(dm)) {
+      if (far) {
         const double t = rcp_refined(dm), u = -t;
         double va, vl = 0.0, vh = 0.0;
-        if (short_series) {
-          va = MP[(1 + kMrShort) * nb + b];
-          if (MODE & 1) vl = MP[(1 + kMrTerms + kMrShort) * nb + b];
-          if (MODE & 2) vh = MP[(1 + 2 * kMrTerms + kMrShort) * nb + b];
-#pragma unroll
-          for (int k = kMrShort - 2; k >= 0; --k) {
-            va = fma(va, u, MP[(2 + k) * nb + b]);
-            if (MODE & 1) vl = fma(vl, u, MP[(2 + kMrTerms + k) * nb + b]);
-            if (MODE & 2) vh = fma(vh, u, MP[(2 + 2 * kMrTerms + k) * nb + b]);
-          }
-        } else {
-          va = MP[(1 + kMrTerms) * nb + b];
-          if (MODE & 1) vl = MP[(1 + 2 * kMrTerms) * nb + b];
-          if (MODE & 2) vh = MP[(1 + 3 * kMrTerms) * nb + b];
-#pragma unroll
-          for (int k = kMrTerms - 2; k >= 0; --k) {
-            va = fma(va, u, MP[(2 + k) * nb + b]);
-            if (MODE & 1) vl = fma(vl, u, MP[(2 + kMrTerms + k) * nb + b]);
-            if (MODE & 2) vh = fma(vh, u, MP[(2 + 2 * kMrTerms + k) * nb + b]);
-          }
-        }
+        if (tier == 0)
+          rows_horner<MODE, kMrShort>(MP, nb, b, u, va, vl, vh);
+        else if (tier == 1)
+          rows_horner<MODE, kMrMid>(MP, nb, b, u, va, vl, vh);
+        else
+          rows_horner<MODE, kMrTerms>(MP, nb, b, u, va, vl, vh);
         s2 = fma(t * t, va, s2);
         if (MODE & 1) sl = fma(t, vl, sl);
         if (MODE & 2) sh = fma(t, vh, sh);
