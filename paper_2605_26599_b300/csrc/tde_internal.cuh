@@ -45,6 +45,7 @@ struct MState {
   int32_t K;     // active rank after deflation
   int32_t base;  // first index of this merge's roots in its root list
   double rho;    // rho' = 2 |beta|
+  double rhoinv; // 1 / rho
   double zsq;    // sum of active z^2
   int32_t big;   // 1: roots in the warp-per-root list (K >= warp_min_k)
   int32_t surv;  // survivors of the negligible-z test (active + rotation-deflated)

@@ -578,6 +578,7 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
       st.K = K;
       st.base = s_base;
       st.rho = rho;
+      st.rhoinv = 1.0 / rho;
       st.zsq = zsq;
       st.big = big ? 1 : 0;
       st.surv = S;
@@ -1057,6 +1058,7 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
       st.K = K;
       st.base = base;
       st.rho = rho;
+      st.rhoinv = 1.0 / rho;
       st.zsq = zsq;
       st.big = big ? 1 : 0;
       st.surv = S;

@@ -109,9 +109,9 @@ struct SecState {
 // (origin j, or K-1 for the last root, and the half width), the caller sweeps
 // there, and sec_init_finish picks the origin (the nearer pole) from the sign of
 // w and sets the half-interval bracket.
-__device__ __forceinline__ void sec_init_point(const double* D, int K, int j, double rho, double zsq,
-                                               SecState& q) {
-  q.rhoinv = 1.0 / rho;
+__device__ __forceinline__ void sec_init_point(const double* D, int K, int j, double rho,
+                                               double rhoinv, double zsq, SecState& q) {
+  q.rhoinv = rhoinv;
   if (j < K - 1) {
     q.jl = j;
     q.jr = j + 1;
@@ -221,6 +221,23 @@ __device__ __forceinline__ int sec_step(SecState& q, double hw, bool third) {
   else
     q.tlo = fmax(q.tlo, q.tau);
   if (q.thi - q.tlo <= 2.0 * kEps * fmax(fabs(q.tlo), fabs(q.thi))) return 0;
+  // Short last step: with w''/2 known and the Newton step -w / w' below 2^-20 |tau|,
+  // the second-order step eta = -w / (w' + (w''/2) eta_N) of the Taylor model
+  // w + w' eta + (w''/2) eta^2 is final.  The origin pole sits at distance |tau|
+  // and every other one farther, so the dropped cubic term moves eta by at most
+  // |eta| (eta / tau)^2 < 2^-40 |eta|, and the float rounding of w''/2 by
+  // 2^-24 |eta / tau| |eta|: both below 2^-60 |tau|.
+  if (third) {
+    const double dw = q.s.dpsi + q.s.dphi;
+    if (fabs(q.w) <= 0x1p-20 * fabs(q.tau) * dw) {
+      const double eta = -(q.w * dw) * rcp_refined(fma(dw, dw, -hw * q.w));
+      const double ntau = q.tau + eta;
+      if (ntau > q.tlo && ntau < q.thi) {
+        q.tau = ntau;
+        return 0;
+      }
+    }
+  }
   const double a = q.ol - q.tau, b = q.orr - q.tau;  // Delta of the two model poles
   if (q.wprev != 0.0 && fabs(q.w) > 0.1 * fabs(q.wprev)) q.exact = true;
   q.wprev = q.w;
@@ -272,31 +289,35 @@ struct Stage32 {
   int org, jl, jr, sweeps;
   bool live;
   float rhoinv, tau, tlo, thi, lo_int, hi_int, ol, orr, gap, inv;
-  double dorg, S;
+  double dorg, S, Sinv;
   Sec32 s;
 };
 
 template <class Sweep32>
-__device__ __forceinline__ bool s32_begin(const double* D, int K, int j, double rho, double zsq,
-                                          const Sweep32& sw32, Stage32& st) {
+__device__ __forceinline__ bool s32_begin(const double* D, int K, int j, double rho,
+                                          double rhoinv, double zsq, const Sweep32& sw32,
+                                          Stage32& st) {
   st.jl = (j < K - 1) ? j : K - 2;
   st.jr = st.jl + 1;
   const double width = (j < K - 1) ? D[st.jr] - D[st.jl] : rho * zsq;
   if (!(width >= 0x1p-90 && width <= 0x1p90) || !sw32.resolves(st.jl, st.jr, j == K - 1, width))
     return false;
-  const int ex = ilogb(width);
-  st.S = ldexp(1.0, ex);
-  st.inv = ldexpf(1.0f, -ex);
-  st.rhoinv = float(st.S / rho);
+  // S = 2^ex and its inverse built from the exponent bits (width is a normal
+  // double in [2^-90, 2^90]), so that every scaling below is an exact multiply
+  const int ex = int((__double_as_longlong(width) >> 52) & 0x7ff) - 1023;
+  st.S = __longlong_as_double((long long)(1023 + ex) << 52);
+  st.Sinv = __longlong_as_double((long long)(1023 - ex) << 52);
+  st.inv = __int_as_float((127 - ex) << 23);
+  st.rhoinv = float(st.S * rhoinv);
   st.sweeps = 0;
   st.live = false;
   if (j < K - 1) {
-    st.gap = float(width / st.S);
+    st.gap = float(width * st.Sinv);
     st.org = j;
     st.tau = 0.5f * st.gap;
   } else {
     st.org = K - 1;
-    st.hi_int = float(width / st.S);
+    st.hi_int = float(width * st.Sinv);
     st.lo_int = 0.0f;
     st.tau = 0.5f * st.hi_int;
     st.tlo = 0.0f;
@@ -325,8 +346,8 @@ __device__ __forceinline__ void s32_first(const double* D, int K, int j, Stage32
     }
   }
   st.dorg = D[st.org];
-  st.ol = float((D[st.jl] - st.dorg) / st.S);
-  st.orr = float((D[st.jr] - st.dorg) / st.S);
+  st.ol = float((D[st.jl] - st.dorg) * st.Sinv);
+  st.orr = float((D[st.jr] - st.dorg) * st.Sinv);
   st.live = true;
 }
 
@@ -372,17 +393,16 @@ __device__ __forceinline__ void s32_after(Stage32& st, float eta, bool have) {
 
 // w''/2 in natural units from its value in the stage's units (S^3 w''/2)
 __device__ __forceinline__ double hw_natural(const Stage32& st, float hws) {
-  const double inv = 1.0 / st.S;
-  return double(hws) * (inv * inv * inv);
+  return double(hws) * (st.Sinv * st.Sinv * st.Sinv);
 }
 
 // single-precision sweep at the FP64 stage's tau, for w''/2 (natural units)
 template <class Sweep32>
 __device__ __forceinline__ double hw_at(const Sweep32& sw32, const Stage32& st, const SecState& q) {
-  return hw_natural(st, sw32(q.org, q.jl, float(q.tau / st.S), st.inv).hw);
+  return hw_natural(st, sw32(q.org, q.jl, float(q.tau * st.Sinv), st.inv).hw);
 }
 
-__device__ __forceinline__ bool s32_finish(const double* D, const double* Z, double rho,
+__device__ __forceinline__ bool s32_finish(const double* D, const double* Z, double rhoinv,
                                            const Stage32& st, SecState& q, double* hw) {
   if (!(isfinite(st.rhoinv + st.s.psi + st.s.phi) && isfinite(st.s.hw) && st.tau > st.lo_int &&
         st.tau < st.hi_int))
@@ -393,7 +413,7 @@ __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, dou
   q.tau = double(st.tau) * st.S;
   q.tlo = double(st.lo_int) * st.S;
   q.thi = double(st.hi_int) * st.S;
-  q.rhoinv = 1.0 / rho;
+  q.rhoinv = rhoinv;
   q.dorg = st.dorg;
   q.zorg2 = Z[st.org] * Z[st.org];
   q.ol = D[st.jl] - st.dorg;
@@ -407,8 +427,8 @@ __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, dou
 // Solves root j; returns the number of FP64 pole sweeps (*n32 the single-precision
 // ones), *ok = false if capped.  One root per caller (a warp or a thread).
 template <class Sweep, class Sweep32>
-__device__ int secular_root(const double* D, const double* Z, int K, int j, double rho, double zsq,
-                            Sweep& sweep, Sweep32& sw32, int* org_out,
+__device__ int secular_root(const double* D, const double* Z, int K, int j, double rho,
+                            double rhoinv, double zsq, Sweep& sweep, Sweep32& sw32, int* org_out,
                             double* tau_out, bool* ok, int* n32) {
   *ok = true;
   *n32 = 0;
@@ -421,7 +441,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
   double hw = 0.0;
   Stage32 st;
   bool third = false;
-  if (s32_begin(D, K, j, rho, zsq, sw32, st)) {
+  if (s32_begin(D, K, j, rho, rhoinv, zsq, sw32, st)) {
     st.s = sw32(st.org, st.jl, st.tau, st.inv);
     s32_first(D, K, j, st);
     for (;;) {
@@ -433,13 +453,13 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
       if (!st.live) break;
     }
     *n32 = st.sweeps;
-    third = s32_finish(D, Z, rho, st, q, &hw);
+    third = s32_finish(D, Z, rhoinv, st, q, &hw);
   }
   if (third) {
     q.s = sweep(q.dorg, q.tau, q.jl);
     q.w = q.rhoinv + q.s.psi + q.s.phi;
   } else {
-    sec_init_point(D, K, j, rho, zsq, q);
+    sec_init_point(D, K, j, rho, rhoinv, zsq, q);
     q.s = sweep(q.dorg, q.tau, q.jl);
     sec_init_finish(D, Z, K, j, rho, zsq, q);
   }
@@ -471,7 +491,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
 // secular_root; all 32 lanes must call it together.
 template <class Sweep, class Sweep32>
 __device__ int secular_root_sync(const double* D, const double* Z, int K, int j, double rho,
-                                 double zsq, bool valid, Sweep& sweep, Sweep32& sw32,
+                                 double rhoinv, double zsq, bool valid, Sweep& sweep, Sweep32& sw32,
                                  int* org_out, double* tau_out, bool* ok, int* n32) {
   constexpr unsigned kFull = 0xffffffffu;
   *ok = true;
@@ -479,7 +499,7 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
   const bool act = valid && K > 1;
   Stage32 st;
   st.live = false;
-  const bool in32 = act && s32_begin(D, K, j, rho, zsq, sw32, st);
+  const bool in32 = act && s32_begin(D, K, j, rho, rhoinv, zsq, sw32, st);
   if (in32) {
     st.s = sw32(st.org, st.jl, st.tau, st.inv);
     s32_first(D, K, j, st);
@@ -501,9 +521,9 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
   bool third = false;
   if (in32) {
     *n32 = st.sweeps;
-    third = s32_finish(D, Z, rho, st, q, &hw);
+    third = s32_finish(D, Z, rhoinv, st, q, &hw);
   }
-  if (act && !third) sec_init_point(D, K, j, rho, zsq, q);
+  if (act && !third) sec_init_point(D, K, j, rho, rhoinv, zsq, q);
   if (act) q.s = sweep(q.dorg, q.tau, q.jl);
   if (act) {
     if (third)
@@ -546,17 +566,23 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
 // Block expansion of the FP64 sums (merges with K >= mp_min_k, warp-per-root
 // kernel).  The K poles are cut into nb = K / 128 blocks of consecutive poles (the
 // last one takes the remainder).  Per block, k_block_moments stores its centre m,
-// its radius r (largest |D_i - m|) and the moments
-//   M_k = sum_{i in block} z_i^2 (D_i - m)^k,
-// so that for lambda outside the block, with t = 1 / (m - lambda),
-//   sum z_i^2 / (D_i - lambda)   = t   sum_k M_k (-t)^k,
-//   sum z_i^2 / (D_i - lambda)^2 = t^2 sum_k (k + 1) M_k (-t)^k
-// (k = 0 .. 34).
-// A sweep takes a block through these series when r <= |m - lambda| / 3: with 35
-// terms the dropped part is below 3^-35 (1 + 1/3) / (1 - 1/3) < 2^-54 of the
+// its radius r (largest |D_i - m|) and the normalised moments
+//   M'_k = sum_{i in block} z_i^2 ((D_i - m) / r)^k,
+// so that for lambda outside the block, with t = 1 / (m - lambda) and x = -r t,
+//   sum z_i^2 / (D_i - lambda)   = t   sum_k M'_k x^k,
+//   sum z_i^2 / (D_i - lambda)^2 = t^2 sum_k (k + 1) M'_k x^k.
+// A sweep takes a block through these series when r <= |m - lambda| / 3 (|x| <= 1/3):
+// with 35 terms the dropped part is below 3^-35 (1 + 1/3) / (1 - 1/3) < 2^-54 of the
 // block's own sum_i |z_i^2 / (D_i - lambda)|, under the rounding bound of the
 // convergence test.  A round of 32 blocks all within 1/4 of their distance stops
 // after 27 terms (4^-27 (5/3) < 2^-53), all within 1/16 after 14 (16^-14 = 2^-56).
+// Only the head of each series runs in FP64: from term H on, Horner's rule runs in
+// float on float copies of the same moments and enters the FP64 chain as its
+// starting value.  The float part's error, about 3 x 2^-24 |x|^H of M'_0, stays
+// below 2^-55 for the value with H = 21 / 17 / 9 (x within 1/3, 1/4, 1/16), and below
+// 2^-40 for the derivative with H = 14 / 11 / 6.  The derivative only shapes the
+// step and the error bound: a relative error of 2^-40 moves the last step
+// (|eta| <= 2^-18 |tau|) by under 2^-58 |tau|.
 // Every other block (the root's own and its neighbours) is summed exactly.  The
 // block lies wholly on one side of lambda, so it adds to psi or phi as a whole.
 // m - lambda is formed as (m - D_org) - tau, like every Delta.
@@ -564,7 +590,9 @@ constexpr int kMpBlock = 128;  // poles per block
 constexpr int kMpTerms = 35;   // series terms (radius <= 1/3 of the distance)
 constexpr int kMpMid = 27;     // enough when radius <= 1/4 of the distance
 constexpr int kMpShort = 14;   // enough when radius <= 1/16 of the distance (16^-14 = 2^-56)
-constexpr int kMpFields = 2 + 2 * kMpTerms;  // m, r, M_k, (k + 1) M_k
+constexpr int kHv2 = 21, kHv1 = 17, kHv0 = 9;  // FP64 heads of the value series
+constexpr int kHd2 = 14, kHd1 = 11, kHd0 = 6;  // FP64 heads of the derivative series
+constexpr int kMpFields = 3 + kHv2 + kHd2;     // m, r, 3 r, M'_k (k < 21), (k + 1) M'_k (k < 14)
 
 // Series tier of a round of 32 blocks (warp vote over the lanes whose block, of
 // radius r at distance dist, is far): 0 if all of them are within 1/16 of their
@@ -573,6 +601,27 @@ __device__ __forceinline__ int series_tier(double r, double dist, bool far) {
   if (__all_sync(0xffffffffu, !far || 16.0 * r <= dist)) return 0;
   if (__all_sync(0xffffffffu, !far || 4.0 * r <= dist)) return 1;
   return 2;
+}
+
+// The same tests on the bit patterns of non-negative doubles (ordered like their
+// values), so that they take no FP64 instruction: adding j << 52 multiplies a
+// normal double by 2^j.  `dist` is |m - lambda|, r3 the stored 3 r.
+struct FarTest {
+  bool far;
+  int tier;
+};
+__device__ __forceinline__ FarTest far_test_bits(double dm, double r, double r3, bool valid) {
+  const long long db = __double_as_longlong(dm) & 0x7fffffffffffffffLL;
+  const long long rb = __double_as_longlong(r);
+  FarTest ft;
+  ft.far = valid && db >= __double_as_longlong(r3);
+  if (__all_sync(0xffffffffu, !ft.far || db >= rb + (4LL << 52)))
+    ft.tier = 0;
+  else if (__all_sync(0xffffffffu, !ft.far || db >= rb + (2LL << 52)))
+    ft.tier = 1;
+  else
+    ft.tier = 2;
+  return ft;
 }
 
 // Horner evaluation of two interleaved series of N terms, coefficient-major data
@@ -588,26 +637,53 @@ __device__ __forceinline__ void horner2(const double* c0, const double* c1, int 
     v1 = fma(v1, u, c1[k * nb]);
   }
 }
+
+// The value and derivative series of one far block (N terms, FP64 heads HV and
+// HD): float Horner over the tails (fa: M'_k, fb: (k + 1) M'_k), then FP64 Horner
+// over the heads (ca, cb) from the tails' values.
+template <int N, int HV, int HD>
+__device__ __forceinline__ void series_mixed(const double* ca, const double* cb, const float* fa,
+                                             const float* fb, int nb, double x, double& val,
+                                             double& der) {
+  static_assert(HD <= HV && HV < N, "heads inside the series");
+  const float xf = __double2float_rn(x);
+  float tv = fa[(N - 1) * nb], td = fb[(N - 1) * nb];
+#pragma unroll
+  for (int k = N - 2; k >= HD; --k) {
+    if (k >= HV) tv = fmaf(tv, xf, fa[k * nb]);
+    td = fmaf(td, xf, fb[k * nb]);
+  }
+  double v = double(tv), d = double(td);
+#pragma unroll
+  for (int k = HV - 1; k >= 0; --k) {
+    v = fma(v, x, ca[k * nb]);
+    if (k < HD) d = fma(d, x, cb[k * nb]);
+  }
+  val = v;
+  der = d;
+}
 static_assert(kMpFields <= kMpBlock, "block data must fit the merge's rows (fields x K / 128 <= K)");
 
-// The single-precision stage uses the same blocks, with float data placed after the
-// FP64 data (field q of block b at BF[q nb + b], BF = (float*)(MPD + lo + 56 nb)):
-// the centre minus the merge's midrange as a float pair, the radius, and the
-// normalised moments M'_k = sum z_i^2 ((D_i - m) / r)^k, k < 18, times 1, k + 1
-// and (k + 1)(k + 2) / 2.  In the stage's units (offsets / S, sums x S) a far block
-// with d = (m - lambda) / S and x = -(r / S) / d adds
+// Float data of the blocks, placed after the FP64 data (field q of block b at
+// BF[q nb + b], BF = (float*)(MPD + lo + 38 nb)): the centre minus the merge's
+// midrange as a float pair, the radius, the normalised moments M'_k and
+// (k + 1) M'_k (k < 35; the tails of the FP64 series and the single-precision
+// stage's w and w') and (k + 1)(k + 2) / 2 M'_k (k < 18, its w''/2).  In the stage's
+// units (offsets / S, sums x S) a far block with d = (m - lambda) / S and
+// x = -(r / S) / d adds
 //   w: (1/d) sum M'_k x^k,  w': (1/d)^2 sum (k + 1) M'_k x^k,
 //   w''/2: (1/d)^3 sum (k + 1)(k + 2)/2 M'_k x^k,
 // far blocks (|x| <= 1/3) take 18 terms, rounds within 1/16 10: the dropped part
 // stays below 2^-27 of the block's terms, under the rounding of the float sums.
 // The normalisation keeps every float in range.
-constexpr int kMfTerms = 18;  // radius <= 1/3: 3^-18 x 2 < 2^-27
+constexpr int kMfTerms = 35;  // float M'_k and (k + 1) M'_k
+constexpr int kMf32 = 18;     // terms of the single-precision stage: 3^-18 x 2 < 2^-27
 constexpr int kMfShort = 10;  // radius <= 1/16: 16^-10 = 2^-40
-constexpr int kMfFields = 3 + 3 * kMfTerms;  // centre hi, lo, radius, three series
+constexpr int kMfFields = 3 + 2 * kMfTerms + kMf32;  // centre hi, lo, radius, three series
 static_assert(2 * kMpFields + kMfFields <= 2 * kMpBlock, "both block data sets fit the merge's rows");
 
 // Block data of the merge at lo lives coefficient-major in MPD + lo: field q of
-// block b at [q * nb + b] (56 nb <= K entries, inside the merge's rows).
+// block b at [q * nb + b] (84 nb <= K entries, inside the merge's rows).
 __device__ __forceinline__ int mp_blocks(int K, int mp_min_k) {
   return K >= mp_min_k ? K / kMpBlock : 0;
 }
@@ -673,6 +749,30 @@ __device__ __forceinline__ void lane_sums(const double* __restrict__ D, const do
   dsum = (d0 + d1) + (d2 + d3);
 }
 
+// Adds the terms of poles b + lane, b + lane + 32, ... below e to two chains of
+// z^2 / Delta and two of (z / Delta)^2 (the block-expanded sweep keeps them over
+// all its near blocks and combines them once).
+__device__ __forceinline__ void lane_acc(const double* __restrict__ D, const double* __restrict__ Z,
+                                         int b, int e, int lane, double dorg, double tau,
+                                         double& a0, double& a1, double& d0, double& d1) {
+  int i = b + lane;
+  for (; i + 32 < e; i += 64) {
+    const double z0 = Z[i], z1 = Z[i + 32];
+    const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+    const double t1 = z1 * rcp_refined((D[i + 32] - dorg) - tau);
+    a0 = fma(z0, t0, a0);
+    d0 = fma(t0, t0, d0);
+    a1 = fma(z1, t1, a1);
+    d1 = fma(t1, t1, d1);
+  }
+  if (i < e) {
+    const double z0 = Z[i];
+    const double t0 = z0 * rcp_refined((D[i] - dorg) - tau);
+    a0 = fma(z0, t0, a0);
+    d0 = fma(t0, t0, d0);
+  }
+}
+
 // All 32 lanes sum one root.  With nb > 0 (block expansion) lane l takes blocks
 // l, l + 32, ...: a far block through its series, and the near blocks found in
 // each round of 32 are summed exactly by the whole warp.  `pairs` and `blocks`
@@ -684,6 +784,7 @@ struct WarpSweep {
   int lane;
   int nb;
   const double* __restrict__ MP;
+  const float* __restrict__ MF;
   mutable unsigned long long pairs;
   mutable unsigned blocks;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
@@ -693,25 +794,28 @@ struct WarpSweep {
       lane_sums(D, Z, jl + 1, K, lane, dorg, tau, f, df);
       pairs += unsigned(K);
     } else {
+      double pa0 = 0.0, pa1 = 0.0, pd0 = 0.0, pd1 = 0.0;  // near poles left of lambda
+      double fa0 = 0.0, fa1 = 0.0, fd0 = 0.0, fd1 = 0.0;  // and right of it
       for (int b0 = 0; b0 < nb; b0 += 32) {
         const int b = b0 + lane;
         bool near = false;
         const double dm = b < nb ? (MP[b] - dorg) - tau : 1.0;  // m - lambda
         const double rb = b < nb ? MP[nb + b] : 0.0;
-        const bool far = b < nb && 3.0 * rb <= fabs(dm);
-        const int tier = series_tier(rb, fabs(dm), far);
+        const FarTest ft = far_test_bits(dm, rb, b < nb ? MP[2 * nb + b] : 0.0, b < nb);
         if (b < nb) {
-          if (far) {
-            const double t = rcp_refined(dm), u = -t;
-            const double* c0 = MP + 2 * nb + b;
-            const double* c1 = MP + (2 + kMpTerms) * nb + b;
+          if (ft.far) {
+            const double t = rcp_refined(dm), x = -rb * t;
+            const double* ca = MP + 3 * nb + b;
+            const double* cb = MP + (3 + kHv2) * nb + b;
+            const float* fa = MF + 3 * nb + b;
+            const float* fb = MF + (3 + kMfTerms) * nb + b;
             double val, der;
-            if (tier == 0)
-              horner2<kMpShort>(c0, c1, nb, u, val, der);
-            else if (tier == 1)
-              horner2<kMpMid>(c0, c1, nb, u, val, der);
+            if (ft.tier == 0)
+              series_mixed<kMpShort, kHv0, kHd0>(ca, cb, fa, fb, nb, x, val, der);
+            else if (ft.tier == 1)
+              series_mixed<kMpMid, kHv1, kHd1>(ca, cb, fa, fb, nb, x, val, der);
             else
-              horner2<kMpTerms>(c0, c1, nb, u, val, der);
+              series_mixed<kMpTerms, kHv2, kHd2>(ca, cb, fa, fb, nb, x, val, der);
             if (dm > 0.0) {
               f = fma(t, val, f);
               df = fma(t * t, der, df);
@@ -730,16 +834,15 @@ struct WarpSweep {
           nm &= nm - 1;
           const int i0 = bb * kMpBlock, i1 = (bb == nb - 1) ? K : i0 + kMpBlock;
           const int mid = min(max(jl + 1, i0), i1);
-          double a, da;
-          lane_sums(D, Z, i0, mid, lane, dorg, tau, a, da);
-          p += a;
-          dp += da;
-          lane_sums(D, Z, mid, i1, lane, dorg, tau, a, da);
-          f += a;
-          df += da;
+          lane_acc(D, Z, i0, mid, lane, dorg, tau, pa0, pa1, pd0, pd1);
+          lane_acc(D, Z, mid, i1, lane, dorg, tau, fa0, fa1, fd0, fd1);
           pairs += unsigned(i1 - i0);
         }
       }
+      p += pa0 + pa1;
+      dp += pd0 + pd1;
+      f += fa0 + fa1;
+      df += fd0 + fd1;
     }
     SecSums s;
     s.psi = warp_sum(p);
@@ -922,11 +1025,11 @@ struct WarpSweep32 : Copies32 {
                 vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
               }
             } else {
-              va = A[(kMfTerms - 1) * nb];
-              vb = A[(2 * kMfTerms - 1) * nb];
-              vc = A[(3 * kMfTerms - 1) * nb];
+              va = A[(kMf32 - 1) * nb];
+              vb = A[(kMfTerms + kMf32 - 1) * nb];
+              vc = A[(2 * kMfTerms + kMf32 - 1) * nb];
 #pragma unroll
-              for (int k = kMfTerms - 2; k >= 0; --k) {
+              for (int k = kMf32 - 2; k >= 0; --k) {
                 va = fmaf(va, x, A[k * nb]);
                 vb = fmaf(vb, x, A[(kMfTerms + k) * nb]);
                 vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
@@ -1065,35 +1168,27 @@ __global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
       const int i0 = b * kMpBlock, i1 = (b == nbb - 1) ? K : i0 + kMpBlock;
       const double m = 0.5 * (D[i0] + D[i1 - 1]);
       const double rad = fmax(m - D[i0], D[i1 - 1] - m);
-      double mo[kMpTerms], mf[kMfTerms];
+      double mo[kMfTerms];  // normalised: sum z^2 ((D_i - m) / r)^k
 #pragma unroll
-      for (int k = 0; k < kMpTerms; ++k) mo[k] = 0.0;
-#pragma unroll
-      for (int k = 0; k < kMfTerms; ++k) mf[k] = 0.0;
+      for (int k = 0; k < kMfTerms; ++k) mo[k] = 0.0;
       const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
       for (int i = i0 + lane; i < i1; i += 32) {
-        const double y = D[i] - m, w = Z[i] * Z[i];
-        double pw = w, pn = w;
+        const double y = (D[i] - m) * rinv;
+        double pn = Z[i] * Z[i];
 #pragma unroll
-        for (int k = 0; k < kMpTerms; ++k) {
-          mo[k] += pw;
-          pw *= y;
-        }
-#pragma unroll
-        for (int k = 0; k < kMfTerms; ++k) {  // normalised: ((D_i - m) / r)^k
-          mf[k] += pn;
-          pn *= y * rinv;
+        for (int k = 0; k < kMfTerms; ++k) {
+          mo[k] += pn;
+          pn *= y;
         }
       }
 #pragma unroll
-      for (int k = 0; k < kMpTerms; ++k) mo[k] = warp_sum(mo[k]);
-#pragma unroll
-      for (int k = 0; k < kMfTerms; ++k) mf[k] = warp_sum(mf[k]);
+      for (int k = 0; k < kMfTerms; ++k) mo[k] = warp_sum(mo[k]);
       double* MP = a.MPD + lo;
       float* BF = reinterpret_cast<float*>(MP + kMpFields * nbb);
       if (lane == 0) {
         MP[b] = m;
         MP[nbb + b] = rad;
+        MP[2 * nbb + b] = 3.0 * rad;
         const double c = m - a.ms[gg].shift;
         const float ch = __double2float_rn(c);
         BF[b] = ch;
@@ -1101,18 +1196,15 @@ __global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
         BF[2 * nbb + b] = __double2float_rn(rad);
       }
 #pragma unroll
-      for (int k = 0; k < kMpTerms; ++k)
-        if (lane == (k & 31)) {
-          MP[(2 + k) * nbb + b] = mo[k];
-          MP[(2 + kMpTerms + k) * nbb + b] = double(k + 1) * mo[k];
-        }
-#pragma unroll
       for (int k = 0; k < kMfTerms; ++k)
-        if (lane == ((k + 16) & 31)) {
-          BF[(3 + k) * nbb + b] = __double2float_rn(mf[k]);
-          BF[(3 + kMfTerms + k) * nbb + b] = __double2float_rn(double(k + 1) * mf[k]);
-          BF[(3 + 2 * kMfTerms + k) * nbb + b] =
-              __double2float_rn(0.5 * double((k + 1) * (k + 2)) * mf[k]);
+        if (lane == (k & 31)) {
+          if (k < kHv2) MP[(3 + k) * nbb + b] = mo[k];
+          if (k < kHd2) MP[(3 + kHv2 + k) * nbb + b] = double(k + 1) * mo[k];
+          BF[(3 + k) * nbb + b] = __double2float_rn(mo[k]);
+          BF[(3 + kMfTerms + k) * nbb + b] = __double2float_rn(double(k + 1) * mo[k]);
+          if (k < kMf32)
+            BF[(3 + 2 * kMfTerms + k) * nbb + b] =
+                __double2float_rn(0.5 * double((k + 1) * (k + 2)) * mo[k]);
         }
     }
   }
@@ -1138,7 +1230,7 @@ __global__ void k_secular_thread(RootArgs a) {
     int org = 0, n32 = 0;
     double tau = 0.0;
     bool ok = true;
-    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw,
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.rhoinv, ms.zsq, valid, sw,
                                          sw32, &org, &tau, &ok, &n32);
     if (valid) {
       secular_store(a, lo, j, org, tau, sweeps, K, ok, true);
@@ -1171,7 +1263,7 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
     int org = 0, n32 = 0;
     double tau = 0.0;
     bool ok = true;
-    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.zsq, valid, sw,
+    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.rhoinv, ms.zsq, valid, sw,
                                          sw32, &org, &tau, &ok, &n32);
     if (valid) {
       secular_store(a, lo, j, org, tau, sweeps, K, ok, gl == 0);
@@ -1197,14 +1289,14 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     const int q = rl - ms.base, lo = a.M[g].lo;
     const int j = (q & 1) ? ms.K - 1 - (q >> 1) : (q >> 1);
     const int nb = mp_blocks(ms.K, a.mp_min_k);
-    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, 0ull, 0u};
-    WarpSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, nb,
-                     reinterpret_cast<const float*>(a.MPD + lo + kMpFields * nb)};
+    const float* mf = reinterpret_cast<const float*>(a.MPD + lo + kMpFields * nb);
+    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, mf, 0ull, 0u};
+    WarpSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, nb, mf};
     int org, n32;
     double tau;
     bool ok;
     const int sweeps =
-        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.zsq, sw, sw32, &org, &tau, &ok,
+        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.rhoinv, ms.zsq, sw, sw32, &org, &tau, &ok,
                      &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
     tally.add_counted(sw.pairs, sw.blocks, sweeps, n32, ms.K);
