@@ -594,18 +594,12 @@ constexpr int kHv2 = 21, kHv1 = 17, kHv0 = 9;  // FP64 heads of the value series
 constexpr int kHd2 = 14, kHd1 = 11, kHd0 = 6;  // FP64 heads of the derivative series
 constexpr int kMpFields = 3 + kHv2 + kHd2;     // m, r, 3 r, M'_k (k < 21), (k + 1) M'_k (k < 14)
 
-// Series tier of a round of 32 blocks (warp vote over the lanes whose block, of
-// radius r at distance dist, is far): 0 if all of them are within 1/16 of their
-// distance, 1 if within 1/4, else 2.
-__device__ __forceinline__ int series_tier(double r, double dist, bool far) {
-  if (__all_sync(0xffffffffu, !far || 16.0 * r <= dist)) return 0;
-  if (__all_sync(0xffffffffu, !far || 4.0 * r <= dist)) return 1;
-  return 2;
-}
-
-// The same tests on the bit patterns of non-negative doubles (ordered like their
-// values), so that they take no FP64 instruction: adding j << 52 multiplies a
-// normal double by 2^j.  `dist` is |m - lambda|, r3 the stored 3 r.
+// Far test and series tier of a round of 32 blocks (warp vote over the lanes whose
+// block, of radius r at distance |dm| from the point, is far): far when 3 r <= |dm|;
+// tier 0 if all far blocks of the round are within 1/16 of their distance, 1 if
+// within 1/4, else 2.  The tests compare the bit patterns of non-negative doubles
+// (ordered like their values), so that they take no FP64 instruction: adding
+// j << 52 multiplies a normal double by 2^j; r3 is the stored 3 r.
 struct FarTest {
   bool far;
   int tier;
@@ -622,20 +616,6 @@ __device__ __forceinline__ FarTest far_test_bits(double dm, double r, double r3,
   else
     ft.tier = 2;
   return ft;
-}
-
-// Horner evaluation of two interleaved series of N terms, coefficient-major data
-// (the first series' coefficient k at c0[k * nb], the second's at c1[k * nb])
-template <int N>
-__device__ __forceinline__ void horner2(const double* c0, const double* c1, int nb, double u,
-                                        double& v0, double& v1) {
-  v0 = c0[(N - 1) * nb];
-  v1 = c1[(N - 1) * nb];
-#pragma unroll
-  for (int k = N - 2; k >= 0; --k) {
-    v0 = fma(v0, u, c0[k * nb]);
-    v1 = fma(v1, u, c1[k * nb]);
-  }
 }
 
 // The value and derivative series of one far block (N terms, FP64 heads HV and
@@ -1391,19 +1371,39 @@ __global__ void k_lowner_thread(RootArgs a) {
 // (P_j - D_i) with P_j = D_j for j < i and D_{j+1} for j >= i.  The K - 1 pairs
 // are cut into the blocks of the secular expansion (pairs j in [128 b, 128 b +
 // 128), the last block up to K - 1); block b spans [D_b0, D_b1] around its centre
-// m with radius r.  For D_i far from it (r <= |D_i - m| / 4) its pairs sum to
-//   sum_j log f_j = -sum_{k>=1} (G_k / k) w^k,  w = 1 / (D_i - m),
+// m with radius r.  For D_i far from it (r <= |D_i - m| / 3) its pairs sum to
+//   sum_j log f_j = -w sum_{k>=0} c_k x^k,  w = 1 / (D_i - m),  x = r w,
+//   c_k = G_{k+1} / ((k + 1) r^k),
 //   G_k = sum_j (lambda_j - m)^k - (P_j - m)^k = sum_j a_j h_{k-1}(lambda_j - m, P_j - m),
 // a_j = lambda_j - P_j and h the complete homogeneous sum, so G_k carries no
-// cancellation; the block lies wholly on one side of D_i, so P_j = D_j (left, set
-// L) or D_{j+1} (right, set R) for all its pairs.  A block is far when
-// r <= |D_i - m| / 3; with 35 terms (27 for rounds within 1/4, 14 within 1/16) the
-// dropped part is below 2^-53 of sum_j |a_j| / |D_i - m| <= 1 (absolute, in the
-// log), and the far blocks' sum enters zhat^2 through one exp.  Near blocks
-// multiply their factors directly.
-constexpr int kMlTerms = 35;  // far: radius <= 1/3 of the distance; 27 within 1/4, 14 within 1/16
-constexpr int kMlFields = 2 + 2 * kMlTerms;  // m, r, G^L_k / k, G^R_k / k
-static_assert(kMlFields <= kMpBlock, "block data must fit the merge's rows");
+// cancellation and |c_k| <= sum_j |a_j|; the block lies wholly on one side of D_i,
+// so P_j = D_j (left, set L) or D_{j+1} (right, set R) for all its pairs.  With 35
+// terms (27 for rounds within 1/4, 14 within 1/16) the dropped part is below 2^-53
+// of sum_j |a_j| / |D_i - m| <= 1 (absolute, in the log), and the far blocks' sum
+// enters zhat^2 through one exp.  As in the secular sweep only the first 21 / 17 / 9
+// terms run in FP64 and the rest in float (error below 2^-55 of the same bound).
+// Near blocks multiply their factors directly.
+constexpr int kMlTerms = 35;   // far: radius <= 1/3 of the distance; 27 within 1/4, 14 within 1/16
+constexpr int kMlHead = kHv2;  // FP64 coefficients stored per side
+constexpr int kTailBase = kHv0;  // float copies start at this term (every tier's head reaches it)
+constexpr int kMlFields = 3 + 2 * kMlHead;                // m, r, 3 r, c^L_k, c^R_k (k < 21)
+constexpr int kMlFloats = 2 * (kMlTerms - kTailBase);     // c^L_k, c^R_k (9 <= k < 35) as floats
+static_assert(2 * kMlFields + kMlFloats <= 2 * kMpBlock, "block data must fit the merge's rows");
+
+// One series of N terms with an FP64 head of H terms (coefficients c[k * nb]) and
+// a float tail (coefficients f[(k - kTailBase) * nb]), at x.
+template <int N, int H>
+__device__ __forceinline__ double series1_mixed(const double* c, const float* f, int nb, double x) {
+  static_assert(H >= kTailBase && H < N, "head inside the series");
+  const float xf = __double2float_rn(x);
+  float tv = f[(N - 1 - kTailBase) * nb];
+#pragma unroll
+  for (int k = N - 2; k >= H; --k) tv = fmaf(tv, xf, f[(k - kTailBase) * nb]);
+  double v = double(tv);
+#pragma unroll
+  for (int k = H - 1; k >= 0; --k) v = fma(v, x, c[k * nb]);
+  return v;
+}
 
 __device__ __forceinline__ int lowner_block_end(int b, int nb, int K) {
   return b == nb - 1 ? K - 1 : (b + 1) * kMpBlock;
@@ -1439,22 +1439,26 @@ __global__ void __launch_bounds__(128) k_lowner_moments(RootArgs a) {
       const double* TAU = a.TAU + lo;
       const int j0 = b * kMpBlock, j1 = lowner_block_end(b, nbb, K);
       const double m = 0.5 * (D[j0] + D[j1]);
+      const double rad = fmax(m - D[j0], D[j1] - m);
+      const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
       double* MP = a.MPR + lo;
+      float* MF = reinterpret_cast<float*>(MP + kMlFields * nbb);
       if (lane == 0) {
         MP[b] = m;
-        MP[nbb + b] = fmax(m - D[j0], D[j1] - m);
+        MP[nbb + b] = rad;
+        MP[2 * nbb + b] = 3.0 * rad;
       }
       for (int side = 0; side < 2; ++side) {  // L: partner D_j, R: partner D_{j+1}
-        double gk[kMlTerms];
+        double gk[kMlTerms];  // G_{k+1} / r^k
 #pragma unroll
         for (int k = 0; k < kMlTerms; ++k) gk[k] = 0.0;
         for (int jj = j0 + lane; jj < j1; jj += 32) {
           const double P = D[jj + side];
-          const double u = (DORG[jj] - m) + TAU[jj], v = P - m;
+          const double u = ((DORG[jj] - m) + TAU[jj]) * rinv, v = (P - m) * rinv;
           const double aj = (DORG[jj] - P) + TAU[jj];
           double h = 1.0, vk = 1.0;
 #pragma unroll
-          for (int k = 0; k < kMlTerms; ++k) {  // G_{k+1} += a h_k
+          for (int k = 0; k < kMlTerms; ++k) {  // G_{k+1} / r^k += a h_k(u, v)
             gk[k] = fma(aj, h, gk[k]);
             vk *= v;
             h = fma(u, h, vk);
@@ -1462,8 +1466,12 @@ __global__ void __launch_bounds__(128) k_lowner_moments(RootArgs a) {
         }
 #pragma unroll
         for (int k = 0; k < kMlTerms; ++k) {
-          const double s = warp_sum(gk[k]);
-          if (lane == (k & 31)) MP[(2 + side * kMlTerms + k) * nbb + b] = s / double(k + 1);
+          const double c = warp_sum(gk[k]) / double(k + 1);
+          if (lane == (k & 31)) {
+            if (k < kMlHead) MP[(3 + side * kMlHead + k) * nbb + b] = c;
+            if (k >= kTailBase)
+              MF[(side * (kMlTerms - kTailBase) + k - kTailBase) * nbb + b] = __double2float_rn(c);
+          }
         }
       }
     }
@@ -1504,29 +1512,26 @@ __global__ void k_lowner_warp(RootArgs a) {
       pairs += unsigned(K);
     } else {
       const double* MP = a.MPR + lo;
+      const float* MF = reinterpret_cast<const float*>(MP + kMlFields * nb);
       for (int b0 = 0; b0 < nb; b0 += 32) {
         const int b = b0 + lane;
         bool near = false;
         const double dm = b < nb ? Di - MP[b] : 1.0;
         const double rb = b < nb ? MP[nb + b] : 0.0;
-        const bool far = b < nb && 3.0 * rb <= fabs(dm);
-        const int tier = series_tier(rb, fabs(dm), far);
+        const FarTest ft = far_test_bits(dm, rb, b < nb ? MP[2 * nb + b] : 0.0, b < nb);
         if (b < nb) {
-          if (far) {
-            const double w = rcp_refined(dm);
-            const double* c = MP + (2 + (dm < 0.0 ? kMlTerms : 0)) * nb + b;  // right of D_i: R
-            const int nt = tier == 0 ? kMpShort : (tier == 1 ? kMpMid : kMlTerms);
-            double val = c[(nt - 1) * nb];
-            if (tier == 0) {
-#pragma unroll
-              for (int k = kMpShort - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
-            } else if (tier == 1) {
-#pragma unroll
-              for (int k = kMpMid - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
-            } else {
-#pragma unroll
-              for (int k = kMlTerms - 2; k >= 0; --k) val = fma(val, w, c[k * nb]);
-            }
+          if (ft.far) {
+            const double w = rcp_refined(dm), x = rb * w;
+            const int side = dm < 0.0 ? 1 : 0;  // right of D_i: R
+            const double* c = MP + (3 + side * kMlHead) * nb + b;
+            const float* f = MF + side * (kMlTerms - kTailBase) * nb + b;
+            double val;
+            if (ft.tier == 0)
+              val = series1_mixed<kMpShort, kHv0>(c, f, nb, x);
+            else if (ft.tier == 1)
+              val = series1_mixed<kMpMid, kHv1>(c, f, nb, x);
+            else
+              val = series1_mixed<kMlTerms, kHv2>(c, f, nb, x);
             slog = fma(-w, val, slog);
           } else {
             near = true;
@@ -1643,19 +1648,25 @@ __device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* 
 }
 
 // Block expansion of the row sums (merges with K >= mp_min_k): with the blocks of
-// the secular expansion and t = 1 / (m - lambda_j), a block far from lambda_j
-// (r <= |m - lambda_j| / 3) adds
-//   t^2 sum_k (k + 1) A_k (-t)^k  to  sum zhat_i^2 / Delta_ij^2,   A_k = sum zhat^2 y^k,
-//   t   sum_k L_k (-t)^k          to  sum ALO_i zhat_i / Delta_ij,  L_k = sum zhat ALO y^k,
-//   t   sum_k H_k (-t)^k          to  sum AHI_i zhat_i / Delta_ij,  H_k = sum zhat AHI y^k,
-// y = D_i - m, with 40 terms (32 for rounds within 1/4 of their distance, 16 within
-// 1/16): the dropped part stays below 2^-55 of the sum of the block's |terms| for
-// the squared kernel and below 2^-60 for the others.
+// the secular expansion, t = 1 / (m - lambda_j) and x = -r t, a block far from
+// lambda_j (r <= |m - lambda_j| / 3) adds
+//   t^2 sum_k (k + 1) A_k x^k  to  sum zhat_i^2 / Delta_ij^2,   A_k = sum zhat^2 y^k,
+//   t   sum_k L_k x^k          to  sum ALO_i zhat_i / Delta_ij,  L_k = sum zhat ALO y^k,
+//   t   sum_k H_k x^k          to  sum AHI_i zhat_i / Delta_ij,  H_k = sum zhat AHI y^k,
+// y = (D_i - m) / r, with 40 terms (32 for rounds within 1/4 of their distance, 16
+// within 1/16): the dropped part stays below 2^-55 of the sum of the block's
+// |terms| for the squared kernel and below 2^-60 for the others.  The first 24 / 19
+// / 9 terms of the squared kernel and 21 / 17 / 9 of the others run in FP64, the
+// rest in float: the float part's error, about 3 (k + 1) 2^-24 |x|^k from the head's
+// end k on, stays below 2^-55 of the same sums.
 constexpr int kMrTerms = 40;  // far: radius <= 1/3 of the distance
 constexpr int kMrMid = 32;    // radius <= 1/4
 constexpr int kMrShort = 16;  // radius <= 1/16 of the distance: 17 x 16^-16 < 2^-59
-constexpr int kMrFields = 2 + 3 * kMrTerms;  // m, r, (k + 1) A_k, L_k, H_k
-static_assert(kMrFields <= kMpBlock, "block data must fit the merge's rows");
+constexpr int kMrHa2 = 24, kMrHa1 = 19, kMrHa0 = 9;  // FP64 heads of the squared kernel
+constexpr int kMrHl2 = kHv2, kMrHl1 = kHv1, kMrHl0 = kHv0;  // and of the two row kernels
+constexpr int kMrFields = 3 + kMrHa2 + 2 * kMrHl2;  // m, r, 3 r, (k + 1) A_k, L_k, H_k (heads)
+constexpr int kMrTail = kMrTerms - kTailBase;       // float terms per kernel (9 <= k < 40)
+static_assert(2 * kMrFields + 3 * kMrTail <= 2 * kMpBlock, "block data must fit the merge's rows");
 
 // Moments of the row sums, one warp per block (found as in k_block_moments).
 __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
@@ -1687,10 +1698,14 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
       const double* ZH = a.ZHAT + lo;
       const int i0 = b * kMpBlock, i1 = (b == nbb - 1) ? K : i0 + kMpBlock;
       const double m = 0.5 * (D[i0] + D[i1 - 1]);
+      const double rad = fmax(m - D[i0], D[i1 - 1] - m);
+      const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
       double* MP = a.MPR + lo;
+      float* MF = reinterpret_cast<float*>(MP + kMrFields * nbb);
       if (lane == 0) {
         MP[b] = m;
-        MP[nbb + b] = fmax(m - D[i0], D[i1 - 1] - m);
+        MP[nbb + b] = rad;
+        MP[2 * nbb + b] = 3.0 * rad;
       }
       for (int which = 0; which < 3; ++which) {  // zhat^2 (stored times k + 1), zhat ALO, zhat AHI
         const double* W = which == 1 ? a.ALO + lo : a.AHI + lo;
@@ -1698,7 +1713,7 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
 #pragma unroll
         for (int k = 0; k < kMrTerms; ++k) mo[k] = 0.0;
         for (int i = i0 + lane; i < i1; i += 32) {
-          const double y = D[i] - m;
+          const double y = (D[i] - m) * rinv;
           double pw = ZH[i] * (which == 0 ? ZH[i] : W[i]);
 #pragma unroll
           for (int k = 0; k < kMrTerms; ++k) {
@@ -1706,30 +1721,57 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
             pw *= y;
           }
         }
+        const int head = which == 0 ? kMrHa2 : kMrHl2;
+        const int off = which == 0 ? 0 : kMrHa2 + (which - 1) * kMrHl2;
 #pragma unroll
         for (int k = 0; k < kMrTerms; ++k) {
-          const double v = warp_sum(mo[k]);
-          if (lane == (k & 31)) MP[(2 + which * kMrTerms + k) * nbb + b] = which == 0 ? double(k + 1) * v : v;
+          const double v0 = warp_sum(mo[k]);
+          const double v = which == 0 ? double(k + 1) * v0 : v0;
+          if (lane == (k & 31)) {
+            if (k < head) MP[(3 + off + k) * nbb + b] = v;
+            if (k >= kTailBase) MF[(which * kMrTail + k - kTailBase) * nbb + b] = __double2float_rn(v);
+          }
         }
       }
     }
   }
 }
 
-// the row sums' series of one far block, N terms (coefficient-major block data)
-template <int MODE, int N>
-__device__ __forceinline__ void rows_horner(const double* __restrict__ MP, int nb, int b, double u,
-                                            double& va, double& vl, double& vh) {
-  const double* A = MP + 2 * nb + b;
-  va = A[(N - 1) * nb];
-  if (MODE & 1) vl = A[(kMrTerms + N - 1) * nb];
-  if (MODE & 2) vh = A[(2 * kMrTerms + N - 1) * nb];
+// The row sums' series of one far block at x: N terms, FP64 heads HA (squared
+// kernel) and HL (row kernels), float tails.
+template <int MODE, int N, int HA, int HL>
+__device__ __forceinline__ void rows_mixed(const double* __restrict__ MP,
+                                           const float* __restrict__ MF, int nb, int b, double x,
+                                           double& va, double& vl, double& vh) {
+  static_assert(HL <= HA && HL >= kTailBase && HA < N, "heads inside the series");
+  const double* CA = MP + 3 * nb + b;
+  const double* CL = MP + (3 + kMrHa2) * nb + b;
+  const double* CH = MP + (3 + kMrHa2 + kMrHl2) * nb + b;
+  const float* FA = MF + b;
+  const float* FL = MF + kMrTail * nb + b;
+  const float* FH = MF + 2 * kMrTail * nb + b;
+  const float xf = __double2float_rn(x);
+  float ta = FA[(N - 1 - kTailBase) * nb], tl = 0.f, th = 0.f;
+  if (MODE & 1) tl = FL[(N - 1 - kTailBase) * nb];
+  if (MODE & 2) th = FH[(N - 1 - kTailBase) * nb];
 #pragma unroll
-  for (int k = N - 2; k >= 0; --k) {
-    va = fma(va, u, A[k * nb]);
-    if (MODE & 1) vl = fma(vl, u, A[(kMrTerms + k) * nb]);
-    if (MODE & 2) vh = fma(vh, u, A[(2 * kMrTerms + k) * nb]);
+  for (int k = N - 2; k >= HL; --k) {
+    if (k >= HA) ta = fmaf(ta, xf, FA[(k - kTailBase) * nb]);
+    if (MODE & 1) tl = fmaf(tl, xf, FL[(k - kTailBase) * nb]);
+    if (MODE & 2) th = fmaf(th, xf, FH[(k - kTailBase) * nb]);
   }
+  double a = double(ta), l = double(tl), h = double(th);
+#pragma unroll
+  for (int k = HA - 1; k >= 0; --k) {
+    a = fma(a, x, CA[k * nb]);
+    if (k < HL) {
+      if (MODE & 1) l = fma(l, x, CL[k * nb]);
+      if (MODE & 2) h = fma(h, x, CH[k * nb]);
+    }
+  }
+  va = a;
+  vl = l;
+  vh = h;
 }
 
 // Row sums of one root with the block expansion (all 32 lanes): far blocks one per
@@ -1741,24 +1783,24 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
                                                        int lane, double dorg, double tau,
                                                        double& s2o, double& slo, double& sho,
                                                        unsigned& exact, unsigned& series) {
+  const float* MF = reinterpret_cast<const float*>(MP + kMrFields * nb);
   double s2 = 0.0, sl = 0.0, sh = 0.0;
   for (int b0 = 0; b0 < nb; b0 += 32) {
     const int b = b0 + lane;
     bool near = false;
     const double dm = b < nb ? (MP[b] - dorg) - tau : 1.0;  // m - lambda
     const double rb = b < nb ? MP[nb + b] : 0.0;
-    const bool far = b < nb && 3.0 * rb <= fabs(dm);
-    const int tier = series_tier(rb, fabs(dm), far);
+    const FarTest ft = far_test_bits(dm, rb, b < nb ? MP[2 * nb + b] : 0.0, b < nb);
     if (b < nb) {
-      if (far) {
-        const double t = rcp_refined(dm), u = -t;
+      if (ft.far) {
+        const double t = rcp_refined(dm), x = -rb * t;
         double va, vl = 0.0, vh = 0.0;
-        if (tier == 0)
-          rows_horner<MODE, kMrShort>(MP, nb, b, u, va, vl, vh);
-        else if (tier == 1)
-          rows_horner<MODE, kMrMid>(MP, nb, b, u, va, vl, vh);
+        if (ft.tier == 0)
+          rows_mixed<MODE, kMrShort, kMrHa0, kMrHl0>(MP, MF, nb, b, x, va, vl, vh);
+        else if (ft.tier == 1)
+          rows_mixed<MODE, kMrMid, kMrHa1, kMrHl1>(MP, MF, nb, b, x, va, vl, vh);
         else
-          rows_horner<MODE, kMrTerms>(MP, nb, b, u, va, vl, vh);
+          rows_mixed<MODE, kMrTerms, kMrHa2, kMrHl2>(MP, MF, nb, b, x, va, vl, vh);
         s2 = fma(t * t, va, s2);
         if (MODE & 1) sl = fma(t, vl, sl);
         if (MODE & 2) sh = fma(t, vh, sh);
