@@ -413,6 +413,18 @@ __device__ __forceinline__ double rcp_refined(double x) {
   return fma(r, ee, r);
 }
 
+// Reciprocal square root in about five FP64 operations: a hardware approximation
+// y0 of x^(-1/2) refined by the third-order step y = y0 (1 + e/2 + 3 e^2/8) with
+// e = 1 - x y0^2, the binomial series of (1 - e)^(-1/2) truncated after the
+// quadratic term; the relative error drops from about |e|/2 to (5/16)|e|^3 plus the
+// final rounding.  For finite x > 0 (callers keep 1 / sqrt(x) for anything else).
+__device__ __forceinline__ double rsqrt_refined(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double e = fma(-x, y * y, 1.0);
+  return fma(y, e * fma(e, 0.375, 0.5), y);
+}
+
 extern thread_local int64_t g_launches;
 
 }  // namespace tde

@@ -696,6 +696,27 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp sums of four values in six FP64 additions instead of twenty: the first
+// exchange leaves lanes 0-15 the partial sums of a, b and lanes 16-31 those of c,
+// d, the second one value per lane quarter (a, b, c, d in lanes 0-7, 8-15, 16-23,
+// 24-31), three more finish each quarter, and shuffles broadcast the totals.
+__device__ __forceinline__ void warp_sum4(double& a, double& b, double& c, double& d) {
+  const int lane = threadIdx.x & 31;
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  double x0 = hi16 ? c : a, x1 = hi16 ? d : b;
+  const double y0 = hi16 ? a : c, y1 = hi16 ? b : d;
+  x0 += __shfl_xor_sync(0xffffffffu, y0, 16);
+  x1 += __shfl_xor_sync(0xffffffffu, y1, 16);
+  double z = hi8 ? x1 : x0;
+  z += __shfl_xor_sync(0xffffffffu, hi8 ? x0 : x1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+  a = __shfl_sync(0xffffffffu, z, 0);
+  b = __shfl_sync(0xffffffffu, z, 8);
+  c = __shfl_sync(0xffffffffu, z, 16);
+  d = __shfl_sync(0xffffffffu, z, 24);
+}
+
 // the 32 lanes of a warp stride over the poles (left and right ranges separately)
 // Sum of z_i^2 / Delta_i and (z_i / Delta_i)^2 over i = b + lane, b + lane + 32, ...
 // below e, four independent chains per lane.
@@ -825,10 +846,11 @@ struct WarpSweep {
       df += fd0 + fd1;
     }
     SecSums s;
-    s.psi = warp_sum(p);
-    s.dpsi = warp_sum(dp);
-    s.phi = warp_sum(f);
-    s.dphi = warp_sum(df);
+    warp_sum4(p, dp, f, df);
+    s.psi = p;
+    s.dpsi = dp;
+    s.phi = f;
+    s.dphi = df;
     return s;
   }
 };
@@ -1318,9 +1340,12 @@ __device__ __forceinline__ void me_mul(MantExp& x, const MantExp& y) {
   me_renorm(x);
 }
 
-// num / den as one double (the result is O(1) or below: it is a z-hat square)
+// num / den as one double (the result is O(1) or below: it is a z-hat square).  A
+// renormalised mantissa lies in [1, 2) (biased exponent 1023), where the refined
+// reciprocal needs no range care; anything else takes a division.
 __device__ __forceinline__ double me_ratio(const MantExp& num, const MantExp& den) {
-  return ldexp(num.m / den.m, num.e - den.e);
+  const bool unit = ((__double2hiint(den.m) >> 20) & 0x7ff) == 1023;
+  return ldexp(unit ? num.m * rcp_refined(den.m) : num.m / den.m, num.e - den.e);
 }
 
 __device__ __forceinline__ void lowner_pair(const double* AD, const double* DORG, const double* TAU,
@@ -1330,9 +1355,9 @@ __device__ __forceinline__ void lowner_pair(const double* AD, const double* DORG
 }
 
 __device__ __forceinline__ void lowner_store(const RootArgs& a, int lo, int i, double Di, int K,
-                                             double rho, MantExp num, MantExp den,
+                                             double rhoinv, MantExp num, MantExp den,
                                              double slog = 0.0) {
-  const double last = ((a.DORG[lo + K - 1] - Di) + a.TAU[lo + K - 1]) / rho;
+  const double last = ((a.DORG[lo + K - 1] - Di) + a.TAU[lo + K - 1]) * rhoinv;
   const double z2 = me_ratio(num, den) * last * (slog != 0.0 ? exp(slog) : 1.0);
   a.ZHAT[lo + i] = copysign(sqrt(fmax(z2, 0.0)), a.AZ[lo + i]);
 }
@@ -1361,7 +1386,7 @@ __global__ void k_lowner_thread(RootArgs a) {
     for (; j < K - 1; ++j) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
     me_renorm(num);
     me_renorm(den);
-    lowner_store(a, lo, i, Di, K, ms.rho, num, den);
+    lowner_store(a, lo, i, Di, K, ms.rhoinv, num, den);
     work_add(a.st, kWorkLownerPairs, unsigned(K));
   }
 }
@@ -1558,7 +1583,7 @@ __global__ void k_lowner_warp(RootArgs a) {
       me_mul(num, pn);
       me_mul(den, pd);
     }
-    if (lane == 0) lowner_store(a, lo, i, Di, K, ms.rho, num, den, slog);
+    if (lane == 0) lowner_store(a, lo, i, Di, K, ms.rhoinv, num, den, slog);
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkLownerPairs], (unsigned long long)pairs);
   if (lane == 0 && series) atomicAdd(&a.st->work[kWorkLownerFarBlocks], (unsigned long long)series);
@@ -1642,9 +1667,11 @@ __device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* 
     if (MODE & 1) sl = fma(AL[i], t0, sl);
     if (MODE & 2) sh = fma(AH[i], t0, sh);
   }
-  s2o = warp_sum(s2 + s2b);
-  slo = (MODE & 1) ? warp_sum(sl + slb) : 0.0;
-  sho = (MODE & 2) ? warp_sum(sh + shb) : 0.0;
+  double a = s2 + s2b, l = (MODE & 1) ? sl + slb : 0.0, h = (MODE & 2) ? sh + shb : 0.0, u = 0.0;
+  warp_sum4(a, l, h, u);
+  s2o = a;
+  slo = l;
+  sho = h;
 }
 
 // Block expansion of the row sums (merges with K >= mp_min_k): with the blocks of
@@ -1823,9 +1850,11 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
       exact += unsigned(i1 - i0);
     }
   }
-  s2o = warp_sum(s2);
-  slo = (MODE & 1) ? warp_sum(sl) : 0.0;
-  sho = (MODE & 2) ? warp_sum(sh) : 0.0;
+  double l = (MODE & 1) ? sl : 0.0, h = (MODE & 2) ? sh : 0.0, u = 0.0;
+  warp_sum4(s2, l, h, u);
+  s2o = s2;
+  slo = l;
+  sho = h;
 }
 
 __global__ void k_rows_warp(RootArgs a) {
@@ -1865,7 +1894,7 @@ __global__ void k_rows_warp(RootArgs a) {
       pairs += unsigned(K);
     }
     if (lane == 0) {
-      const double inv = 1.0 / sqrt(s2);
+      const double inv = (s2 > 0.0 && s2 < 0x1p1000) ? rsqrt_refined(s2) : 1.0 / sqrt(s2);
       if (a.RINU) a.RINU[lo + j] = inv;
       a.ROWLO[lo + j] = sl * inv;
       a.ROWHI[lo + j] = sh * inv;
