@@ -50,17 +50,18 @@ FAMILIES = ("a_uniform11", "b_toeplitz", "c_wilkinson", "d_glued_wilkinson")
 # reciprocal or division each counted once.  Per (pole, root) pair summed or
 # multiplied term by term: secular sweep 1 reciprocal + 4 (Delta, z^2 t, the psi and
 # psi' sums); Lowner 1 division + 2; boundary rows 1 reciprocal + 6 (Delta, zhat t,
-# t^2, low row, high row, norm).  Per far block taken through its series (block
-# expansion of large merges): secular 58 (m - lambda 2, reciprocal 1, two 27-term
-# Horner chains 52, three to accumulate); Lowner 29 (D_i - m, reciprocal, a 27-term
-# chain 26, accumulate); boundary rows 34 per series (a 32-term chain 31, its
-# accumulate, and its share of m - lambda, the reciprocal and t^2).
-OPS = {  # stage: (ops per exact pair, pair counter, ops per series unit, series counter)
-    "secular": (5, "secular_pairs", 58, "secular_far_blocks"),
-    "lowner": (3, "lowner_pairs", 29, "lowner_far_blocks"),
-    "rows": (7, "rows_pairs", 34, "rows_far_series"),
+# t^2, low row, high row, norm).  Far blocks taken through their series (block
+# expansion of large merges) are counted on the device, per evaluation, as the FP64
+# operations they take: the FP64 Horner head of each series (its length set by the
+# block's separation tier) plus the block's distance, reciprocal, argument and
+# accumulation; the float tails of the series are not counted.
+OPS = {  # stage: (ops per exact pair, pair counter, series operations counter)
+    "secular": (5, "secular_pairs", "secular_series_ops"),
+    "lowner": (3, "lowner_pairs", "lowner_series_ops"),
+    "rows": (7, "rows_pairs", "rows_series_ops"),
 }
-OPS_PER_UNIT = {k: {"per_pair": v[0], "per_series": v[2]} for k, v in OPS.items()}
+OPS_PER_UNIT = {k: {"per_pair": v[0], "series": "FP64 operations counted on the device"}
+                for k, v in OPS.items()}
 # nominal FP64 rate of the part (1.25 TFLOP/s, an FMA counting two), in operations per
 # second with an FMA counting one: 148 SMs x 2.032 GHz x about 2.08 FMA per SM clock
 NOMINAL_FP64_OPS = 0.625e12
@@ -68,8 +69,8 @@ NOMINAL_FP64_OPS = 0.625e12
 
 def stage_ops(stage: str, work: dict) -> int:
     """Algorithmic FP64 operations of one stage from the device work counters."""
-    pp, pc, ps, sc = OPS[stage]
-    return pp * work[pc] + ps * work[sc]
+    pp, pc, sc = OPS[stage]
+    return pp * work[pc] + work[sc]
 
 
 def family_inputs(n: int):
@@ -322,7 +323,8 @@ def run_ours(args, rank: int, world: int, dist) -> None:
     # device work of one step (identical every step)
     work = {k: 0 for k in ("secular_pairs", "secular32_pairs", "lowner_pairs", "rows_pairs", "secular_sweeps",
                            "secular32_sweeps", "roots", "deflated", "rotations", "leaf_rotations",
-                           "secular_far_blocks", "lowner_far_blocks", "rows_far_series")}
+                           "secular_far_blocks", "lowner_far_blocks", "rows_far_series",
+                           "secular_series_ops", "lowner_series_ops", "rows_series_ops")}
     per_family_work = {}
     for name in FAMILIES:
         w = tde.read_work(wss[name])
@@ -374,7 +376,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
                      "frac_nominal": achieved / (NOMINAL_FP64_OPS / 1e12),
                      "algorithmic_ops_per_step": ops,
                      "units_per_step": {"exact_pairs": work[OPS[dominant][1]],
-                                        "series": work[OPS[dominant][3]]},
+                                        "series_ops": work[OPS[dominant][2]]},
                      "launches_per_step": klaunch[dominant],
                      "avg_launch_ms": ktimes[dominant] / max(klaunch[dominant], 1)})
     else:

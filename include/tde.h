@@ -234,7 +234,10 @@ int tde_profile_collect_steps(int nids, int nsteps, double* ms, int64_t* launche
  * group of up to four rows of a merge), out[14] pole blocks taken through their
  * series in FP64 secular sweeps, out[15] series evaluated for the boundary-row sums
  * (two or three per far pole block), out[16] pair blocks taken through their series in the
- * Lowner products.  n <= 17 entries are copied.  The counters are
+ * Lowner products, out[17..19] the FP64 operations of the series evaluations of
+ * the secular sweeps, Lowner products and boundary rows (each far block's FP64
+ * Horner head plus its distance, reciprocal, argument and accumulation; the
+ * float tails are not counted).  n <= 20 entries are copied.  The counters are
  * reset at the start of every compute call that uses the workspace. */
 int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
 

@@ -37,7 +37,8 @@ KERNEL_NAMES = ("plan", "scale", "leaves", "form", "deflate", "secular", "lowner
 WORK_NAMES = ("secular_pairs", "secular_sweeps", "lowner_pairs", "rows_pairs", "roots", "deflated",
               "rotations", "leaf_rotations", "sorts", "sorted_entries", "secular32_pairs",
               "secular32_sweeps", "sel_row_pairs", "sel_sweep_pairs", "secular_far_blocks",
-              "rows_far_series", "lowner_far_blocks")
+              "rows_far_series", "lowner_far_blocks", "secular_series_ops", "lowner_series_ops",
+              "rows_series_ops")
 
 
 class TdeError(RuntimeError):

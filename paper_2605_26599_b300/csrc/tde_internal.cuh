@@ -96,6 +96,9 @@ enum WorkCounter {
   kWorkRowsFarSeries,     // series evaluated for the row sums (two or three per far block:
                           // the norm and the rows the merge needs)
   kWorkLownerFarBlocks,   // pair blocks taken through their series in the Löwner products
+  kWorkSecularSeriesOps,  // FP64 operations of those series evaluations (each one's FP64
+  kWorkLownerSeriesOps,   // Horner head, its distance, reciprocal, argument and
+  kWorkRowsSeriesOps,     // accumulation), per stage
   kNumWork
 };
 

@@ -575,12 +575,13 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
 // with 35 terms the dropped part is below 3^-35 (1 + 1/3) / (1 - 1/3) < 2^-54 of the
 // block's own sum_i |z_i^2 / (D_i - lambda)|, under the rounding bound of the
 // convergence test.  A round of 32 blocks all within 1/4 of their distance stops
-// after 27 terms (4^-27 (5/3) < 2^-53), all within 1/16 after 14 (16^-14 = 2^-56).
+// after 27 terms (4^-27 (5/3) < 2^-53), all within 1/16 after 14 (16^-14 = 2^-56),
+// all within 1/64 after 10 (64^-10 = 2^-60).
 // Only the head of each series runs in FP64: from term H on, Horner's rule runs in
 // float on float copies of the same moments and enters the FP64 chain as its
 // starting value.  The float part's error, about 3 x 2^-24 |x|^H of M'_0, stays
-// below 2^-55 for the value with H = 21 / 17 / 9 (x within 1/3, 1/4, 1/16), and below
-// 2^-40 for the derivative with H = 14 / 11 / 6.  The derivative only shapes the
+// below 2^-55 for the value with H = 21 / 17 / 9 / 6 (x within 1/3, 1/4, 1/16, 1/64),
+// and below 2^-40 for the derivative with H = 14 / 11 / 6 / 4.  The derivative only shapes the
 // step and the error bound: a relative error of 2^-40 moves the last step
 // (|eta| <= 2^-18 |tau|) by under 2^-58 |tau|.
 // Every other block (the root's own and its neighbours) is summed exactly.  The
@@ -590,14 +591,19 @@ constexpr int kMpBlock = 128;  // poles per block
 constexpr int kMpTerms = 35;   // series terms (radius <= 1/3 of the distance)
 constexpr int kMpMid = 27;     // enough when radius <= 1/4 of the distance
 constexpr int kMpShort = 14;   // enough when radius <= 1/16 of the distance (16^-14 = 2^-56)
-constexpr int kHv2 = 21, kHv1 = 17, kHv0 = 9;  // FP64 heads of the value series
-constexpr int kHd2 = 14, kHd1 = 11, kHd0 = 6;  // FP64 heads of the derivative series
-constexpr int kMpFields = 3 + kHv2 + kHd2;     // m, r, 3 r, M'_k (k < 21), (k + 1) M'_k (k < 14)
+constexpr int kMpTiny = 10;    // enough when radius <= 1/64 of the distance (64^-10 = 2^-60)
+// FP64 heads of the value and derivative series, tiers 0..3 (1/64, 1/16, 1/4, 1/3)
+constexpr int kHv0 = 6, kHv1 = 9, kHv2 = 17, kHv3 = 21;
+constexpr int kHd0 = 4, kHd1 = 6, kHd2 = 11, kHd3 = 14;
+constexpr int kMpFields = 3 + kHv3 + kHd3;     // m, r, 3 r, M'_k (k < 21), (k + 1) M'_k (k < 14)
+// FP64 operations of a far block besides its heads (work counter): m - lambda 2,
+// reciprocal 1, x 1, accumulation 3 (t val, t^2, t^2 der)
+constexpr int kSecSeriesOverhead = 7;
 
 // Far test and series tier of a round of 32 blocks (warp vote over the lanes whose
 // block, of radius r at distance |dm| from the point, is far): far when 3 r <= |dm|;
-// tier 0 if all far blocks of the round are within 1/16 of their distance, 1 if
-// within 1/4, else 2.  The tests compare the bit patterns of non-negative doubles
+// tier 0 if all far blocks of the round are within 1/64 of their distance, 1 if
+// within 1/16, 2 if within 1/4, else 3.  The tests compare the bit patterns of non-negative doubles
 // (ordered like their values), so that they take no FP64 instruction: adding
 // j << 52 multiplies a normal double by 2^j; r3 is the stored 3 r.
 struct FarTest {
@@ -609,12 +615,14 @@ __device__ __forceinline__ FarTest far_test_bits(double dm, double r, double r3,
   const long long rb = __double_as_longlong(r);
   FarTest ft;
   ft.far = valid && db >= __double_as_longlong(r3);
-  if (__all_sync(0xffffffffu, !ft.far || db >= rb + (4LL << 52)))
+  if (__all_sync(0xffffffffu, !ft.far || db >= rb + (6LL << 52)))
     ft.tier = 0;
-  else if (__all_sync(0xffffffffu, !ft.far || db >= rb + (2LL << 52)))
+  else if (__all_sync(0xffffffffu, !ft.far || db >= rb + (4LL << 52)))
     ft.tier = 1;
-  else
+  else if (__all_sync(0xffffffffu, !ft.far || db >= rb + (2LL << 52)))
     ft.tier = 2;
+  else
+    ft.tier = 3;
   return ft;
 }
 
@@ -788,6 +796,7 @@ struct WarpSweep {
   const float* __restrict__ MF;
   mutable unsigned long long pairs;
   mutable unsigned blocks;
+  mutable unsigned sops;
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
     double p = 0.0, dp = 0.0, f = 0.0, df = 0.0;
     if (nb == 0) {
@@ -807,16 +816,18 @@ struct WarpSweep {
           if (ft.far) {
             const double t = rcp_refined(dm), x = -rb * t;
             const double* ca = MP + 3 * nb + b;
-            const double* cb = MP + (3 + kHv2) * nb + b;
+            const double* cb = MP + (3 + kHv3) * nb + b;
             const float* fa = MF + 3 * nb + b;
             const float* fb = MF + (3 + kMfTerms) * nb + b;
             double val, der;
             if (ft.tier == 0)
-              series_mixed<kMpShort, kHv0, kHd0>(ca, cb, fa, fb, nb, x, val, der);
+              series_mixed<kMpTiny, kHv0, kHd0>(ca, cb, fa, fb, nb, x, val, der);
             else if (ft.tier == 1)
-              series_mixed<kMpMid, kHv1, kHd1>(ca, cb, fa, fb, nb, x, val, der);
+              series_mixed<kMpShort, kHv1, kHd1>(ca, cb, fa, fb, nb, x, val, der);
+            else if (ft.tier == 2)
+              series_mixed<kMpMid, kHv2, kHd2>(ca, cb, fa, fb, nb, x, val, der);
             else
-              series_mixed<kMpTerms, kHv2, kHd2>(ca, cb, fa, fb, nb, x, val, der);
+              series_mixed<kMpTerms, kHv3, kHd3>(ca, cb, fa, fb, nb, x, val, der);
             if (dm > 0.0) {
               f = fma(t, val, f);
               df = fma(t * t, der, df);
@@ -829,7 +840,12 @@ struct WarpSweep {
           }
         }
         unsigned nm = __ballot_sync(0xffffffffu, near);
-        blocks += unsigned(min(32, nb - b0) - __popc(nm));
+        const unsigned nfar = __popc(__ballot_sync(0xffffffffu, ft.far));
+        blocks += nfar;
+        sops += nfar * unsigned(kSecSeriesOverhead + (ft.tier == 0   ? kHv0 + kHd0
+                                                      : ft.tier == 1 ? kHv1 + kHd1
+                                                      : ft.tier == 2 ? kHv2 + kHd2
+                                                                     : kHv3 + kHd3));
         while (nm) {
           const int bb = b0 + __ffs(nm) - 1;
           nm &= nm - 1;
@@ -1093,16 +1109,18 @@ __device__ __forceinline__ void secular_store(const RootArgs& a, int lo, int j, 
 
 // per-thread tallies of the device work counters, flushed once per thread
 struct SecTally {
-  unsigned long long pairs = 0;
+  unsigned long long pairs = 0, sops = 0;
   unsigned sweeps = 0, pairs32 = 0, sweeps32 = 0, roots = 0, blocks = 0;
   __device__ __forceinline__ void add(int n64, int n32, int K) {
-    add_counted((unsigned long long)n64 * unsigned(K), 0u, n64, n32, K);
+    add_counted((unsigned long long)n64 * unsigned(K), 0u, 0u, n64, n32, K);
   }
-  // FP64 work given as exact pole terms and block series evaluations
-  __device__ __forceinline__ void add_counted(unsigned long long exact, unsigned nblocks, int n64,
-                                              int n32, int K) {
+  // FP64 work given as exact pole terms and block series evaluations (and their
+  // FP64 operations)
+  __device__ __forceinline__ void add_counted(unsigned long long exact, unsigned nblocks,
+                                              unsigned nops, int n64, int n32, int K) {
     pairs += exact;
     blocks += nblocks;
+    sops += nops;
     sweeps += unsigned(n64);
     pairs32 += unsigned(n32) * unsigned(K);
     sweeps32 += unsigned(n32);
@@ -1112,6 +1130,7 @@ struct SecTally {
     if (!roots) return;
     atomicAdd(&st->work[kWorkSecularPairs], pairs);
     if (blocks) atomicAdd(&st->work[kWorkSecularFarBlocks], (unsigned long long)blocks);
+    if (sops) atomicAdd(&st->work[kWorkSecularSeriesOps], sops);
     atomicAdd(&st->work[kWorkSecularSweeps], (unsigned long long)sweeps);
     atomicAdd(&st->work[kWorkSecular32Pairs], (unsigned long long)pairs32);
     atomicAdd(&st->work[kWorkSecular32Sweeps], (unsigned long long)sweeps32);
@@ -1200,8 +1219,8 @@ __global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
 #pragma unroll
       for (int k = 0; k < kMfTerms; ++k)
         if (lane == (k & 31)) {
-          if (k < kHv2) MP[(3 + k) * nbb + b] = mo[k];
-          if (k < kHd2) MP[(3 + kHv2 + k) * nbb + b] = double(k + 1) * mo[k];
+          if (k < kHv3) MP[(3 + k) * nbb + b] = mo[k];
+          if (k < kHd3) MP[(3 + kHv3 + k) * nbb + b] = double(k + 1) * mo[k];
           BF[(3 + k) * nbb + b] = __double2float_rn(mo[k]);
           BF[(3 + kMfTerms + k) * nbb + b] = __double2float_rn(double(k + 1) * mo[k]);
           if (k < kMf32)
@@ -1292,7 +1311,7 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     const int j = (q & 1) ? ms.K - 1 - (q >> 1) : (q >> 1);
     const int nb = mp_blocks(ms.K, a.mp_min_k);
     const float* mf = reinterpret_cast<const float*>(a.MPD + lo + kMpFields * nb);
-    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, mf, 0ull, 0u};
+    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, mf, 0ull, 0u, 0u};
     WarpSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, nb, mf};
     int org, n32;
     double tau;
@@ -1301,7 +1320,7 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
         secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.rhoinv, ms.zsq, sw, sw32, &org, &tau, &ok,
                      &n32);
     secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
-    tally.add_counted(sw.pairs, sw.blocks, sweeps, n32, ms.K);
+    tally.add_counted(sw.pairs, sw.blocks, sw.sops, sweeps, n32, ms.K);
   }
   if (lane == 0) tally.flush(a.st);
   claim_finish_block(a.st);
@@ -1403,16 +1422,18 @@ __global__ void k_lowner_thread(RootArgs a) {
 // a_j = lambda_j - P_j and h the complete homogeneous sum, so G_k carries no
 // cancellation and |c_k| <= sum_j |a_j|; the block lies wholly on one side of D_i,
 // so P_j = D_j (left, set L) or D_{j+1} (right, set R) for all its pairs.  With 35
-// terms (27 for rounds within 1/4, 14 within 1/16) the dropped part is below 2^-53
-// of sum_j |a_j| / |D_i - m| <= 1 (absolute, in the log), and the far blocks' sum
-// enters zhat^2 through one exp.  As in the secular sweep only the first 21 / 17 / 9
-// terms run in FP64 and the rest in float (error below 2^-55 of the same bound).
+// terms (27 for rounds within 1/4, 14 within 1/16, 10 within 1/64) the dropped part
+// is below 2^-53 of sum_j |a_j| / |D_i - m| <= 1 (absolute, in the log), and the far
+// blocks' sum enters zhat^2 through one exp.  As in the secular sweep only the first
+// 21 / 17 / 9 / 6 terms run in FP64 and the rest in float (error below 2^-55 of the
+// same bound).
 // Near blocks multiply their factors directly.
 constexpr int kMlTerms = 35;   // far: radius <= 1/3 of the distance; 27 within 1/4, 14 within 1/16
-constexpr int kMlHead = kHv2;  // FP64 coefficients stored per side
+constexpr int kMlSeriesOverhead = 4;  // FP64 operations besides the head: D_i - m, 1/., x, accumulation
+constexpr int kMlHead = kHv3;  // FP64 coefficients stored per side
 constexpr int kTailBase = kHv0;  // float copies start at this term (every tier's head reaches it)
 constexpr int kMlFields = 3 + 2 * kMlHead;                // m, r, 3 r, c^L_k, c^R_k (k < 21)
-constexpr int kMlFloats = 2 * (kMlTerms - kTailBase);     // c^L_k, c^R_k (9 <= k < 35) as floats
+constexpr int kMlFloats = 2 * (kMlTerms - kTailBase);     // c^L_k, c^R_k (6 <= k < 35) as floats
 static_assert(2 * kMlFields + kMlFloats <= 2 * kMpBlock, "block data must fit the merge's rows");
 
 // One series of N terms with an FP64 head of H terms (coefficients c[k * nb]) and
@@ -1509,6 +1530,7 @@ __global__ void k_lowner_warp(RootArgs a) {
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned pairs = 0, series = 0;
+  unsigned long long sops = 0;
   for (uint32_t r = warp; r < total; r += nwarps) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
@@ -1552,18 +1574,25 @@ __global__ void k_lowner_warp(RootArgs a) {
             const float* f = MF + side * (kMlTerms - kTailBase) * nb + b;
             double val;
             if (ft.tier == 0)
-              val = series1_mixed<kMpShort, kHv0>(c, f, nb, x);
+              val = series1_mixed<kMpTiny, kHv0>(c, f, nb, x);
             else if (ft.tier == 1)
-              val = series1_mixed<kMpMid, kHv1>(c, f, nb, x);
+              val = series1_mixed<kMpShort, kHv1>(c, f, nb, x);
+            else if (ft.tier == 2)
+              val = series1_mixed<kMpMid, kHv2>(c, f, nb, x);
             else
-              val = series1_mixed<kMlTerms, kHv2>(c, f, nb, x);
+              val = series1_mixed<kMlTerms, kHv3>(c, f, nb, x);
             slog = fma(-w, val, slog);
           } else {
             near = true;
           }
         }
         unsigned nm = __ballot_sync(0xffffffffu, near);
-        series += unsigned(min(32, nb - b0) - __popc(nm));
+        const unsigned nfar = unsigned(min(32, nb - b0) - __popc(nm));
+        series += nfar;
+        sops += nfar * unsigned(kMlSeriesOverhead + (ft.tier == 0   ? kHv0
+                                                     : ft.tier == 1 ? kHv1
+                                                     : ft.tier == 2 ? kHv2
+                                                                    : kHv3));
         while (nm) {
           const int bb = b0 + __ffs(nm) - 1;
           nm &= nm - 1;
@@ -1587,6 +1616,7 @@ __global__ void k_lowner_warp(RootArgs a) {
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkLownerPairs], (unsigned long long)pairs);
   if (lane == 0 && series) atomicAdd(&a.st->work[kWorkLownerFarBlocks], (unsigned long long)series);
+  if (lane == 0 && sops) atomicAdd(&a.st->work[kWorkLownerSeriesOps], sops);
 }
 
 // ---------------------------------------------------------------------------
@@ -1681,18 +1711,19 @@ __device__ __forceinline__ void rows_warp_sweep(const double* AD, const double* 
 //   t   sum_k L_k x^k          to  sum ALO_i zhat_i / Delta_ij,  L_k = sum zhat ALO y^k,
 //   t   sum_k H_k x^k          to  sum AHI_i zhat_i / Delta_ij,  H_k = sum zhat AHI y^k,
 // y = (D_i - m) / r, with 40 terms (32 for rounds within 1/4 of their distance, 16
-// within 1/16): the dropped part stays below 2^-55 of the sum of the block's
-// |terms| for the squared kernel and below 2^-60 for the others.  The first 24 / 19
-// / 9 terms of the squared kernel and 21 / 17 / 9 of the others run in FP64, the
-// rest in float: the float part's error, about 3 (k + 1) 2^-24 |x|^k from the head's
+// within 1/16, 10 within 1/64): the dropped part stays below 2^-55 of the sum of the
+// block's |terms| for the squared kernel and below 2^-60 for the others.  The first
+// 24 / 19 / 9 / 6 terms of the squared kernel and 21 / 17 / 9 / 6 of the others run
+// in FP64, the rest in float: the float part's error, about 3 (k + 1) 2^-24 |x|^k from the head's
 // end k on, stays below 2^-55 of the same sums.
 constexpr int kMrTerms = 40;  // far: radius <= 1/3 of the distance
 constexpr int kMrMid = 32;    // radius <= 1/4
 constexpr int kMrShort = 16;  // radius <= 1/16 of the distance: 17 x 16^-16 < 2^-59
-constexpr int kMrHa2 = 24, kMrHa1 = 19, kMrHa0 = 9;  // FP64 heads of the squared kernel
-constexpr int kMrHl2 = kHv2, kMrHl1 = kHv1, kMrHl0 = kHv0;  // and of the two row kernels
-constexpr int kMrFields = 3 + kMrHa2 + 2 * kMrHl2;  // m, r, 3 r, (k + 1) A_k, L_k, H_k (heads)
-constexpr int kMrTail = kMrTerms - kTailBase;       // float terms per kernel (9 <= k < 40)
+constexpr int kMrTiny = 10;   // radius <= 1/64 of the distance: 11 x 64^-10 < 2^-56
+constexpr int kMrHa0 = 6, kMrHa1 = 9, kMrHa2 = 19, kMrHa3 = 24;  // FP64 heads of the squared kernel
+constexpr int kMrHl0 = kHv0, kMrHl1 = kHv1, kMrHl2 = kHv2, kMrHl3 = kHv3;  // and of the two rows
+constexpr int kMrFields = 3 + kMrHa3 + 2 * kMrHl3;  // m, r, 3 r, (k + 1) A_k, L_k, H_k (heads)
+constexpr int kMrTail = kMrTerms - kTailBase;       // float terms per kernel (6 <= k < 40)
 static_assert(2 * kMrFields + 3 * kMrTail <= 2 * kMpBlock, "block data must fit the merge's rows");
 
 // Moments of the row sums, one warp per block (found as in k_block_moments).
@@ -1748,8 +1779,8 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
             pw *= y;
           }
         }
-        const int head = which == 0 ? kMrHa2 : kMrHl2;
-        const int off = which == 0 ? 0 : kMrHa2 + (which - 1) * kMrHl2;
+        const int head = which == 0 ? kMrHa3 : kMrHl3;
+        const int off = which == 0 ? 0 : kMrHa3 + (which - 1) * kMrHl3;
 #pragma unroll
         for (int k = 0; k < kMrTerms; ++k) {
           const double v0 = warp_sum(mo[k]);
@@ -1772,8 +1803,8 @@ __device__ __forceinline__ void rows_mixed(const double* __restrict__ MP,
                                            double& va, double& vl, double& vh) {
   static_assert(HL <= HA && HL >= kTailBase && HA < N, "heads inside the series");
   const double* CA = MP + 3 * nb + b;
-  const double* CL = MP + (3 + kMrHa2) * nb + b;
-  const double* CH = MP + (3 + kMrHa2 + kMrHl2) * nb + b;
+  const double* CL = MP + (3 + kMrHa3) * nb + b;
+  const double* CH = MP + (3 + kMrHa3 + kMrHl3) * nb + b;
   const float* FA = MF + b;
   const float* FL = MF + kMrTail * nb + b;
   const float* FH = MF + 2 * kMrTail * nb + b;
@@ -1809,7 +1840,8 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
                                                        int nb, const double* __restrict__ MP,
                                                        int lane, double dorg, double tau,
                                                        double& s2o, double& slo, double& sho,
-                                                       unsigned& exact, unsigned& series) {
+                                                       unsigned& exact, unsigned& series,
+                                                       unsigned long long& sops) {
   const float* MF = reinterpret_cast<const float*>(MP + kMrFields * nb);
   double s2 = 0.0, sl = 0.0, sh = 0.0;
   for (int b0 = 0; b0 < nb; b0 += 32) {
@@ -1823,11 +1855,13 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
         const double t = rcp_refined(dm), x = -rb * t;
         double va, vl = 0.0, vh = 0.0;
         if (ft.tier == 0)
-          rows_mixed<MODE, kMrShort, kMrHa0, kMrHl0>(MP, MF, nb, b, x, va, vl, vh);
+          rows_mixed<MODE, kMrTiny, kMrHa0, kMrHl0>(MP, MF, nb, b, x, va, vl, vh);
         else if (ft.tier == 1)
-          rows_mixed<MODE, kMrMid, kMrHa1, kMrHl1>(MP, MF, nb, b, x, va, vl, vh);
+          rows_mixed<MODE, kMrShort, kMrHa1, kMrHl1>(MP, MF, nb, b, x, va, vl, vh);
+        else if (ft.tier == 2)
+          rows_mixed<MODE, kMrMid, kMrHa2, kMrHl2>(MP, MF, nb, b, x, va, vl, vh);
         else
-          rows_mixed<MODE, kMrTerms, kMrHa2, kMrHl2>(MP, MF, nb, b, x, va, vl, vh);
+          rows_mixed<MODE, kMrTerms, kMrHa3, kMrHl3>(MP, MF, nb, b, x, va, vl, vh);
         s2 = fma(t * t, va, s2);
         if (MODE & 1) sl = fma(t, vl, sl);
         if (MODE & 2) sh = fma(t, vh, sh);
@@ -1836,7 +1870,12 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
       }
     }
     unsigned nm = __ballot_sync(0xffffffffu, near);
-    series += unsigned(min(32, nb - b0) - __popc(nm)) * (MODE == 3 ? 3u : 2u);  // chains
+    const unsigned nfar = unsigned(min(32, nb - b0) - __popc(nm)), chains = MODE == 3 ? 3u : 2u;
+    series += nfar * chains;
+    const unsigned ha = ft.tier == 0 ? kMrHa0 : ft.tier == 1 ? kMrHa1 : ft.tier == 2 ? kMrHa2 : kMrHa3;
+    const unsigned hl = ft.tier == 0 ? kMrHl0 : ft.tier == 1 ? kMrHl1 : ft.tier == 2 ? kMrHl2 : kMrHl3;
+    // heads, then m - lambda 2, reciprocal 1, x 1, t^2 1 and one accumulation per chain
+    sops += nfar * (ha + (chains - 1) * hl + 5 + chains);
     while (nm) {
       const int bb = b0 + __ffs(nm) - 1;
       nm &= nm - 1;
@@ -1863,6 +1902,7 @@ __global__ void k_rows_warp(RootArgs a) {
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   unsigned pairs = 0, series = 0;
+  unsigned long long sops = 0;
   for (uint32_t r = warp; r < total; r += nwarps) {
     int rl;
     const int g = warp_list_merge(a, r, &rl);
@@ -1881,9 +1921,9 @@ __global__ void k_rows_warp(RootArgs a) {
     if (nb > 0) {
       const double* MP = a.MPR + lo;
       switch (rows_mode(a, m)) {
-        case 1: rows_warp_sweep_blocks<1>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series); break;
-        case 2: rows_warp_sweep_blocks<2>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series); break;
-        default: rows_warp_sweep_blocks<3>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series); break;
+        case 1: rows_warp_sweep_blocks<1>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series, sops); break;
+        case 2: rows_warp_sweep_blocks<2>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series, sops); break;
+        default: rows_warp_sweep_blocks<3>(AD, ZH, AL, AH, K, nb, MP, lane, dorg, tau, s2, sl, sh, pairs, series, sops); break;
       }
     } else {
       switch (rows_mode(a, m)) {
@@ -1902,6 +1942,7 @@ __global__ void k_rows_warp(RootArgs a) {
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkRowsPairs], (unsigned long long)pairs);
   if (lane == 0 && series) atomicAdd(&a.st->work[kWorkRowsFarSeries], (unsigned long long)series);
+  if (lane == 0 && sops) atomicAdd(&a.st->work[kWorkRowsSeriesOps], sops);
 }
 
 // Restores the saved roots of one step: tau, D_org and lambda = D_org + tau (the

@@ -106,6 +106,13 @@ def test_expansion_counts_and_default(tde):
         tde.set_multipole(prev)
     assert work["secular_far_blocks"] > 0 and work_exact["secular_far_blocks"] == 0
     assert work["secular_pairs"] < work_exact["secular_pairs"]
+    # FP64 operations per far-block evaluation: the overhead plus the tier's heads
+    # (secular 7 + 10 .. 35, Lowner 4 + 6 .. 21, rows 5 + chains + heads)
+    fb, lb = work["secular_far_blocks"], work["lowner_far_blocks"]
+    assert 17 * fb <= work["secular_series_ops"] <= 42 * fb
+    assert lb > 0 and 10 * lb <= work["lowner_series_ops"] <= 25 * lb
+    assert work["rows_series_ops"] > 0 and work_exact["rows_series_ops"] == 0
+    assert work_exact["secular_series_ops"] == work_exact["lowner_series_ops"] == 0
     assert np.abs(lam - lam_exact).max() <= 16 * EPS * oracle.norm1(d, e)
 
 
