@@ -725,6 +725,53 @@ __device__ __forceinline__ void warp_sum4(double& a, double& b, double& c, doubl
   d = __shfl_sync(0xffffffffu, z, 24);
 }
 
+// Warp sums of V values per lane by recursive halving: at each exchange (lane
+// offsets 16, 8, 4, 2, 1) a lane keeps the upper or lower half of its list (an odd
+// list gains a zero) and adds its partner's copy of that half, so the five
+// exchanges take about V FP64 additions instead of 5 V.  Afterwards v[j], j <
+// warp_halved_len(V), holds the total of entry halving_index<V>(lane, j), or
+// padding where that is -1.
+__host__ __device__ constexpr int halved(int L) { return (L + 1) / 2; }
+__host__ __device__ constexpr int warp_halved_len(int V) { return halved(halved(halved(halved(halved(V))))); }
+
+template <int L, int V>
+__device__ __forceinline__ void halve_step(double (&v)[V], int o, bool up) {
+  constexpr int H = halved(L);
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const double lo = v[j];
+    const double hi = (j + H < L) ? v[j + H] : 0.0;
+    v[j] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, o);
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void warp_sum_halving(double (&v)[V], int lane) {
+  constexpr int L1 = halved(V), L2 = halved(L1), L3 = halved(L2), L4 = halved(L3);
+  halve_step<V>(v, 16, lane & 16);
+  halve_step<L1>(v, 8, lane & 8);
+  halve_step<L2>(v, 4, lane & 4);
+  halve_step<L3>(v, 2, lane & 2);
+  halve_step<L4>(v, 1, lane & 1);
+}
+
+// Entry held in slot j after warp_sum_halving: undo the exchanges from the last
+// one, adding the kept half's offset; a slot that was padding at any exchange is -1.
+template <int V>
+__device__ __forceinline__ int halving_index(int lane, int j) {
+  constexpr int L1 = halved(V), L2 = halved(L1), L3 = halved(L2), L4 = halved(L3), L5 = halved(L4);
+  int k = j + ((lane & 1) ? L5 : 0);
+  if (k >= L4) return -1;
+  k += (lane & 2) ? L4 : 0;
+  if (k >= L3) return -1;
+  k += (lane & 4) ? L3 : 0;
+  if (k >= L2) return -1;
+  k += (lane & 8) ? L2 : 0;
+  if (k >= L1) return -1;
+  k += (lane & 16) ? L1 : 0;
+  return k < V ? k : -1;
+}
+
 // the 32 lanes of a warp stride over the poles (left and right ranges separately)
 // Sum of z_i^2 / Delta_i and (z_i / Delta_i)^2 over i = b + lane, b + lane + 32, ...
 // below e, four independent chains per lane.
@@ -881,6 +928,30 @@ __device__ __forceinline__ T group_sum(T v, unsigned mask) {
   return v;
 }
 
+// Group sums of four values (G >= 4 lanes): the first exchange leaves the lower
+// half of the group the partial sums of a, b and the upper half those of c, d, the
+// second one value per quarter, the rest finish each quarter, and shuffles within
+// the group broadcast the totals (3 FP64 additions for G = 4 instead of 8).
+template <int G>
+__device__ __forceinline__ void group_sum4(double& a, double& b, double& c, double& d,
+                                           unsigned mask) {
+  static_assert(G >= 4 && G <= 32, "four quarters");
+  const int gl = threadIdx.x & (G - 1);
+  const bool h = gl & (G / 2), q = gl & (G / 4);
+  double x0 = h ? c : a, x1 = h ? d : b;
+  const double y0 = h ? a : c, y1 = h ? b : d;
+  x0 += __shfl_xor_sync(mask, y0, G / 2);
+  x1 += __shfl_xor_sync(mask, y1, G / 2);
+  double z = q ? x1 : x0;
+  z += __shfl_xor_sync(mask, q ? x0 : x1, G / 4);
+#pragma unroll
+  for (int o = G / 8; o > 0; o >>= 1) z += __shfl_xor_sync(mask, z, o);
+  a = __shfl_sync(mask, z, 0, G);
+  b = __shfl_sync(mask, z, G / 4, G);
+  c = __shfl_sync(mask, z, G / 2, G);
+  d = __shfl_sync(mask, z, 3 * G / 4, G);
+}
+
 template <int G>
 __device__ __forceinline__ void group_lane_sums(const double* __restrict__ D,
                                                 const double* __restrict__ Z, int b, int e, int gl,
@@ -917,11 +988,12 @@ struct GroupSweep {
     double p, dp, f, df;
     group_lane_sums<G>(D, Z, 0, jl + 1, gl, dorg, tau, p, dp);
     group_lane_sums<G>(D, Z, jl + 1, K, gl, dorg, tau, f, df);
+    group_sum4<G>(p, dp, f, df, mask);
     SecSums s;
-    s.psi = group_sum<G>(p, mask);
-    s.dpsi = group_sum<G>(dp, mask);
-    s.phi = group_sum<G>(f, mask);
-    s.dphi = group_sum<G>(df, mask);
+    s.psi = p;
+    s.dpsi = dp;
+    s.phi = f;
+    s.dphi = df;
     return s;
   }
 };
@@ -1202,8 +1274,7 @@ __global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
           pn *= y;
         }
       }
-#pragma unroll
-      for (int k = 0; k < kMfTerms; ++k) mo[k] = warp_sum(mo[k]);
+      warp_sum_halving(mo, lane);
       double* MP = a.MPD + lo;
       float* BF = reinterpret_cast<float*>(MP + kMpFields * nbb);
       if (lane == 0) {
@@ -1217,16 +1288,18 @@ __global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
         BF[2 * nbb + b] = __double2float_rn(rad);
       }
 #pragma unroll
-      for (int k = 0; k < kMfTerms; ++k)
-        if (lane == (k & 31)) {
-          if (k < kHv3) MP[(3 + k) * nbb + b] = mo[k];
-          if (k < kHd3) MP[(3 + kHv3 + k) * nbb + b] = double(k + 1) * mo[k];
-          BF[(3 + k) * nbb + b] = __double2float_rn(mo[k]);
-          BF[(3 + kMfTerms + k) * nbb + b] = __double2float_rn(double(k + 1) * mo[k]);
+      for (int jj = 0; jj < warp_halved_len(kMfTerms); ++jj) {
+        const int k = halving_index<kMfTerms>(lane, jj);
+        if (k >= 0) {
+          const double m0 = mo[jj], m1 = double(k + 1) * m0;
+          if (k < kHv3) MP[(3 + k) * nbb + b] = m0;
+          if (k < kHd3) MP[(3 + kHv3 + k) * nbb + b] = m1;
+          BF[(3 + k) * nbb + b] = __double2float_rn(m0);
+          BF[(3 + kMfTerms + k) * nbb + b] = __double2float_rn(m1);
           if (k < kMf32)
-            BF[(3 + 2 * kMfTerms + k) * nbb + b] =
-                __double2float_rn(0.5 * double((k + 1) * (k + 2)) * mo[k]);
+            BF[(3 + 2 * kMfTerms + k) * nbb + b] = __double2float_rn(0.5 * double(k + 2) * m1);
         }
+      }
     }
   }
 }
@@ -1510,10 +1583,12 @@ __global__ void __launch_bounds__(128) k_lowner_moments(RootArgs a) {
             h = fma(u, h, vk);
           }
         }
+        warp_sum_halving(gk, lane);
 #pragma unroll
-        for (int k = 0; k < kMlTerms; ++k) {
-          const double c = warp_sum(gk[k]) / double(k + 1);
-          if (lane == (k & 31)) {
+        for (int jj = 0; jj < warp_halved_len(kMlTerms); ++jj) {
+          const int k = halving_index<kMlTerms>(lane, jj);
+          if (k >= 0) {
+            const double c = gk[jj] / double(k + 1);
             if (k < kMlHead) MP[(3 + side * kMlHead + k) * nbb + b] = c;
             if (k >= kTailBase)
               MF[(side * (kMlTerms - kTailBase) + k - kTailBase) * nbb + b] = __double2float_rn(c);
@@ -1781,11 +1856,12 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
         }
         const int head = which == 0 ? kMrHa3 : kMrHl3;
         const int off = which == 0 ? 0 : kMrHa3 + (which - 1) * kMrHl3;
+        warp_sum_halving(mo, lane);
 #pragma unroll
-        for (int k = 0; k < kMrTerms; ++k) {
-          const double v0 = warp_sum(mo[k]);
-          const double v = which == 0 ? double(k + 1) * v0 : v0;
-          if (lane == (k & 31)) {
+        for (int jj = 0; jj < warp_halved_len(kMrTerms); ++jj) {
+          const int k = halving_index<kMrTerms>(lane, jj);
+          if (k >= 0) {
+            const double v = which == 0 ? double(k + 1) * mo[jj] : mo[jj];
             if (k < head) MP[(3 + off + k) * nbb + b] = v;
             if (k >= kTailBase) MF[(which * kMrTail + k - kTailBase) * nbb + b] = __double2float_rn(v);
           }
