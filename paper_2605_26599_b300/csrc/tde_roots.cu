@@ -267,7 +267,7 @@ __device__ __forceinline__ int sec_step(SecState& q, double hw, bool third) {
 }
 
 constexpr int kMaxSweeps = 64;
-constexpr int kMaxSweeps32 = 6;
+constexpr int kMaxSweeps32 = 16;
 
 // Single-precision stage for root j, all of it in float, as steps that a driver
 // interleaves with its sweeps (`sw32(org, jl, tau, inv)` evaluates the sums):
@@ -279,8 +279,11 @@ constexpr int kMaxSweeps32 = 6;
 //               resolution, no move, non-finite)
 //   s32_after   after the sweep at the new point: stop below 2^-10 |tau| or at
 //               kMaxSweeps32 sweeps
-//   s32_finish  on success fills q for the FP64 stage (origin, tau, the whole
-//               interval as bracket) and *hw with w''/2 at tau
+//   s32_finish  for a finite w and tau inside the interval fills q for the FP64
+//               stage (origin, tau, the whole interval as bracket) and *hw with
+//               w''/2 at tau; *hw_ok is false where w''/2 overflowed the float range
+//               (a root within about 2^-40 S of its origin), and the FP64 stage
+//               then starts from tau with the two-term model
 // The stage works in units of S, the power of two at or below the root's interval
 // width (offsets and tau divided by S, w and its sums multiplied by S, so the
 // derivative sums of poles closer than 2^-40 stay inside the float range); inv is
@@ -403,9 +406,10 @@ __device__ __forceinline__ double hw_at(const Sweep32& sw32, const Stage32& st, 
 }
 
 __device__ __forceinline__ bool s32_finish(const double* D, const double* Z, double rhoinv,
-                                           const Stage32& st, SecState& q, double* hw) {
-  if (!(isfinite(st.rhoinv + st.s.psi + st.s.phi) && isfinite(st.s.hw) && st.tau > st.lo_int &&
-        st.tau < st.hi_int))
+                                           const Stage32& st, SecState& q, double* hw,
+                                           bool* hw_ok) {
+  *hw_ok = isfinite(st.s.hw);  // overflows for a root within ~2^-40 S of its origin
+  if (!(isfinite(st.rhoinv + st.s.psi + st.s.phi) && st.tau > st.lo_int && st.tau < st.hi_int))
     return false;
   q.org = st.org;
   q.jl = st.jl;
@@ -440,7 +444,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
   SecState q;
   double hw = 0.0;
   Stage32 st;
-  bool third = false;
+  bool third = false, handed = false;
   if (s32_begin(D, K, j, rho, rhoinv, zsq, sw32, st)) {
     st.s = sw32(st.org, st.jl, st.tau, st.inv);
     s32_first(D, K, j, st);
@@ -453,9 +457,11 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
       if (!st.live) break;
     }
     *n32 = st.sweeps;
-    third = s32_finish(D, Z, rhoinv, st, q, &hw);
+    bool hw_ok;
+    handed = s32_finish(D, Z, rhoinv, st, q, &hw, &hw_ok);
+    third = handed && hw_ok;
   }
-  if (third) {
+  if (handed) {
     q.s = sweep(q.dorg, q.tau, q.jl);
     q.w = q.rhoinv + q.s.psi + q.s.phi;
   } else {
@@ -518,15 +524,17 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
   q.org = 0;
   q.tau = 0.0;
   double hw = 0.0;
-  bool third = false;
+  bool third = false, handed = false;
   if (in32) {
     *n32 = st.sweeps;
-    third = s32_finish(D, Z, rhoinv, st, q, &hw);
+    bool hw_ok;
+    handed = s32_finish(D, Z, rhoinv, st, q, &hw, &hw_ok);
+    third = handed && hw_ok;
   }
-  if (act && !third) sec_init_point(D, K, j, rho, rhoinv, zsq, q);
+  if (act && !handed) sec_init_point(D, K, j, rho, rhoinv, zsq, q);
   if (act) q.s = sweep(q.dorg, q.tau, q.jl);
   if (act) {
-    if (third)
+    if (handed)
       q.w = q.rhoinv + q.s.psi + q.s.phi;
     else
       sec_init_finish(D, Z, K, j, rho, zsq, q);
