@@ -267,7 +267,7 @@ __device__ __forceinline__ int sec_step(SecState& q, double hw, bool third) {
 }
 
 constexpr int kMaxSweeps = 64;
-constexpr int kMaxSweeps32 = 16;
+constexpr int kMaxSweeps32 = 24;
 
 // Single-precision stage for root j, all of it in float, as steps that a driver
 // interleaves with its sweeps (`sw32(org, jl, tau, inv)` evaluates the sums):
