@@ -203,6 +203,14 @@ int tde_plan_query(int64_t batch, const int64_t* offsets_host, int32_t leaf, int
  * arrays, on `stream`.  Exposed so tests can compare it with IEEE 1/x. */
 int tde_check_reciprocal(int64_t n, const double* x, double* out, void* stream);
 
+/* Applies the solver's device reciprocal square root (a hardware approximation y0
+ * of x^(-1/2) refined by the third-order step y0 (1 + e/2 + 3 e^2/8),
+ * e = 1 - x y0^2; used for the boundary-row normalisation) to x[0..n) -> out[0..n),
+ * device arrays, on `stream`.  Defined for finite x > 0.  Exposed so tests can
+ * compare it with CUDA's rsqrt and with IEEE 1/sqrt(x).  TDE_EINVAL for n < 0 or
+ * null arrays with n > 0. */
+int tde_check_rsqrt(int64_t n, const double* x, double* out, void* stream);
+
 /* Number of kernel launches the last compute call on this thread enqueued. */
 int64_t tde_last_launch_count(void);
 

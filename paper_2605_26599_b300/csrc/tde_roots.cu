@@ -2134,7 +2134,22 @@ __global__ void k_check_reciprocal(int64_t n, const double* __restrict__ x, doub
     out[i] = rcp_refined(x[i]);
 }
 
+__global__ void k_check_rsqrt(int64_t n, const double* __restrict__ x, double* out) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    out[i] = rsqrt_refined(x[i]);
+}
+
 }  // namespace tde
+
+extern "C" int tde_check_rsqrt(int64_t n, const double* x, double* out, void* stream) {
+  using namespace tde;
+  if (n < 0 || (n > 0 && (x == nullptr || out == nullptr))) return TDE_EINVAL;
+  if (n == 0) return TDE_OK;
+  const int grid = int(std::min<int64_t>((n + 255) / 256, 148 * 8));
+  k_check_rsqrt<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(n, x, out);
+  return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
+}
 
 extern "C" int tde_check_reciprocal(int64_t n, const double* x, double* out, void* stream) {
   using namespace tde;

@@ -40,3 +40,24 @@ def test_refined_reciprocal_matches_ieee_division(lib):
     rel = np.abs(got - ref) / np.abs(ref)
     # within one unit in the last place of IEEE 1/x
     assert rel.max() <= 2 * EPS, rel.max()
+
+
+def test_refined_rsqrt_matches_cuda_and_ieee(lib):
+    import torch
+
+    rng = np.random.default_rng(1)
+    mant = rng.uniform(1.0, 4.0, 200000)
+    expo = rng.integers(-400, 400, 200000)
+    x = np.ldexp(mant, expo)
+    x = np.concatenate([x, [1.0, 2.0, 3.0, 0.25, 1e-300, 1e300, 1.0 - 2 ** -52, 1.0 + 2 ** -52]])
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    rc = lib.tde_check_rsqrt(x.shape[0], ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    got = out.cpu().numpy()
+    ieee = 1.0 / np.sqrt(x)                  # correctly rounded sqrt, then division
+    cuda = torch.rsqrt(xt).cpu().numpy()     # CUDA's own reciprocal square root
+    assert (np.abs(got - ieee) / ieee).max() <= 2 * EPS
+    assert (np.abs(got - cuda) / cuda).max() <= 2 * EPS
+    assert lib.tde_check_rsqrt(-1, None, None, None) == -1
