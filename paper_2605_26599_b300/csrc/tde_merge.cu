@@ -229,69 +229,81 @@ __device__ void run_boundaries(int S, const int32_t* surv, const double* D, cons
 // Tiles of kTile are sorted in shared memory (bitonic), then merged pairwise.
 // Returns a pointer to the buffer (A or B) holding the result.
 constexpr int kTile = 1024;
-__device__ int block_sort(int n, unsigned long long* KA, int32_t* IA, unsigned long long* KB,
-                          int32_t* IB, unsigned long long* skey, int32_t* sidx) {
-  for (int t0 = 0; t0 < n; t0 += kTile) {
-    int len = min(kTile, n - t0);
-    int p2 = 1;
-    while (p2 < len) p2 <<= 1;
-    for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-      skey[i] = (i < len) ? KA[t0 + i] : ~0ull;
-      sidx[i] = (i < len) ? IA[t0 + i] : -1;
-    }
-    __syncthreads();
-    for (int size = 2; size <= p2; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-          int j = i ^ stride;
-          if (j > i) {
-            bool up = (i & size) == 0;
-            unsigned long long ki = skey[i], kj = skey[j];
-            if ((ki > kj) == up) {
-              skey[i] = kj;
-              skey[j] = ki;
-              int32_t x = sidx[i];
-              sidx[i] = sidx[j];
-              sidx[j] = x;
-            }
+
+// Bitonic sort of one tile [t0, t0 + len) of KA / IA in shared memory, in place.
+__device__ void sort_tile(int t0, int len, unsigned long long* KA, int32_t* IA,
+                          unsigned long long* skey, int32_t* sidx) {
+  int p2 = 1;
+  while (p2 < len) p2 <<= 1;
+  for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+    skey[i] = (i < len) ? KA[t0 + i] : ~0ull;
+    sidx[i] = (i < len) ? IA[t0 + i] : -1;
+  }
+  __syncthreads();
+  for (int size = 2; size <= p2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        int j = i ^ stride;
+        if (j > i) {
+          bool up = (i & size) == 0;
+          unsigned long long ki = skey[i], kj = skey[j];
+          if ((ki > kj) == up) {
+            skey[i] = kj;
+            skey[j] = ki;
+            int32_t x = sidx[i];
+            sidx[i] = sidx[j];
+            sidx[j] = x;
           }
         }
-        __syncthreads();
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < len; i += blockDim.x) {
+    KA[t0 + i] = skey[i];
+    IA[t0 + i] = sidx[i];
+  }
+  __syncthreads();
+}
+
+// Entries [first, n) with stride `step` of one pairwise merge pass (runs of
+// `width` sorted entries in src, pairs merged into dst): each entry finds its place
+// by a binary search in its partner run (ties: the left run first).
+__device__ void merge_pass(int n, int width, int first, int step, const unsigned long long* src_k,
+                           const int32_t* src_i, unsigned long long* dst_k, int32_t* dst_i) {
+  for (int e = first; e < n; e += step) {
+    int run = e / width;
+    int run_lo = run * width;
+    int pair_lo = (run & ~1) * width;
+    int partner_lo = (run & 1) ? pair_lo : pair_lo + width;
+    int partner_len = max(0, min(width, n - partner_lo));
+    unsigned long long key = src_k[e];
+    int lo = 0, hi = partner_len;
+    if (run & 1) {  // right run: partner entries <= key come first
+      while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (src_k[partner_lo + m] <= key) lo = m + 1; else hi = m;
+      }
+    } else {  // left run: partner entries < key come first
+      while (lo < hi) {
+        int m = (lo + hi) >> 1;
+        if (src_k[partner_lo + m] < key) lo = m + 1; else hi = m;
       }
     }
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-      KA[t0 + i] = skey[i];
-      IA[t0 + i] = sidx[i];
-    }
-    __syncthreads();
+    int dst = pair_lo + (e - run_lo) + lo;
+    dst_k[dst] = key;
+    dst_i[dst] = src_i[e];
   }
+}
+
+__device__ int block_sort(int n, unsigned long long* KA, int32_t* IA, unsigned long long* KB,
+                          int32_t* IB, unsigned long long* skey, int32_t* sidx) {
+  for (int t0 = 0; t0 < n; t0 += kTile) sort_tile(t0, min(kTile, n - t0), KA, IA, skey, sidx);
   int which = 0;
   unsigned long long *src_k = KA, *dst_k = KB;
   int32_t *src_i = IA, *dst_i = IB;
   for (int width = kTile; width < n; width <<= 1) {
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-      int run = e / width;
-      int run_lo = run * width;
-      int pair_lo = (run & ~1) * width;
-      int partner_lo = (run & 1) ? pair_lo : pair_lo + width;
-      int partner_len = max(0, min(width, n - partner_lo));
-      unsigned long long key = src_k[e];
-      int lo = 0, hi = partner_len;
-      if (run & 1) {  // right run: partner entries <= key come first
-        while (lo < hi) {
-          int m = (lo + hi) >> 1;
-          if (src_k[partner_lo + m] <= key) lo = m + 1; else hi = m;
-        }
-      } else {  // left run: partner entries < key come first
-        while (lo < hi) {
-          int m = (lo + hi) >> 1;
-          if (src_k[partner_lo + m] < key) lo = m + 1; else hi = m;
-        }
-      }
-      int dst = pair_lo + (e - run_lo) + lo;
-      dst_k[dst] = key;
-      dst_i[dst] = src_i[e];
-    }
+    merge_pass(n, width, threadIdx.x, blockDim.x, src_k, src_i, dst_k, dst_i);
     __syncthreads();
     unsigned long long* tk = src_k;
     src_k = dst_k;
@@ -610,7 +622,7 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
 //     segment is needed (usually one in all);
 //   * the segmented run sums (step 4) take as carry-in the sum from the last run
 //     start in the CTAs before, from per-CTA aggregates;
-//   * the sort of rotated eigenvalues (step 6, rare) runs in CTA 0.
+//   * the sort of rotated eigenvalues (step 6) is spread over the C CTAs (cluster_sort).
 // Values a CTA publishes live in its shared memory (ClusterSlot) and are read
 // through distributed shared memory after a cluster barrier; each field is
 // written once per merge and the merge loop ends with a barrier before reuse.
@@ -625,6 +637,32 @@ struct ClusterSlot {
 // (the barrier's arrive has release and its wait acquire semantics at cluster
 // scope, which covers global memory).
 __device__ __forceinline__ void cluster_sync_mem(cg::cluster_group& cl) { cl.sync(); }
+
+// block_sort over the C CTAs of a cluster: CTA r sorts the tiles r, r + C, ... and
+// takes the entries r NT + tid, stride C NT, of every merge pass; cluster barriers
+// (which order the global writes) separate the passes.  Same passes, same result.
+__device__ int cluster_sort(cg::cluster_group& cl, int r, int C, int n, unsigned long long* KA,
+                            int32_t* IA, unsigned long long* KB, int32_t* IB,
+                            unsigned long long* skey, int32_t* sidx) {
+  for (int t0 = r * kTile; t0 < n; t0 += C * kTile) sort_tile(t0, min(kTile, n - t0), KA, IA, skey, sidx);
+  cluster_sync_mem(cl);
+  int which = 0;
+  unsigned long long *src_k = KA, *dst_k = KB;
+  int32_t *src_i = IA, *dst_i = IB;
+  for (int width = kTile; width < n; width <<= 1) {
+    merge_pass(n, width, r * int(blockDim.x) + int(threadIdx.x), C * int(blockDim.x), src_k, src_i,
+               dst_k, dst_i);
+    cluster_sync_mem(cl);
+    unsigned long long* tk = src_k;
+    src_k = dst_k;
+    dst_k = tk;
+    int32_t* ti = src_i;
+    src_i = dst_i;
+    dst_i = ti;
+    which ^= 1;
+  }
+  return which;
+}
 
 // Sum of an int field over the ranks before r and over all C ranks, computed by
 // every warp on its own (lane q reads rank q).
@@ -989,19 +1027,15 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
     int unsorted = lane < C ? cl.map_shared_rank(&slot, lane)->unsorted : 0;
     unsorted = __any_sync(0xffffffffu, unsorted != 0) ? 1 : 0;
     if (unsorted) {
-      if (r == 0) {
-        if (tid == 0) {
-          atomicAdd(&a.st->work[kWorkSorts], 1ull);
-          atomicAdd(&a.st->work[kWorkSortedEntries], (unsigned long long)FR);
-        }
-        for (int k = tid; k < FR; k += NT) a.KEYA[lo + k] = order_key(D[RPOS[k]]);
-        __syncthreads();
-        const int which =
-            block_sort(FR, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);
-        if (tid == 0) slot.which = which;
+      if (r == 0 && tid == 0) {
+        atomicAdd(&a.st->work[kWorkSorts], 1ull);
+        atomicAdd(&a.st->work[kWorkSortedEntries], (unsigned long long)FR);
       }
+      for (int k = r * NT + tid; k < FR; k += C * NT) a.KEYA[lo + k] = order_key(D[RPOS[k]]);
       cluster_sync_mem(cl);
-      if (cl.map_shared_rank(&slot, 0)->which) RPOS = a.IDXB + lo;
+      const int which =
+          cluster_sort(cl, r, C, FR, a.KEYA + lo, a.IDXA + lo, a.KEYB + lo, a.IDXB + lo, s_key, s_idx);
+      if (which) RPOS = a.IDXB + lo;
     }
 
     // 7. merge the two ascending lists after the K active poles
