@@ -684,6 +684,25 @@ __device__ __forceinline__ int mp_blocks(int K, int mp_min_k) {
   return K >= mp_min_k ? K / kMpBlock : 0;
 }
 
+// Superblocks: 32 consecutive blocks (4096 poles, the last one up to K) with the
+// same kind of data, formed in merges of at least kSbMin blocks and at most 32
+// superblocks.  A sweep first takes every superblock that is far from the point
+// through its series and skips its round of 32 blocks; the rest go block by block.
+// Their data follow the blocks' float data (field q of superblock s at [q nsb + s]).
+constexpr int kSbBlocks = 32;
+constexpr int kSbMin = 128;
+__device__ __forceinline__ int sb_count(int nb) {
+  const int nsb = (nb + kSbBlocks - 1) / kSbBlocks;
+  return (nb >= kSbMin && nsb <= 32) ? nsb : 0;
+}
+__device__ __forceinline__ double* sb_data(double* MPD_lo, int nb) {
+  return MPD_lo + kMpFields * nb + (kMfFields * nb + 1) / 2;
+}
+// per 32 blocks (4096 rows): their data and one superblock's, each at most
+// kMpFields + (kMfFields + 1) / 2 + 1 doubles
+static_assert((kSbBlocks + 1) * (kMpFields + (kMfFields + 1) / 2 + 1) <= kSbBlocks * kMpBlock,
+              "block and superblock data fit the merge's rows");
+
 // one thread evaluates all K poles
 struct ThreadSweep {
   const double* __restrict__ D;
@@ -852,6 +871,36 @@ struct WarpSweep {
   mutable unsigned long long pairs;
   mutable unsigned blocks;
   mutable unsigned sops;
+  int nsb;                         // superblocks (0: none)
+  const double* __restrict__ SP;   // their FP64 data
+  const float* __restrict__ SF;    // and float data
+  // One far block (or superblock) of data C / F with nc entries per field at lane
+  // slot b: adds its series to p, dp (left of lambda) or f, df.
+  __device__ __forceinline__ void far_series(const double* C, const float* F, int nc, int b,
+                                             double dm, double rb, int tier, double& p,
+                                             double& dp, double& f, double& df) const {
+    const double t = rcp_refined(dm), x = -rb * t;
+    const double* ca = C + 3 * nc + b;
+    const double* cb = C + (3 + kHv3) * nc + b;
+    const float* fa = F + 3 * nc + b;
+    const float* fb = F + (3 + kMfTerms) * nc + b;
+    double val, der;
+    if (tier == 0)
+      series_mixed<kMpTiny, kHv0, kHd0>(ca, cb, fa, fb, nc, x, val, der);
+    else if (tier == 1)
+      series_mixed<kMpShort, kHv1, kHd1>(ca, cb, fa, fb, nc, x, val, der);
+    else if (tier == 2)
+      series_mixed<kMpMid, kHv2, kHd2>(ca, cb, fa, fb, nc, x, val, der);
+    else
+      series_mixed<kMpTerms, kHv3, kHd3>(ca, cb, fa, fb, nc, x, val, der);
+    if (dm > 0.0) {
+      f = fma(t, val, f);
+      df = fma(t * t, der, df);
+    } else {
+      p = fma(t, val, p);
+      dp = fma(t * t, der, dp);
+    }
+  }
   __device__ __forceinline__ SecSums operator()(double dorg, double tau, int jl) const {
     double p = 0.0, dp = 0.0, f = 0.0, df = 0.0;
     if (nb == 0) {
@@ -861,39 +910,27 @@ struct WarpSweep {
     } else {
       double pa0 = 0.0, pa1 = 0.0, pd0 = 0.0, pd1 = 0.0;  // near poles left of lambda
       double fa0 = 0.0, fa1 = 0.0, fd0 = 0.0, fd1 = 0.0;  // and right of it
-      for (int b0 = 0; b0 < nb; b0 += 32) {
+      unsigned sfar = 0;  // superblocks taken whole
+      // round -1 (if any) goes over the superblocks, rounds 0, 1, ... over the blocks
+      for (int rd = nsb > 0 ? -1 : 0; rd * 32 < nb; ++rd) {
+        const bool sup = rd < 0;
+        if (!sup && ((sfar >> rd) & 1u)) continue;  // the round went through its superblock
+        const double* C = sup ? SP : MP;
+        const float* F = sup ? SF : MF;
+        const int nc = sup ? nsb : nb, b0 = sup ? 0 : rd * 32;
         const int b = b0 + lane;
         bool near = false;
-        const double dm = b < nb ? (MP[b] - dorg) - tau : 1.0;  // m - lambda
-        const double rb = b < nb ? MP[nb + b] : 0.0;
-        const FarTest ft = far_test_bits(dm, rb, b < nb ? MP[2 * nb + b] : 0.0, b < nb);
-        if (b < nb) {
+        const double dm = b < nc ? (C[b] - dorg) - tau : 1.0;  // m - lambda
+        const double rb = b < nc ? C[nc + b] : 0.0;
+        const FarTest ft = far_test_bits(dm, rb, b < nc ? C[2 * nc + b] : 0.0, b < nc);
+        if (b < nc) {
           if (ft.far) {
-            const double t = rcp_refined(dm), x = -rb * t;
-            const double* ca = MP + 3 * nb + b;
-            const double* cb = MP + (3 + kHv3) * nb + b;
-            const float* fa = MF + 3 * nb + b;
-            const float* fb = MF + (3 + kMfTerms) * nb + b;
-            double val, der;
-            if (ft.tier == 0)
-              series_mixed<kMpTiny, kHv0, kHd0>(ca, cb, fa, fb, nb, x, val, der);
-            else if (ft.tier == 1)
-              series_mixed<kMpShort, kHv1, kHd1>(ca, cb, fa, fb, nb, x, val, der);
-            else if (ft.tier == 2)
-              series_mixed<kMpMid, kHv2, kHd2>(ca, cb, fa, fb, nb, x, val, der);
-            else
-              series_mixed<kMpTerms, kHv3, kHd3>(ca, cb, fa, fb, nb, x, val, der);
-            if (dm > 0.0) {
-              f = fma(t, val, f);
-              df = fma(t * t, der, df);
-            } else {
-              p = fma(t, val, p);
-              dp = fma(t * t, der, dp);
-            }
+            far_series(C, F, nc, b, dm, rb, ft.tier, p, dp, f, df);
           } else {
-            near = true;
+            near = !sup;
           }
         }
+        if (sup) sfar = __ballot_sync(0xffffffffu, ft.far);
         unsigned nm = __ballot_sync(0xffffffffu, near);
         const unsigned nfar = __popc(__ballot_sync(0xffffffffu, ft.far));
         blocks += nfar;
@@ -1312,6 +1349,104 @@ __global__ void __launch_bounds__(128) k_block_moments(RootArgs a) {
   }
 }
 
+// Superblock data from the block data (one warp per superblock, lane = block): with
+// the superblock's centre m_S and radius R, a = (m_b - m_S) / R and c = r_b / R
+// (|a| + c <= 1), its normalised moments are the exact binomial translation
+//   M'_k = sum_b sum_{j<=k} C(k, j) a^(k-j) c^j M'^b_j,
+// summed over the blocks; each term is bounded by the block's M'_0, so the shift
+// adds no cancellation.  M'^b_j comes from the FP64 heads for j < 21 (which alone
+// make the superblock's FP64 heads) and from the float copies above.
+__global__ void __launch_bounds__(128) k_super_moments(RootArgs a) {
+  const uint32_t total = warp_list_total(a);
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  constexpr int kSbPoles = kSbBlocks * kMpBlock;
+  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
+    const uint32_t r = base + lane;
+    int g = 0, j = 0, nsb = 0, nb = 0;
+    bool head = false;
+    if (r < total) {
+      int rl;
+      g = warp_list_merge(a, r, &rl);
+      const MState ms = a.ms[g];
+      j = rl - ms.base;
+      nb = mp_blocks(ms.K, a.mp_min_k);
+      nsb = sb_count(nb);
+      head = nsb > 0 && (j % kSbPoles) == 0 && j / kSbPoles < nsb;
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int gg = __shfl_sync(0xffffffffu, g, src);
+      const int sb = __shfl_sync(0xffffffffu, j, src) / kSbPoles;
+      const int nbb = __shfl_sync(0xffffffffu, nb, src), nss = __shfl_sync(0xffffffffu, nsb, src);
+      const int lo = a.M[gg].lo, K = a.ms[gg].K;
+      const double* D = a.AD + lo;
+      const int i0 = sb * kSbPoles, i1 = (sb == nss - 1) ? K : i0 + kSbPoles;
+      const double m = 0.5 * (D[i0] + D[i1 - 1]);
+      const double rad = fmax(m - D[i0], D[i1 - 1] - m);
+      const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
+      const double* MP = a.MPD + lo;
+      const float* BF = reinterpret_cast<const float*>(MP + kMpFields * nbb);
+      double* SP = sb_data(a.MPD + lo, nbb);
+      float* SF = reinterpret_cast<float*>(SP + kMpFields * nss);
+      const int b = sb * kSbBlocks + lane;
+      double S[kMfTerms];
+#pragma unroll
+      for (int k = 0; k < kMfTerms; ++k) S[k] = 0.0;
+      if (b < nbb && b < (sb + 1) * kSbBlocks) {
+        const double av = (MP[b] - m) * rinv, cv = MP[nbb + b] * rinv;
+        double v[kMfTerms];  // c^j M'^b_j
+        double cj = 1.0;
+#pragma unroll
+        for (int q = 0; q < kMfTerms; ++q) {
+          const double mj = q < kHv3 ? MP[(3 + q) * nbb + b] : double(BF[(3 + q) * nbb + b]);
+          v[q] = cj * mj;
+          cj *= cv;
+        }
+        // P holds C(k, q) a^(k - q), q <= k (Pascal's rule, one row per k)
+        double P[kMfTerms];
+#pragma unroll
+        for (int q = 0; q < kMfTerms; ++q) P[q] = 0.0;
+        P[0] = 1.0;
+#pragma unroll
+        for (int k = 0; k < kMfTerms; ++k) {
+          if (k > 0) {
+#pragma unroll
+            for (int q = kMfTerms - 1; q >= 1; --q)
+              if (q <= k) P[q] = fma(av, P[q], P[q - 1]);
+            P[0] *= av;
+          }
+          double acc = 0.0;
+#pragma unroll
+          for (int q = 0; q < kMfTerms; ++q)
+            if (q <= k) acc = fma(P[q], v[q], acc);
+          S[k] = acc;
+        }
+      }
+      warp_sum_halving(S, lane);
+      if (lane == 0) {
+        SP[sb] = m;
+        SP[nss + sb] = rad;
+        SP[2 * nss + sb] = 3.0 * rad;
+      }
+#pragma unroll
+      for (int jj = 0; jj < warp_halved_len(kMfTerms); ++jj) {
+        const int k = halving_index<kMfTerms>(lane, jj);
+        if (k >= 0) {
+          const double m0 = S[jj], m1 = double(k + 1) * m0;
+          if (k < kHv3) SP[(3 + k) * nss + sb] = m0;
+          if (k < kHd3) SP[(3 + kHv3 + k) * nss + sb] = m1;
+          SF[(3 + k) * nss + sb] = __double2float_rn(m0);
+          SF[(3 + kMfTerms + k) * nss + sb] = __double2float_rn(m1);
+        }
+      }
+    }
+  }
+}
+
 // One thread per root.  The loop over roots advances a whole warp at a time (32
 // consecutive roots), which keeps every lane in step for the warp votes of
 // secular_root_sync.
@@ -1392,7 +1527,10 @@ __global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
     const int j = (q & 1) ? ms.K - 1 - (q >> 1) : (q >> 1);
     const int nb = mp_blocks(ms.K, a.mp_min_k);
     const float* mf = reinterpret_cast<const float*>(a.MPD + lo + kMpFields * nb);
-    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, mf, 0ull, 0u, 0u};
+    const int nsb = sb_count(nb);
+    const double* sp = sb_data(a.MPD + lo, nb);
+    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, mf, 0ull, 0u, 0u, nsb, sp,
+                 reinterpret_cast<const float*>(sp + kMpFields * nsb)};
     WarpSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, nb, mf};
     int org, n32;
     double tau;
@@ -2096,6 +2234,10 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   if (plan.step_maxsize[step] >= ra.mp_min_k) {
     k_block_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
     ++launches;
+    if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {
+      k_super_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+      ++launches;
+    }
   }
   switch (G) {
     case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;

@@ -186,3 +186,26 @@ def test_gradient_with_expansion(tde, name):
     gd, ge = gd.cpu().numpy(), ge.cpu().numpy()[: n - 1]
     assert np.max(np.abs(gd - rd)) <= 1e-8 * np.max(np.abs(rd))
     assert np.max(np.abs(ge - re_)) <= 1e-8 * np.max(np.abs(re_))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("offdiag", [-1.0, 0.25])
+def test_superblocks_toeplitz_closed_form(tde, offdiag):
+    """Toeplitz n = 65536: its top merges hold 16k-33k poles, so the secular sweeps
+    go through superblocks of 32 blocks.  Every eigenvalue against the closed form
+    d + 2 e cos(k pi / (n + 1))."""
+    import torch
+
+    n = 65536
+    d, e = inputs.toeplitz(n, 2.0, offdiag)
+    dt, et = torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda()
+    ws = tde.Workspace(tde.workspace_bytes(n, 8))
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    tde.eigvals(dt, et, leaf=8, out=out, ws=ws)
+    lam = out.cpu().numpy()
+    k = np.arange(1, n + 1)
+    exact = np.sort(2.0 + 2.0 * offdiag * np.cos(k * np.pi / (n + 1)))
+    norm = 2.0 + 2.0 * abs(offdiag)
+    assert np.abs(lam - exact).max() <= 8 * EPS * norm
+    work = tde.read_work(ws)
+    assert work["secular_far_blocks"] > 0
