@@ -690,13 +690,24 @@ __device__ __forceinline__ int mp_blocks(int K, int mp_min_k) {
 // through its series and skips its round of 32 blocks; the rest go block by block.
 // Their data follow the blocks' float data (field q of superblock s at [q nsb + s]).
 constexpr int kSbBlocks = 32;
-constexpr int kSbMin = 128;
+constexpr int kSbMin = 192;  // below, the superblock round costs about what it saves
 __device__ __forceinline__ int sb_count(int nb) {
   const int nsb = (nb + kSbBlocks - 1) / kSbBlocks;
   return (nb >= kSbMin && nsb <= 32) ? nsb : 0;
 }
 __device__ __forceinline__ double* sb_data(double* MPD_lo, int nb) {
   return MPD_lo + kMpFields * nb + (kMfFields * nb + 1) / 2;
+}
+
+// In place, v_k <- sum_{q<=k} C(k, q) a^(k-q) v_q (k < N): N - 1 passes of
+// v_j += a v_(j-1) from the top down, pass i starting at j = i (Pascal's rule).
+template <int N>
+__device__ __forceinline__ void binomial_shift(double (&v)[N], double a) {
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+#pragma unroll
+    for (int j = N - 1; j >= i; --j) v[j] = fma(a, v[j - 1], v[j]);
+  }
 }
 // per 32 blocks (4096 rows): their data and one superblock's, each at most
 // kMpFields + (kMfFields + 1) / 2 + 1 doubles
@@ -1398,33 +1409,14 @@ __global__ void __launch_bounds__(128) k_super_moments(RootArgs a) {
       for (int k = 0; k < kMfTerms; ++k) S[k] = 0.0;
       if (b < nbb && b < (sb + 1) * kSbBlocks) {
         const double av = (MP[b] - m) * rinv, cv = MP[nbb + b] * rinv;
-        double v[kMfTerms];  // c^j M'^b_j
-        double cj = 1.0;
+        double cj = 1.0;  // S_q = c^q M'^b_q, then shifted by a
 #pragma unroll
         for (int q = 0; q < kMfTerms; ++q) {
           const double mj = q < kHv3 ? MP[(3 + q) * nbb + b] : double(BF[(3 + q) * nbb + b]);
-          v[q] = cj * mj;
+          S[q] = cj * mj;
           cj *= cv;
         }
-        // P holds C(k, q) a^(k - q), q <= k (Pascal's rule, one row per k)
-        double P[kMfTerms];
-#pragma unroll
-        for (int q = 0; q < kMfTerms; ++q) P[q] = 0.0;
-        P[0] = 1.0;
-#pragma unroll
-        for (int k = 0; k < kMfTerms; ++k) {
-          if (k > 0) {
-#pragma unroll
-            for (int q = kMfTerms - 1; q >= 1; --q)
-              if (q <= k) P[q] = fma(av, P[q], P[q - 1]);
-            P[0] *= av;
-          }
-          double acc = 0.0;
-#pragma unroll
-          for (int q = 0; q < kMfTerms; ++q)
-            if (q <= k) acc = fma(P[q], v[q], acc);
-          S[k] = acc;
-        }
+        binomial_shift(S, av);
       }
       warp_sum_halving(S, lane);
       if (lane == 0) {
@@ -1654,6 +1646,12 @@ constexpr int kTailBase = kHv0;  // float copies start at this term (every tier'
 constexpr int kMlFields = 3 + 2 * kMlHead;                // m, r, 3 r, c^L_k, c^R_k (k < 21)
 constexpr int kMlFloats = 2 * (kMlTerms - kTailBase);     // c^L_k, c^R_k (6 <= k < 35) as floats
 static_assert(2 * kMlFields + kMlFloats <= 2 * kMpBlock, "block data must fit the merge's rows");
+// superblocks of pair blocks (same rule as the secular sums; data after the blocks')
+static_assert((kSbBlocks + 1) * (kMlFields + (kMlFloats + 1) / 2 + 1) <= kSbBlocks * kMpBlock,
+              "block and superblock data fit the merge's rows");
+__device__ __forceinline__ double* lowner_sb_data(double* MPR_lo, int nb) {
+  return MPR_lo + kMlFields * nb + (kMlFloats * nb + 1) / 2;
+}
 
 // One series of N terms with an FP64 head of H terms (coefficients c[k * nb]) and
 // a float tail (coefficients f[(k - kTailBase) * nb]), at x.
@@ -1745,6 +1743,84 @@ __global__ void __launch_bounds__(128) k_lowner_moments(RootArgs a) {
   }
 }
 
+// Superblock coefficients of the Löwner log sums from those of its pair blocks: with
+// a = (m_b - m_S) / R and c = r_b / R, c^S_k = sum_b sum_{q<=k} C(k, q) a^(k-q) c^q c^b_q
+// on each side (G_(k+1) translated to the new centre and rescaled; |a| + c <= 1).
+__global__ void __launch_bounds__(128) k_lowner_super(RootArgs a) {
+  const uint32_t total = warp_list_total(a);
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  constexpr int kSbPoles = kSbBlocks * kMpBlock;
+  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
+    const uint32_t r = base + lane;
+    int g = 0, j = 0, nb = 0, nsb = 0;
+    bool head = false;
+    if (r < total) {
+      int rl;
+      g = warp_list_merge(a, r, &rl);
+      const Merge mg = a.M[g];
+      const MState ms = a.ms[g];
+      j = rl - ms.base;
+      nb = ((uint32_t(mg.info) & kRootBit) && !a.all_merges) ? 0 : mp_blocks(ms.K, a.mp_min_k);
+      nsb = sb_count(nb);
+      head = nsb > 0 && (j % kSbPoles) == 0 && j / kSbPoles < nsb;
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int gg = __shfl_sync(0xffffffffu, g, src);
+      const int sb = __shfl_sync(0xffffffffu, j, src) / kSbPoles;
+      const int nbb = __shfl_sync(0xffffffffu, nb, src), nss = __shfl_sync(0xffffffffu, nsb, src);
+      const int lo = a.M[gg].lo, K = a.ms[gg].K;
+      const double* D = a.AD + lo;
+      const int j0 = sb * kSbPoles, j1 = (sb == nss - 1) ? K - 1 : j0 + kSbPoles;
+      const double m = 0.5 * (D[j0] + D[j1]);
+      const double rad = fmax(m - D[j0], D[j1] - m);
+      const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
+      const double* MP = a.MPR + lo;
+      const float* MF = reinterpret_cast<const float*>(MP + kMlFields * nbb);
+      double* SP = lowner_sb_data(a.MPR + lo, nbb);
+      float* SF = reinterpret_cast<float*>(SP + kMlFields * nss);
+      const int b = sb * kSbBlocks + lane;
+      const bool mine = b < nbb && lane < kSbBlocks;
+      if (lane == 0) {
+        SP[sb] = m;
+        SP[nss + sb] = rad;
+        SP[2 * nss + sb] = 3.0 * rad;
+      }
+      for (int side = 0; side < 2; ++side) {
+        double S[kMlTerms];
+#pragma unroll
+        for (int k = 0; k < kMlTerms; ++k) S[k] = 0.0;
+        if (mine) {
+          const double av = (MP[b] - m) * rinv, cv = MP[nbb + b] * rinv;
+          double cq = 1.0;
+#pragma unroll
+          for (int q = 0; q < kMlTerms; ++q) {
+            const double c = q < kMlHead ? MP[(3 + side * kMlHead + q) * nbb + b]
+                                         : double(MF[(side * (kMlTerms - kTailBase) + q - kTailBase) * nbb + b]);
+            S[q] = cq * c;
+            cq *= cv;
+          }
+          binomial_shift(S, av);
+        }
+        warp_sum_halving(S, lane);
+#pragma unroll
+        for (int jj = 0; jj < warp_halved_len(kMlTerms); ++jj) {
+          const int k = halving_index<kMlTerms>(lane, jj);
+          if (k >= 0) {
+            if (k < kMlHead) SP[(3 + side * kMlHead + k) * nss + sb] = S[jj];
+            if (k >= kTailBase)
+              SF[(side * (kMlTerms - kTailBase) + k - kTailBase) * nss + sb] = __double2float_rn(S[jj]);
+          }
+        }
+      }
+    }
+  }
+}
+
 __global__ void k_lowner_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
@@ -1781,7 +1857,41 @@ __global__ void k_lowner_warp(RootArgs a) {
     } else {
       const double* MP = a.MPR + lo;
       const float* MF = reinterpret_cast<const float*>(MP + kMlFields * nb);
+      const int nsb = sb_count(nb);
+      const double* SP = lowner_sb_data(a.MPR + lo, nb);
+      const float* SF = reinterpret_cast<const float*>(SP + kMlFields * nsb);
+      unsigned sfar = 0;  // superblocks taken whole (their rounds are skipped below)
+      if (nsb > 0) {
+        const int sb = lane;
+        const double dm = sb < nsb ? Di - SP[sb] : 1.0;
+        const double rb = sb < nsb ? SP[nsb + sb] : 0.0;
+        const FarTest ft = far_test_bits(dm, rb, sb < nsb ? SP[2 * nsb + sb] : 0.0, sb < nsb);
+        if (ft.far) {
+          const double w = rcp_refined(dm), x = rb * w;
+          const int side = dm < 0.0 ? 1 : 0;  // right of D_i: R
+          const double* c = SP + (3 + side * kMlHead) * nsb + sb;
+          const float* f = SF + side * (kMlTerms - kTailBase) * nsb + sb;
+          double val;
+          if (ft.tier == 0)
+            val = series1_mixed<kMpTiny, kHv0>(c, f, nsb, x);
+          else if (ft.tier == 1)
+            val = series1_mixed<kMpShort, kHv1>(c, f, nsb, x);
+          else if (ft.tier == 2)
+            val = series1_mixed<kMpMid, kHv2>(c, f, nsb, x);
+          else
+            val = series1_mixed<kMlTerms, kHv3>(c, f, nsb, x);
+          slog = fma(-w, val, slog);
+        }
+        sfar = __ballot_sync(0xffffffffu, ft.far);
+        const unsigned nfar = __popc(sfar);
+        series += nfar;
+        sops += nfar * unsigned(kMlSeriesOverhead + (ft.tier == 0   ? kHv0
+                                                     : ft.tier == 1 ? kHv1
+                                                     : ft.tier == 2 ? kHv2
+                                                                    : kHv3));
+      }
       for (int b0 = 0; b0 < nb; b0 += 32) {
+        if ((sfar >> (b0 / 32)) & 1u) continue;  // the round went through its superblock
         const int b = b0 + lane;
         bool near = false;
         const double dm = b < nb ? Di - MP[b] : 1.0;
@@ -1946,6 +2056,12 @@ constexpr int kMrHl0 = kHv0, kMrHl1 = kHv1, kMrHl2 = kHv2, kMrHl3 = kHv3;  // an
 constexpr int kMrFields = 3 + kMrHa3 + 2 * kMrHl3;  // m, r, 3 r, (k + 1) A_k, L_k, H_k (heads)
 constexpr int kMrTail = kMrTerms - kTailBase;       // float terms per kernel (6 <= k < 40)
 static_assert(2 * kMrFields + 3 * kMrTail <= 2 * kMpBlock, "block data must fit the merge's rows");
+// superblocks (same rule as the secular sums; data after the blocks')
+static_assert((kSbBlocks + 1) * (kMrFields + (3 * kMrTail + 1) / 2 + 1) <= kSbBlocks * kMpBlock,
+              "block and superblock data fit the merge's rows");
+__device__ __forceinline__ double* rows_sb_data(double* MPR_lo, int nb) {
+  return MPR_lo + kMrFields * nb + (3 * kMrTail * nb + 1) / 2;
+}
 
 // Moments of the row sums, one warp per block (found as in k_block_moments).
 __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
@@ -2017,6 +2133,86 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
   }
 }
 
+// Superblock moments of the row sums from the blocks' (binomial translation of
+// A'_k, L'_k, H'_k as for the secular moments; A is stored times k + 1).
+__global__ void __launch_bounds__(128) k_rows_super(RootArgs a) {
+  const uint32_t total = warp_list_total(a);
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  constexpr int kSbPoles = kSbBlocks * kMpBlock;
+  for (uint32_t base = gw * 32; base < total; base += nw * 32) {
+    const uint32_t r = base + lane;
+    int g = 0, j = 0, nb = 0, nsb = 0;
+    bool head = false;
+    if (r < total) {
+      int rl;
+      g = warp_list_merge(a, r, &rl);
+      const Merge mg = a.M[g];
+      const MState ms = a.ms[g];
+      j = rl - ms.base;
+      nb = ((uint32_t(mg.info) & kRootBit) && !a.all_merges) ? 0 : mp_blocks(ms.K, a.mp_min_k);
+      nsb = sb_count(nb);
+      head = nsb > 0 && (j % kSbPoles) == 0 && j / kSbPoles < nsb;
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, head);
+    while (hm) {
+      const int src = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int gg = __shfl_sync(0xffffffffu, g, src);
+      const int sb = __shfl_sync(0xffffffffu, j, src) / kSbPoles;
+      const int nbb = __shfl_sync(0xffffffffu, nb, src), nss = __shfl_sync(0xffffffffu, nsb, src);
+      const int lo = a.M[gg].lo, K = a.ms[gg].K;
+      const double* D = a.AD + lo;
+      const int i0 = sb * kSbPoles, i1 = (sb == nss - 1) ? K : i0 + kSbPoles;
+      const double m = 0.5 * (D[i0] + D[i1 - 1]);
+      const double rad = fmax(m - D[i0], D[i1 - 1] - m);
+      const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
+      const double* MP = a.MPR + lo;
+      const float* MF = reinterpret_cast<const float*>(MP + kMrFields * nbb);
+      double* SP = rows_sb_data(a.MPR + lo, nbb);
+      float* SF = reinterpret_cast<float*>(SP + kMrFields * nss);
+      const int b = sb * kSbBlocks + lane;
+      const bool mine = b < nbb && lane < kSbBlocks;
+      if (lane == 0) {
+        SP[sb] = m;
+        SP[nss + sb] = rad;
+        SP[2 * nss + sb] = 3.0 * rad;
+      }
+      for (int which = 0; which < 3; ++which) {  // A (stored times k + 1), L, H
+        const int head = which == 0 ? kMrHa3 : kMrHl3;
+        const int off = which == 0 ? 0 : kMrHa3 + (which - 1) * kMrHl3;
+        double S[kMrTerms];
+#pragma unroll
+        for (int k = 0; k < kMrTerms; ++k) S[k] = 0.0;
+        if (mine) {
+          const double av = (MP[b] - m) * rinv, cv = MP[nbb + b] * rinv;
+          double cq = 1.0;
+#pragma unroll
+          for (int q = 0; q < kMrTerms; ++q) {
+            double c = q < head ? MP[(3 + off + q) * nbb + b]
+                                : double(MF[(which * kMrTail + q - kTailBase) * nbb + b]);
+            if (which == 0) c /= double(q + 1);
+            S[q] = cq * c;
+            cq *= cv;
+          }
+          binomial_shift(S, av);
+        }
+        warp_sum_halving(S, lane);
+#pragma unroll
+        for (int jj = 0; jj < warp_halved_len(kMrTerms); ++jj) {
+          const int k = halving_index<kMrTerms>(lane, jj);
+          if (k >= 0) {
+            const double v = which == 0 ? double(k + 1) * S[jj] : S[jj];
+            if (k < head) SP[(3 + off + k) * nss + sb] = v;
+            if (k >= kTailBase) SF[(which * kMrTail + k - kTailBase) * nss + sb] = __double2float_rn(v);
+          }
+        }
+      }
+    }
+  }
+}
+
 // The row sums' series of one far block at x: N terms, FP64 heads HA (squared
 // kernel) and HL (row kernels), float tails.
 template <int MODE, int N, int HA, int HL>
@@ -2065,8 +2261,40 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
                                                        unsigned& exact, unsigned& series,
                                                        unsigned long long& sops) {
   const float* MF = reinterpret_cast<const float*>(MP + kMrFields * nb);
+  const int nsb = sb_count(nb);
+  const double* SP = rows_sb_data(const_cast<double*>(MP), nb);
+  const float* SF = reinterpret_cast<const float*>(SP + kMrFields * nsb);
   double s2 = 0.0, sl = 0.0, sh = 0.0;
+  unsigned sfar = 0;  // superblocks taken whole (their rounds are skipped below)
+  if (nsb > 0) {
+    const int sb = lane;
+    const double dm = sb < nsb ? (SP[sb] - dorg) - tau : 1.0;
+    const double rb = sb < nsb ? SP[nsb + sb] : 0.0;
+    const FarTest ft = far_test_bits(dm, rb, sb < nsb ? SP[2 * nsb + sb] : 0.0, sb < nsb);
+    if (ft.far) {
+      const double t = rcp_refined(dm), x = -rb * t;
+      double va, vl = 0.0, vh = 0.0;
+      if (ft.tier == 0)
+        rows_mixed<MODE, kMrTiny, kMrHa0, kMrHl0>(SP, SF, nsb, sb, x, va, vl, vh);
+      else if (ft.tier == 1)
+        rows_mixed<MODE, kMrShort, kMrHa1, kMrHl1>(SP, SF, nsb, sb, x, va, vl, vh);
+      else if (ft.tier == 2)
+        rows_mixed<MODE, kMrMid, kMrHa2, kMrHl2>(SP, SF, nsb, sb, x, va, vl, vh);
+      else
+        rows_mixed<MODE, kMrTerms, kMrHa3, kMrHl3>(SP, SF, nsb, sb, x, va, vl, vh);
+      s2 = fma(t * t, va, s2);
+      if (MODE & 1) sl = fma(t, vl, sl);
+      if (MODE & 2) sh = fma(t, vh, sh);
+    }
+    sfar = __ballot_sync(0xffffffffu, ft.far);
+    const unsigned nfar = __popc(sfar), chains = MODE == 3 ? 3u : 2u;
+    series += nfar * chains;
+    const unsigned ha = ft.tier == 0 ? kMrHa0 : ft.tier == 1 ? kMrHa1 : ft.tier == 2 ? kMrHa2 : kMrHa3;
+    const unsigned hl = ft.tier == 0 ? kMrHl0 : ft.tier == 1 ? kMrHl1 : ft.tier == 2 ? kMrHl2 : kMrHl3;
+    sops += nfar * (ha + (chains - 1) * hl + 5 + chains);
+  }
   for (int b0 = 0; b0 < nb; b0 += 32) {
+    if ((sfar >> (b0 / 32)) & 1u) continue;  // the round went through its superblock
     const int b = b0 + lane;
     bool near = false;
     const double dm = b < nb ? (MP[b] - dorg) - tau : 1.0;  // m - lambda
@@ -2253,6 +2481,10 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
     if (plan.step_maxsize[step] >= ra.mp_min_k) {
       k_lowner_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
       ++launches;
+      if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {
+        k_lowner_super<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+        ++launches;
+      }
     }
     k_lowner_thread<<<tgrid, 128, 0, s>>>(ra);
     k_lowner_warp<<<wgrid, 128, 0, s>>>(ra);
@@ -2261,6 +2493,10 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
     if (plan.step_maxsize[step] >= ra.mp_min_k) {
       k_rows_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
       ++launches;
+      if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {
+        k_rows_super<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+        ++launches;
+      }
     }
     k_rows_thread<<<tgrid, 128, 0, s>>>(ra);
     k_rows_warp<<<wgrid, 128, 0, s>>>(ra);
