@@ -1746,11 +1746,11 @@ __global__ void __launch_bounds__(128) k_lowner_moments(RootArgs a) {
 // Superblock coefficients of the Löwner log sums from those of its pair blocks: with
 // a = (m_b - m_S) / R and c = r_b / R, c^S_k = sum_b sum_{q<=k} C(k, q) a^(k-q) c^q c^b_q
 // on each side (G_(k+1) translated to the new centre and rescaled; |a| + c <= 1).
-__global__ void __launch_bounds__(128) k_lowner_super(RootArgs a) {
+__global__ void __launch_bounds__(64) k_lowner_super(RootArgs a) {  // 2 warps: L, R
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int side = threadIdx.x >> 5;  // the block's warps share the roots, one side each
+  const uint32_t gw = blockIdx.x, nw = gridDim.x;
   constexpr int kSbPoles = kSbBlocks * kMpBlock;
   for (uint32_t base = gw * 32; base < total; base += nw * 32) {
     const uint32_t r = base + lane;
@@ -1785,12 +1785,12 @@ __global__ void __launch_bounds__(128) k_lowner_super(RootArgs a) {
       float* SF = reinterpret_cast<float*>(SP + kMlFields * nss);
       const int b = sb * kSbBlocks + lane;
       const bool mine = b < nbb && lane < kSbBlocks;
-      if (lane == 0) {
+      if (lane == 0 && side == 0) {
         SP[sb] = m;
         SP[nss + sb] = rad;
         SP[2 * nss + sb] = 3.0 * rad;
       }
-      for (int side = 0; side < 2; ++side) {
+      {
         double S[kMlTerms];
 #pragma unroll
         for (int k = 0; k < kMlTerms; ++k) S[k] = 0.0;
@@ -2135,11 +2135,11 @@ __global__ void __launch_bounds__(128) k_rows_moments(RootArgs a) {
 
 // Superblock moments of the row sums from the blocks' (binomial translation of
 // A'_k, L'_k, H'_k as for the secular moments; A is stored times k + 1).
-__global__ void __launch_bounds__(128) k_rows_super(RootArgs a) {
+__global__ void __launch_bounds__(96) k_rows_super(RootArgs a) {  // 3 warps: A, L, H
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int which = threadIdx.x >> 5;  // the block's warps share the roots, one weight each
+  const uint32_t gw = blockIdx.x, nw = gridDim.x;
   constexpr int kSbPoles = kSbBlocks * kMpBlock;
   for (uint32_t base = gw * 32; base < total; base += nw * 32) {
     const uint32_t r = base + lane;
@@ -2174,12 +2174,12 @@ __global__ void __launch_bounds__(128) k_rows_super(RootArgs a) {
       float* SF = reinterpret_cast<float*>(SP + kMrFields * nss);
       const int b = sb * kSbBlocks + lane;
       const bool mine = b < nbb && lane < kSbBlocks;
-      if (lane == 0) {
+      if (lane == 0 && which == 0) {
         SP[sb] = m;
         SP[nss + sb] = rad;
         SP[2 * nss + sb] = 3.0 * rad;
       }
-      for (int which = 0; which < 3; ++which) {  // A (stored times k + 1), L, H
+      {  // A (stored times k + 1), L, H
         const int head = which == 0 ? kMrHa3 : kMrHl3;
         const int off = which == 0 ? 0 : kMrHa3 + (which - 1) * kMrHl3;
         double S[kMrTerms];
@@ -2192,7 +2192,7 @@ __global__ void __launch_bounds__(128) k_rows_super(RootArgs a) {
           for (int q = 0; q < kMrTerms; ++q) {
             double c = q < head ? MP[(3 + off + q) * nbb + b]
                                 : double(MF[(which * kMrTail + q - kTailBase) * nbb + b]);
-            if (which == 0) c /= double(q + 1);
+            if (which == 0) c *= 1.0 / double(q + 1);
             S[q] = cq * c;
             cq *= cv;
           }
@@ -2482,7 +2482,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
       k_lowner_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
       ++launches;
       if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {
-        k_lowner_super<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+        k_lowner_super<<<int(std::min<int64_t>((nrows + 31) / 32, 148 * 32)), 64, 0, s>>>(ra);
         ++launches;
       }
     }
@@ -2494,7 +2494,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
       k_rows_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
       ++launches;
       if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {
-        k_rows_super<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
+        k_rows_super<<<int(std::min<int64_t>((nrows + 31) / 32, 148 * 32)), 96, 0, s>>>(ra);
         ++launches;
       }
     }
