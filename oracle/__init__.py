@@ -12,6 +12,9 @@ Contents (each function cites the passage of the paper it follows):
   (``sturm.c``), the definition of the quantity the boundary-row D&C returns
   (Sec. 3.1, Eq. dc-split / merge-problem: the spectrum of T; Theorem
   "BR computes the same eigenvalues as conventional D&C").
+* ``sturm_counts`` / ``certify`` / ``certified_error`` -- the same Sturm count at
+  many points, which certifies every eigenvalue of a computed spectrum within a
+  radius from 2n counts (lambda_k >= x iff count(x) <= k).
 * ``jacobi_eigh`` -- dense cyclic Jacobi in plain C for n <= 64, an independent
   second route to the spectrum and to the eigenvector rows.
 * ``gate`` / ``e_fwd`` / ``e_bwd`` -- the acceptance bound 8 n eps ||T||_1 and the
@@ -71,6 +74,8 @@ def _load():
             lib.oracle_eigvals_bisect_select.restype = ctypes.c_int
             lib.oracle_eigvals_bisect_select.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int64,
                                                          i64p, dp]
+            lib.oracle_sturm_counts.restype = ctypes.c_int
+            lib.oracle_sturm_counts.argtypes = [ctypes.c_int64, dp, dp, ctypes.c_int64, dp, i64p]
             lib.oracle_jacobi_eigh.restype = ctypes.c_int
             lib.oracle_jacobi_eigh.argtypes = [ctypes.c_int, dp, dp, dp]
             _lib = lib
@@ -107,6 +112,57 @@ def sturm_count(d, e, x: float) -> int:
     """Number of eigenvalues of tridiag(e, d, e) strictly below x."""
     d, e, n = _prep(d, e)
     return int(_load().oracle_sturm_count(n, _dp(d), _dp(e), float(x)))
+
+
+def sturm_counts(d, e, xs) -> np.ndarray:
+    """For every query point x: the number of eigenvalues of tridiag(e, d, e) strictly
+    below x (negative LDL^T pivots of T - xI, Sylvester's law of inertia)."""
+    global last_threads
+    d, e, n = _prep(d, e)
+    xs = np.ascontiguousarray(xs, dtype=np.float64)
+    out = np.zeros(xs.shape[0], dtype=np.int64)
+    if xs.shape[0]:
+        last_threads = _load().oracle_sturm_counts(
+            n, _dp(d), _dp(e), xs.shape[0], _dp(xs), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return out
+
+
+def certify(d, e, lam_hat, radius):
+    """Certify a computed spectrum eigenvalue by eigenvalue without bisecting it.
+
+    ``lam_hat`` is ascending; ``radius`` is a scalar or one value per index.  The
+    k-th smallest eigenvalue (0-based) lambda_k of T satisfies
+    lambda_k >= lam_hat[k] - r  iff  count(lam_hat[k] - r) <= k, and
+    lambda_k <  lam_hat[k] + r  iff  count(lam_hat[k] + r) >= k + 1,
+    so ``|lam_hat[k] - lambda_k| <= r`` holds exactly where both conditions hold
+    (the definition of the spectrum, Sec. 3.1; 2n Sturm counts in all).  Returns the
+    boolean array of certified indices."""
+    lam_hat = np.asarray(lam_hat, dtype=np.float64)
+    n = lam_hat.shape[0]
+    if n != len(d):
+        raise ValueError("lam_hat must hold one value per row of T")
+    r = np.broadcast_to(np.asarray(radius, dtype=np.float64), (n,))
+    c = sturm_counts(d, e, np.concatenate([lam_hat - r, lam_hat + r]))
+    k = np.arange(n)
+    return (c[:n] <= k) & (c[n:] >= k + 1)
+
+
+def certified_error(d, e, lam_hat, gate_value, levels=(1, 8, 64, 512)):
+    """Smallest radius gate_value / L, L in ``levels`` (ascending), at which every
+    eigenvalue of ``lam_hat`` is certified by :func:`certify`; returns
+    (radius, number of indices not certified at the gate itself).  The radius is
+    an upper bound on max_k |lam_hat[k] - lambda_k| (up to the Sturm count's own
+    rounding, a few eps ||T||_1) and ``inf`` when the gate itself fails."""
+    ok = certify(d, e, lam_hat, gate_value)
+    nfail = int(np.count_nonzero(~ok))
+    if nfail:
+        return float("inf"), nfail
+    best = float(gate_value)
+    for lv in levels[1:]:
+        if not np.all(certify(d, e, lam_hat, gate_value / lv)):
+            break
+        best = float(gate_value) / lv
+    return best, 0
 
 
 def eigvals_bisect(d, e) -> np.ndarray:

@@ -21,6 +21,10 @@
  *     bracketed by the Gershgorin interval and bisected until the bracket is
  *     narrower than max(2 eps |x|, eps ||T||_1), eps = DBL_EPSILON.
  *
+ *     The same count for many query points (oracle_sturm_counts) certifies a
+ *     computed spectrum without bisecting it: lambda_k lies in [x - g, x + g)
+ *     exactly when count(x - g) <= k and count(x + g) >= k + 1.
+ *
  *  2. Dense cyclic Jacobi (oracle_jacobi_eigh) for n <= 64: a sweep of plane
  *     rotations that annihilate each off-diagonal entry in turn until the
  *     off-diagonal Frobenius mass is below 1e-30 of the total.  Returns
@@ -144,6 +148,55 @@ int oracle_eigvals_bisect_select(int64_t n, const double* d, const double* e, in
           lo = mid;
       }
       out[t] = lo + 0.5 * (hi - lo);
+    }
+  }
+  free(e2);
+  return used;
+}
+
+/* counts[t] = number of eigenvalues of T strictly below xs[t], t in [0, nx): the
+ * count of count_below for many query points (used to certify a computed
+ * spectrum: lambda_k >= x  <=>  count(x) <= k, and lambda_k < x  <=>  count(x) >= k+1).
+ * Query points are taken eight at a time so that the eight independent pivot
+ * recurrences share one pass over d and e; each recurrence performs exactly the
+ * operations of count_below, in the same order, so every count equals the
+ * single-point count bit for bit.  Returns the number of OpenMP threads used. */
+int oracle_sturm_counts(int64_t n, const double* d, const double* e, int64_t nx,
+                        const double* xs, int64_t* counts) {
+  if (nx <= 0) return 0;
+  if (n <= 0) {
+    for (int64_t t = 0; t < nx; ++t) counts[t] = 0;
+    return 1;
+  }
+  double* e2 = (double*)malloc(sizeof(double) * (size_t)(n > 1 ? n - 1 : 1));
+  for (int64_t i = 0; i + 1 < n; ++i) e2[i] = e[i] * e[i];
+  const double pivmin = pivmin_of(n, e);
+  int used = 1;
+#pragma omp parallel
+  {
+#ifdef _OPENMP
+#pragma omp single
+    used = omp_get_num_threads();
+#endif
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t t0 = 0; t0 < nx; t0 += 8) {
+      const int64_t nb = (nx - t0 < 8) ? nx - t0 : 8;
+      double x[8], q[8];
+      int64_t c[8];
+      for (int j = 0; j < 8; ++j) {
+        x[j] = xs[t0 + (j < nb ? j : nb - 1)];
+        q[j] = d[0] - x[j];
+        if (fabs(q[j]) < pivmin) q[j] = -pivmin;
+        c[j] = (q[j] < 0.0) ? 1 : 0;
+      }
+      for (int64_t i = 1; i < n; ++i) {
+        for (int j = 0; j < 8; ++j) {
+          q[j] = (d[i] - x[j]) - e2[i - 1] / q[j];
+          if (fabs(q[j]) < pivmin) q[j] = -pivmin;
+          c[j] += (q[j] < 0.0) ? 1 : 0;
+        }
+      }
+      for (int64_t j = 0; j < nb; ++j) counts[t0 + j] = c[j];
     }
   }
   free(e2);

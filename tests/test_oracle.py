@@ -269,3 +269,101 @@ def test_paper_workspace_formulas_match_printed_values(oracle_mod):
         assert got == pytest.approx(float(internal), rel=0.01)
     # Sec. 5.3: D/E plus BR workspace is about 172 N bytes
     assert oracle_mod.paper_workspace_bytes(1 << 16)["br_with_de"] == 172 * (1 << 16)
+
+
+# ---- Sturm counts at many points and the certification built on them ----------
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 300])
+@pytest.mark.parametrize("ab", [(2.0, -1.0), (-0.3, 1.7)])
+def test_sturm_counts_toeplitz_closed_form(oracle_mod, n, ab):
+    # count(x) = #{k : a + 2b cos(k pi/(n+1)) < x}, from the closed-form spectrum
+    a, b = ab
+    d, e = inputs.toeplitz(n, a, b)
+    ref = toeplitz_spectrum(n, a, b)
+    rng = np.random.default_rng(n)
+    xs = np.concatenate([rng.uniform(ref[0] - 1, ref[-1] + 1, 200),
+                         0.5 * (ref[:-1] + ref[1:]), [ref[0] - 5.0, ref[-1] + 5.0]])
+    # keep query points clear of the eigenvalues by far more than the count's rounding
+    xs = xs[np.min(np.abs(xs[:, None] - ref[None, :]), axis=1) > 1e-9]
+    got = oracle_mod.sturm_counts(d, e, xs)
+    want = np.searchsorted(ref, xs, side="left")
+    assert np.array_equal(got, want)
+
+
+def test_sturm_counts_equal_single_point_counts(oracle_mod):
+    # the batched count performs the single-point recurrence per query point, so the
+    # two agree exactly even where x sits on an eigenvalue to the last bit
+    d, e = inputs.glued_wilkinson(97)
+    lam = oracle_mod.eigvals_bisect(d, e)
+    xs = np.concatenate([lam, lam + 1e-15, lam - 1e-15, [0.0, 3.0]])
+    got = oracle_mod.sturm_counts(d, e, xs)
+    assert [oracle_mod.sturm_count(d, e, x) for x in xs] == list(got)
+
+
+@pytest.mark.parametrize("n", [5, 64, 1000])
+def test_certify_toeplitz_closed_form_and_planted_errors(oracle_mod, n):
+    d, e = inputs.toeplitz(n, 2.0, -1.0)
+    ref = toeplitz_spectrum(n, 2.0, -1.0)
+    g = 8 * n * EPS * oracle_mod.norm1(d, e)
+    assert oracle_mod.certify(d, e, ref, g).all()
+    k = n // 2
+    # an eigenvalue off by 2 gates fails at exactly its index
+    bad = ref.copy()
+    bad[k] += 2 * g
+    ok = oracle_mod.certify(d, e, np.sort(bad), g)
+    assert not ok[k] and ok.sum() >= n - 1
+    # a dropped eigenvalue replaced by a duplicate of its neighbour is caught too
+    bad = ref.copy()
+    bad[k] = bad[k - 1] if k > 0 else bad[1]
+    assert not oracle_mod.certify(d, e, np.sort(bad), g).all()
+
+
+@pytest.mark.parametrize("fam", ["uniform11", "glued_wilkinson", "graded", "paper_clustered"])
+def test_certify_accepts_lapack_and_rejects_shift(oracle_mod, fam):
+    # LAPACK's eigvalsh (a library routine the oracle does not use) is certified within
+    # the gate; the same spectrum shifted by 3 gates is rejected everywhere
+    n = 600
+    d, e = inputs.family(fam, n, seed=2)
+    e = e[: n - 1]
+    lam = np.linalg.eigvalsh(oracle_mod.dense(d, e))
+    g = 8 * n * EPS * oracle_mod.norm1(d, e)
+    assert oracle_mod.certify(d, e, lam, g).all()
+    r, nfail = oracle_mod.certified_error(d, e, lam, g)
+    assert nfail == 0 and r <= g
+    assert not oracle_mod.certify(d, e, lam + 3 * g, g).any()
+
+
+# ---- the gate's norm, the gate and the paper's error metrics, by hand ------------
+
+
+def test_norm1_hand_values(oracle_mod):
+    # ||T||_1 = max_j (|e_{j-1}| + |d_j| + |e_j|); one case per row position of the max,
+    # each such that dropping any one term of the winning row changes the result
+    cases = [
+        ([-6.0, 1.0, 0.5], [1.5, 0.25], 7.5),     # row 0: 6 + 1.5
+        ([0.1, -5.0, 0.2], [2.0, -0.25], 7.25),   # row 1: 2 + 5 + 0.25
+        ([1.0, -2.0, 3.0], [0.5, -4.0], 7.0),     # row 2: 4 + 3
+        ([0.0, 0.0, 0.0, 0.0], [1.0, -3.0, 2.5], 5.5),  # zero diagonal
+        ([-2.5], [], 2.5),                        # order 1
+    ]
+    for d, e, want in cases:
+        assert oracle_mod.norm1(np.array(d), np.array(e)) == want
+        if len(d) > 1:  # the induced 1-norm of the dense matrix, by LAPACK
+            assert np.linalg.norm(oracle_mod.dense(d, e), 1) == want
+
+
+def test_gate_hand_value(oracle_mod):
+    # 8 n eps ||T||_1 with n = 3, ||T||_1 = 7, eps = 2^-52
+    assert oracle_mod.gate(np.array([1.0, -2.0, 3.0]), np.array([0.5, -4.0])) == 168.0 * 2.0 ** -52
+    assert oracle_mod.EPS == 2.0 ** -52
+
+
+def test_paper_error_metrics_hand_values(oracle_mod):
+    # e_fwd = ||l_hat - l||_inf / max(1, ||l||_inf), e_bwd = ||l_hat - l||_inf / max(1, ||T||_1)
+    d, e = np.array([1.0, -2.0, 3.0]), np.array([0.5, -4.0])  # ||T||_1 = 7
+    assert oracle_mod.e_fwd([1.0, 2.5, -3.0], [1.0, 2.0, -4.0]) == 1.0 / 4.0
+    assert oracle_mod.e_fwd([0.5, 0.75], [0.5, 0.625]) == 0.125  # max |l| < 1: floor 1
+    assert oracle_mod.e_bwd([1.0, 2.5, -3.0], [1.0, 2.0, -4.0], d, e) == 1.0 / 7.0
+    small = np.array([0.1, 0.1]), np.array([0.2])  # ||T||_1 = 0.3 < 1: floor 1
+    assert oracle_mod.e_bwd([0.0, 0.5], [0.0, 0.25], *small) == 0.25
