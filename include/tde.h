@@ -62,9 +62,10 @@ int tde_eigvals_workspace(int64_t n, int32_t leaf, size_t* bytes);
  *   d       [n]   diagonal
  *   e       [n-1] off-diagonal (e[i] couples rows i and i+1); may be NULL if n <= 1
  *   lambda  [n]   output, eigenvalues in ascending order
- * Internally scales T by 1 / max|T|, sets negligible off-diagonals
+ * Internally scales T by the power of two 2^-floor(log2 max|T|) (exact; the
+ * eigenvalues are unscaled exactly), sets negligible off-diagonals
  * (|e_i| <= eps sqrt|d_i| sqrt|d_{i+1}|) to zero (Sec. 4.2 driver), solves the
- * leaves by implicit QL keeping two eigenvector rows, and merges level by level. */
+ * leaves by implicit QR keeping two eigenvector rows, and merges level by level. */
 int tde_eigvals(int64_t n, const double* d, const double* e, double* lambda, int32_t leaf,
                 void* ws, size_t ws_bytes, void* stream);
 
@@ -169,23 +170,27 @@ int tde_measure_fp64_peak(double* fma_per_s);
 
 /* Launch-shape tuning for subsequent calls on this thread (0 restores a default):
  *   warp_min_k      merges whose active rank reaches this solve one warp per root
- *                   (default 256), smaller ones one thread per root;
+ *                   (default 256); smaller ones give four lanes of a warp to each
+ *                   root, or one thread below order 24;
  *   small_list_min  a step with fewer small-merge roots than this hands them to the
  *                   warp-per-root kernels too (default 18944 = 148 SMs x 4 warps x 32).
  * They change the time, and the eigenvalues only at the level of rounding (the
- * kernels sum in different orders, and only the warp-per-root kernel uses the
- * cluster expansion of the secular sums). */
+ * kernels sum in different orders, and only the warp-per-root kernels use the
+ * block expansion of tde_set_multipole). */
 int tde_set_tuning(int32_t warp_min_k, int32_t small_list_min);
 
-/* Threshold of the secular solver's block expansion for subsequent calls on this
- * thread: FP64 sweeps of merges whose active rank K reaches min_k (and that the
- * warp-per-root kernel solves) sum the poles of distant 128-pole blocks through a
- * 27-term series of the block's moments instead of term by term (series error
- * below 2^-53 of the block's terms), and so do the boundary-row sums of those
- * merges (32 terms, below 2^-58) and the Lowner products in log form (27 terms,
- * below 2^-55 absolute in the log).  min_k = 0 restores the default (1024); any
- * other value below 256 is TDE_EINVAL; a value above every K turns the expansion
- * off.  *previous (if not NULL) receives the value in force before the call. */
+/* Threshold of the block expansion for subsequent calls on this thread: in merges
+ * whose active rank K reaches min_k (and that the warp-per-root kernels solve), the
+ * FP64 secular sweeps, the Lowner products (in log form) and the boundary-row sums
+ * take distant blocks of 128 poles through series of the block's normalised
+ * moments instead of term by term; the series length follows the block's
+ * separation (radius / distance <= 1/64, 1/16, 1/4, 1/3: 10, 14, 27, 35 terms for
+ * the secular and Lowner sums, 10, 16, 32, 40 for the row sums), which keeps the
+ * series error below the rounding of the sums it replaces.  Merges of 192 or more
+ * blocks also take distant superblocks of 32 blocks.  min_k = 0 restores the
+ * default (1024); any other value below 256 is TDE_EINVAL; a value above every K
+ * turns the expansion off.  *previous (if not NULL) receives the value in force
+ * before the call. */
 int tde_set_multipole(int32_t min_k, int32_t* previous);
 /* out[0] = warp_min_k, out[1] = small_list_min of this thread. */
 int tde_get_tuning(int32_t* out);
@@ -258,13 +263,23 @@ int tde_read_work(const void* ws, void* stream, unsigned long long* out, int n);
  * this library.  The workspace is a 4 MiB array compiled into the library, kept
  * on every GPU that loads it until the process exits.  d, e, lambda, leaf and
  * stream mean what they mean for tde_eigvals; n must not exceed
- * TDE_NOALLOC_MAX_N (TDE_EWORKSPACE otherwise, nothing enqueued).  No memory is
- * allocated.  The first call on a device looks up the array's device address;
- * make that first call before any stream capture.  All calls share the one
- * array: calls that overlap on the GPU race and must be serialised by the
- * caller.  The device status word is not readable for this entry point. */
+ * TDE_NOALLOC_MAX_N (TDE_EWORKSPACE otherwise, nothing enqueued), for any leaf
+ * order.  No memory is allocated.  The first call on a device looks up the
+ * array's device address in the device's primary context and caches it; make
+ * that first call before any stream capture, and do not use this entry point
+ * after cudaDeviceReset or from a non-primary context (the array may have moved).
+ * All calls share the one array: calls that overlap on the GPU race and must be
+ * serialised by the caller.  Numerical failures found on the device are read
+ * with tde_noalloc_get_info. */
 int tde_eigvals_noalloc(int64_t n, const double* d, const double* e, double* lambda,
                         int32_t leaf, void* stream);
+
+/* Device status word of the last tde_eigvals_noalloc call on the current device
+ * that enqueued work (n >= 1), read on `stream` (synchronises it; use the
+ * stream of that call or one ordered after it).  *info receives 0 or a positive
+ * tde_status code, as tde_get_info does for a caller workspace.  Allocates
+ * nothing.  The paper has no counterpart. */
+int tde_noalloc_get_info(void* stream, int32_t* info);
 
 #ifdef __cplusplus
 }

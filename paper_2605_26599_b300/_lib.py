@@ -28,7 +28,7 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
            "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning",
            "tde_eigvals_backward_workspace", "tde_eigvals_backward", "tde_eigvecs_rows_workspace",
            "tde_eigvecs_rows", "tde_dense_eigvals_workspace", "tde_dense_eigvals",
-           "tde_set_multipole", "tde_check_rsqrt")
+           "tde_set_multipole", "tde_check_rsqrt", "tde_noalloc_get_info")
 
 MAX_SEL_ROWS = 1024  # TDE_MAX_SEL_ROWS
 
@@ -80,6 +80,7 @@ def load() -> ctypes.CDLL:
                                         ctypes.POINTER(ctypes.c_int64)]
     lib.tde_read_work.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
     lib.tde_eigvals_noalloc.argtypes = [i64, vp, vp, vp, i32, vp]
+    lib.tde_noalloc_get_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.tde_plan_query.argtypes = [i64, vp, i32, ctypes.POINTER(ctypes.c_int64)]
     lib.tde_check_reciprocal.argtypes = [i64, vp, vp, vp]
     lib.tde_check_rsqrt.argtypes = [i64, vp, vp, vp]

@@ -17,7 +17,10 @@
 // the first call on each device looks the address up with cudaGetSymbolAddress
 // (with that device current) and caches it; later calls on the device reuse it.
 // Because the lookup may load the module, make the first call on a device
-// before any stream capture begins.
+// before any stream capture begins.  The cached address belongs to the device's
+// primary context: after cudaDeviceReset, or from a different context on the
+// same device, the module is loaded again and the array may move, so such
+// callers must not use this entry point (it has no way to notice the change).
 //
 // Sharing: every call on a device uses the same array and it keeps the previous
 // call's contents.  The solver resets what must start at zero (the status word,
@@ -25,7 +28,9 @@
 // cudaMemsetAsync, and writes every other section before reading it.  Calls whose
 // execution overlaps on the GPU (different streams without ordering, or several
 // host threads) race on the array and corrupt each other's results; serialise
-// them.  tde_get_info / tde_read_work do not apply to this entry point.
+// them.  The device status word (no convergence, non-finite input) sits at the
+// start of the array like at the start of a caller workspace; tde_noalloc_get_info
+// reads it.  tde_read_work does not apply to this entry point.
 #include <mutex>
 
 #include "tde_internal.cuh"
@@ -85,4 +90,14 @@ extern "C" int tde_eigvals_noalloc(int64_t n, const double* d, const double* e, 
   k_noalloc_offsets<<<1, 1, 0, s>>>(w.offsets, n);
   g_launches += 1;
   return run_solver(p, w, w.offsets, d, e, lambda, s);
+}
+
+extern "C" int tde_noalloc_get_info(void* stream, int32_t* info) {
+  using namespace tde;
+  if (info == nullptr) return TDE_EINVAL;
+  void* base = nullptr;
+  const int rc = noalloc_scratch(&base);
+  if (rc != TDE_OK) return rc;
+  // the Status record opens the workspace carved from the array (carve_workspace)
+  return tde_get_info(base, stream, info);
 }

@@ -109,6 +109,7 @@ def test_argument_validation_without_device_work():
     off = np.array([1, 5], dtype=np.int64)  # offsets[0] != 0
     assert lib.tde_eigvals_batched_workspace(1, off.ctypes.data, 0, ctypes.byref(sz)) == _lib.TDE_EINVAL
     assert lib.tde_eigvals_noalloc(16385, fake, fake, fake, 0, None) == _lib.TDE_EWORKSPACE
+    assert lib.tde_noalloc_get_info(None, None) == _lib.TDE_EINVAL
     # requested eigenvector rows
     assert lib.tde_eigvecs_rows_workspace(100, _lib.MAX_SEL_ROWS + 1, 0, ctypes.byref(sz)) == _lib.TDE_EINVAL
     assert lib.tde_eigvecs_rows_workspace(100, -1, 0, ctypes.byref(sz)) == _lib.TDE_EINVAL
@@ -148,3 +149,16 @@ def test_python_binding_refuses_cpu_tensors():
 
     with pytest.raises(TypeError):
         tde.eigvals(torch.zeros(4, dtype=torch.float64), torch.zeros(3, dtype=torch.float64))
+
+
+def test_noalloc_array_holds_every_accepted_call():
+    # tde_eigvals_noalloc promises every order up to TDE_NOALLOC_MAX_N = 16384 with any
+    # leaf order: the workspace such a call carves must fit its 4 MiB array
+    lib = _lib.load()
+    sz = ctypes.c_size_t()
+    worst = 0
+    for leaf in range(1, 65):
+        for n in (16384, 16383, 12289, 8193):
+            assert lib.tde_eigvals_workspace(n, leaf, ctypes.byref(sz)) == _lib.TDE_OK
+            worst = max(worst, sz.value)
+    assert worst <= 4 << 20, worst
