@@ -1,9 +1,12 @@
 """GPU parity at the full single-matrix workload sizes (n = 32768 ... 262144).
 
-The oracle computes sampled eigenvalue indices one by one (Sturm bisection); the
-rest of the spectrum is checked through properties that hold at any size: the
-trace and Frobenius invariants, the closed-form Toeplitz spectrum, ascending
-order and the O(n) workspace bound."""
+Every eigenvalue is certified against the oracle's Sturm counts: the k-th
+computed value lambda_hat_k passes when count(lambda_hat_k - g) <= k and
+count(lambda_hat_k + g) >= k + 1, i.e. the k-th eigenvalue of T lies within the
+gate g = 8 n eps ||T||_1 of it (2n counts per matrix, no bisection).  A sample of
+indices is also bisected by the oracle to report the observed error, and the
+trace and Frobenius invariants, the closed-form Toeplitz spectrum, ascending order
+and the O(n) workspace bound are checked beside it."""
 import numpy as np
 import pytest
 
@@ -42,6 +45,9 @@ def check_full(d, e, lam, sample=192):
     tn = oracle.norm1(d, e)
     gate = 8 * n * EPS * tn
     assert np.all(np.diff(lam) >= 0)
+    ok = oracle.certify(d, e, lam, gate)
+    bad = np.nonzero(~ok)[0]
+    assert bad.size == 0, f"{bad.size} eigenvalues outside the gate, first at index {bad[:8]}"
     ks = sample_indices(n, sample)
     ref = oracle.eigvals_select(d, e, ks)
     err = float(np.max(np.abs(lam[ks] - ref)))

@@ -1,7 +1,7 @@
 """GPU parity of the secular solver's block expansion.
 
 In FP64 sweeps of large merges, distant blocks of 128 poles are summed through a
-27-term series of their moments, and only the blocks near the current point term
+series of their moments (10 to 35 terms by separation), and only the blocks near the current point term
 by term.  The tests lower the threshold so that every merge with 256 or more
 active poles goes through the expansion in the warp-per-root kernel.  They compare
 every eigenvalue with the Sturm bisection oracle, and the error with that of the
@@ -66,6 +66,7 @@ CASES = [
     ("glued 21 1e-11", lambda: glued(3000, 21, 1e-11)),
     ("glued 11 1e-8", lambda: glued(2500, 11, 1e-8)),
     ("glued 7 1e-6", lambda: glued(2000, 7, 1e-6)),
+    ("glued 31 1e-9", lambda: glued(3100, 31, 1e-9)),
 ]
 
 
