@@ -12,7 +12,8 @@
 //     warp per root (per pole for z-hat); the 32 lanes stride over the poles and
 //     the partial sums are combined with shuffles, so the whole warp shares one
 //     root's iteration count;
-//   * smaller merges: one thread per root, consecutive roots in a warp.
+//   * smaller merges: four lanes of a warp per root (one thread per root below
+//     order 24), the roots of a warp moving in warp-synchronous rounds.
 // Reciprocals use rcp_refined (three fused multiply-adds) instead of IEEE
 // division.
 #include <algorithm>
@@ -684,16 +685,60 @@ __device__ __forceinline__ int mp_blocks(int K, int mp_min_k) {
   return K >= mp_min_k ? K / kMpBlock : 0;
 }
 
-// Superblocks: 32 consecutive blocks (4096 poles, the last one up to K) with the
-// same kind of data, formed in merges of at least kSbMin blocks and at most 32
-// superblocks.  A sweep first takes every superblock that is far from the point
-// through its series and skips its round of 32 blocks; the rest go block by block.
+// Superblocks: sbs consecutive blocks (the last one takes the remainder) with the
+// same kind of data, at most 32 per merge.  A sweep first takes every superblock
+// that is far from the point through its series (one superblock per lane), then
+// goes block by block over the superblocks it did not take whole, 32 blocks per
+// round.  The secular sums and the Löwner products use sbs = 8 in merges of 65 to
+// 256 blocks (16 up to 512, 32 up to 1024 blocks): the near superblocks (the
+// point's own and its neighbours) then hold about 24 blocks, one round, so a sweep
+// takes two rounds of series where one block per lane would take nb / 32.  The
+// row sums keep 32-block superblocks from 192 blocks: their block data (121
+// doubles per block) leave no room for smaller ones inside the merge's rows.
 // Their data follow the blocks' float data (field q of superblock s at [q nsb + s]).
-constexpr int kSbBlocks = 32;
-constexpr int kSbMin = 192;  // below, the superblock round costs about what it saves
-__device__ __forceinline__ int sb_count(int nb) {
-  const int nsb = (nb + kSbBlocks - 1) / kSbBlocks;
-  return (nb >= kSbMin && nsb <= 32) ? nsb : 0;
+constexpr int kSbMin = 65;       // from here the superblock round saves block rounds
+constexpr int kSbRows = 32;      // superblock size of the row sums
+constexpr int kSbRowsMin = 192;  // and their threshold (below it the round costs what it saves)
+static_assert(kSbRows == 32, "the row sums' block rounds coincide with their superblocks");
+__device__ __forceinline__ int sb_size(int nb) { return nb <= 256 ? 8 : nb <= 512 ? 16 : 32; }
+__device__ __forceinline__ int sb_count(int nb, int sbs, int min_nb) {
+  if (nb < min_nb || sbs == 0) return 0;
+  const int nsb = (nb + sbs - 1) / sbs;
+  return nsb <= 32 ? nsb : 0;
+}
+// superblocks of the secular sums and Löwner products
+__device__ __forceinline__ int sb_count(int nb) { return sb_count(nb, sb_size(nb), kSbMin); }
+// superblocks of the row sums
+__device__ __forceinline__ int sb_count_rows(int nb) { return sb_count(nb, kSbRows, kSbRowsMin); }
+
+// The blocks a sweep takes one by one after its superblock round: those of the
+// superblocks it did not take whole (all blocks without superblocks), in
+// ascending order; entry idx of the list is block kept_block(k, idx).
+struct KeptBlocks {
+  unsigned keep;  // superblocks not taken whole
+  int sbs, count;
+};
+__device__ __forceinline__ KeptBlocks kept_blocks(int nsb, int sbs, unsigned sfar, int nb) {
+  KeptBlocks k;
+  if (nsb == 0) {
+    k.keep = 0u;
+    k.sbs = 0;
+    k.count = nb;
+    return k;
+  }
+  k.sbs = sbs;
+  k.keep = (nsb >= 32 ? 0xffffffffu : (1u << nsb) - 1u) & ~sfar;
+  k.count = __popc(k.keep) * sbs;
+  if ((k.keep >> (nsb - 1)) & 1u) k.count -= nsb * sbs - nb;  // the last superblock is short
+  return k;
+}
+// block of list entry idx, or -1 past the end of the list
+__device__ __forceinline__ int kept_block(const KeptBlocks& k, int idx) {
+  if (idx >= k.count) return -1;
+  if (k.sbs == 0) return idx;
+  unsigned m = k.keep;
+  for (int q = idx / k.sbs; q > 0; --q) m &= m - 1;  // skip the kept superblocks before it
+  return (__ffs(m) - 1) * k.sbs + idx % k.sbs;
 }
 __device__ __forceinline__ double* sb_data(double* MPD_lo, int nb) {
   return MPD_lo + kMpFields * nb + (kMfFields * nb + 1) / 2;
@@ -709,9 +754,9 @@ __device__ __forceinline__ void binomial_shift(double (&v)[N], double a) {
     for (int j = N - 1; j >= i; --j) v[j] = fma(a, v[j - 1], v[j]);
   }
 }
-// per 32 blocks (4096 rows): their data and one superblock's, each at most
-// kMpFields + (kMfFields + 1) / 2 + 1 doubles
-static_assert((kSbBlocks + 1) * (kMpFields + (kMfFields + 1) / 2 + 1) <= kSbBlocks * kMpBlock,
+// per 8 blocks (1024 rows, the smallest superblock): their data and one
+// superblock's, each at most kMpFields + (kMfFields + 1) / 2 + 1 doubles
+static_assert((8 + 1) * (kMpFields + (kMfFields + 1) / 2 + 1) <= 8 * kMpBlock,
               "block and superblock data fit the merge's rows");
 
 // one thread evaluates all K poles
@@ -921,36 +966,30 @@ struct WarpSweep {
     } else {
       double pa0 = 0.0, pa1 = 0.0, pd0 = 0.0, pd1 = 0.0;  // near poles left of lambda
       double fa0 = 0.0, fa1 = 0.0, fd0 = 0.0, fd1 = 0.0;  // and right of it
-      unsigned sfar = 0;  // superblocks taken whole
-      // round -1 (if any) goes over the superblocks, rounds 0, 1, ... over the blocks
-      for (int rd = nsb > 0 ? -1 : 0; rd * 32 < nb; ++rd) {
-        const bool sup = rd < 0;
-        if (!sup && ((sfar >> rd) & 1u)) continue;  // the round went through its superblock
-        const double* C = sup ? SP : MP;
-        const float* F = sup ? SF : MF;
-        const int nc = sup ? nsb : nb, b0 = sup ? 0 : rd * 32;
-        const int b = b0 + lane;
-        bool near = false;
-        const double dm = b < nc ? (C[b] - dorg) - tau : 1.0;  // m - lambda
-        const double rb = b < nc ? C[nc + b] : 0.0;
-        const FarTest ft = far_test_bits(dm, rb, b < nc ? C[2 * nc + b] : 0.0, b < nc);
-        if (b < nc) {
-          if (ft.far) {
-            far_series(C, F, nc, b, dm, rb, ft.tier, p, dp, f, df);
-          } else {
-            near = !sup;
-          }
-        }
-        if (sup) sfar = __ballot_sync(0xffffffffu, ft.far);
-        unsigned nm = __ballot_sync(0xffffffffu, near);
+      // one round: the lane's block (or superblock) b of data C / F with nc entries
+      // per field through its series if it is far from the point
+      auto far_round = [&](const double* C, const float* F, int nc, int b, bool valid) -> bool {
+        const double dm = valid ? (C[b] - dorg) - tau : 1.0;  // m - lambda
+        const double rb = valid ? C[nc + b] : 0.0;
+        const FarTest ft = far_test_bits(dm, rb, valid ? C[2 * nc + b] : 0.0, valid);
+        if (ft.far) far_series(C, F, nc, b, dm, rb, ft.tier, p, dp, f, df);
         const unsigned nfar = __popc(__ballot_sync(0xffffffffu, ft.far));
         blocks += nfar;
         sops += nfar * unsigned(kSecSeriesOverhead + (ft.tier == 0   ? kHv0 + kHd0
                                                       : ft.tier == 1 ? kHv1 + kHd1
                                                       : ft.tier == 2 ? kHv2 + kHd2
                                                                      : kHv3 + kHd3));
+        return ft.far;
+      };
+      unsigned sfar = 0;  // superblocks taken whole
+      if (nsb > 0) sfar = __ballot_sync(0xffffffffu, far_round(SP, SF, nsb, lane, lane < nsb));
+      const KeptBlocks kb = kept_blocks(nsb, sb_size(nb), sfar, nb);
+      for (int base = 0; base < kb.count; base += 32) {
+        const int b = kept_block(kb, base + lane);
+        const bool far = far_round(MP, MF, nb, b < 0 ? 0 : b, b >= 0);
+        unsigned nm = __ballot_sync(0xffffffffu, b >= 0 && !far);
         while (nm) {
-          const int bb = b0 + __ffs(nm) - 1;
+          const int bb = __shfl_sync(0xffffffffu, b, __ffs(nm) - 1);
           nm &= nm - 1;
           const int i0 = bb * kMpBlock, i1 = (bb == nb - 1) ? K : i0 + kMpBlock;
           const int mid = min(max(jl + 1, i0), i1);
@@ -1372,7 +1411,6 @@ __global__ void __launch_bounds__(128) k_super_moments(RootArgs a) {
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  constexpr int kSbPoles = kSbBlocks * kMpBlock;
   for (uint32_t base = gw * 32; base < total; base += nw * 32) {
     const uint32_t r = base + lane;
     int g = 0, j = 0, nsb = 0, nb = 0;
@@ -1384,18 +1422,20 @@ __global__ void __launch_bounds__(128) k_super_moments(RootArgs a) {
       j = rl - ms.base;
       nb = mp_blocks(ms.K, a.mp_min_k);
       nsb = sb_count(nb);
-      head = nsb > 0 && (j % kSbPoles) == 0 && j / kSbPoles < nsb;
+      const int sbp = sb_size(nb) * kMpBlock;  // poles per superblock
+      head = nsb > 0 && (j % sbp) == 0 && j / sbp < nsb;
     }
     unsigned hm = __ballot_sync(0xffffffffu, head);
     while (hm) {
       const int src = __ffs(hm) - 1;
       hm &= hm - 1;
       const int gg = __shfl_sync(0xffffffffu, g, src);
-      const int sb = __shfl_sync(0xffffffffu, j, src) / kSbPoles;
       const int nbb = __shfl_sync(0xffffffffu, nb, src), nss = __shfl_sync(0xffffffffu, nsb, src);
+      const int sbs = sb_size(nbb), sbp = sbs * kMpBlock;
+      const int sb = __shfl_sync(0xffffffffu, j, src) / sbp;
       const int lo = a.M[gg].lo, K = a.ms[gg].K;
       const double* D = a.AD + lo;
-      const int i0 = sb * kSbPoles, i1 = (sb == nss - 1) ? K : i0 + kSbPoles;
+      const int i0 = sb * sbp, i1 = (sb == nss - 1) ? K : i0 + sbp;
       const double m = 0.5 * (D[i0] + D[i1 - 1]);
       const double rad = fmax(m - D[i0], D[i1 - 1] - m);
       const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
@@ -1403,11 +1443,11 @@ __global__ void __launch_bounds__(128) k_super_moments(RootArgs a) {
       const float* BF = reinterpret_cast<const float*>(MP + kMpFields * nbb);
       double* SP = sb_data(a.MPD + lo, nbb);
       float* SF = reinterpret_cast<float*>(SP + kMpFields * nss);
-      const int b = sb * kSbBlocks + lane;
+      const int b = sb * sbs + lane;
       double S[kMfTerms];
 #pragma unroll
       for (int k = 0; k < kMfTerms; ++k) S[k] = 0.0;
-      if (b < nbb && b < (sb + 1) * kSbBlocks) {
+      if (b < nbb && lane < sbs) {
         const double av = (MP[b] - m) * rinv, cv = MP[nbb + b] * rinv;
         double cj = 1.0;  // S_q = c^q M'^b_q, then shifted by a
 #pragma unroll
@@ -1502,38 +1542,222 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
   if (gl == 0) tally.flush(a.st);
 }
 
-// Roots differ in cost (one to several sweeps in each precision), so warps claim
-// them one at a time instead of a fixed stride, which would leave a tail.  Within a
-// merge the claims alternate between the two ends of the spectrum and move inward:
-// the costly roots (narrow gaps, many sweeps) sit at the ends, and a costly root
-// claimed last would run alone on one SM sub-partition while the others idle.
-__global__ void __launch_bounds__(128, 4) k_secular_warp(RootArgs a) {
-  const uint32_t total = warp_list_total(a);
+// Warp-cooperative form for the warp kernel: lane l owns one root (its own merge,
+// origin, bracket and model state), and every sweep is summed by the whole warp,
+// one root at a time.  Each round the warp sweeps, in turn, every root that needs a
+// sweep (ballot), broadcasting its point (origin, tau, jl) and its merge; lane l
+// keeps the sums of its own root (the warp reductions are butterflies, so every
+// lane holds the same totals).  The per-root scalar work (the model step,
+// convergence test, the stage hand-over) then runs once for all 32 roots, lane
+// parallel, instead of once per root at warp width: on this part an FP64
+// instruction occupies the pipe for the whole warp however few lanes are active.
+// Same steps and stopping rules as secular_root; all 32 lanes must call it.
+// `co` supplies the cooperative sweeps: sweep32(src, org, jl, tau, inv) and
+// sweep64(src, dorg, tau, jl) sum the root of lane src.
+template <class Coop, class Copies>
+__device__ int secular_root_coop(const double* D, const double* Z, int K, int j, double rho,
+                                 double rhoinv, double zsq, bool valid, const Copies& cp, Coop& co,
+                                 int* org_out, double* tau_out, bool* ok, int* n32) {
+  constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  SecTally tally;
-  for (uint32_t r = claim_next_item(a.st); r < total; r = claim_next_item(a.st)) {
-    int rl;
-    const int g = warp_list_merge(a, r, &rl);
-    const MState ms = a.ms[g];
-    const int q = rl - ms.base, lo = a.M[g].lo;
-    const int j = (q & 1) ? ms.K - 1 - (q >> 1) : (q >> 1);
-    const int nb = mp_blocks(ms.K, a.mp_min_k);
-    const float* mf = reinterpret_cast<const float*>(a.MPD + lo + kMpFields * nb);
-    const int nsb = sb_count(nb);
-    const double* sp = sb_data(a.MPD + lo, nb);
-    WarpSweep sw{a.AD + lo, a.AZ + lo, ms.K, lane, nb, a.MPD + lo, mf, 0ull, 0u, 0u, nsb, sp,
-                 reinterpret_cast<const float*>(sp + kMpFields * nsb)};
-    WarpSweep32 sw32{{a.AD32 + lo, a.AZ32 + lo, ms.K}, lane, nb, mf};
-    int org, n32;
-    double tau;
-    bool ok;
-    const int sweeps =
-        secular_root(a.AD + lo, a.AZ + lo, ms.K, j, ms.rho, ms.rhoinv, ms.zsq, sw, sw32, &org, &tau, &ok,
-                     &n32);
-    secular_store(a, lo, j, org, tau, sweeps, ms.K, ok, lane == 0);
-    tally.add_counted(sw.pairs, sw.blocks, sw.sops, sweeps, n32, ms.K);
+  *ok = true;
+  *n32 = 0;
+  const bool act = valid && K > 1;
+  Stage32 st;
+  st.live = false;
+  st.org = 0;
+  st.jl = 0;
+  st.tau = 0.0f;
+  st.inv = 1.0f;
+  // cooperative single-precision sweeps of the flagged lanes at (org, jl, tf, st.inv)
+  auto sweep32_all = [&](bool flag, int org, int jl, float tf, Sec32& out) {
+    unsigned m = __ballot_sync(kFull, flag);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const Sec32 s = co.sweep32(src, __shfl_sync(kFull, org, src), __shfl_sync(kFull, jl, src),
+                                 __shfl_sync(kFull, tf, src), __shfl_sync(kFull, st.inv, src));
+      if (lane == src) out = s;
+    }
+  };
+  const bool in32 = act && s32_begin(D, K, j, rho, rhoinv, zsq, cp, st);
+  sweep32_all(in32, st.org, st.jl, st.tau, st.s);
+  if (in32) s32_first(D, K, j, st);
+  for (;;) {
+    float eta = 0.0f;
+    bool have = false;
+    const bool need = in32 && st.live && s32_step(st, &eta, &have);
+    if (!__any_sync(kFull, need)) break;
+    sweep32_all(need, st.org, st.jl, st.tau, st.s);
+    if (need) s32_after(st, eta, have);
   }
-  if (lane == 0) tally.flush(a.st);
+  SecState q;
+  q.org = 0;
+  q.jl = 0;
+  q.tau = 0.0;
+  q.dorg = 0.0;
+  double hw = 0.0;
+  bool third = false, handed = false;
+  if (in32) {
+    *n32 = st.sweeps;
+    bool hw_ok;
+    handed = s32_finish(D, Z, rhoinv, st, q, &hw, &hw_ok);
+    third = handed && hw_ok;
+  }
+  if (act && !handed) sec_init_point(D, K, j, rho, rhoinv, zsq, q);
+  // cooperative FP64 sweeps of the flagged lanes at (q.dorg, q.tau, q.jl)
+  auto sweep64_all = [&](bool flag) {
+    unsigned m = __ballot_sync(kFull, flag);
+    while (m) {
+      const int src = __ffs(m) - 1;
+      m &= m - 1;
+      const SecSums s = co.sweep64(src, __shfl_sync(kFull, q.dorg, src), __shfl_sync(kFull, q.tau, src),
+                                   __shfl_sync(kFull, q.jl, src));
+      if (lane == src) q.s = s;
+    }
+  };
+  sweep64_all(act);
+  if (act) {
+    if (handed)
+      q.w = q.rhoinv + q.s.psi + q.s.phi;
+    else
+      sec_init_finish(D, Z, K, j, rho, zsq, q);
+  }
+  int sweeps = act ? 1 : 0;
+  bool go = act;
+  for (;;) {
+    if (go) {
+      if (sec_step(q, hw, third) == 0) {
+        go = false;
+      } else if (sweeps >= kMaxSweeps) {
+        *ok = false;
+        go = false;
+      }
+    }
+    if (!__any_sync(kFull, go)) break;
+    // w''/2 at the new point from a single-precision sweep (third-order steps)
+    const bool h3 = go && third;
+    Sec32 s3;
+    sweep32_all(h3, q.org, q.jl, h3 ? float(q.tau * st.Sinv) : 0.0f, s3);
+    if (h3) {
+      hw = hw_natural(st, s3.hw);
+      ++*n32;
+    }
+    sweep64_all(go);
+    if (go) {
+      q.w = q.rhoinv + q.s.psi + q.s.phi;
+      ++sweeps;
+    }
+  }
+  if (valid && K == 1) {
+    *org_out = 0;
+    *tau_out = rho * Z[0] * Z[0];
+    return 0;
+  }
+  *org_out = q.org;
+  *tau_out = q.tau;
+  return sweeps;
+}
+
+// Cooperative sweeps of the warp kernel: the root of lane src lives in the merge at
+// row lo (order K, nb pole blocks, nsb superblocks), broadcast from that lane; the
+// FP64 work counters accumulate warp-uniformly.
+struct WarpCoop {
+  const RootArgs* a;
+  int lane, lo, K, nb;
+  unsigned long long pairs = 0;
+  unsigned blocks = 0, sops = 0;
+  __device__ __forceinline__ void merge_of(int src, int& slo, int& sK, int& snb) const {
+    slo = __shfl_sync(0xffffffffu, lo, src);
+    sK = __shfl_sync(0xffffffffu, K, src);
+    snb = __shfl_sync(0xffffffffu, nb, src);
+  }
+  __device__ __forceinline__ Sec32 sweep32(int src, int org, int jl, float tau, float inv) const {
+    int slo, sK, snb;
+    merge_of(src, slo, sK, snb);
+    const float* mf = reinterpret_cast<const float*>(a->MPD + slo + kMpFields * snb);
+    const WarpSweep32 sw{{a->AD32 + slo, a->AZ32 + slo, sK}, lane, snb, mf};
+    return sw(org, jl, tau, inv);
+  }
+  __device__ __forceinline__ SecSums sweep64(int src, double dorg, double tau, int jl) {
+    int slo, sK, snb;
+    merge_of(src, slo, sK, snb);
+    const float* mf = reinterpret_cast<const float*>(a->MPD + slo + kMpFields * snb);
+    const int nsb = sb_count(snb);
+    const double* sp = sb_data(a->MPD + slo, snb);
+    const WarpSweep sw{a->AD + slo, a->AZ + slo, sK, lane, snb, a->MPD + slo, mf, 0ull, 0u, 0u, nsb, sp,
+                       reinterpret_cast<const float*>(sp + kMpFields * nsb)};
+    const SecSums s = sw(dorg, tau, jl);
+    pairs += sw.pairs;
+    blocks += sw.blocks;
+    sops += sw.sops;
+    return s;
+  }
+};
+
+// The warp kernel takes its list in tiles of T consecutive entries, one root per
+// lane (lanes T..31 idle in the scalar steps, busy in every sweep).  T is the
+// power of two at or below a quarter of the list length per launched warp, capped
+// at 32: a warp sweeps the roots of its tile one after another, so larger tiles
+// would leave warps without work on short lists (whose sweeps are latency-bound)
+// and leave a tail of whole tiles at the end of long ones; with about four tiles
+// per warp the claims still balance, and T = 32 cuts the per-root scalar work
+// 32-fold.  Roots differ in cost (one to several sweeps in each precision),
+// so warps claim tiles one at a time instead of a fixed stride, which would leave
+// a tail.  Within a merge the list alternates between the two ends of the
+// spectrum and moves inward (entry q is root q / 2 from the bottom for even q,
+// from the top for odd q), so the costly roots (narrow gaps, many sweeps, at the
+// ends) are claimed first and the cheap middle roots form the tail.
+__global__ void __launch_bounds__(128, 3) k_secular_warp(RootArgs a) {
+  const uint32_t total = warp_list_total(a);
+  const uint32_t per_warp = total / (4 * ((gridDim.x * blockDim.x) >> 5));
+  const uint32_t T = per_warp >= 32 ? 32u : per_warp >= 16 ? 16u : per_warp >= 8 ? 8u
+                   : per_warp >= 4 ? 4u : per_warp >= 2 ? 2u : 1u;
+  const uint32_t tiles = (total + T - 1) / T;
+  const int lane = threadIdx.x & 31;
+  unsigned long long pairs = 0, sops = 0, pairs32 = 0;  // pairs, sops: warp-uniform
+  unsigned blocks = 0, sweeps64 = 0, sweeps32 = 0, roots = 0;
+  for (uint32_t t = claim_next_item(a.st); t < tiles; t = claim_next_item(a.st)) {
+    const uint32_t r = t * T + uint32_t(lane);
+    const bool valid = uint32_t(lane) < T && r < total;
+    int rl = 0, g = 0;
+    if (valid) g = warp_list_merge(a, r, &rl);
+    const MState ms = valid ? a.ms[g] : MState{};
+    const int q = rl - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
+    const int j = (q & 1) ? K - 1 - (q >> 1) : (q >> 1);
+    WarpCoop co{&a, lane, lo, K, mp_blocks(K, a.mp_min_k)};
+    const Copies32 cp{a.AD32 + lo, a.AZ32 + lo, K};
+    int org = 0, n32 = 0;
+    double tau = 0.0;
+    bool ok = true;
+    const int sweeps = secular_root_coop(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.rhoinv, ms.zsq, valid,
+                                         cp, co, &org, &tau, &ok, &n32);
+    if (valid) {
+      secular_store(a, lo, j, org, tau, sweeps, K, ok, true);
+      sweeps64 += unsigned(sweeps);
+      sweeps32 += unsigned(n32);
+      pairs32 += (unsigned long long)n32 * unsigned(K);
+      roots += 1;
+    }
+    pairs += co.pairs;
+    blocks += co.blocks;
+    sops += co.sops;
+  }
+  // per-lane tallies summed over the warp, one atomic per counter per warp
+  sweeps64 = __reduce_add_sync(0xffffffffu, sweeps64);
+  sweeps32 = __reduce_add_sync(0xffffffffu, sweeps32);
+  roots = __reduce_add_sync(0xffffffffu, roots);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pairs32 += __shfl_xor_sync(0xffffffffu, pairs32, o);
+  if (lane == 0 && roots) {
+    atomicAdd(&a.st->work[kWorkSecularPairs], pairs);
+    if (blocks) atomicAdd(&a.st->work[kWorkSecularFarBlocks], (unsigned long long)blocks);
+    if (sops) atomicAdd(&a.st->work[kWorkSecularSeriesOps], sops);
+    atomicAdd(&a.st->work[kWorkSecularSweeps], (unsigned long long)sweeps64);
+    atomicAdd(&a.st->work[kWorkSecular32Pairs], pairs32);
+    atomicAdd(&a.st->work[kWorkSecular32Sweeps], (unsigned long long)sweeps32);
+    atomicAdd(&a.st->work[kWorkRoots], (unsigned long long)roots);
+  }
   claim_finish_block(a.st);
 }
 
@@ -1647,7 +1871,7 @@ constexpr int kMlFields = 3 + 2 * kMlHead;                // m, r, 3 r, c^L_k, c
 constexpr int kMlFloats = 2 * (kMlTerms - kTailBase);     // c^L_k, c^R_k (6 <= k < 35) as floats
 static_assert(2 * kMlFields + kMlFloats <= 2 * kMpBlock, "block data must fit the merge's rows");
 // superblocks of pair blocks (same rule as the secular sums; data after the blocks')
-static_assert((kSbBlocks + 1) * (kMlFields + (kMlFloats + 1) / 2 + 1) <= kSbBlocks * kMpBlock,
+static_assert((8 + 1) * (kMlFields + (kMlFloats + 1) / 2 + 1) <= 8 * kMpBlock,
               "block and superblock data fit the merge's rows");
 __device__ __forceinline__ double* lowner_sb_data(double* MPR_lo, int nb) {
   return MPR_lo + kMlFields * nb + (kMlFloats * nb + 1) / 2;
@@ -1751,7 +1975,6 @@ __global__ void __launch_bounds__(64) k_lowner_super(RootArgs a) {  // 2 warps: 
   const int lane = threadIdx.x & 31;
   const int side = threadIdx.x >> 5;  // the block's warps share the roots, one side each
   const uint32_t gw = blockIdx.x, nw = gridDim.x;
-  constexpr int kSbPoles = kSbBlocks * kMpBlock;
   for (uint32_t base = gw * 32; base < total; base += nw * 32) {
     const uint32_t r = base + lane;
     int g = 0, j = 0, nb = 0, nsb = 0;
@@ -1764,18 +1987,20 @@ __global__ void __launch_bounds__(64) k_lowner_super(RootArgs a) {  // 2 warps: 
       j = rl - ms.base;
       nb = ((uint32_t(mg.info) & kRootBit) && !a.all_merges) ? 0 : mp_blocks(ms.K, a.mp_min_k);
       nsb = sb_count(nb);
-      head = nsb > 0 && (j % kSbPoles) == 0 && j / kSbPoles < nsb;
+      const int sbp = sb_size(nb) * kMpBlock;  // pairs per superblock
+      head = nsb > 0 && (j % sbp) == 0 && j / sbp < nsb;
     }
     unsigned hm = __ballot_sync(0xffffffffu, head);
     while (hm) {
       const int src = __ffs(hm) - 1;
       hm &= hm - 1;
       const int gg = __shfl_sync(0xffffffffu, g, src);
-      const int sb = __shfl_sync(0xffffffffu, j, src) / kSbPoles;
       const int nbb = __shfl_sync(0xffffffffu, nb, src), nss = __shfl_sync(0xffffffffu, nsb, src);
+      const int sbs = sb_size(nbb), sbp = sbs * kMpBlock;
+      const int sb = __shfl_sync(0xffffffffu, j, src) / sbp;
       const int lo = a.M[gg].lo, K = a.ms[gg].K;
       const double* D = a.AD + lo;
-      const int j0 = sb * kSbPoles, j1 = (sb == nss - 1) ? K - 1 : j0 + kSbPoles;
+      const int j0 = sb * sbp, j1 = (sb == nss - 1) ? K - 1 : j0 + sbp;
       const double m = 0.5 * (D[j0] + D[j1]);
       const double rad = fmax(m - D[j0], D[j1] - m);
       const double rinv = rad > 0.0 ? 1.0 / rad : 0.0;
@@ -1783,8 +2008,8 @@ __global__ void __launch_bounds__(64) k_lowner_super(RootArgs a) {  // 2 warps: 
       const float* MF = reinterpret_cast<const float*>(MP + kMlFields * nbb);
       double* SP = lowner_sb_data(a.MPR + lo, nbb);
       float* SF = reinterpret_cast<float*>(SP + kMlFields * nss);
-      const int b = sb * kSbBlocks + lane;
-      const bool mine = b < nbb && lane < kSbBlocks;
+      const int b = sb * sbs + lane;
+      const bool mine = b < nbb && lane < sbs;
       if (lane == 0 && side == 0) {
         SP[sb] = m;
         SP[nss + sb] = rad;
@@ -1860,72 +2085,45 @@ __global__ void k_lowner_warp(RootArgs a) {
       const int nsb = sb_count(nb);
       const double* SP = lowner_sb_data(a.MPR + lo, nb);
       const float* SF = reinterpret_cast<const float*>(SP + kMlFields * nsb);
-      unsigned sfar = 0;  // superblocks taken whole (their rounds are skipped below)
-      if (nsb > 0) {
-        const int sb = lane;
-        const double dm = sb < nsb ? Di - SP[sb] : 1.0;
-        const double rb = sb < nsb ? SP[nsb + sb] : 0.0;
-        const FarTest ft = far_test_bits(dm, rb, sb < nsb ? SP[2 * nsb + sb] : 0.0, sb < nsb);
+      // one round: the lane's pair block (or superblock) b of data C / F with nc
+      // entries per field through its log series if it is far from D_i
+      auto far_round = [&](const double* C, const float* F, int nc, int b, bool valid) -> bool {
+        const double dm = valid ? Di - C[b] : 1.0;
+        const double rb = valid ? C[nc + b] : 0.0;
+        const FarTest ft = far_test_bits(dm, rb, valid ? C[2 * nc + b] : 0.0, valid);
         if (ft.far) {
           const double w = rcp_refined(dm), x = rb * w;
           const int side = dm < 0.0 ? 1 : 0;  // right of D_i: R
-          const double* c = SP + (3 + side * kMlHead) * nsb + sb;
-          const float* f = SF + side * (kMlTerms - kTailBase) * nsb + sb;
+          const double* c = C + (3 + side * kMlHead) * nc + b;
+          const float* f = F + side * (kMlTerms - kTailBase) * nc + b;
           double val;
           if (ft.tier == 0)
-            val = series1_mixed<kMpTiny, kHv0>(c, f, nsb, x);
+            val = series1_mixed<kMpTiny, kHv0>(c, f, nc, x);
           else if (ft.tier == 1)
-            val = series1_mixed<kMpShort, kHv1>(c, f, nsb, x);
+            val = series1_mixed<kMpShort, kHv1>(c, f, nc, x);
           else if (ft.tier == 2)
-            val = series1_mixed<kMpMid, kHv2>(c, f, nsb, x);
+            val = series1_mixed<kMpMid, kHv2>(c, f, nc, x);
           else
-            val = series1_mixed<kMlTerms, kHv3>(c, f, nsb, x);
+            val = series1_mixed<kMlTerms, kHv3>(c, f, nc, x);
           slog = fma(-w, val, slog);
         }
-        sfar = __ballot_sync(0xffffffffu, ft.far);
-        const unsigned nfar = __popc(sfar);
+        const unsigned nfar = __popc(__ballot_sync(0xffffffffu, ft.far));
         series += nfar;
         sops += nfar * unsigned(kMlSeriesOverhead + (ft.tier == 0   ? kHv0
                                                      : ft.tier == 1 ? kHv1
                                                      : ft.tier == 2 ? kHv2
                                                                     : kHv3));
-      }
-      for (int b0 = 0; b0 < nb; b0 += 32) {
-        if ((sfar >> (b0 / 32)) & 1u) continue;  // the round went through its superblock
-        const int b = b0 + lane;
-        bool near = false;
-        const double dm = b < nb ? Di - MP[b] : 1.0;
-        const double rb = b < nb ? MP[nb + b] : 0.0;
-        const FarTest ft = far_test_bits(dm, rb, b < nb ? MP[2 * nb + b] : 0.0, b < nb);
-        if (b < nb) {
-          if (ft.far) {
-            const double w = rcp_refined(dm), x = rb * w;
-            const int side = dm < 0.0 ? 1 : 0;  // right of D_i: R
-            const double* c = MP + (3 + side * kMlHead) * nb + b;
-            const float* f = MF + side * (kMlTerms - kTailBase) * nb + b;
-            double val;
-            if (ft.tier == 0)
-              val = series1_mixed<kMpTiny, kHv0>(c, f, nb, x);
-            else if (ft.tier == 1)
-              val = series1_mixed<kMpShort, kHv1>(c, f, nb, x);
-            else if (ft.tier == 2)
-              val = series1_mixed<kMpMid, kHv2>(c, f, nb, x);
-            else
-              val = series1_mixed<kMlTerms, kHv3>(c, f, nb, x);
-            slog = fma(-w, val, slog);
-          } else {
-            near = true;
-          }
-        }
-        unsigned nm = __ballot_sync(0xffffffffu, near);
-        const unsigned nfar = unsigned(min(32, nb - b0) - __popc(nm));
-        series += nfar;
-        sops += nfar * unsigned(kMlSeriesOverhead + (ft.tier == 0   ? kHv0
-                                                     : ft.tier == 1 ? kHv1
-                                                     : ft.tier == 2 ? kHv2
-                                                                    : kHv3));
+        return ft.far;
+      };
+      unsigned sfar = 0;  // superblocks taken whole
+      if (nsb > 0) sfar = __ballot_sync(0xffffffffu, far_round(SP, SF, nsb, lane, lane < nsb));
+      const KeptBlocks kb = kept_blocks(nsb, sb_size(nb), sfar, nb);
+      for (int base = 0; base < kb.count; base += 32) {
+        const int b = kept_block(kb, base + lane);
+        const bool far = far_round(MP, MF, nb, b < 0 ? 0 : b, b >= 0);
+        unsigned nm = __ballot_sync(0xffffffffu, b >= 0 && !far);
         while (nm) {
-          const int bb = b0 + __ffs(nm) - 1;
+          const int bb = __shfl_sync(0xffffffffu, b, __ffs(nm) - 1);
           nm &= nm - 1;
           const int j0 = bb * kMpBlock, j1 = lowner_block_end(bb, nb, K);
           for (int j = j0 + lane; j < j1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
@@ -2057,7 +2255,7 @@ constexpr int kMrFields = 3 + kMrHa3 + 2 * kMrHl3;  // m, r, 3 r, (k + 1) A_k, L
 constexpr int kMrTail = kMrTerms - kTailBase;       // float terms per kernel (6 <= k < 40)
 static_assert(2 * kMrFields + 3 * kMrTail <= 2 * kMpBlock, "block data must fit the merge's rows");
 // superblocks (same rule as the secular sums; data after the blocks')
-static_assert((kSbBlocks + 1) * (kMrFields + (3 * kMrTail + 1) / 2 + 1) <= kSbBlocks * kMpBlock,
+static_assert((kSbRows + 1) * (kMrFields + (3 * kMrTail + 1) / 2 + 1) <= kSbRows * kMpBlock,
               "block and superblock data fit the merge's rows");
 __device__ __forceinline__ double* rows_sb_data(double* MPR_lo, int nb) {
   return MPR_lo + kMrFields * nb + (3 * kMrTail * nb + 1) / 2;
@@ -2140,7 +2338,7 @@ __global__ void __launch_bounds__(96) k_rows_super(RootArgs a) {  // 3 warps: A,
   const int lane = threadIdx.x & 31;
   const int which = threadIdx.x >> 5;  // the block's warps share the roots, one weight each
   const uint32_t gw = blockIdx.x, nw = gridDim.x;
-  constexpr int kSbPoles = kSbBlocks * kMpBlock;
+  constexpr int kSbPoles = kSbRows * kMpBlock;
   for (uint32_t base = gw * 32; base < total; base += nw * 32) {
     const uint32_t r = base + lane;
     int g = 0, j = 0, nb = 0, nsb = 0;
@@ -2152,7 +2350,7 @@ __global__ void __launch_bounds__(96) k_rows_super(RootArgs a) {  // 3 warps: A,
       const MState ms = a.ms[g];
       j = rl - ms.base;
       nb = ((uint32_t(mg.info) & kRootBit) && !a.all_merges) ? 0 : mp_blocks(ms.K, a.mp_min_k);
-      nsb = sb_count(nb);
+      nsb = sb_count_rows(nb);
       head = nsb > 0 && (j % kSbPoles) == 0 && j / kSbPoles < nsb;
     }
     unsigned hm = __ballot_sync(0xffffffffu, head);
@@ -2172,8 +2370,8 @@ __global__ void __launch_bounds__(96) k_rows_super(RootArgs a) {  // 3 warps: A,
       const float* MF = reinterpret_cast<const float*>(MP + kMrFields * nbb);
       double* SP = rows_sb_data(a.MPR + lo, nbb);
       float* SF = reinterpret_cast<float*>(SP + kMrFields * nss);
-      const int b = sb * kSbBlocks + lane;
-      const bool mine = b < nbb && lane < kSbBlocks;
+      const int b = sb * kSbRows + lane;
+      const bool mine = b < nbb && lane < kSbRows;
       if (lane == 0 && which == 0) {
         SP[sb] = m;
         SP[nss + sb] = rad;
@@ -2261,7 +2459,7 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
                                                        unsigned& exact, unsigned& series,
                                                        unsigned long long& sops) {
   const float* MF = reinterpret_cast<const float*>(MP + kMrFields * nb);
-  const int nsb = sb_count(nb);
+  const int nsb = sb_count_rows(nb);
   const double* SP = rows_sb_data(const_cast<double*>(MP), nb);
   const float* SF = reinterpret_cast<const float*>(SP + kMrFields * nsb);
   double s2 = 0.0, sl = 0.0, sh = 0.0;
@@ -2294,7 +2492,7 @@ __device__ __forceinline__ void rows_warp_sweep_blocks(const double* AD, const d
     sops += nfar * (ha + (chains - 1) * hl + 5 + chains);
   }
   for (int b0 = 0; b0 < nb; b0 += 32) {
-    if ((sfar >> (b0 / 32)) & 1u) continue;  // the round went through its superblock
+    if ((sfar >> (b0 / kSbRows)) & 1u) continue;  // the round went through its superblock
     const int b = b0 + lane;
     bool near = false;
     const double dm = b < nb ? (MP[b] - dorg) - tau : 1.0;  // m - lambda
@@ -2462,7 +2660,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   if (plan.step_maxsize[step] >= ra.mp_min_k) {
     k_block_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
     ++launches;
-    if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {
+    if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {  // superblocks possible
       k_super_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
       ++launches;
     }
@@ -2473,7 +2671,8 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
     case 8: k_secular_group<8><<<ggrid, 128, 0, s>>>(ra); break;
     default: k_secular_group<16><<<ggrid, 128, 0, s>>>(ra); break;
   }
-  k_secular_warp<<<wgrid, 128, 0, s>>>(ra);
+  // three resident blocks per SM (168 registers per thread); each warp claims tiles
+  k_secular_warp<<<148 * 3, 128, 0, s>>>(ra);
   }
   prof_end(kKSecular, s);
   if (plan.step_has_nonroot[step] || all_merges) {
@@ -2493,7 +2692,7 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
     if (plan.step_maxsize[step] >= ra.mp_min_k) {
       k_rows_moments<<<int(std::min<int64_t>((nrows + 127) / 128, 148 * 8)), 128, 0, s>>>(ra);
       ++launches;
-      if (plan.step_maxsize[step] >= int64_t(kSbMin) * kMpBlock) {
+      if (plan.step_maxsize[step] >= int64_t(kSbRowsMin) * kMpBlock) {
         k_rows_super<<<int(std::min<int64_t>((nrows + 31) / 32, 148 * 32)), 96, 0, s>>>(ra);
         ++launches;
       }
