@@ -131,9 +131,16 @@ int tde_eigvals_batched(int64_t batch, const int64_t* offsets_host, const int64_
                         const double* d, const double* e, double* lambda, int32_t leaf,
                         void* ws, size_t ws_bytes, void* stream);
 
-/* Workspace for tde_eigvals_backward with the given packing (leaf <= 32). */
+/* Workspace for tde_eigvals_backward with the given packing (leaf <= 32): the
+ * default O(n) layout with 4 checkpoint slots (see tde_eigvals_backward). */
 int tde_eigvals_backward_workspace(int64_t batch, const int64_t* offsets_host, int32_t leaf,
                                    size_t* bytes);
+
+/* Workspace for tde_eigvals_backward with `slots` checkpoint slots (slots >= 1;
+ * slots = 0, or at least the number of merge steps, gives the levels layout that
+ * checkpoints every level).  More slots trade memory for less recomputation. */
+int tde_eigvals_backward_workspace_slots(int64_t batch, const int64_t* offsets_host, int32_t leaf,
+                                         int32_t slots, size_t* bytes);
 
 /* Gradient of a loss of the eigenvalues with respect to d and e (reverse mode),
  * for a packed batch as in tde_eigvals_batched (batch = 1 with offsets {0, n} for
@@ -142,16 +149,22 @@ int tde_eigvals_backward_workspace(int64_t batch, const int64_t* offsets_host, i
  *   lambda      [N]  output: the eigenvalues (may be NULL)
  *   grad_d      [N]  output: dL/dd
  *   grad_e      [N]  output: dL/de (entry at the last row of each matrix is 0)
- * Method: a forward pass that checkpoints the boundary-row state and the secular
- * roots at every tree level, then a reverse sweep over the merges (top-down) that
- * rebuilds each merge from its checkpoints (the roots are restored, not solved
- * again) and pulls the adjoints back through the placement,
- * the secular eigen-decomposition (implicit differentiation of every root and of
- * the Cauchy form of the boundary rows), the deflation and the formation of the
- * merge problem; the leaves use the adjoint of their full eigen-decomposition and
- * the tearing d -= |beta| of Eq. (1).  Deflation decisions and the tree are
- * constants of the differentiation.  Simple (distinct) eigenvalues are assumed.
- * Workspace: O(n log n) (5 n doubles of checkpoint per level). */
+ * Method: implicit differentiation of every merge, in a reverse sweep over the
+ * merge steps (top-down) that rebuilds each merge from the boundary-row state at
+ * its input and pulls the adjoints back through the placement, the secular
+ * eigen-decomposition (implicit differentiation of every root and of the Cauchy
+ * form of the boundary rows), the deflation and the formation of the merge
+ * problem; the leaves use the adjoint of their full eigen-decomposition and the
+ * tearing d -= |beta| of Eq. (1).  Deflation decisions and the tree are constants
+ * of the differentiation.  Simple (distinct) eigenvalues are assumed.
+ * Workspace, chosen from ws_bytes: with the size of
+ * tde_eigvals_backward_workspace (or of tde_eigvals_backward_workspace_slots for S
+ * slots) the states of S levels are checkpointed and the others recomputed
+ * forward in a bisection schedule, each rebuilt merge solving its roots again:
+ * O(n) memory for a fixed S.  A workspace of the levels layout
+ * (tde_eigvals_backward_workspace_slots with slots = 0) checkpoints every level
+ * and every step's roots (O(n log n)) and recomputes nothing.  Both layouts give
+ * the same gradient.  Sizes below the one-slot layout return TDE_EWORKSPACE. */
 int tde_eigvals_backward(int64_t batch, const int64_t* offsets_host, const int64_t* offsets_dev,
                          const double* d, const double* e, const double* grad_lambda,
                          double* lambda, double* grad_d, double* grad_e, int32_t leaf,

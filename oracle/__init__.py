@@ -27,6 +27,8 @@ Contents (each function cites the passage of the paper it follows):
 * ``torn_subproblem`` -- the Cuppen tearing of Eq. (1) / Eq. dc-split.
 * ``grad_dense`` -- dL/dd, dL/de for L = sum_i w_i lambda_i^2 from the dense
   eigenvectors: d lambda_i / d d_j = q_ji^2, d lambda_i / d e_j = 2 q_ji q_(j+1)i.
+* ``grad_dense_spectral`` -- the same for a spectral loss sum_i F(lambda_i), given
+  F' (defined across multiple eigenvalues).
 * ``paper_workspace_bytes`` -- the paper's workspace formulas (Sec. 4.2, Sec. 5.3).
 
 Parity pins for every function live in ``tests/test_oracle.py``.
@@ -331,6 +333,20 @@ def grad_dense(d, e, w):
     simple eigenvalue: d lambda_i = q_i^T dT q_i)."""
     lam, q = eigh_dense(d, e)
     coef = 2.0 * np.asarray(w, dtype=np.float64) * lam
+    gd = (q * q) @ coef
+    ge = 2.0 * ((q[:-1, :] * q[1:, :]) @ coef)
+    return gd, ge
+
+
+def grad_dense_spectral(d, e, fprime):
+    """Gradient of the spectral function L = sum_i F(lambda_i) = trace F(T) with
+    respect to d and e, from the dense eigen-decomposition: dL/dd_j = sum_i
+    F'(lambda_i) q_ji^2 and dL/de_j = 2 sum_i F'(lambda_i) q_ji q_(j+1)i (the first-order
+    perturbation of each eigenvalue; summed over an eigenspace of equal
+    eigenvalues it involves only that eigenspace's projector, so it is defined for
+    multiple eigenvalues too).  ``fprime`` maps the eigenvalues to F'(lambda)."""
+    lam, q = eigh_dense(d, e)
+    coef = np.asarray(fprime(lam), dtype=np.float64)
     gd = (q * q) @ coef
     ge = 2.0 * ((q[:-1, :] * q[1:, :]) @ coef)
     return gd, ge

@@ -270,21 +270,31 @@ def get_tuning() -> dict:
     return {"warp_min_k": int(out[0]), "small_list_min": int(out[1])}
 
 
-def backward_workspace_bytes(offsets, leaf: int = 8) -> int:
-    """Device workspace bytes for tde_eigvals_backward on a packing."""
+def backward_workspace_bytes(offsets, leaf: int = 8, slots: int | None = None) -> int:
+    """Device workspace bytes for tde_eigvals_backward on a packing: the default O(n)
+    layout (4 checkpoint slots) when ``slots`` is None, else the layout with that many
+    slots (0: every level checkpointed, no recomputation)."""
     off = _host_offsets(offsets)
     out = ctypes.c_size_t()
-    _lib.check("tde_eigvals_backward_workspace",
-               _lib.load().tde_eigvals_backward_workspace(off.shape[0] - 1, off.ctypes.data, int(leaf),
-                                                          ctypes.byref(out)))
+    if slots is None:
+        _lib.check("tde_eigvals_backward_workspace",
+                   _lib.load().tde_eigvals_backward_workspace(off.shape[0] - 1, off.ctypes.data,
+                                                              int(leaf), ctypes.byref(out)))
+    else:
+        _lib.check("tde_eigvals_backward_workspace_slots",
+                   _lib.load().tde_eigvals_backward_workspace_slots(
+                       off.shape[0] - 1, off.ctypes.data, int(leaf), int(slots), ctypes.byref(out)))
     return int(out.value)
 
 
 def eigvals_backward(d, e, grad_lambda, offsets=None, leaf: int = 8, ws: Workspace | None = None,
-                     stream=None, check: bool = True, offsets_dev=None, lam_out=None):
+                     stream=None, check: bool = True, offsets_dev=None, lam_out=None,
+                     slots: int | None = None):
     """(lambda, dL/dd, dL/de) for dL/dlambda = grad_lambda, by the adjoint sweep of
     tde_eigvals_backward.  offsets=None means one matrix of order len(d); e is
-    packed like d (the entry at each matrix's last row is ignored, its gradient 0)."""
+    packed like d (the entry at each matrix's last row is ignored, its gradient 0).
+    The workspace layout follows ``slots`` (see backward_workspace_bytes); a
+    caller-provided ``ws`` larger than that picks the layout its size allows."""
     torch = _torch()
     _check_tensor(d, "d")
     _check_tensor(grad_lambda, "grad_lambda")
@@ -304,7 +314,7 @@ def eigvals_backward(d, e, grad_lambda, offsets=None, leaf: int = 8, ws: Workspa
         return lam, gd, ge[:0]
     if offsets_dev is None:
         offsets_dev = torch.from_numpy(off).to(d.device)
-    need = backward_workspace_bytes(off, leaf)
+    need = backward_workspace_bytes(off, leaf, slots)
     ws = Workspace(need, d.device) if ws is None else ws.ensure(need)
     rc = _lib.load().tde_eigvals_backward(
         off.shape[0] - 1, off.ctypes.data, ctypes.c_void_p(offsets_dev.data_ptr()),

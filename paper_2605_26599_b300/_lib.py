@@ -28,7 +28,8 @@ EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspac
            "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning",
            "tde_eigvals_backward_workspace", "tde_eigvals_backward", "tde_eigvecs_rows_workspace",
            "tde_eigvecs_rows", "tde_dense_eigvals_workspace", "tde_dense_eigvals",
-           "tde_set_multipole", "tde_check_rsqrt", "tde_noalloc_get_info")
+           "tde_set_multipole", "tde_check_rsqrt", "tde_noalloc_get_info",
+           "tde_eigvals_backward_workspace_slots")
 
 MAX_SEL_ROWS = 1024  # TDE_MAX_SEL_ROWS
 
@@ -86,6 +87,7 @@ def load() -> ctypes.CDLL:
     lib.tde_check_rsqrt.argtypes = [i64, vp, vp, vp]
     lib.tde_set_tuning.argtypes = [i32, i32]
     lib.tde_eigvals_backward_workspace.argtypes = [i64, vp, i32, szp]
+    lib.tde_eigvals_backward_workspace_slots.argtypes = [i64, vp, i32, i32, szp]
     lib.tde_eigvals_backward.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp, sz, vp]
     lib.tde_get_tuning.argtypes = [ctypes.POINTER(ctypes.c_int32)]
     lib.tde_set_multipole.argtypes = [i32, ctypes.POINTER(ctypes.c_int32)]

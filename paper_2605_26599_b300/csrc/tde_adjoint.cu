@@ -46,9 +46,23 @@
 //      e_bar_i = 2 A_bar_i,i+1, and the tearing d_cut -= |beta| gives
 //      e_bar_cut -= sgn(beta) (d_bar of the two torn diagonal entries).
 // Deflation decisions, the tree and the scaling are constants of the
-// differentiation (eigenvalue derivatives are scale invariant).  Memory: the
-// checkpoints hold 5 n doubles per merge step (n log n overall); every other
-// buffer is O(n).
+// differentiation (eigenvalue derivatives are scale invariant).
+// Memory.  Reversing merge step s needs the boundary-row state at its input
+// (level s).  Two layouts, chosen from the caller's workspace size:
+//   * slots (the default, O(n)): S checkpoint slots of one level state each
+//     (3 n doubles; S = 4 by default, at least 1).  Levels are reversed by
+//     bisection: to reverse steps [lo, hi) from the state of level lo, the state
+//     of level mid = lo + ceil((hi - lo) / 2) is recomputed forward into the next
+//     slot, [mid, hi) is reversed from it, then [lo, mid); with no slot left the
+//     steps of a segment are reversed one by one, each from a forward
+//     recomputation into the scratch level.  The first forward pass already stores
+//     the levels of the schedule's first descent (0, L/2, 3L/4, ...), so the costly
+//     top steps are never recomputed.  Each reversed step solves its secular roots
+//     again while rebuilding its merge;
+//   * levels (when the workspace holds them): the state at every level and every
+//     step's roots (tau, D_org) are checkpointed in the forward pass (5 n doubles
+//     per step, O(n log n)); the rebuild restores the roots instead of solving.
+// Both give the same gradient.  Every other buffer is O(n).
 #include <algorithm>
 
 #include "tde_internal.cuh"
@@ -59,8 +73,10 @@ constexpr int kMaxBwdLeaf = 32;
 
 struct AdjWorkspace {
   Workspace fw;
-  double* CK;                          // steps x 3 x N checkpoints
-  double* CR;                          // steps x 2 x N saved roots (tau, D_org)
+  int slots;                           // checkpoint slots (levels layout: one per step)
+  bool levels;                         // every level's state and roots checkpointed
+  double* CK;                          // slots x 3 x N level states
+  double* CR;                          // levels layout: steps x 2 x N saved roots (tau, D_org)
   double *GL, *GBL, *GBH;              // adjoint of the current level's state
   double *ALB, *ABL, *ABH;             // adjoints of a merge's [active | deflated] outputs
   double *RLT, *RAL, *RBE, *RGA, *RINU, *RC;  // per active root: g, h, scratch, 1/nu, 2 lbar c + h
@@ -74,19 +90,26 @@ struct AdjWorkspace {
 
 static size_t align_up_adj(size_t x) { return (x + 255) & ~size_t(255); }
 
-size_t carve_adjoint(const Plan& plan, void* base, AdjWorkspace* aw) {
+constexpr int kDefaultSlots = 4;
+
+// Workspace of the adjoint: the forward workspace, the checkpoints (levels layout
+// when levels is true, else `slots` level states), then the O(n) adjoint arrays.
+size_t carve_adjoint(const Plan& plan, void* base, AdjWorkspace* aw, bool levels, int slots) {
   AdjWorkspace w{};
   size_t off = carve_workspace(plan, base, &w.fw);
   off = align_up_adj(off);
   const size_t N = size_t(std::max<int64_t>(plan.nrows, 1));
+  const int steps = std::max(plan.steps, 1);
+  w.levels = levels;
+  w.slots = levels ? steps : std::max(1, std::min(slots, steps));
   char* b = static_cast<char*>(base);
   auto take = [&](size_t bytes) -> double* {
     double* p = b ? reinterpret_cast<double*>(b + off) : nullptr;
     off += align_up_adj(bytes);
     return p;
   };
-  w.CK = take(8 * N * 3 * size_t(std::max(plan.steps, 1)));
-  w.CR = take(8 * N * 2 * size_t(std::max(plan.steps, 1)));
+  w.CK = take(8 * N * 3 * size_t(w.slots));
+  w.CR = levels ? take(8 * N * 2 * size_t(steps)) : nullptr;
   double** arrs[] = {&w.GL,  &w.GBL, &w.GBH, &w.ALB,  &w.ABL, &w.ABH, &w.RLT,  &w.RAL,
                      &w.RBE, &w.RGA, &w.RINU, &w.RC,  &w.PDB, &w.PZB, &w.PRLB, &w.PRHB,
                      &w.MDB, &w.MZB, &w.MRLB, &w.MRHB, &w.KBAR, &w.LAMOUT};
@@ -97,10 +120,6 @@ size_t carve_adjoint(const Plan& plan, void* base, AdjWorkspace* aw) {
   return off;
 }
 
-static LevelState checkpoint(const AdjWorkspace& w, int s, int64_t N) {
-  double* base = w.CK + size_t(s) * 3 * size_t(N);
-  return LevelState{base, base + N, base + 2 * N};
-}
 
 struct AdjArgs {
   const Merge* M;
@@ -592,6 +611,129 @@ __global__ void k_adj_init(int64_t nrows, const double* __restrict__ grad_lambda
 void launch_leaves_to(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s,
                       LevelState out);
 
+// Reverses merge step st: rebuilds its merge internals from the state `in` of
+// level st (the roots restored from `roots` when given, else solved again) and
+// pulls the adjoints of the parents' state back to the children's.
+static void adjoint_step(const Plan& plan, const AdjWorkspace& w, int st, LevelState in,
+                         const RootsCheckpoint* roots, double* lambda, double* grad_e,
+                         cudaStream_t s) {
+  const Workspace& ws = w.fw;
+  const int64_t N = plan.nrows;
+  const Merge* M = ws.merges + plan.step_base[st];
+  const int64_t cnt = plan.step_count[st];
+  cudaMemsetAsync(&ws.status->root_count[st], 0, 4, s);
+  cudaMemsetAsync(&ws.status->root_count_big[st], 0, 4, s);
+  cudaMemsetAsync(w.RHOBAR, 0, 8 * size_t(cnt), s);
+  const LevelState scratch{ws.LAM, ws.BLO, ws.BHI};
+  launch_step(plan, ws, st, lambda, s, in, scratch, /*recompute=*/true, nullptr, w.RINU, roots);
+  AdjArgs a;
+  a.M = M;
+  a.cnt = cnt;
+  a.nrows = N;
+  a.ms = ws.mstate;
+  a.ROOTMAP = ws.ROOTMAP;
+  a.ROOTMAP2 = ws.ROOTMAP2;
+  a.count = &ws.status->root_count[st];
+  a.count2 = &ws.status->root_count_big[st];
+  a.LAMA = ws.D;
+  a.AD = ws.AD;
+  a.AZ = ws.AZ;
+  a.ALO = ws.ALO;
+  a.AHI = ws.AHI;
+  a.TAU = ws.TAU;
+  a.DORG = reinterpret_cast<const double*>(ws.KEYA);
+  a.ZHAT = ws.Z;
+  a.ROWLO = ws.RLO;
+  a.ROWHI = ws.RHI;
+  a.D = ws.D;
+  a.Z = ws.Z;
+  a.RLO = ws.RLO;
+  a.RHI = ws.RHI;
+  a.es = ws.es;
+  a.SURV = ws.SURV;
+  a.OUTIDX = ws.OUTIDX;
+  a.ACTMAP = ws.ACTMAP;
+  a.KEEPIDX = ws.KEEPIDX;
+  a.PFLAG = ws.PFLAG;
+  a.RFLAG = ws.RFLAG;
+  a.in = in;
+  a.w = w;
+  a.grad_e = grad_e;
+  const int flat = int(std::min<int64_t>((N + 255) / 256, 148 * 8));
+  const int ggrid = int(std::min<int64_t>((N * 4 + 127) / 128, 148 * 16));
+  k_adj_place<<<flat, 256, 0, s>>>(a);
+  k_adj_pairs<4><<<ggrid, 128, 0, s>>>(a, 0);
+  k_adj_pairs<32><<<148 * 8, 128, 0, s>>>(a, 1);
+  k_adj_poles<4><<<ggrid, 128, 0, s>>>(a, 0);
+  k_adj_poles<32><<<148 * 8, 128, 0, s>>>(a, 1);
+  k_adj_kappa<<<148 * 8, 128, 0, s>>>(a);
+  launch_form(plan, ws, st, in, s);  // restore D, z, RLO, RHI of the merge problem
+  const int dgrid = int(std::min<int64_t>(cnt, 148 * 8));
+  k_adj_deflate<<<dgrid, 256, 0, s>>>(a);
+  k_adj_form<<<flat, 256, 0, s>>>(a);
+  g_launches += 9;
+}
+
+// Copies level state a to b (three arrays of n doubles).
+static int copy_state(LevelState src, LevelState dst, int64_t N, cudaStream_t s) {
+  const size_t bytes = 8 * size_t(N);
+  if (cudaMemcpyAsync(dst.lam, src.lam, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dst.blo, src.blo, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(dst.bhi, src.bhi, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return TDE_ECUDA;
+  return TDE_OK;
+}
+
+// Bisection schedule of the slots layout (see the file header).
+struct Reverser {
+  const Plan& plan;
+  const AdjWorkspace& w;
+  double* lambda;
+  double* grad_e;
+  cudaStream_t s;
+  int rc = TDE_OK;
+  LevelState slot(int k) const {
+    const int64_t N = plan.nrows;
+    double* base = w.CK + size_t(k) * 3 * size_t(N);
+    return LevelState{base, base + N, base + 2 * N};
+  }
+  // the state of level `to` into dst (in place), from the state of level `from` in src;
+  // each recomputed step's root lists start empty again (its deflation appends to them)
+  void forward(LevelState src, int from, LevelState dst, int to) {
+    if (rc == TDE_OK) rc = copy_state(src, dst, plan.nrows, s);
+    for (int k = from; k < to; ++k) {
+      if (cudaMemsetAsync(&w.fw.status->root_count[k], 0, 4, s) != cudaSuccess ||
+          cudaMemsetAsync(&w.fw.status->root_count_big[k], 0, 4, s) != cudaSuccess)
+        rc = TDE_ECUDA;
+      launch_step(plan, w.fw, k, lambda, s, dst, dst);
+    }
+  }
+  static int mid_of(int lo, int hi) { return lo + (hi - lo + 1) / 2; }
+  // reverses steps [lo, hi) from the state of level lo held in slot sl; slots
+  // sl + 1 ... hold the first descent's levels when `primed` (filled by the first
+  // forward pass), else they are free
+  void run(int lo, int hi, int sl, bool primed) {
+    if (hi <= lo) return;
+    if (hi - lo == 1) {
+      adjoint_step(plan, w, lo, slot(sl), nullptr, lambda, grad_e, s);
+      return;
+    }
+    if (sl + 1 >= w.slots) {  // no free slot: each step from a recomputation into the scratch level
+      const LevelState scratch{w.fw.LAM, w.fw.BLO, w.fw.BHI};
+      for (int st = hi - 1; st > lo; --st) {
+        forward(slot(sl), lo, scratch, st);
+        adjoint_step(plan, w, st, scratch, nullptr, lambda, grad_e, s);
+      }
+      adjoint_step(plan, w, lo, slot(sl), nullptr, lambda, grad_e, s);
+      return;
+    }
+    const int mid = mid_of(lo, hi);
+    if (!primed) forward(slot(sl), lo, slot(sl + 1), mid);
+    run(mid, hi, sl + 1, primed);
+    run(lo, mid, sl, false);
+  }
+};
+
 int run_adjoint(const Plan& plan, const AdjWorkspace& w, const int64_t* offsets_dev,
                 const double* d, const double* e, const double* grad_lambda, double* lambda,
                 double* grad_d, double* grad_e, cudaStream_t s) {
@@ -601,87 +743,70 @@ int run_adjoint(const Plan& plan, const AdjWorkspace& w, const int64_t* offsets_
   if (cudaMemsetAsync(ws.status, 0, sizeof(Status), s) != cudaSuccess) return TDE_ECUDA;
   if (cudaMemsetAsync(ws.sigma_bits, 0, 8 * size_t(plan.batch), s) != cudaSuccess)
     return TDE_ECUDA;
-  // 1. forward with checkpoints
+  const LevelState scratch{ws.LAM, ws.BLO, ws.BHI};
+  Reverser rv{plan, w, lambda, grad_e, s};
+  // 1. forward pass: the eigenvalues, and the checkpoints
   launch_plan(plan, ws, offsets_dev, s);
   launch_scale(plan, ws, offsets_dev, d, e, s);
-  const LevelState scratch{ws.LAM, ws.BLO, ws.BHI};
-  launch_leaves_to(plan, ws, lambda, s, plan.steps > 0 ? checkpoint(w, 0, N) : scratch);
-  for (int st = 0; st < plan.steps; ++st) {
-    const LevelState out = st + 1 < plan.steps ? checkpoint(w, st + 1, N) : scratch;
-    launch_step(plan, ws, st, lambda, s, checkpoint(w, st, N), out);
-    double* cr = w.CR + size_t(st) * 2 * size_t(N);
-    if (cudaMemcpyAsync(cr, ws.TAU, 8 * size_t(N), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(cr + N, ws.KEYA, 8 * size_t(N), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      return TDE_ECUDA;
+  launch_leaves_to(plan, ws, lambda, s, plan.steps > 0 ? rv.slot(0) : scratch);
+  if (w.levels) {
+    for (int st = 0; st < plan.steps; ++st) {
+      const LevelState out = st + 1 < plan.steps ? rv.slot(st + 1) : scratch;
+      launch_step(plan, ws, st, lambda, s, rv.slot(st), out);
+      double* cr = w.CR + size_t(st) * 2 * size_t(N);
+      if (cudaMemcpyAsync(cr, ws.TAU, 8 * size_t(N), cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+          cudaMemcpyAsync(cr + N, ws.KEYA, 8 * size_t(N), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return TDE_ECUDA;
+    }
+  } else if (plan.steps > 0) {
+    // in place on the scratch level; the levels of the schedule's first descent
+    // (0, then mid of [previous, steps), ...) are copied into slots 1, 2, ...
+    if (copy_state(rv.slot(0), scratch, N, s) != TDE_OK) return TDE_ECUDA;
+    int next_slot = 1, lo = 0;
+    int want = (w.slots > 1 && plan.steps > 1) ? Reverser::mid_of(0, plan.steps) : -1;
+    for (int st = 0; st < plan.steps; ++st) {
+      launch_step(plan, ws, st, lambda, s, scratch, scratch);
+      if (st + 1 == want) {
+        if (copy_state(scratch, rv.slot(next_slot), N, s) != TDE_OK) return TDE_ECUDA;
+        ++next_slot;
+        lo = want;
+        want = (next_slot < w.slots && plan.steps - lo > 1) ? Reverser::mid_of(lo, plan.steps) : -1;
+      }
+    }
   }
   const int flat = int(std::min<int64_t>((N + 255) / 256, 148 * 8));
   k_adj_init<<<flat, 256, 0, s>>>(N, grad_lambda, w.GL, w.GBL, w.GBH, grad_e);
   g_launches += 1;
   // 2. reverse sweep
-  for (int st = plan.steps - 1; st >= 0; --st) {
-    const Merge* M = ws.merges + plan.step_base[st];
-    const int64_t cnt = plan.step_count[st];
-    if (cudaMemsetAsync(&ws.status->root_count[st], 0, 4, s) != cudaSuccess) return TDE_ECUDA;
-    if (cudaMemsetAsync(&ws.status->root_count_big[st], 0, 4, s) != cudaSuccess) return TDE_ECUDA;
-    if (cudaMemsetAsync(w.RHOBAR, 0, 8 * size_t(cnt), s) != cudaSuccess) return TDE_ECUDA;
-    const LevelState in = checkpoint(w, st, N);
-    const double* cr = w.CR + size_t(st) * 2 * size_t(N);
-    const RootsCheckpoint roots{cr, cr + N};
-    launch_step(plan, ws, st, lambda, s, in, scratch, /*recompute=*/true, nullptr, w.RINU, &roots);
-    AdjArgs a;
-    a.M = M;
-    a.cnt = cnt;
-    a.nrows = N;
-    a.ms = ws.mstate;
-    a.ROOTMAP = ws.ROOTMAP;
-    a.ROOTMAP2 = ws.ROOTMAP2;
-    a.count = &ws.status->root_count[st];
-    a.count2 = &ws.status->root_count_big[st];
-    a.LAMA = ws.D;
-    a.AD = ws.AD;
-    a.AZ = ws.AZ;
-    a.ALO = ws.ALO;
-    a.AHI = ws.AHI;
-    a.TAU = ws.TAU;
-    a.DORG = reinterpret_cast<const double*>(ws.KEYA);
-    a.ZHAT = ws.Z;
-    a.ROWLO = ws.RLO;
-    a.ROWHI = ws.RHI;
-    a.D = ws.D;
-    a.Z = ws.Z;
-    a.RLO = ws.RLO;
-    a.RHI = ws.RHI;
-    a.es = ws.es;
-    a.SURV = ws.SURV;
-    a.OUTIDX = ws.OUTIDX;
-    a.ACTMAP = ws.ACTMAP;
-    a.KEEPIDX = ws.KEEPIDX;
-    a.PFLAG = ws.PFLAG;
-    a.RFLAG = ws.RFLAG;
-    a.in = in;
-    a.w = w;
-    a.grad_e = grad_e;
-    const int ggrid = int(std::min<int64_t>((N * 4 + 127) / 128, 148 * 16));
-    k_adj_place<<<flat, 256, 0, s>>>(a);
-    k_adj_pairs<4><<<ggrid, 128, 0, s>>>(a, 0);
-    k_adj_pairs<32><<<148 * 8, 128, 0, s>>>(a, 1);
-    k_adj_poles<4><<<ggrid, 128, 0, s>>>(a, 0);
-    k_adj_poles<32><<<148 * 8, 128, 0, s>>>(a, 1);
-    k_adj_kappa<<<148 * 8, 128, 0, s>>>(a);
-    launch_form(plan, ws, st, in, s);  // restore D, z, RLO, RHI of the merge problem
-    const int dgrid = int(std::min<int64_t>(cnt, 148 * 8));
-    k_adj_deflate<<<dgrid, 256, 0, s>>>(a);
-    k_adj_form<<<flat, 256, 0, s>>>(a);
-    g_launches += 9;
+  if (w.levels) {
+    for (int st = plan.steps - 1; st >= 0; --st) {
+      const double* cr = w.CR + size_t(st) * 2 * size_t(N);
+      const RootsCheckpoint roots{cr, cr + N};
+      adjoint_step(plan, w, st, rv.slot(st), &roots, lambda, grad_e, s);
+    }
+  } else {
+    rv.run(0, plan.steps, 0, true);
+    if (rv.rc != TDE_OK) return rv.rc;
   }
   // 3. leaves
   const int lgrid = int(std::min<int64_t>((plan.nleaves + 63) / 64, 148 * 32));
-  const LevelState leafstate = plan.steps > 0 ? checkpoint(w, 0, N) : scratch;
+  const LevelState leafstate = plan.steps > 0 ? rv.slot(0) : scratch;
   k_adj_leaves<<<std::max(lgrid, 1), 64, 0, s>>>(ws.leaves, plan.nleaves, ws.ds, ws.es, w.GL,
                                                   w.GBL, w.GBH, leafstate, grad_d, grad_e,
                                                   ws.status);
   g_launches += 1;
   return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
+}
+
+// Bytes of the slots layout with `slots` checkpoint slots, and of the levels layout.
+static int backward_sizes(int64_t batch, const int64_t* offsets_host, int32_t leaf, int slots,
+                          Plan* p, size_t* slots_bytes, size_t* levels_bytes) {
+  int rc = build_plan(batch, offsets_host, leaf, p);
+  if (rc != TDE_OK) return rc;
+  if (p->leaf > kMaxBwdLeaf) return TDE_EINVAL;
+  if (slots_bytes) *slots_bytes = carve_adjoint(*p, nullptr, nullptr, false, slots);
+  if (levels_bytes) *levels_bytes = carve_adjoint(*p, nullptr, nullptr, true, 0);
+  return TDE_OK;
 }
 
 }  // namespace tde
@@ -692,10 +817,17 @@ extern "C" int tde_eigvals_backward_workspace(int64_t batch, const int64_t* offs
                                               int32_t leaf, size_t* bytes) {
   if (bytes == nullptr) return TDE_EINVAL;
   Plan p;
-  int rc = build_plan(batch, offsets_host, leaf, &p);
+  return backward_sizes(batch, offsets_host, leaf, kDefaultSlots, &p, bytes, nullptr);
+}
+
+extern "C" int tde_eigvals_backward_workspace_slots(int64_t batch, const int64_t* offsets_host,
+                                                    int32_t leaf, int32_t slots, size_t* bytes) {
+  if (bytes == nullptr || slots < 0) return TDE_EINVAL;
+  Plan p;
+  size_t sb = 0, lb = 0;
+  const int rc = backward_sizes(batch, offsets_host, leaf, slots == 0 ? 1 : slots, &p, &sb, &lb);
   if (rc != TDE_OK) return rc;
-  if (p.leaf > kMaxBwdLeaf) return TDE_EINVAL;
-  *bytes = carve_adjoint(p, nullptr, nullptr);
+  *bytes = (slots == 0 || slots >= p.steps) ? lb : sb;
   return TDE_OK;
 }
 
@@ -706,17 +838,24 @@ extern "C" int tde_eigvals_backward(int64_t batch, const int64_t* offsets_host,
                                     void* stream) {
   g_launches = 0;
   Plan p;
-  int rc = build_plan(batch, offsets_host, leaf, &p);
+  size_t one = 0, lb = 0;
+  int rc = backward_sizes(batch, offsets_host, leaf, 1, &p, &one, &lb);
   if (rc != TDE_OK) return rc;
-  if (p.leaf > kMaxBwdLeaf) return TDE_EINVAL;
   if (p.nrows == 0) return TDE_OK;
   if (offsets_dev == nullptr || d == nullptr || grad_lambda == nullptr || grad_d == nullptr ||
       grad_e == nullptr || ws == nullptr || (p.nrows > 1 && e == nullptr))
     return TDE_EINVAL;
   if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return TDE_EINVAL;
+  if (ws_bytes < one) return TDE_EWORKSPACE;
+  // the levels layout when it fits, else as many slots as fit
+  const bool levels = ws_bytes >= lb;
+  int slots = 1;
+  if (!levels)
+    while (slots + 1 < std::max(p.steps, 1) &&
+           carve_adjoint(p, nullptr, nullptr, false, slots + 1) <= ws_bytes)
+      ++slots;
   AdjWorkspace w;
-  size_t need = carve_adjoint(p, ws, &w);
-  if (ws_bytes < need) return TDE_EWORKSPACE;
+  carve_adjoint(p, ws, &w, levels, slots);
   return run_adjoint(p, w, offsets_dev, d, e, grad_lambda, lambda, grad_d, grad_e,
                      static_cast<cudaStream_t>(stream));
 }

@@ -380,6 +380,9 @@ void launch_sel_gather(const SelArgs& sa, const int32_t* MAP, int64_t nsel, int6
 
 // One merge step: reads the children's state from `in` and writes the parents'
 // state to `out` (in == out is allowed: a merge's children occupy its own rows).
+// The step's two root-list counters (Status::root_count[step], root_count_big[step])
+// must be zero on entry: the deflation appends the roots of every merge to them, so
+// a caller that runs a step again first clears them.
 // With recompute = true only the merge internals are rebuilt (no place): used by
 // the adjoint, which also forces z-hat and rows at root merges.  With `sel` the
 // requested eigenvector rows are carried through the step as well (z-hat and the

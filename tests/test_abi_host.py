@@ -162,3 +162,20 @@ def test_noalloc_array_holds_every_accepted_call():
             assert lib.tde_eigvals_workspace(n, leaf, ctypes.byref(sz)) == _lib.TDE_OK
             worst = max(worst, sz.value)
     assert worst <= 4 << 20, worst
+
+
+def test_backward_workspace_default_is_o_n():
+    # the adjoint's default workspace keeps a fixed number of checkpoint slots: its
+    # bytes per row stay below 512 and flat in n; more slots or the every-level
+    # layout cost more, the one-slot layout less
+    import paper_2605_26599_b300 as tde
+
+    flat = [tde.backward_workspace_bytes([0, n], 8) / n for n in (1 << 13, 1 << 16, 1 << 20)]
+    assert max(flat) <= 512 and max(flat) - min(flat) <= 4
+    assert tde.backward_workspace_bytes([0, 1000], 8) <= 512 * 1000  # 256-byte alignment of ~30 arrays
+    n = 1 << 16
+    sizes = [tde.backward_workspace_bytes([0, n], 8, slots=s) for s in (1, 2, 4, 8)]
+    assert sizes == sorted(sizes) and sizes[2] == tde.backward_workspace_bytes([0, n], 8)
+    assert tde.backward_workspace_bytes([0, n], 8, slots=0) > sizes[-1]
+    off = np.arange(257, dtype=np.int64) * 8192
+    assert tde.backward_workspace_bytes(off, 8) <= 512 * int(off[-1])

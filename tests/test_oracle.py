@@ -367,3 +367,35 @@ def test_paper_error_metrics_hand_values(oracle_mod):
     assert oracle_mod.e_bwd([1.0, 2.5, -3.0], [1.0, 2.0, -4.0], d, e) == 1.0 / 7.0
     small = np.array([0.1, 0.1]), np.array([0.2])  # ||T||_1 = 0.3 < 1: floor 1
     assert oracle_mod.e_bwd([0.0, 0.5], [0.0, 0.25], *small) == 0.25
+
+
+def test_grad_dense_spectral_closed_forms_and_finite_differences(oracle_mod):
+    # F(x) = x^2: L = trace(T^2) = sum d^2 + 2 sum e^2, gradient (2 d, 4 e) exactly;
+    # F(x) = x: L = trace(T), gradient (1, 0)
+    for fam in ("wilkinson", "glued_wilkinson", "uniform11"):
+        d, e = inputs.family(fam, 45, seed=2)
+        e = e[:44]
+        gd, ge = oracle_mod.grad_dense_spectral(d, e, lambda x: 2.0 * x)
+        assert np.abs(gd - 2 * d).max() < 1e-12 * max(1, np.abs(d).max())
+        assert np.abs(ge - 4 * e).max() < 1e-12 * max(1, np.abs(d).max())
+        gd, ge = oracle_mod.grad_dense_spectral(d, e, np.ones_like)
+        assert np.abs(gd - 1).max() < 1e-13 and np.abs(ge).max() < 1e-13
+    # F(x) = sin x + x^2 / 2: central differences of sum F(lambda) from the bisection oracle
+    d, e = inputs.normal_absnormal(30, seed=8, e_scale=0.5)
+    gd, ge = oracle_mod.grad_dense_spectral(d, e, lambda x: np.cos(x) + x)
+
+    def L(dd, ee):
+        lam = oracle_mod.eigvals_bisect(dd, ee)
+        return float(np.sum(np.sin(lam) + 0.5 * lam * lam))
+
+    h = 1e-6
+    for j in (0, 13, 29):
+        dp, dm = d.copy(), d.copy()
+        dp[j] += h
+        dm[j] -= h
+        assert abs((L(dp, e) - L(dm, e)) / (2 * h) - gd[j]) < 1e-6
+    for j in (0, 17, 28):
+        ep, em = e.copy(), e.copy()
+        ep[j] += h
+        em[j] -= h
+        assert abs((L(d, ep) - L(d, em)) / (2 * h) - ge[j]) < 1e-6
