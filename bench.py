@@ -733,6 +733,13 @@ def configs_section(args, dev) -> dict:
         "ms": ms, "eigvals_per_s": 2048 / (ms * 1e-3), "leaf": 32, "workspace_bytes": wsb,
         "max_err_all": float(np.abs(lam - ref).max()),
         "max_err_all_over_gate": float(np.abs(lam - ref).max()) / gate, "device_status": info}
+    # the same matrix with the default leaf order (the leaf QR is a chain of dependent
+    # FP64 operations, so shorter leaves and more merge levels win on this part)
+    ms8, lam8, info8, wsb8 = _time_solve(tde, torch.from_numpy(d).to(dev), torch.from_numpy(e).to(dev),
+                                         args.leaf, reps=max(args.steps, 5))
+    res["n2048_uniform11_default_leaf"] = {
+        "ms": ms8, "eigvals_per_s": 2048 / (ms8 * 1e-3), "leaf": args.leaf,
+        "max_err_all_over_gate": float(np.abs(lam8 - ref).max()) / gate, "device_status": info8}
     for n in (131072, 262144):
         for fam in ("normal", "graded"):
             d, e = inputs.family(fam, n, seed=0)

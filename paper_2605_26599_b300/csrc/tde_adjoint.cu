@@ -485,29 +485,20 @@ __device__ bool leaf_qr_full(int m, double* a, double* b, double* Q) {
     if (!isfinite(mu)) mu = a[hi];
     double x = a[lo] - mu, y = b[lo];
     for (int i = lo; i < hi; ++i) {
-      const double r = sqrt(x * x + y * y);
-      double c = 1.0, s = 0.0;
-      if (r > 0.0) {  // the same arithmetic as the forward leaf solver
-        const double inv = 1.0 / r;
-        c = x * inv;
-        s = y * inv;
-      }
+      double c, s, r;
+      leaf_givens(x, y, c, s, r);  // the same rotation as the forward leaf solver
       if (i > lo) b[i - 1] = r;
-      const double ai = a[i], aj = a[i + 1], bi = b[i];
-      const double cc = c * c, ss = s * s, cs = c * s;
-      a[i] = cc * ai + 2.0 * cs * bi + ss * aj;
-      a[i + 1] = ss * ai - 2.0 * cs * bi + cc * aj;
-      b[i] = cs * (aj - ai) + (cc - ss) * bi;
+      leaf_rotate(c, s, a[i], a[i + 1], b[i], a[i], a[i + 1], b[i]);
       if (i + 1 < hi) {
         const double bn = b[i + 1];
         y = s * bn;
         b[i + 1] = c * bn;
         x = b[i];
       }
-      for (int r0 = 0; r0 < m; ++r0) {
+      for (int r0 = 0; r0 < m; ++r0) {  // the tracked rows' update of the forward, every row
         const double p = Q[r0 * kMaxBwdLeaf + i], q = Q[r0 * kMaxBwdLeaf + i + 1];
-        Q[r0 * kMaxBwdLeaf + i] = c * p + s * q;
-        Q[r0 * kMaxBwdLeaf + i + 1] = c * q - s * p;
+        Q[r0 * kMaxBwdLeaf + i] = fma(c, p, s * q);
+        Q[r0 * kMaxBwdLeaf + i + 1] = fma(c, q, -(s * p));
       }
     }
   }

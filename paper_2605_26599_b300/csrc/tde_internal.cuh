@@ -431,6 +431,42 @@ __device__ __forceinline__ double rsqrt_refined(double x) {
   return fma(y, e * fma(e, 0.375, 0.5), y);
 }
 
+// Plane rotation of the leaf QR sweeps: (c, s) = (x, y) / r with r = sqrt(x^2 + y^2),
+// formed from r^2 (one fused multiply-add) and its refined reciprocal square root
+// (c = x / r, s = y / r, r = r^2 / r) instead of an IEEE square root and division,
+// whose dependent latencies (hundreds of cycles each on this part's FP64 units)
+// would dominate the chain of a bulge chase.  The identity (1, 0, 0) when r^2 is
+// zero or below the normal range, where both entries are negligible next to the
+// scaled matrix (whose largest entry lies in [1, 2)).  Every leaf QR (the forward
+// solver, the requested-row leaves and the adjoint's full-Q leaves) uses this one
+// function, so all of them apply bitwise the same rotations.
+__device__ __forceinline__ void leaf_givens(double x, double y, double& c, double& s, double& r) {
+  const double r2 = fma(x, x, y * y);
+  if (r2 >= 2.2250738585072014e-308) {  // DBL_MIN
+    const double inv = rsqrt_refined(r2);
+    c = x * inv;
+    s = y * inv;
+    r = r2 * inv;
+  } else {
+    c = 1.0;
+    s = 0.0;
+    r = 0.0;
+  }
+}
+
+// Similarity T <- G^T T G of one bulge-chase rotation on the 2 x 2 block
+// [[ai, bi], [bi, aj]] of the leaf tridiagonal: the new diagonal pair and coupling.
+// Written with explicit fused multiply-adds so that every leaf QR (forward,
+// requested rows, adjoint) rounds identically.
+__device__ __forceinline__ void leaf_rotate(double c, double s, double ai, double aj, double bi,
+                                            double& ai_out, double& aj_out, double& bi_out) {
+  const double cc = c * c, ss = s * s, cs = c * s;
+  const double t = 2.0 * (cs * bi);
+  ai_out = fma(cc, ai, fma(ss, aj, t));
+  aj_out = fma(ss, ai, fma(cc, aj, -t));
+  bi_out = fma(cs, aj - ai, (cc - ss) * bi);
+}
+
 extern thread_local int64_t g_launches;
 
 }  // namespace tde

@@ -10,8 +10,11 @@
 // Q = G_1 G_2 ..., and by the selected-row lemma (Lemma "selected-row
 // multiplication") its first and last rows are obtained by applying the same
 // rotations to e_1^T and e_m^T only -- the leaf never forms Q.
-// One thread owns one leaf; the outputs are the eigenvalues in ascending order
-// with the matching first-row (blo) and last-row (bhi) entries.
+// One thread owns one leaf (warps hold one to 32 leaves, see k_leaves); the
+// outputs are the eigenvalues in ascending order with the matching first-row (blo)
+// and last-row (bhi) entries.
+#include <algorithm>
+
 #include "tde_internal.cuh"
 
 namespace tde {
@@ -49,47 +52,59 @@ __device__ __noinline__ bool leaf_qr_two_rows(int m, double* a, double* b, doubl
     double root = sqrt(half * half + bh * bh);
     double mu = a[hi] - bh * bh / (half + (half >= 0.0 ? root : -root));
     if (!isfinite(mu)) mu = a[hi];
-    // first rotation from the first column of T - mu I, then chase the bulge
-    double x = a[lo] - mu, y = b[lo];
+    // first rotation from the first column of T - mu I, then chase the bulge.  The
+    // entries one rotation hands to the next (the new a[i+1], b[i+1] and the tracked
+    // rows' entries at column i+1) stay in registers: only entries the chase has not
+    // touched yet are loaded, so the chain of rotations never waits on a local-memory
+    // round trip.
+    double ai = a[lo], bi = b[lo], p0 = r0[lo], p1 = r1[lo];
+    double x = ai - mu, y = bi;
     *rot += unsigned(hi - lo);
     for (int i = lo; i < hi; ++i) {
-      double r = sqrt(x * x + y * y);
-      double c = 1.0, s = 0.0;
-      if (r > 0.0) {
-        double inv = 1.0 / r;
-        c = x * inv;
-        s = y * inv;
-      }
+      double c, s, r;
+      leaf_givens(x, y, c, s, r);
       if (i > lo) b[i - 1] = r;  // the bulge is annihilated into the coupling
-      double ai = a[i], aj = a[i + 1], bi = b[i];
-      double cc = c * c, ss = s * s, cs = c * s;
-      a[i] = cc * ai + 2.0 * cs * bi + ss * aj;
-      a[i + 1] = ss * ai - 2.0 * cs * bi + cc * aj;
-      b[i] = cs * (aj - ai) + (cc - ss) * bi;
+      const double aj = a[i + 1], q0 = r0[i + 1], q1 = r1[i + 1];
+      double na, naj, nb;
+      leaf_rotate(c, s, ai, aj, bi, na, naj, nb);
+      a[i] = na;
+      ai = naj;
       if (i + 1 < hi) {
-        double bn = b[i + 1];
+        const double bn = b[i + 1];
         y = s * bn;  // new bulge at (i, i+2)
-        b[i + 1] = c * bn;
-        x = b[i];
+        bi = c * bn;
+        x = nb;
+      } else {
+        b[i] = nb;
       }
       // Q <- Q G_i on columns (i, i+1) for the two tracked rows
-      double p0 = r0[i], q0 = r0[i + 1];
-      r0[i] = c * p0 + s * q0;
-      r0[i + 1] = c * q0 - s * p0;
-      double p1 = r1[i], q1 = r1[i + 1];
-      r1[i] = c * p1 + s * q1;
-      r1[i + 1] = c * q1 - s * p1;
+      r0[i] = fma(c, p0, s * q0);
+      p0 = fma(c, q0, -(s * p0));
+      r1[i] = fma(c, p1, s * q1);
+      p1 = fma(c, q1, -(s * p1));
     }
+    a[hi] = ai;
+    r0[hi] = p0;
+    r1[hi] = p1;
   }
   return true;
 }
 
-__global__ void k_leaves(const Leaf* __restrict__ leaves, int64_t nleaves,
-                         const double* __restrict__ ds, const double* __restrict__ es,
-                         const unsigned long long* __restrict__ sigma_bits, double* LAM,
-                         double* BLO, double* BHI, double* out, Status* st) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < nleaves;
-       t += int64_t(gridDim.x) * blockDim.x) {
+// One leaf per lane of the first `per` lanes of each one-warp block.  A leaf's QR is
+// a chain of dependent FP64 operations, and an FP64 warp instruction occupies the
+// SM's FP64 unit for the whole warp however few lanes are active, so the host picks
+// `per` to put few warps on each SM: few leaves (n = 2048, leaf 32: 64 leaves) get
+// one leaf per warp, each warp alone on its SM; many leaves share warps, up to 32.
+__global__ void __launch_bounds__(32) k_leaves(const Leaf* __restrict__ leaves, int64_t nleaves,
+                                               int per, const double* __restrict__ ds,
+                                               const double* __restrict__ es,
+                                               const unsigned long long* __restrict__ sigma_bits,
+                                               double* LAM, double* BLO, double* BHI, double* out,
+                                               Status* st) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t w = blockIdx.x; w * per < nleaves; w += gridDim.x) {
+    const int64_t t = w * per + lane;
+    if (lane >= per || t >= nleaves) continue;
     const Leaf lf = leaves[t];
     const int m = lf.hi - lf.lo;
     double a[kMaxLeaf], b[kMaxLeaf], r0[kMaxLeaf], r1[kMaxLeaf];
@@ -136,12 +151,14 @@ __global__ void k_leaves(const Leaf* __restrict__ leaves, int64_t nleaves,
 void launch_leaves_to(const Plan& plan, const Workspace& ws, double* lambda, cudaStream_t s,
                       LevelState out) {
   if (plan.nleaves == 0) return;
-  int block = 64;
-  int64_t grid = (plan.nleaves + block - 1) / block;
-  if (grid > 148 * 32) grid = 148 * 32;
+  // leaves per warp: about two warps per SM before warps take more than one leaf
+  const int64_t per64 = (plan.nleaves + 2 * 148 - 1) / (2 * 148);
+  const int per = int(std::min<int64_t>(32, std::max<int64_t>(1, per64)));
+  int64_t grid = (plan.nleaves + per - 1) / per;
+  if (grid > 148 * 64) grid = 148 * 64;
   prof_begin(kKLeaves, s);
-  k_leaves<<<int(grid), block, 0, s>>>(ws.leaves, plan.nleaves, ws.ds, ws.es, ws.sigma_bits,
-                                       out.lam, out.blo, out.bhi, lambda, ws.status);
+  k_leaves<<<int(grid), 32, 0, s>>>(ws.leaves, plan.nleaves, per, ws.ds, ws.es, ws.sigma_bits,
+                                    out.lam, out.blo, out.bhi, lambda, ws.status);
   prof_end(kKLeaves, s);
   g_launches += 1;
 }
