@@ -34,6 +34,7 @@ struct DenseArgs {
   double* P;   // per tile of the sweep: 64 row partial sums, then 64 column partial sums
   double* d;   // [n]
   double* e;   // [n]
+  unsigned* done;  // blocks of the current k_dense_reduce launch that have finished
 };
 
 __device__ __forceinline__ double block_reduce_sum(double v, double* sm) {
@@ -74,16 +75,18 @@ __device__ __forceinline__ double block_reduce_max(double v, double* sm) {
   return r;
 }
 
-// Column step j (one block): finish column j-1's update vector w from its product
-// y, apply column j-1's rank-2 update to column j, store d_j, build column j's
-// reflector (v, tau, e_j).  Buffers of column j use slot j & 1.  Three passes
-// over the column: y.v; then w, the column update and the sums for the norm of
-// the new subdiagonal part (v_{j-1}[0] = 1, so w[0] is known to every thread
-// after the first pass); then v.
-__global__ void __launch_bounds__(kColThreads) k_dense_column(DenseArgs a, int64_t j) {
-  __shared__ double sm[32];
+// Column step j (one block, any multiple of 32 threads): finish column j-1's update
+// vector w from its product y, apply column j-1's rank-2 update to column j, store
+// d_j, build column j's reflector (v, tau, e_j).  Buffers of column j use slot
+// j & 1.  Three passes over the column: y.v; then w, the column update and the sums
+// for the norm of the new subdiagonal part (v_{j-1}[0] = 1, so w[0] is known to every
+// thread after the first pass); then v.  The reflector's scalars (a hypot and two
+// divisions) are formed by one thread and broadcast: issued by every warp they
+// would cost the FP64 unit once per warp.  y is read past L1 (__ldcg): when the
+// step runs in the last block of k_dense_reduce, other blocks of that launch wrote it.
+__device__ void column_step(const DenseArgs& a, int64_t j, double* sm) {
   const int64_t n = a.n;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, nt = blockDim.x;
   const int cur = int(j & 1), prv = cur ^ 1;
   double* col = a.A + j * n;  // column j
   const int64_t m = n - j - 1;  // length of x = A[j+1:, j]
@@ -94,19 +97,19 @@ __global__ void __launch_bounds__(kColThreads) k_dense_column(DenseArgs a, int64
     const int64_t mm = n - j;
     const double tp = a.tau[prv];
     const double* __restrict__ v = a.V + prv * n;
-    const double* __restrict__ y = a.Y + prv * n;
+    const double* y = a.Y + prv * n;
     double* __restrict__ w = a.W + prv * n;
     double* __restrict__ cj = col + j;
     double dot = 0.0;
 #pragma unroll 4
-    for (int64_t i = t; i < mm; i += kColThreads) dot = fma(y[i], v[i], dot);
+    for (int64_t i = t; i < mm; i += nt) dot = fma(__ldcg(y + i), v[i], dot);
     dot = block_reduce_sum(dot, sm);
     const double alpha = -0.5 * tp * tp * dot;
-    const double w0 = fma(alpha, v[0], tp * y[0]);
+    const double w0 = fma(alpha, v[0], tp * __ldcg(y));
     // A[r, j] -= v[r-j] w[0] + w[r-j] v[0] (v[0] = 1); rows r > j+1 feed the norm
 #pragma unroll 4
-    for (int64_t i = t; i < mm; i += kColThreads) {
-      const double wi = fma(alpha, v[i], tp * y[i]);
+    for (int64_t i = t; i < mm; i += nt) {
+      const double wi = fma(alpha, v[i], tp * __ldcg(y + i));
       w[i] = wi;
       const double c = cj[i] - fma(v[i], w0, wi);
       cj[i] = c;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kColThreads) k_dense_column(DenseArgs a, int64
       }
     }
   } else {
-    for (int64_t i = t + 1; i < m; i += blockDim.x) {
+    for (int64_t i = t + 1; i < m; i += nt) {
       const double c = x[i];
       ss = fma(c, c, ss);
       mx = fmax(mx, fabs(c));
@@ -132,28 +135,36 @@ __global__ void __launch_bounds__(kColThreads) k_dense_column(DenseArgs a, int64
     // the plain sum of squares under- or overflowed: recompute it scaled by max |x_i|
     const double inv = 1.0 / mx;
     double s2 = 0.0;
-    for (int64_t i = t + 1; i < m; i += blockDim.x) {
+    for (int64_t i = t + 1; i < m; i += nt) {
       const double q = x[i] * inv;
       s2 = fma(q, q, s2);
     }
     ss = block_reduce_sum(s2, sm) * mx * mx;
   }
-  const double alpha = x[0];
-  const double xnorm = sqrt(ss);
-  double tau = 0.0, beta = alpha, scale = 0.0;
-  if (mx > 0.0) {
-    beta = -copysign(hypot(alpha, xnorm), alpha);
-    tau = (beta - alpha) / beta;
-    scale = 1.0 / (alpha - beta);
-  }
-  double* __restrict__ v = a.V + cur * n;
-  const double* __restrict__ xr = x;
-#pragma unroll 4
-  for (int64_t i = t; i < m; i += kColThreads) v[i] = (i == 0) ? 1.0 : xr[i] * scale;
   if (t == 0) {
+    const double alpha = x[0];
+    const double xnorm = sqrt(ss);
+    double tau = 0.0, beta = alpha, scale = 0.0;
+    if (mx > 0.0) {
+      beta = -copysign(hypot(alpha, xnorm), alpha);
+      tau = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    sm[0] = scale;
     a.tau[cur] = tau;
     a.e[j] = beta;
   }
+  __syncthreads();
+  const double scale = sm[0];
+  double* __restrict__ v = a.V + cur * n;
+  const double* __restrict__ xr = x;
+#pragma unroll 4
+  for (int64_t i = t; i < m; i += nt) v[i] = (i == 0) ? 1.0 : xr[i] * scale;
+}
+
+__global__ void __launch_bounds__(kColThreads) k_dense_column(DenseArgs a, int64_t j) {
+  __shared__ double sm[32];
+  column_step(a, j, sm);
 }
 
 // Fused sweep for column j over the trailing lower triangle B = A[j+1:, j+1:]
@@ -274,6 +285,19 @@ __global__ void __launch_bounds__(256) k_dense_reduce(DenseArgs a, int64_t j) {
   if (threadIdx.x < kDenseTile && i < m)
     a.Y[int(j & 1) * a.n + i] = (s_acc[0][threadIdx.x] + s_acc[1][threadIdx.x]) +
                                 (s_acc[2][threadIdx.x] + s_acc[3][threadIdx.x]);
+  // the last block of the launch to finish takes column j + 1's step, which needs
+  // every row of y (the ticket orders it after the other blocks' writes; no block
+  // waits for another)
+  __shared__ unsigned s_ticket;
+  __shared__ double sm[32];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_ticket = atomicAdd(a.done, 1u);
+  __syncthreads();
+  if (s_ticket != gridDim.x - 1) return;
+  __threadfence();
+  column_step(a, j + 1, sm);
+  if (threadIdx.x == 0) *a.done = 0u;  // ready for the next launch on this stream
 }
 
 // ---- driver -------------------------------------------------------------------
@@ -281,7 +305,7 @@ size_t dense_workspace(int64_t n, size_t tri_bytes) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t N = size_t(std::max<int64_t>(n, 1));
   const size_t T = (N + kDenseTile - 1) / kDenseTile;
-  return al(tri_bytes) + al(8 * N * N) + 6 * al(8 * N) + al(16) + 2 * al(8 * N) +
+  return al(tri_bytes) + al(8 * N * N) + 6 * al(8 * N) + al(16) + 2 * al(8 * N) + al(16) +
          al(8 * (T * (T + 1) / 2) * 2 * kDenseTile);
 }
 
@@ -308,23 +332,26 @@ int dense_reduce(int64_t n, const double* A, int64_t lda, void* ws, size_t tri_b
   p += al(8 * N);
   a.e = reinterpret_cast<double*>(p);
   p += al(8 * N);
-  a.P = reinterpret_cast<double*>(p);
+  a.done = reinterpret_cast<unsigned*>(p);
+  p += al(16);
+  a.P = reinterpret_cast<double*>(p);  // last: its size follows from the tile count
   *d_out = a.d;
   *e_out = a.e;
   if (cudaMemcpy2DAsync(a.A, 8 * N, A, 8 * size_t(lda), 8 * N, N, cudaMemcpyDeviceToDevice, s) !=
       cudaSuccess)
     return TDE_ECUDA;
   if (cudaMemsetAsync(a.e, 0, 8 * N, s) != cudaSuccess) return TDE_ECUDA;
-  for (int64_t j = 0; j < n; ++j) {
-    k_dense_column<<<1, kColThreads, 0, s>>>(a, j);
+  if (cudaMemsetAsync(a.done, 0, 16, s) != cudaSuccess) return TDE_ECUDA;
+  // column 0's step, then per column j: the sweep and the reduction of its product,
+  // whose last block takes column j + 1's step
+  k_dense_column<<<1, kColThreads, 0, s>>>(a, 0);
+  g_launches += 1;
+  for (int64_t j = 0; j + 1 < n; ++j) {
     const int64_t m = n - j - 1;
-    if (m > 0) {
-      const int64_t T = (m + kDenseTile - 1) / kDenseTile;
-      k_dense_sweep<<<unsigned(T * (T + 1) / 2), 256, 0, s>>>(a, j);
-      k_dense_reduce<<<unsigned(T), 256, 0, s>>>(a, j);
-      g_launches += 2;
-    }
-    g_launches += 1;
+    const int64_t T = (m + kDenseTile - 1) / kDenseTile;
+    k_dense_sweep<<<unsigned(T * (T + 1) / 2), 256, 0, s>>>(a, j);
+    k_dense_reduce<<<unsigned(T), 256, 0, s>>>(a, j);
+    g_launches += 2;
   }
   return cudaGetLastError() == cudaSuccess ? TDE_OK : TDE_ECUDA;
 }
