@@ -609,7 +609,7 @@ def dense_section(args, dev, fma_per_s: float) -> dict:
     import paper_2605_26599_b300 as tde
 
     res = {}
-    for n in (2048, 8192):
+    for n in (int(x) for x in args.dense_sizes.split(",") if x):
         a = inputs.dense_goe(n, seed=1)
         at = torch.from_numpy(a).to(dev)
         ws = tde.Workspace(tde.dense_eigvals_workspace_bytes(n, args.leaf), dev)
@@ -900,6 +900,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every extra measurement (see --extras)")
+    ap.add_argument("--dense-sizes", default="2048,8192",
+                    help="orders of the dense front end's section (comma list)")
     ap.add_argument("--extras", default="configs,batched,backward,sweep,rows,dense,context",
                     help="which extra measurements to run (comma list of configs, batched, "
                          "backward, sweep, rows, dense, context)")

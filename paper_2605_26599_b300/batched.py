@@ -160,3 +160,35 @@ def autotune(offsets, d, e, leaves=DEFAULT_LEAVES, warp_min_ks=DEFAULT_WARP_MIN_
 
 def log2_ceil(n: int) -> int:
     return int(math.ceil(math.log2(max(n, 1))))
+
+
+def _main(argv=None) -> None:
+    """Time graph replays of the batched forest on the synthetic packing of 4096
+    Lanczos-style tridiagonals (orders log-uniform in [64, 4096]) and print one JSON
+    line: ``python -m paper_2605_26599_b300.batched [--leaf 16] [--warp-min-k 512]
+    [--reps 3]``."""
+    import argparse
+
+    import torch
+
+    from . import inputs, last_launch_count
+
+    ap = argparse.ArgumentParser(description=_main.__doc__.split("\n")[0])
+    ap.add_argument("--leaf", type=int, default=16)
+    ap.add_argument("--warp-min-k", type=int, default=512)
+    ap.add_argument("--reps", type=int, default=3)
+    args = ap.parse_args(argv)
+    d, e, off = inputs.batched_lanczos()
+    dt, et = torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda()
+    set_tuning(args.warp_min_k)
+    solver = BatchedSolver(off, leaf=args.leaf)
+    launches = last_launch_count()
+    ms = _time_solver(solver, dt, et, args.reps)
+    set_tuning()
+    print(json.dumps({"matrices": len(off) - 1, "rows": int(off[-1]), "leaf": args.leaf,
+                      "warp_min_k": args.warp_min_k, "replay_ms": ms,
+                      "launches_per_replay": launches}))
+
+
+if __name__ == "__main__":
+    _main()
