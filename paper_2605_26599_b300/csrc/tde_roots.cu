@@ -1172,12 +1172,61 @@ struct GroupSweep32 : Copies32 {
 };
 
 // Single-precision sums of the warp kernel (all 32 lanes on one root).  With nb > 0
-// lane l takes blocks l, l + 32, ...: far blocks through their float series, near
-// blocks term by term by the whole warp.
+// a sweep first takes the far superblocks (nsb > 0; one per lane), then goes block
+// by block over the superblocks it did not take whole, 32 blocks per round: far
+// blocks through their float series, near blocks term by term by the whole warp.
 struct WarpSweep32 : Copies32 {
   int lane;
   int nb;
   const float* __restrict__ BF;
+  int nsb;                         // superblocks (0: none)
+  const float* __restrict__ SF;    // their float data (the blocks' layout, nsb entries per field)
+  // lane's block (or superblock) b of float data F with nc entries per field, at
+  // offset d (units of S) from the point: far -> its series into (p, dp) or (f, df), h
+  __device__ __forceinline__ bool far_series32(const float* F, int nc, int b, bool valid, float2 ho,
+                                               float tau, float inv, float& p, float& dp, float& f,
+                                               float& df, float& h) const {
+    const float d = valid ? fmaf((F[b] - ho.x) + (F[nc + b] - ho.y), inv, -tau) : 1.f;
+    const float rs = valid ? F[2 * nc + b] * inv : 0.f;
+    const bool far = valid && 3.f * rs <= fabsf(d);
+    const bool tail = __all_sync(0xffffffffu, !far || 16.f * rs <= fabsf(d));
+    if (far) {
+      const float q = rcp_approx32(d), x = -rs * q;
+      const float* A = F + 3 * nc + b;
+      float va, vb, vc;
+      if (tail) {
+        va = A[(kMfShort - 1) * nc];
+        vb = A[(kMfTerms + kMfShort - 1) * nc];
+        vc = A[(2 * kMfTerms + kMfShort - 1) * nc];
+#pragma unroll
+        for (int k = kMfShort - 2; k >= 0; --k) {
+          va = fmaf(va, x, A[k * nc]);
+          vb = fmaf(vb, x, A[(kMfTerms + k) * nc]);
+          vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nc]);
+        }
+      } else {
+        va = A[(kMf32 - 1) * nc];
+        vb = A[(kMfTerms + kMf32 - 1) * nc];
+        vc = A[(2 * kMfTerms + kMf32 - 1) * nc];
+#pragma unroll
+        for (int k = kMf32 - 2; k >= 0; --k) {
+          va = fmaf(va, x, A[k * nc]);
+          vb = fmaf(vb, x, A[(kMfTerms + k) * nc]);
+          vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nc]);
+        }
+      }
+      const float q2 = q * q;
+      if (d > 0.f) {
+        f = fmaf(q, va, f);
+        df = fmaf(q2, vb, df);
+      } else {
+        p = fmaf(q, va, p);
+        dp = fmaf(q2, vb, dp);
+      }
+      h = fmaf(q2 * q, vc, h);
+    }
+    return far;
+  }
   __device__ __forceinline__ Sec32 operator()(int org, int jl, float tau, float inv) const {
     const float2 ho = H[org];
     float p = 0.f, dp = 0.f, f = 0.f, df = 0.f, h = 0.f;
@@ -1187,55 +1236,17 @@ struct WarpSweep32 : Copies32 {
       range32(H, Z, jl + 1, K, lane, 32, ho, tau, inv, f, df, hr);
       h = hl + hr;
     } else {
-      for (int b0 = 0; b0 < nb; b0 += 32) {
-        const int b = b0 + lane;
-        bool near = false;
-        const float d = b < nb ? fmaf((BF[b] - ho.x) + (BF[nb + b] - ho.y), inv, -tau) : 1.f;
-        const float rs = b < nb ? BF[2 * nb + b] * inv : 0.f;
-        const bool far = b < nb && 3.f * rs <= fabsf(d);
-        const bool tail = __all_sync(0xffffffffu, !far || 16.f * rs <= fabsf(d));
-        if (b < nb) {
-          if (far) {
-            const float q = rcp_approx32(d), x = -rs * q;
-            const float* A = BF + 3 * nb + b;
-            float va, vb, vc;
-            if (tail) {
-              va = A[(kMfShort - 1) * nb];
-              vb = A[(kMfTerms + kMfShort - 1) * nb];
-              vc = A[(2 * kMfTerms + kMfShort - 1) * nb];
-#pragma unroll
-              for (int k = kMfShort - 2; k >= 0; --k) {
-                va = fmaf(va, x, A[k * nb]);
-                vb = fmaf(vb, x, A[(kMfTerms + k) * nb]);
-                vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
-              }
-            } else {
-              va = A[(kMf32 - 1) * nb];
-              vb = A[(kMfTerms + kMf32 - 1) * nb];
-              vc = A[(2 * kMfTerms + kMf32 - 1) * nb];
-#pragma unroll
-              for (int k = kMf32 - 2; k >= 0; --k) {
-                va = fmaf(va, x, A[k * nb]);
-                vb = fmaf(vb, x, A[(kMfTerms + k) * nb]);
-                vc = fmaf(vc, x, A[(2 * kMfTerms + k) * nb]);
-              }
-            }
-            const float q2 = q * q;
-            if (d > 0.f) {
-              f = fmaf(q, va, f);
-              df = fmaf(q2, vb, df);
-            } else {
-              p = fmaf(q, va, p);
-              dp = fmaf(q2, vb, dp);
-            }
-            h = fmaf(q2 * q, vc, h);
-          } else {
-            near = true;
-          }
-        }
-        unsigned nm = __ballot_sync(0xffffffffu, near);
+      unsigned sfar = 0;  // superblocks taken whole
+      if (nsb > 0)
+        sfar = __ballot_sync(0xffffffffu, far_series32(SF, nsb, lane, lane < nsb, ho, tau, inv, p, dp,
+                                                        f, df, h));
+      const KeptBlocks kb = kept_blocks(nsb, sb_size(nb), sfar, nb);
+      for (int base = 0; base < kb.count; base += 32) {
+        const int b = kept_block(kb, base + lane);
+        const bool far = far_series32(BF, nb, b < 0 ? 0 : b, b >= 0, ho, tau, inv, p, dp, f, df, h);
+        unsigned nm = __ballot_sync(0xffffffffu, b >= 0 && !far);
         while (nm) {
-          const int bb = b0 + __ffs(nm) - 1;
+          const int bb = __shfl_sync(0xffffffffu, b, __ffs(nm) - 1);
           nm &= nm - 1;
           const int i0 = bb * kMpBlock, i1 = (bb == nb - 1) ? K : i0 + kMpBlock;
           const int mid = min(max(jl + 1, i0), i1);
@@ -1463,6 +1474,11 @@ __global__ void __launch_bounds__(128) k_super_moments(RootArgs a) {
         SP[sb] = m;
         SP[nss + sb] = rad;
         SP[2 * nss + sb] = 3.0 * rad;
+        const double c = m - a.ms[gg].shift;  // the single-precision stage's centre pair
+        const float ch = __double2float_rn(c);
+        SF[sb] = ch;
+        SF[nss + sb] = __double2float_rn(c - double(ch));
+        SF[2 * nss + sb] = __double2float_rn(rad);
       }
 #pragma unroll
       for (int jj = 0; jj < warp_halved_len(kMfTerms); ++jj) {
@@ -1473,6 +1489,8 @@ __global__ void __launch_bounds__(128) k_super_moments(RootArgs a) {
           if (k < kHd3) SP[(3 + kHv3 + k) * nss + sb] = m1;
           SF[(3 + k) * nss + sb] = __double2float_rn(m0);
           SF[(3 + kMfTerms + k) * nss + sb] = __double2float_rn(m1);
+          if (k < kMf32)
+            SF[(3 + 2 * kMfTerms + k) * nss + sb] = __double2float_rn(0.5 * double(k + 2) * m1);
         }
       }
     }
@@ -1676,7 +1694,10 @@ struct WarpCoop {
     int slo, sK, snb;
     merge_of(src, slo, sK, snb);
     const float* mf = reinterpret_cast<const float*>(a->MPD + slo + kMpFields * snb);
-    const WarpSweep32 sw{{a->AD32 + slo, a->AZ32 + slo, sK}, lane, snb, mf};
+    const int nsb = sb_count(snb);
+    const double* sp = sb_data(a->MPD + slo, snb);
+    const WarpSweep32 sw{{a->AD32 + slo, a->AZ32 + slo, sK}, lane, snb, mf, nsb,
+                         reinterpret_cast<const float*>(sp + kMpFields * nsb)};
     return sw(org, jl, tau, inv);
   }
   __device__ __forceinline__ SecSums sweep64(int src, double dorg, double tau, int jl) {
