@@ -85,3 +85,46 @@ def test_large_o_n_workspace(tde, fam, n):
     assert tde.workspace_bytes(n) <= 256 * n
     lam = solve(tde, d, e)
     check_full(d, e, lam, sample=96)
+
+
+def _certify_packed(d, e, off, lam):
+    """Every eigenvalue of every matrix of a packing, certified at its own gate."""
+    bad = []
+    for k in range(len(off) - 1):
+        a, b = int(off[k]), int(off[k + 1])
+        if b == a:
+            continue
+        dk, ek = d[a:b], e[a:b - 1]
+        gate = 8 * (b - a) * EPS * oracle.norm1(dk, ek) + 1e-300
+        assert np.all(np.diff(lam[a:b]) >= 0)
+        ok = oracle.certify(dk, ek, lam[a:b], gate)
+        if not ok.all():
+            bad.append((k, b - a, int(np.count_nonzero(~ok))))
+    assert not bad, f"matrices with eigenvalues outside their gate: {bad[:8]}"
+
+
+def test_batched_full_configuration_every_eigenvalue(tde):
+    # the batched workload as specified: 4096 Lanczos-style tridiagonals, orders
+    # log-uniform in [64, 4096] (3,911,691 rows), one forest solve; every eigenvalue
+    # of every matrix certified by Sturm counts
+    import torch
+
+    d, e, off = inputs.batched_lanczos()
+    lam = tde.eigvals_batched(torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda(), off,
+                              leaf=16).cpu().numpy()
+    _certify_packed(d, e, off, lam)
+
+
+def test_gradient_configuration_forward_every_eigenvalue(tde):
+    # the differentiation workload's forward pass: 256 tridiagonals of order 8192
+    # (d ~ N(0,1), e ~ |N(0,0.5)|), every eigenvalue certified, through the batched
+    # solver and through the adjoint's own forward pass (the eigenvalues it returns)
+    import torch
+
+    d, e, off, w = inputs.grad_batch()
+    dt, et = torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda()
+    lam = tde.eigvals_batched(dt, et, off, leaf=8)
+    _certify_packed(d, e, off, lam.cpu().numpy())
+    gl = 2.0 * torch.from_numpy(w).cuda() * lam
+    lam2, _, _ = tde.eigvals_backward(dt, et, gl, offsets=off, leaf=8)
+    assert np.array_equal(lam2.cpu().numpy(), lam.cpu().numpy())
