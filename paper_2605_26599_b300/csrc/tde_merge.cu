@@ -75,11 +75,17 @@ __global__ void k_form(const Merge* __restrict__ M, int64_t cnt, int64_t nrows,
 // A survivor j continues the run (is rotated into it) iff the dropped coupling
 // is at most tol:  |sqrt(W) z_j (D_j - c)| <= tol (W + w_j), c = DW / W, which
 // is tested squared: w_j (W D_j - DW)^2 <= tol^2 W (W + w_j)^2.
+//
+// The walks below evaluate this rule and the run sums at several call sites, and
+// re-use decisions of earlier walks wherever the carry is unchanged, so every
+// product and sum of them is rounded explicitly (__dmul_rn / __dadd_rn are never
+// contracted into an FMA): each inlined copy computes the same bits, and a
+// decision close to the threshold cannot differ between two walks of one input.
 __device__ __forceinline__ bool continues_run(double W, double DW, double Dj, double wj,
                                               double tol2) {
-  double a = fma(W, Dj, -DW);
-  double s = W + wj;
-  return wj * a * a <= tol2 * W * s * s;
+  const double a = fma(W, Dj, -DW);
+  const double s = __dadd_rn(W, wj);
+  return __dmul_rn(__dmul_rn(wj, a), a) <= __dmul_rn(__dmul_rn(__dmul_rn(tol2, W), s), s);
 }
 
 struct T4 {
@@ -119,22 +125,22 @@ __device__ bool run_segment(int begin, int end, const int32_t* surv, const doubl
       int pos = surv[k];
       Dk = D[pos];
       double zk = Z[pos];
-      wk = zk * zk;
+      wk = __dmul_rn(zk, zk);
     }
     const double Dp = shfl_up_d(Dk, 1), wp = shfl_up_d(wk, 1);
     bool guess;
     if (lane == 0)
       guess = valid && have && continues_run(cW, cDW, Dk, wk, tol2);
     else
-      guess = valid && continues_run(wp, Dp * wp, Dk, wk, tol2);
+      guess = valid && continues_run(wp, __dmul_rn(Dp, wp), Dk, wk, tol2);
     int start = 0;
     double W = 0.0, DWv = 0.0;
     for (int iter = 0; iter <= 32; ++iter) {
       W = wk;
-      DWv = Dk * wk;
+      DWv = __dmul_rn(Dk, wk);
       if (lane == 0 && guess) {
-        W += cW;
-        DWv += cDW;
+        W = __dadd_rn(W, cW);
+        DWv = __dadd_rn(DWv, cDW);
       }
       bool h = !guess;
 #pragma unroll
@@ -143,8 +149,8 @@ __device__ bool run_segment(int begin, int end, const int32_t* surv, const doubl
         bool ho = __shfl_up_sync(0xffffffffu, h, o);
         if (lane >= o) {
           if (!h) {
-            W += Wo;
-            DWv += DWo;
+            W = __dadd_rn(W, Wo);
+            DWv = __dadd_rn(DWv, DWo);
           }
           h = h || ho;
         }
@@ -176,7 +182,8 @@ __device__ bool run_segment(int begin, int end, const int32_t* surv, const doubl
 // Run boundaries of all S survivors by the warps of the block.  Long lists are cut
 // into one segment per warp; each warp walks its segment assuming the segment's
 // first survivor is tested against its predecessor alone, then warp 0 re-walks the
-// segments in order with the true carry until the decisions agree again.
+// segments in order with the true carry until the decisions agree again (skipping
+// those whose true carry is the assumed one).
 template <int NT>
 __device__ void run_boundaries(int S, const int32_t* surv, const double* D, const double* Z,
                                double tol2, uint8_t* rflag, double* s_cw, double* s_cdw) {
@@ -198,8 +205,8 @@ __device__ void run_boundaries(int S, const int32_t* surv, const double* D, cons
       if (b > 0) {  // speculative carry: the predecessor alone
         const int pos = surv[b - 1];
         const double z = Z[pos];
-        cW = z * z;
-        cDW = D[pos] * cW;
+        cW = __dmul_rn(z, z);
+        cDW = __dmul_rn(D[pos], cW);
         have = true;
       }
       run_segment(b, e, surv, D, Z, tol2, rflag, cW, cDW, have, false);
@@ -215,6 +222,12 @@ __device__ void run_boundaries(int S, const int32_t* surv, const double* D, cons
       const int b = w * seg, e = min(S, b + seg);
       if (b >= e) break;
       double cW = s_cw[w - 1], cDW = s_cdw[w - 1];
+      // the speculative carry again (same expression, same bits): a segment whose
+      // true carry equals it is already exact
+      const double z = Z[surv[b - 1]], sW = __dmul_rn(z, z), sDW = __dmul_rn(D[surv[b - 1]], sW);
+      if (__double_as_longlong(cW) == __double_as_longlong(sW) &&
+          __double_as_longlong(cDW) == __double_as_longlong(sDW))
+        continue;
       const bool completed = run_segment(b, e, surv, D, Z, tol2, rflag, cW, cDW, true, true);
       if (completed && (threadIdx.x & 31) == 0) {
         s_cw[w] = cW;
@@ -763,22 +776,28 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
     }
     cluster_sync_mem(cl);
 
-    // 3. run boundaries: speculative walk per warp segment, then parallel rounds
+    // 3. run boundaries: speculative walk per warp segment, then parallel rounds in
+    //    which a segment walks again only when the carry it receives differs (bit for
+    //    bit) from the one it last walked with: the same carry gives the same
+    //    decisions and the same carry out, and the walk is FP64-bound
     {
       const int NS = C * NW;
       const int seg = ((S + NS - 1) / NS + 31) & ~31;
       const int sid = r * NW + warp;
       const int b = min(S, sid * seg), e = min(S, b + seg);
       double cW = 0.0, cDW = 0.0;
+      double inW = 0.0, inDW = 0.0;  // carry of the segment's last walk
       if (b < e) {
         bool have = false;
         if (b > 0) {
           const int pos = SURV[b - 1];
           const double z = a.Z[pos];
-          cW = z * z;
-          cDW = a.D[pos] * cW;
+          cW = __dmul_rn(z, z);
+          cDW = __dmul_rn(a.D[pos], cW);
           have = true;
         }
+        inW = cW;
+        inDW = cDW;
         run_segment(b, e, SURV, a.D, a.Z, tol2, RFLAG, cW, cDW, have, false);
       }
       if (lane == 0) {
@@ -795,7 +814,11 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
           const int pr = (sid - 1) / NW, pw = (sid - 1) % NW;
           double W = cl.map_shared_rank(&s_cw[cur][0], pr)[pw];
           double DW = cl.map_shared_rank(&s_cdw[cur][0], pr)[pw];
-          if (run_segment(b, e, SURV, a.D, a.Z, tol2, RFLAG, W, DW, true, true)) {
+          const bool same_in = __double_as_longlong(W) == __double_as_longlong(inW) &&
+                               __double_as_longlong(DW) == __double_as_longlong(inDW);
+          inW = W;
+          inDW = DW;
+          if (!same_in && run_segment(b, e, SURV, a.D, a.Z, tol2, RFLAG, W, DW, true, true)) {
             changed = __double_as_longlong(W) != __double_as_longlong(nW) ||
                       __double_as_longlong(DW) != __double_as_longlong(nDW);
             nW = W;
