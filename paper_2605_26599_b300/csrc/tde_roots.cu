@@ -2067,102 +2067,130 @@ __global__ void __launch_bounds__(64) k_lowner_super(RootArgs a) {  // 2 warps: 
   }
 }
 
+// A warp takes tiles of T consecutive poles (T = the poles per warp, at most 32;
+// tile t goes to warp t mod the warp count): it forms each pole's products and
+// far-block log sum cooperatively as before and leaves them in lane u (the pole's
+// place in the tile), and the closing scalar work -- the ratio, exp of the log
+// sum, the square root -- runs once per tile for all its poles instead of at warp
+// width per pole.
 __global__ void k_lowner_warp(RootArgs a) {
   const uint32_t total = warp_list_total(a);
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t per = (total + nwarps - 1) / nwarps;
+  const uint32_t T = per >= 32 ? 32u : (per == 0 ? 1u : per);
+  const uint32_t tiles = (total + T - 1) / T;
   unsigned pairs = 0, series = 0;
   unsigned long long sops = 0;
-  for (uint32_t r = warp; r < total; r += nwarps) {
-    int rl;
-    const int g = warp_list_merge(a, r, &rl);
-    const Merge m = a.M[g];
-    if ((uint32_t(m.info) & kRootBit) && !a.all_merges) continue;
-    const MState ms = a.ms[g];
-    const int K = ms.K, i = rl - ms.base, lo = m.lo;
-    const double* AD = a.AD + lo;
-    const double* DORG = a.DORG + lo;
-    const double* TAU = a.TAU + lo;
-    const double Di = AD[i];
-    MantExp num{1.0, 0}, den{1.0, 0};
-    double slog = 0.0;  // far blocks' log sum (block expansion)
-    const int nb = mp_blocks(K, a.mp_min_k);
-    if (nb == 0) {
-      int j = lane;
-      for (; j + 7 * 32 < K - 1; j += 8 * 32) {
+  for (uint32_t t = warp; t < tiles; t += nwarps) {
+    // this lane's pole of the tile: its merge and sums, stored after the tile
+    bool keep = false;
+    int k_lo = 0, k_i = 0, k_K = 0;
+    double k_Di = 0.0, k_rhoinv = 0.0, k_slog = 0.0;
+    MantExp k_num{1.0, 0}, k_den{1.0, 0};
+    const uint32_t r_end = min(total, (t + 1) * T);
+    for (uint32_t r = t * T; r < r_end; ++r) {
+      int rl;
+      const int g = warp_list_merge(a, r, &rl);
+      const Merge m = a.M[g];
+      if ((uint32_t(m.info) & kRootBit) && !a.all_merges) continue;
+      const MState ms = a.ms[g];
+      const int K = ms.K, i = rl - ms.base, lo = m.lo;
+      const double* AD = a.AD + lo;
+      const double* DORG = a.DORG + lo;
+      const double* TAU = a.TAU + lo;
+      const double Di = AD[i];
+      MantExp num{1.0, 0}, den{1.0, 0};
+      double slog = 0.0;  // far blocks' log sum (block expansion)
+      const int nb = mp_blocks(K, a.mp_min_k);
+      if (nb == 0) {
+        int j = lane;
+        for (; j + 7 * 32 < K - 1; j += 8 * 32) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) lowner_pair(AD, DORG, TAU, i, Di, j + 32 * u, num.m, den.m);
+          for (int u = 0; u < 8; ++u) lowner_pair(AD, DORG, TAU, i, Di, j + 32 * u, num.m, den.m);
+          me_renorm(num);
+          me_renorm(den);
+        }
+        for (; j < K - 1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
         me_renorm(num);
         me_renorm(den);
-      }
-      for (; j < K - 1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
-      me_renorm(num);
-      me_renorm(den);
-      pairs += unsigned(K);
-    } else {
-      const double* MP = a.MPR + lo;
-      const float* MF = reinterpret_cast<const float*>(MP + kMlFields * nb);
-      const int nsb = sb_count(nb);
-      const double* SP = lowner_sb_data(a.MPR + lo, nb);
-      const float* SF = reinterpret_cast<const float*>(SP + kMlFields * nsb);
-      // one round: the lane's pair block (or superblock) b of data C / F with nc
-      // entries per field through its log series if it is far from D_i
-      auto far_round = [&](const double* C, const float* F, int nc, int b, bool valid) -> bool {
-        const double dm = valid ? Di - C[b] : 1.0;
-        const double rb = valid ? C[nc + b] : 0.0;
-        const FarTest ft = far_test_bits(dm, rb, valid ? C[2 * nc + b] : 0.0, valid);
-        if (ft.far) {
-          const double w = rcp_refined(dm), x = rb * w;
-          const int side = dm < 0.0 ? 1 : 0;  // right of D_i: R
-          const double* c = C + (3 + side * kMlHead) * nc + b;
-          const float* f = F + side * (kMlTerms - kTailBase) * nc + b;
-          double val;
-          if (ft.tier == 0)
-            val = series1_mixed<kMpTiny, kHv0>(c, f, nc, x);
-          else if (ft.tier == 1)
-            val = series1_mixed<kMpShort, kHv1>(c, f, nc, x);
-          else if (ft.tier == 2)
-            val = series1_mixed<kMpMid, kHv2>(c, f, nc, x);
-          else
-            val = series1_mixed<kMlTerms, kHv3>(c, f, nc, x);
-          slog = fma(-w, val, slog);
+        pairs += unsigned(K);
+      } else {
+        const double* MP = a.MPR + lo;
+        const float* MF = reinterpret_cast<const float*>(MP + kMlFields * nb);
+        const int nsb = sb_count(nb);
+        const double* SP = lowner_sb_data(a.MPR + lo, nb);
+        const float* SF = reinterpret_cast<const float*>(SP + kMlFields * nsb);
+        // one round: the lane's pair block (or superblock) b of data C / F with nc
+        // entries per field through its log series if it is far from D_i
+        auto far_round = [&](const double* C, const float* F, int nc, int b, bool valid) -> bool {
+          const double dm = valid ? Di - C[b] : 1.0;
+          const double rb = valid ? C[nc + b] : 0.0;
+          const FarTest ft = far_test_bits(dm, rb, valid ? C[2 * nc + b] : 0.0, valid);
+          if (ft.far) {
+            const double w = rcp_refined(dm), x = rb * w;
+            const int side = dm < 0.0 ? 1 : 0;  // right of D_i: R
+            const double* c = C + (3 + side * kMlHead) * nc + b;
+            const float* f = F + side * (kMlTerms - kTailBase) * nc + b;
+            double val;
+            if (ft.tier == 0)
+              val = series1_mixed<kMpTiny, kHv0>(c, f, nc, x);
+            else if (ft.tier == 1)
+              val = series1_mixed<kMpShort, kHv1>(c, f, nc, x);
+            else if (ft.tier == 2)
+              val = series1_mixed<kMpMid, kHv2>(c, f, nc, x);
+            else
+              val = series1_mixed<kMlTerms, kHv3>(c, f, nc, x);
+            slog = fma(-w, val, slog);
+          }
+          const unsigned nfar = __popc(__ballot_sync(0xffffffffu, ft.far));
+          series += nfar;
+          sops += nfar * unsigned(kMlSeriesOverhead + (ft.tier == 0   ? kHv0
+                                                       : ft.tier == 1 ? kHv1
+                                                       : ft.tier == 2 ? kHv2
+                                                                      : kHv3));
+          return ft.far;
+        };
+        unsigned sfar = 0;  // superblocks taken whole
+        if (nsb > 0) sfar = __ballot_sync(0xffffffffu, far_round(SP, SF, nsb, lane, lane < nsb));
+        const KeptBlocks kb = kept_blocks(nsb, sb_size(nb), sfar, nb);
+        for (int base = 0; base < kb.count; base += 32) {
+          const int b = kept_block(kb, base + lane);
+          const bool far = far_round(MP, MF, nb, b < 0 ? 0 : b, b >= 0);
+          unsigned nm = __ballot_sync(0xffffffffu, b >= 0 && !far);
+          while (nm) {
+            const int bb = __shfl_sync(0xffffffffu, b, __ffs(nm) - 1);
+            nm &= nm - 1;
+            const int j0 = bb * kMpBlock, j1 = lowner_block_end(bb, nb, K);
+            for (int j = j0 + lane; j < j1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
+            me_renorm(num);  // at most four factors per lane since the last renormalisation
+            me_renorm(den);
+            pairs += unsigned(j1 - j0);
+          }
         }
-        const unsigned nfar = __popc(__ballot_sync(0xffffffffu, ft.far));
-        series += nfar;
-        sops += nfar * unsigned(kMlSeriesOverhead + (ft.tier == 0   ? kHv0
-                                                     : ft.tier == 1 ? kHv1
-                                                     : ft.tier == 2 ? kHv2
-                                                                    : kHv3));
-        return ft.far;
-      };
-      unsigned sfar = 0;  // superblocks taken whole
-      if (nsb > 0) sfar = __ballot_sync(0xffffffffu, far_round(SP, SF, nsb, lane, lane < nsb));
-      const KeptBlocks kb = kept_blocks(nsb, sb_size(nb), sfar, nb);
-      for (int base = 0; base < kb.count; base += 32) {
-        const int b = kept_block(kb, base + lane);
-        const bool far = far_round(MP, MF, nb, b < 0 ? 0 : b, b >= 0);
-        unsigned nm = __ballot_sync(0xffffffffu, b >= 0 && !far);
-        while (nm) {
-          const int bb = __shfl_sync(0xffffffffu, b, __ffs(nm) - 1);
-          nm &= nm - 1;
-          const int j0 = bb * kMpBlock, j1 = lowner_block_end(bb, nb, K);
-          for (int j = j0 + lane; j < j1; j += 32) lowner_pair(AD, DORG, TAU, i, Di, j, num.m, den.m);
-          me_renorm(num);  // at most four factors per lane since the last renormalisation
-          me_renorm(den);
-          pairs += unsigned(j1 - j0);
-        }
+        slog = warp_sum(slog);
       }
-      slog = warp_sum(slog);
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      MantExp pn{__shfl_xor_sync(0xffffffffu, num.m, o), __shfl_xor_sync(0xffffffffu, num.e, o)};
-      MantExp pd{__shfl_xor_sync(0xffffffffu, den.m, o), __shfl_xor_sync(0xffffffffu, den.e, o)};
-      me_mul(num, pn);
-      me_mul(den, pd);
+      for (int o = 16; o > 0; o >>= 1) {
+        MantExp pn{__shfl_xor_sync(0xffffffffu, num.m, o), __shfl_xor_sync(0xffffffffu, num.e, o)};
+        MantExp pd{__shfl_xor_sync(0xffffffffu, den.m, o), __shfl_xor_sync(0xffffffffu, den.e, o)};
+        me_mul(num, pn);
+        me_mul(den, pd);
+      }
+      if (uint32_t(lane) == r - t * T) {
+        keep = true;
+        k_lo = lo;
+        k_i = i;
+        k_K = K;
+        k_Di = Di;
+        k_rhoinv = ms.rhoinv;
+        k_slog = slog;
+        k_num = num;
+        k_den = den;
+      }
     }
-    if (lane == 0) lowner_store(a, lo, i, Di, K, ms.rhoinv, num, den, slog);
+    if (keep) lowner_store(a, k_lo, k_i, k_Di, k_K, k_rhoinv, k_num, k_den, k_slog);
   }
   if (lane == 0 && pairs) atomicAdd(&a.st->work[kWorkLownerPairs], (unsigned long long)pairs);
   if (lane == 0 && series) atomicAdd(&a.st->work[kWorkLownerFarBlocks], (unsigned long long)series);
