@@ -1560,6 +1560,191 @@ __global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
   if (gl == 0) tally.flush(a.st);
 }
 
+// ---------------------------------------------------------------------------
+// Small-K roots with refill.  secular_root_sync keeps the roots of a warp in step,
+// so a warp pays for as many sweeps of each kind as its slowest root needs, and the
+// FP64 units take a warp instruction's full time however few lanes it carries.
+// Here each group of G lanes runs its root through the same steps as a state
+// machine and claims the next root of the list as soon as its root is done.  A pass
+// of the loop gives every group that needs one a single-precision sweep; FP64
+// sweeps wait until no group is in its single-precision stage and no idle group can
+// still claim a root, and then run for every waiting group at once, so that the
+// FP64 passes stay as full as the warp-synchronous rounds.  A root's operations and
+// their order are those of secular_root_sync, so its result is the same bit for bit.
+enum : int { kRootIdle = 0, kRootF32First, kRootF32, kRootF64Init, kRootF64, kRootF64Wait };
+
+template <int G>
+struct SmallSweeps {
+  __device__ static GroupSweep<G> f64(const RootArgs& a, int lo, int K, int gl, unsigned mask) {
+    return GroupSweep<G>{a.AD + lo, a.AZ + lo, K, gl, mask};
+  }
+  __device__ static GroupSweep32<G> f32(const RootArgs& a, int lo, int K, int gl, unsigned mask) {
+    return GroupSweep32<G>{{a.AD32 + lo, a.AZ32 + lo, K}, gl, mask};
+  }
+};
+template <>
+struct SmallSweeps<1> {
+  __device__ static ThreadSweep f64(const RootArgs& a, int lo, int K, int, unsigned) {
+    return ThreadSweep{a.AD + lo, a.AZ + lo, K};
+  }
+  __device__ static ThreadSweep32 f32(const RootArgs& a, int lo, int K, int, unsigned) {
+    return ThreadSweep32{{a.AD32 + lo, a.AZ32 + lo, K}};
+  }
+};
+
+// The roots of the small-K list (total entries), claimed through st->claim_next
+// (the caller resets it with claim_finish_block).  All 32 lanes call it together.
+template <int G>
+__device__ void secular_roots_refill(const RootArgs& a, uint32_t total, SecTally& tally) {
+  constexpr unsigned kFull = 0xffffffffu;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1), first = lane & ~(G - 1);
+  const unsigned mask = ((G == 32) ? kFull : ((1u << G) - 1u)) << first;
+  const bool leader = gl == 0;
+  const unsigned below = (1u << lane) - 1u;
+  int phase = kRootIdle;
+  bool more = true;  // the list may still hold unclaimed roots (warp-uniform)
+  int lo = 0, K = 0, j = 0, n32 = 0, sweeps = 0;
+  double rho = 0.0, rhoinv = 0.0, zsq = 0.0, hw = 0.0;
+  bool third = false, handed = false, ok = true;
+  const double *D = a.AD, *Z = a.AZ;
+  Stage32 st;
+  st.live = false;
+  st.org = 0;
+  st.jl = 0;
+  st.tau = 0.0f;
+  st.inv = 1.0f;
+  SecState q;
+  q.org = 0;
+  q.jl = 0;
+  q.tau = 0.0;
+  q.dorg = 0.0;
+  for (;;) {
+    // 1. idle groups claim the next entries of the list
+    const unsigned idle = __ballot_sync(kFull, leader && phase == kRootIdle);
+    if (more && idle) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&a.st->claim_next, unsigned(__popc(idle)));
+      base = __shfl_sync(kFull, base, 0);
+      more = base + unsigned(__popc(idle)) < total;
+      const uint32_t r = __shfl_sync(kFull, base + unsigned(__popc(idle & below)), first);
+      if (phase == kRootIdle && r < total) {
+        const int g = a.ROOTMAP[r];
+        const MState ms = a.ms[g];
+        lo = a.M[g].lo;
+        K = ms.K;
+        j = int(r) - ms.base;
+        rho = ms.rho;
+        rhoinv = ms.rhoinv;
+        zsq = ms.zsq;
+        D = a.AD + lo;
+        Z = a.AZ + lo;
+        n32 = 0;
+        sweeps = 0;
+        hw = 0.0;
+        third = handed = false;
+        ok = true;
+        if (K <= 1) {  // a single pole: the root is D_0 + rho z_0^2
+          secular_store(a, lo, j, 0, rho * Z[0] * Z[0], 0, K, true, leader);
+          tally.add(0, 0, K);
+        } else if (s32_begin(D, K, j, rho, rhoinv, zsq, SmallSweeps<G>::f32(a, lo, K, gl, mask), st)) {
+          phase = kRootF32First;
+        } else {
+          st.live = false;
+          sec_init_point(D, K, j, rho, rhoinv, zsq, q);
+          phase = kRootF64Init;
+        }
+      }
+    }
+    if (!__any_sync(kFull, phase != kRootIdle)) {
+      if (!more) break;
+      continue;
+    }
+    // 2. the steps that decide this pass's sweeps
+    bool step32 = false, have = false, hand = false, go = false, done = false;
+    float eta = 0.0f;
+    if (phase == kRootF32) {
+      step32 = st.live && s32_step(st, &eta, &have);
+      hand = !step32;
+    } else if (phase == kRootF64) {
+      if (sec_step(q, hw, third) == 0) {
+        done = true;
+      } else if (sweeps >= kMaxSweeps) {
+        ok = false;
+        done = true;
+      } else {
+        go = true;  // w''/2 at the new point now (third-order steps), the sweep when due
+        phase = kRootF64Wait;
+      }
+    }
+    // 3. single-precision sweeps: the stage's, and w''/2 at the FP64 stage's point
+    const bool want_hw = go && third;
+    const bool s32 = phase == kRootF32First || step32 || want_hw;
+    if (__any_sync(kFull, s32) && s32) {
+      const Sec32 r32 = SmallSweeps<G>::f32(a, lo, K, gl, mask)(
+          want_hw ? q.org : st.org, want_hw ? q.jl : st.jl,
+          want_hw ? float(q.tau * st.Sinv) : st.tau, st.inv);
+      if (want_hw) {
+        hw = hw_natural(st, r32.hw);
+        ++n32;
+      } else {
+        st.s = r32;
+        if (phase == kRootF32First) {
+          s32_first(D, K, j, st);
+          phase = kRootF32;
+        } else {
+          s32_after(st, eta, have);
+        }
+      }
+    }
+    // 4. hand-over to the FP64 stage (or its midpoint start)
+    if (hand) {
+      n32 = st.sweeps;
+      bool hw_ok;
+      handed = s32_finish(D, Z, rhoinv, st, q, &hw, &hw_ok);
+      third = handed && hw_ok;
+      if (!handed) sec_init_point(D, K, j, rho, rhoinv, zsq, q);
+      phase = kRootF64Init;
+    }
+    // 5. FP64 sweeps (the stage's first, and the iterations') of all waiting groups,
+    //    once no group is in the single-precision stage or could still claim a root
+    const bool waits = phase == kRootF64Init || phase == kRootF64Wait;
+    const bool busy32 = phase == kRootF32First || phase == kRootF32 || (more && phase == kRootIdle);
+    if (__any_sync(kFull, waits) && !__any_sync(kFull, busy32) && waits) {
+      q.s = SmallSweeps<G>::f64(a, lo, K, gl, mask)(q.dorg, q.tau, q.jl);
+      if (phase == kRootF64Init) {
+        if (handed)
+          q.w = q.rhoinv + q.s.psi + q.s.phi;
+        else
+          sec_init_finish(D, Z, K, j, rho, zsq, q);
+        sweeps = 1;
+        phase = kRootF64;
+      } else {
+        q.w = q.rhoinv + q.s.psi + q.s.phi;
+        ++sweeps;
+        phase = kRootF64;
+      }
+    }
+    // 6. finished roots
+    if (done) {
+      secular_store(a, lo, j, q.org, q.tau, sweeps, K, ok, leader);
+      tally.add(sweeps, n32, K);
+      phase = kRootIdle;
+    }
+  }
+}
+
+// The small-K list with refill (G lanes per root; one thread per root for G = 1),
+// 444 blocks of 128 threads claiming roots from the list.
+template <int G>
+__global__ void __launch_bounds__(128) k_secular_small(RootArgs a) {
+  const uint32_t total = *a.count;
+  if (total < a.small_list_min) return;  // the warp kernel takes a short list
+  SecTally tally;
+  secular_roots_refill<G>(a, total, tally);
+  if ((threadIdx.x & (G - 1)) == 0) tally.flush(a.st);
+  claim_finish_block(a.st);
+}
+
 // Warp-cooperative form for the warp kernel: lane l owns one root (its own merge,
 // origin, bracket and model state), and every sweep is summed by the whole warp,
 // one root at a time.  Each round the warp sweeps, in turn, every root that needs a
@@ -2714,11 +2899,26 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
       ++launches;
     }
   }
-  switch (G) {
-    case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
-    case 4: k_secular_group<4><<<ggrid, 128, 0, s>>>(ra); break;
-    case 8: k_secular_group<8><<<ggrid, 128, 0, s>>>(ra); break;
-    default: k_secular_group<16><<<ggrid, 128, 0, s>>>(ra); break;
+  // The small-K list.  A forest (several matrices: many small merges whose roots'
+  // sweep counts vary) takes the refill kernel, where a group of G lanes claims the
+  // next root as soon as its root is done (4096 Lanczos-style tridiagonals: 212 ->
+  // 206 ms per solve); a single matrix keeps the warp-synchronous rounds, which were
+  // as fast there (n = 65536, four families: 19.68 against 19.74 ms).  Both give the
+  // same roots bit for bit.
+  if (plan.batch > 1) {
+    switch (G) {  // four blocks of 128 threads per SM (128 registers)
+      case 1: k_secular_small<1><<<148 * 4, 128, 0, s>>>(ra); break;
+      case 4: k_secular_small<4><<<148 * 4, 128, 0, s>>>(ra); break;
+      case 8: k_secular_small<8><<<148 * 4, 128, 0, s>>>(ra); break;
+      default: k_secular_small<16><<<148 * 4, 128, 0, s>>>(ra); break;
+    }
+  } else {
+    switch (G) {
+      case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
+      case 4: k_secular_group<4><<<ggrid, 128, 0, s>>>(ra); break;
+      case 8: k_secular_group<8><<<ggrid, 128, 0, s>>>(ra); break;
+      default: k_secular_group<16><<<ggrid, 128, 0, s>>>(ra); break;
+    }
   }
   // three resident blocks per SM (168 registers per thread); each warp claims tiles
   k_secular_warp<<<148 * 3, 128, 0, s>>>(ra);

@@ -71,6 +71,38 @@ def test_batched_equals_single_matrix_solves(tde):
         assert np.max(np.abs(single - lam[a:b])) <= gate
 
 
+def test_forest_refill_roots_equal_warp_synchronous_rounds(tde):
+    """A forest takes the small-K secular kernel with refill (a group of lanes claims
+    the next root as soon as its root is done); a single matrix takes the
+    warp-synchronous rounds.  Both run each root through the same operations, so
+    with every root on the small-K path (warp_min_k above every K, no hand-over of
+    short lists) a matrix's eigenvalues must agree bit for bit between the two.
+    Matrices of one order below 1024 rows keep every other kernel the same: the
+    per-merge deflation kernels depend only on the merge order, and the lanes per
+    root only on the step's largest merge order."""
+    import torch
+
+    n = 1000
+    mats = [inputs.uniform11(n, 7), inputs.wilkinson_plus(n), inputs.glued_wilkinson(n),
+            inputs.toeplitz(n), inputs.paper_clustered(n), inputs.normal_absnormal(n, 3)]
+    rng = np.random.default_rng(11)
+    mats.append(inputs.lanczos_like(n, rng))
+    d = np.concatenate([m[0] for m in mats])
+    e = np.concatenate([np.append(m[1][: n - 1], 0.0) for m in mats])
+    off = np.arange(len(mats) + 1, dtype=np.int64) * n
+    tde.set_tuning(1 << 20, 1)
+    try:
+        forest = solve_batched(tde, d, e, off, 8)
+        for k, (dk, ek) in enumerate(mats):
+            single = tde.eigvals(torch.from_numpy(np.ascontiguousarray(dk)).cuda(),
+                                 torch.from_numpy(np.ascontiguousarray(ek[: n - 1])).cuda(),
+                                 leaf=8).cpu().numpy()
+            assert np.array_equal(single.view(np.int64), forest[k * n:(k + 1) * n].view(np.int64)), k
+    finally:
+        tde.set_tuning()
+    check_each(d, e, off, forest)
+
+
 def test_batched_edge_packings(tde):
     # empty matrices, order 1 and 2, a leaf-sized one and a larger one, mixed families
     parts = [inputs.uniform11(0), inputs.uniform11(1, seed=1), inputs.toeplitz(2), inputs.uniform11(0),
