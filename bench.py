@@ -420,6 +420,12 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         roof.update({"achieved": None, "frac": None,
                      "note": f"dominant kernel {dominant} is not an FP64 pair kernel"})
     roof["traffic"] = load_traffic(dominant)
+    executed = load_executed_rate(dominant)
+    if executed is not None:
+        # instruction-level reading of "% FP64 peak": FMA counted twice, against the
+        # measured FMA rate times two
+        executed["frac_of_measured"] = executed["executed_tflops"] / (2.0 * peak_tops)
+        roof["executed_fp64_ncu"] = executed
     roof["numerator_note"] = (
         "algorithmic FP64 operations of the work actually done: exact (pole, root) pairs "
         "at 5/3/7 operations plus the FP64 heads of the block-expansion series of distant "
@@ -881,6 +887,22 @@ def load_traffic(kernel: str):
     if not entry or entry.get("source_hash") != source_hash():
         return None
     return entry.get("dram_bytes_per_launch")
+
+
+def load_executed_rate(kernel: str):
+    """ncu's executed FP64 rate of `kernel`'s top launches ((dadd + dmul + 2 dfma) per
+    second over the launch) from a committed summary, if it was taken on the current
+    kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    entry = rec.get(kernel)
+    if not entry or entry.get("source_hash") != source_hash() or "executed_tflops" not in entry:
+        return None
+    return {k: entry[k] for k in ("executed_tflops", "launches", "what") if k in entry}
 
 
 def main():
