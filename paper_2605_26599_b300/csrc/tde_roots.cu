@@ -77,7 +77,9 @@ struct RootArgs {
 // in units of the root's interval width so that the sums stay in the float range.  It starts at the midpoint of the
 // interval (whose sign of w chooses the origin, the nearer pole), iterates the
 // third-order model until the step is below 2^-10 |tau| and ends with one sweep at
-// the final tau, which also supplies w'' there.  The FP64 stage starts from that
+// the final tau, which also supplies w'' there.  Where the model has no root in the
+// bracket (a root pressed against an origin pole of tiny z), the step goes straight
+// to z_org^2 / (the rest of w) instead of bisecting.  The FP64 stage starts from that
 // tau with the whole interval as bracket; each FP64 sweep gives w and w' to full
 // accuracy, w'' comes from a single-precision sweep at the same point (its error
 // enters the step at second order), and a third-order step below 2^-18 |tau| is
@@ -293,6 +295,7 @@ struct Stage32 {
   int org, jl, jr, sweeps;
   bool live;
   float rhoinv, tau, tlo, thi, lo_int, hi_int, ol, orr, gap, inv;
+  float zorg2;  // z_org^2 of the origin pole (its residue, in the stage's units too)
   double dorg, S, Sinv;
   Sec32 s;
 };
@@ -330,7 +333,8 @@ __device__ __forceinline__ bool s32_begin(const double* D, int K, int j, double 
   return true;
 }
 
-__device__ __forceinline__ void s32_first(const double* D, int K, int j, Stage32& st) {
+__device__ __forceinline__ void s32_first(const double* D, const double* Z, int K, int j,
+                                          Stage32& st) {
   st.sweeps = 1;
   if (j < K - 1) {
     const float h32 = st.tau;
@@ -352,6 +356,7 @@ __device__ __forceinline__ void s32_first(const double* D, int K, int j, Stage32
   st.dorg = D[st.org];
   st.ol = float((D[st.jl] - st.dorg) * st.Sinv);
   st.orr = float((D[st.jr] - st.dorg) * st.Sinv);
+  st.zorg2 = float(Z[st.org] * Z[st.org]);
   st.live = true;
 }
 
@@ -379,7 +384,16 @@ __device__ __forceinline__ bool s32_step(Stage32& st, float* eta_out, bool* have
   }
   float eta = 0.0f;
   const bool have = model_root(w, a, b, P1, P2, st.tau, st.tlo, st.thi, &eta);
-  const float nt = have ? st.tau + eta : 0.5f * (st.tlo + st.thi);
+  float nt = have ? st.tau + eta : 0.5f * (st.tlo + st.thi);
+  if (!have) {
+    // A root pressed against an origin pole of tiny z: that pole's term is invisible
+    // in the sums until tau nears z^2 / w, so the fitted model finds no root in the
+    // bracket.  With the rest of w about constant near the pole, the root sits at
+    // t = z_org^2 / (w + z_org^2 / tau): taken when it lies in the bracket and below
+    // half of |tau| (a ratio, so t keeps its relative accuracy in float).
+    const float t = st.zorg2 / (w + st.zorg2 / st.tau);
+    if (t > st.tlo && t < st.thi && fabsf(t) < 0.5f * fabsf(st.tau)) nt = t;
+  }
   if (nt == st.tau || !(nt > st.lo_int && nt < st.hi_int)) {  // no move: s is at tau
     st.live = false;
     return false;
@@ -448,7 +462,7 @@ __device__ int secular_root(const double* D, const double* Z, int K, int j, doub
   bool third = false, handed = false;
   if (s32_begin(D, K, j, rho, rhoinv, zsq, sw32, st)) {
     st.s = sw32(st.org, st.jl, st.tau, st.inv);
-    s32_first(D, K, j, st);
+    s32_first(D, Z, K, j, st);
     for (;;) {
       float eta = 0.0f;
       bool have = false;
@@ -509,7 +523,7 @@ __device__ int secular_root_sync(const double* D, const double* Z, int K, int j,
   const bool in32 = act && s32_begin(D, K, j, rho, rhoinv, zsq, sw32, st);
   if (in32) {
     st.s = sw32(st.org, st.jl, st.tau, st.inv);
-    s32_first(D, K, j, st);
+    s32_first(D, Z, K, j, st);
   }
   for (;;) {
     float eta = 0.0f;
@@ -1689,7 +1703,7 @@ __device__ void secular_roots_refill(const RootArgs& a, uint32_t total, SecTally
       } else {
         st.s = r32;
         if (phase == kRootF32First) {
-          s32_first(D, K, j, st);
+          s32_first(D, Z, K, j, st);
           phase = kRootF32;
         } else {
           s32_after(st, eta, have);
@@ -1785,7 +1799,7 @@ __device__ int secular_root_coop(const double* D, const double* Z, int K, int j,
   };
   const bool in32 = act && s32_begin(D, K, j, rho, rhoinv, zsq, cp, st);
   sweep32_all(in32, st.org, st.jl, st.tau, st.s);
-  if (in32) s32_first(D, K, j, st);
+  if (in32) s32_first(D, Z, K, j, st);
   for (;;) {
     float eta = 0.0f;
     bool have = false;
