@@ -902,7 +902,8 @@ def load_executed_rate(kernel: str):
     entry = rec.get(kernel)
     if not entry or entry.get("source_hash") != source_hash() or "executed_tflops" not in entry:
         return None
-    return {k: entry[k] for k in ("executed_tflops", "launches", "what") if k in entry}
+    return {"executed_tflops": entry["executed_tflops"], "launches": entry.get("launches"),
+            "what": entry.get("executed_what")}
 
 
 def main():
