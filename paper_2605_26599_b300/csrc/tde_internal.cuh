@@ -12,7 +12,7 @@
 //                         then the deflated eigenvalues of the merge, both sorted)
 //   compact roots         TAU (N doubles) + ORG (N int32): lambda_j = AD[ORG] + TAU
 //                         (Sec. 4.1 compact root representation)
-//   maps                  SEG, ROOTMAP, ROOTMAP2, SURV (N int32), PFLAG, RFLAG (N bytes)
+//   maps                  ROOTMAP, ROOTMAP2, SURV (N int32), PFLAG, RFLAG (N bytes)
 //   sort scratch          KEYA, KEYB (N uint64), IDXA, IDXB (N int32)
 //   plan                  merge and leaf descriptors, per-step merge state
 // Aliases once a buffer is dead within a level: LAMA (roots) -> D, ZHAT -> Z,
@@ -135,7 +135,7 @@ struct Workspace {
   double *D, *Z, *RLO, *RHI;
   double *AD, *AZ, *ALO, *AHI;
   double* TAU;
-  int32_t *ORG, *SEG, *ROOTMAP, *ROOTMAP2, *SURV;
+  int32_t *ORG, *ROOTMAP, *ROOTMAP2, *SURV;
   int32_t* ZPOS;    // negligible-z deflated positions of a merge (deflation step 5)
   int32_t* OUTIDX;  // per merge position: index of its deflated entry in [active | deflated]
   int32_t* ACTMAP;  // per survivor: index of the active pole its run ends in

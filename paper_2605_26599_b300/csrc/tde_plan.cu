@@ -83,9 +83,8 @@ size_t carve_workspace(const Plan& plan, void* base, Workspace* ws) {
   double** dbl[] = {&w.ds, &w.es, &w.LAM, &w.BLO, &w.BHI, &w.D, &w.Z, &w.RLO, &w.RHI,
                     &w.AD, &w.AZ, &w.ALO, &w.AHI, &w.TAU};
   for (double** p : dbl) *p = static_cast<double*>(take(8 * N));
-  int32_t** ints[] = {&w.ORG,  &w.SEG,  &w.ROOTMAP, &w.ROOTMAP2, &w.SURV,
-                      &w.IDXA, &w.IDXB, &w.ZPOS,    &w.OUTIDX,   &w.ACTMAP,
-                      &w.KEEPIDX};
+  int32_t** ints[] = {&w.ORG,  &w.ROOTMAP, &w.ROOTMAP2, &w.SURV,   &w.IDXA,
+                      &w.IDXB, &w.ZPOS,    &w.OUTIDX,   &w.ACTMAP, &w.KEEPIDX};
   for (int32_t** p : ints) *p = static_cast<int32_t*>(take(4 * N));
   w.PFLAG = static_cast<uint8_t*>(take(N));
   w.RFLAG = static_cast<uint8_t*>(take(N + 1));
