@@ -323,10 +323,26 @@ def run_ours(args, rank: int, world: int, dist) -> None:
         one_step()
     torch.cuda.synchronize()
 
+    # stage pass, outside the timed region: an event pair around every kernel of
+    # every stage, for the per-stage times and the choice of the dominant stage
+    tde.profile_select(None)
+    tde.profile_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    tde.profile_enable(False)
+    kprof_all = tde.profile_collect()
+    ktimes = {k: v[0] / args.steps for k, v in kprof_all.items()}
+    dominant = max(ktimes, key=ktimes.get)
+
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
         time.sleep(0.3)
+    # timed region: events around the dominant stage's kernels only, so the
+    # other stages run without event records between their launches
+    tde.profile_select([dominant])
     tde.profile_enable(True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -351,6 +367,7 @@ def run_ours(args, rank: int, world: int, dist) -> None:
     wall = time.perf_counter() - wall0
     tde.profile_enable(False)
     kprof = tde.profile_collect()
+    tde.profile_select(None)
     clocks = sampler.stop() if sampler else None
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     fam_ms = {name: float(np.mean([a.elapsed_time(b) for a, b in fam_ev[name]])) for name in FAMILIES}
@@ -396,10 +413,8 @@ def run_ours(args, rank: int, world: int, dist) -> None:
     # roofline of the dominant kernel
     fma_per_s = tde.measure_fp64_peak()
     peak_tops = fma_per_s / 1e12  # FP64 operations per second, one per FMA
-    ktimes = {k: v[0] / args.steps for k, v in kprof.items()}
-    klaunch = {k: v[1] / args.steps for k, v in kprof.items()}
-    total_k = sum(ktimes.values())
-    dominant = max(ktimes, key=ktimes.get)
+    dom_ms = kprof[dominant][0] / args.steps  # live, from the timed region
+    klaunch = {k: v[1] / args.steps for k, v in kprof_all.items()}
     roof = {"bound": "alu", "kernel": dominant, "unit": "T FP64 ops/s (FMA counted once)",
             "peak": peak_tops,
             "peak_source": "FP64 FMA-chain microbenchmark run in this process; "
@@ -408,14 +423,16 @@ def run_ours(args, rank: int, world: int, dist) -> None:
             "ops_per_unit": OPS_PER_UNIT}
     if dominant in OPS:
         ops = stage_ops(dominant, work)
-        achieved = ops / (ktimes[dominant] * 1e-3) / 1e12
+        achieved = ops / (dom_ms * 1e-3) / 1e12
         roof.update({"achieved": achieved, "frac": achieved / peak_tops,
                      "frac_nominal": achieved / (NOMINAL_FP64_OPS / 1e12),
                      "algorithmic_ops_per_step": ops,
                      "units_per_step": {"exact_pairs": work[OPS[dominant][1]],
                                         "series_ops": work[OPS[dominant][2]]},
+                     "ms_per_step": dom_ms, "timing": "CUDA events around the stage's kernels "
+                                                      "inside the timed region",
                      "launches_per_step": klaunch[dominant],
-                     "avg_launch_ms": ktimes[dominant] / max(klaunch[dominant], 1)})
+                     "avg_launch_ms": dom_ms / max(klaunch[dominant], 1)})
     else:
         roof.update({"achieved": None, "frac": None,
                      "note": f"dominant kernel {dominant} is not an FP64 pair kernel"})
@@ -468,7 +485,10 @@ def run_ours(args, rank: int, world: int, dist) -> None:
                    "l2": "flushed between steps (256 MB write outside the event-timed region); "
                          "inputs are smaller than L2",
                    "per_family_ms": fam_ms, "step_ms_min": float(min(step_ms)),
-                   "kernel_ms_per_step": ktimes, "kernel_events_in_timed_region": True,
+                   "kernel_ms_per_step": ktimes,
+                   "kernel_ms_source": "stage pass before the timed region (events around "
+                                       "every kernel); inside the timed region only the "
+                                       f"{dominant} stage carries events",
                    "wall_s_timed_region": wall, "work_per_step": work},
         "gpu_launches": launches,
         "roofline": roof,

@@ -240,6 +240,10 @@ int64_t tde_last_launch_count(void);
  * deflation and placement, 10 requested-row update) and clears the record.
  * Do not enable it while the stream is being captured into a CUDA graph. */
 int tde_profile_enable(int on);
+/* Kernel classes the profiler records on this thread: bit c of mask selects class c
+ * (numbering as above); 0 selects every class (the default).  Recording fewer
+ * classes puts fewer event records between the kernels of a timed region. */
+int tde_profile_select(uint32_t mask);
 int tde_profile_collect(int nids, double* ms, int64_t* launches);
 /* Like tde_profile_collect, with a per-merge-step breakdown: ms and launches hold
  * (nsteps + 1) rows of nids entries; row 0 is the total, row s + 1 the launches of

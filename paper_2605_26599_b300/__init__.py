@@ -21,7 +21,7 @@ from ._lib import TdeError  # noqa: F401
 
 __all__ = ["eigvals", "eigvals_batched", "eigvals_backward", "TdeEigvals", "eigvals_autograd", "workspace_bytes", "batched_workspace_bytes",
            "get_info", "measure_fp64_peak", "last_launch_count", "TdeError", "Workspace",
-           "profile_enable", "profile_collect", "read_work"]
+           "profile_enable", "profile_select", "profile_collect", "read_work"]
 
 
 def _torch():
@@ -387,6 +387,14 @@ def last_launch_count() -> int:
 def profile_enable(on: bool = True) -> None:
     """Record a CUDA event pair around every kernel of subsequent calls on this thread."""
     _lib.check("tde_profile_enable", _lib.load().tde_profile_enable(1 if on else 0))
+
+
+def profile_select(classes=None) -> None:
+    """Restrict the profiler to the named kernel classes on this thread (None: all)."""
+    mask = 0
+    for name in classes or ():
+        mask |= 1 << _lib.KERNEL_NAMES.index(name)
+    _lib.check("tde_profile_select", _lib.load().tde_profile_select(mask))
 
 
 def profile_collect() -> dict:

@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "TDE_OK", -1: "TDE_EINVAL", -2: "TDE_ECUDA", -3: "TDE_EWORKSP
 # every symbol include/tde.h declares
 EXPORTS = ("tde_eigvals_workspace", "tde_eigvals", "tde_eigvals_batched_workspace",
            "tde_eigvals_batched", "tde_get_info", "tde_measure_fp64_peak",
-           "tde_last_launch_count", "tde_profile_enable", "tde_profile_collect", "tde_read_work",
+           "tde_last_launch_count", "tde_profile_enable", "tde_profile_select", "tde_profile_collect", "tde_read_work",
            "tde_eigvals_noalloc", "tde_plan_query", "tde_check_reciprocal",
            "tde_profile_collect_steps", "tde_set_tuning", "tde_get_tuning",
            "tde_eigvals_backward_workspace", "tde_eigvals_backward", "tde_eigvecs_rows_workspace",
@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
     lib.tde_last_launch_count.restype = ctypes.c_int64
     lib.tde_last_launch_count.argtypes = []
     lib.tde_profile_enable.argtypes = [ctypes.c_int]
+    lib.tde_profile_select.argtypes = [ctypes.c_uint32]
     lib.tde_profile_collect.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_int64)]
     lib.tde_read_work.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]

@@ -21,6 +21,7 @@ static thread_local int g_prof_step = -1;
 static thread_local Tuning g_tuning;
 Tuning& thread_tuning() { return g_tuning; }
 static thread_local bool g_prof_on = false;
+static thread_local uint32_t g_prof_mask = 0xffffffffu;  // kernel classes recorded
 static thread_local std::vector<cudaEvent_t> g_pool;
 static thread_local size_t g_pool_next = 0;
 static thread_local std::vector<ProfRec> g_recs;
@@ -35,13 +36,13 @@ static cudaEvent_t next_event() {
   return g_pool[g_pool_next++];
 }
 void prof_begin(int id, cudaStream_t s) {
-  if (!g_prof_on) return;
+  if (!g_prof_on || !((g_prof_mask >> id) & 1u)) return;
   cudaEvent_t e = next_event();
   cudaEventRecord(e, s);
   g_open[id] = e;
 }
 void prof_end(int id, cudaStream_t s) {
-  if (!g_prof_on) return;
+  if (!g_prof_on || !((g_prof_mask >> id) & 1u)) return;
   cudaEvent_t e = next_event();
   cudaEventRecord(e, s);
   g_recs.push_back(ProfRec{id, g_prof_step, g_open[id], e});
@@ -303,6 +304,11 @@ int tde_plan_query(int64_t batch, const int64_t* offsets_host, int32_t leaf, int
 
 int tde_profile_enable(int on) {
   g_prof_on = on != 0;
+  return TDE_OK;
+}
+
+int tde_profile_select(uint32_t mask) {
+  g_prof_mask = mask != 0u ? mask : 0xffffffffu;
   return TDE_OK;
 }
 

@@ -61,3 +61,37 @@ def test_refined_rsqrt_matches_cuda_and_ieee(lib):
     assert (np.abs(got - ieee) / ieee).max() <= 2 * EPS
     assert (np.abs(got - cuda) / cuda).max() <= 2 * EPS
     assert lib.tde_check_rsqrt(-1, None, None, None) == -1
+
+
+def test_profile_select_records_only_the_chosen_classes(lib):
+    import torch
+
+    import paper_2605_26599_b300 as tde
+
+    n = 4096
+    d = torch.full((n,), 2.0, dtype=torch.float64, device="cuda")
+    e = torch.full((n - 1,), -1.0, dtype=torch.float64, device="cuda")
+    tde.eigvals(d, e)
+    torch.cuda.synchronize()
+    try:
+        tde.profile_select(None)
+        tde.profile_enable(True)
+        lam_all = tde.eigvals(d, e)
+        tde.profile_enable(False)
+        every = tde.profile_collect()
+        tde.profile_select(["secular", "rows"])
+        tde.profile_enable(True)
+        lam_sel = tde.eigvals(d, e)
+        tde.profile_enable(False)
+        chosen = tde.profile_collect()
+    finally:
+        tde.profile_enable(False)
+        tde.profile_select(None)
+    assert every["secular"][1] > 0 and every["rows"][1] > 0 and every["deflate"][1] > 0
+    for name, (ms, count) in chosen.items():
+        if name in ("secular", "rows"):
+            assert count == every[name][1] and ms > 0.0
+        else:
+            assert count == 0 and ms == 0.0
+    # recording fewer events changes no result
+    assert torch.equal(lam_all, lam_sel)
