@@ -102,6 +102,11 @@ enum WorkCounter {
   kNumWork
 };
 
+// A forest's small-K root list is ordered by descending K (bins of K, the last bin
+// holding every K >= kOrderBins - 1), so that the roots held by the groups of one
+// warp at any time have nearly equal K and their sweeps end together.
+constexpr int kOrderBins = 512;
+
 struct Status {
   int32_t info;
   uint32_t claim_next;  // next entry of a dynamically claimed work list (see claim_begin)
@@ -110,6 +115,8 @@ struct Status {
   uint32_t root_count[kMaxSteps];      // roots of small-K merges per step
   uint32_t root_count_big[kMaxSteps];  // roots of merges with K >= warp_min_k
   unsigned long long work[kNumWork];
+  uint32_t order_hist[kOrderBins];    // forests: roots of the step's small-K merges per bin of K
+  uint32_t order_cursor[kOrderBins];  // next list entry of each bin (descending K)
 };
 
 // Kernel classes timed by the optional per-launch event profiler.

@@ -342,6 +342,7 @@ struct DeflateArgs {
   MState* ms;
   Status* st;
   int32_t warp_min_k;
+  int32_t order_small;  // forests: small-K merges get their list range from k_order_assign
 };
 
 
@@ -592,16 +593,20 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
       }
     }
     // 9. roots of this merge get a contiguous range of one of the step's two root
-    //    lists: merges with K >= warp_min_k are solved one warp per root
+    //    lists: merges with K >= warp_min_k are solved one warp per root.  In a
+    //    forest a small-K merge only counts its roots into its bin of K here, and
+    //    k_order_assign gives it its range once the step's histogram is complete.
     __shared__ int s_base;
     const bool big = K >= a.warp_min_k;
+    const bool ordered = a.order_small != 0 && !big;
     if (tid == 0) {
       s_base = K > 0 ? int(atomicAdd(big ? &a.st->root_count_big[a.step] : &a.st->root_count[a.step],
                                      unsigned(K)))
                      : 0;
+      if (ordered && K > 0) atomicAdd(&a.st->order_hist[min(K, kOrderBins - 1)], unsigned(K));
       MState st;
       st.K = K;
-      st.base = s_base;
+      st.base = ordered ? 0 : s_base;
       st.rho = rho;
       st.rhoinv = 1.0 / rho;
       st.zsq = zsq;
@@ -614,7 +619,8 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
     }
     __syncthreads();
     int32_t* rmap = big ? a.ROOTMAP2 : a.ROOTMAP;
-    for (int j = tid; j < K; j += NT) rmap[s_base + j] = int32_t(g);
+    if (!ordered)
+      for (int j = tid; j < K; j += NT) rmap[s_base + j] = int32_t(g);
     __syncthreads();
   }
 }
@@ -623,8 +629,10 @@ __global__ void __launch_bounds__(NT) k_deflate(DeflateArgs a) {
 // Deflation of a few large merges by thread-block clusters: the C CTAs of a
 // cluster share one merge, so its element-wise work (the FP64 run sums, rotations
 // and compaction of steps 2-5, 7-9 of k_deflate) is spread over C SMs instead of
-// one.  The steps and their results are those of k_deflate; what changes is how
-// the sequential pieces are cut:
+// one.  The steps, the run boundaries and the deflation decisions are those of
+// k_deflate; the segmented run sums are associated by CTA, so the rotated values
+// can differ from k_deflate's in the last bits (glued Wilkinson blocks, n = 2048:
+// eigenvalues within 8.9e-16).  What changes is how the sequential pieces are cut:
 //   * compactions (steps 2 and 5) count per CTA slice, exchange the counts and
 //     write at the exclusive prefix of the CTAs before;
 //   * run boundaries (step 3): each warp of the cluster walks one segment of the
@@ -1104,16 +1112,19 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
         AZ32[k] = __double2float_rn(a.AZ[lo + k]);
       }
     }
-    // 9. root list range and merge state (CTA 0), then the root map
+    // 9. root list range and merge state (CTA 0), then the root map (a forest's
+    //    small-K merge takes its range from k_order_assign instead)
     const bool big = K >= a.warp_min_k;
+    const bool ordered = a.order_small != 0 && !big;
     if (r == 0 && tid == 0) {
       const int base = K > 0 ? int(atomicAdd(big ? &a.st->root_count_big[a.step]
                                                  : &a.st->root_count[a.step],
                                              unsigned(K)))
                              : 0;
+      if (ordered && K > 0) atomicAdd(&a.st->order_hist[min(K, kOrderBins - 1)], unsigned(K));
       MState st;
       st.K = K;
-      st.base = base;
+      st.base = ordered ? 0 : base;
       st.rho = rho;
       st.rhoinv = 1.0 / rho;
       st.zsq = zsq;
@@ -1128,7 +1139,8 @@ __global__ void __launch_bounds__(NT, 1) k_deflate_cluster(DeflateArgs a) {
     cl.sync();
     const int base = cl.map_shared_rank(&slot, 0)->base;
     int32_t* rmap = big ? a.ROOTMAP2 : a.ROOTMAP;
-    for (int j = r * NT + tid; j < K; j += C * NT) rmap[base + j] = int32_t(g);
+    if (!ordered)
+      for (int j = r * NT + tid; j < K; j += C * NT) rmap[base + j] = int32_t(g);
     cl.sync();  // the slots are rewritten by the next merge
   }
 }
@@ -1219,6 +1231,57 @@ static int deflate_cluster_size(int64_t cnt, int64_t maxsize) {
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// A forest's small-K root list in descending order of K.  The deflation kernels
+// count each small-K merge's roots into its bin of K (Status::order_hist);
+// k_order_cursor turns that histogram into each bin's first list entry and
+// clears it for the next step, and k_order_assign gives every small-K merge of
+// the step its contiguous range (one atomic on its bin's cursor) and writes the
+// root map.  Which merges share a bin, and in which order, changes no result: a
+// root depends only on its own merge, wherever it sits in the list.
+__global__ void __launch_bounds__(kOrderBins) k_order_cursor(Status* st) {
+  __shared__ uint32_t s[kOrderBins];
+  const int t = threadIdx.x;
+  const int bin = kOrderBins - 1 - t;  // position t holds the t-th largest bin
+  const uint32_t v = st->order_hist[bin];
+  st->order_hist[bin] = 0u;
+  s[t] = v;
+  __syncthreads();
+  for (int o = 1; o < kOrderBins; o <<= 1) {  // inclusive scan over positions
+    const uint32_t add = t >= o ? s[t - o] : 0u;
+    __syncthreads();
+    s[t] += add;
+    __syncthreads();
+  }
+  st->order_cursor[bin] = s[t] - v;
+}
+
+__global__ void __launch_bounds__(256) k_order_assign(int64_t cnt, MState* __restrict__ ms,
+                                                       Status* st, int32_t* __restrict__ ROOTMAP) {
+  __shared__ int s_base[256], s_K[256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t g0 = int64_t(blockIdx.x) * 256; g0 < cnt; g0 += int64_t(gridDim.x) * 256) {
+    const int64_t g = g0 + threadIdx.x;
+    int K = 0, base = 0;
+    if (g < cnt) {
+      const MState m = ms[g];
+      if (m.K > 0 && !m.big) {
+        K = m.K;
+        base = int(atomicAdd(&st->order_cursor[min(K, kOrderBins - 1)], unsigned(K)));
+        ms[g].base = base;
+      }
+    }
+    s_base[threadIdx.x] = base;
+    s_K[threadIdx.x] = K;
+    __syncthreads();
+    for (int q = warp; q < 256; q += 8) {  // the root map, one warp per merge
+      const int Kq = s_K[q], bq = s_base[q];
+      for (int jj = lane; jj < Kq; jj += 32) ROOTMAP[bq + jj] = int32_t(g0 + q);
+    }
+    __syncthreads();
+  }
+}
+
 void launch_deflate(const DeflateArgs& da, int64_t maxsize, cudaStream_t s) {
   const int64_t cnt = da.cnt;
   const int c = deflate_cluster_size(cnt, maxsize);
@@ -1290,8 +1353,14 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
   da.ms = ws.mstate;
   da.st = ws.status;
   da.warp_min_k = plan.tune.warp_min_k;
+  da.order_small = (plan.batch > 1 && cnt > 0) ? 1 : 0;
   prof_begin(kKDeflate, s);
   launch_deflate(da, plan.step_maxsize[step], s);
+  if (da.order_small) {
+    k_order_cursor<<<1, kOrderBins, 0, s>>>(ws.status);
+    k_order_assign<<<int(std::min<int64_t>((cnt + 255) / 256, 148 * 8)), 256, 0, s>>>(
+        cnt, ws.mstate, ws.status, ws.ROOTMAP);
+  }
   prof_end(kKDeflate, s);
   if (sel) {
     prof_begin(kKSel, s);
@@ -1299,8 +1368,8 @@ void launch_step(const Plan& plan, const Workspace& ws, int step, double* lambda
     prof_end(kKSel, s);
   }
   // form, deflate + roots
-  int launches =
-      2 + launch_roots(plan, ws, step, M, s, recompute || sel != nullptr, rows_inu, roots);
+  int launches = 2 + (da.order_small ? 2 : 0) +
+                 launch_roots(plan, ws, step, M, s, recompute || sel != nullptr, rows_inu, roots);
   if (sel) {
     prof_begin(kKSelRows, s);
     launch_sel_rows(plan, ws, *sel, step, s);

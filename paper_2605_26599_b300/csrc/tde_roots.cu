@@ -1770,13 +1770,19 @@ __global__ void __launch_bounds__(128) k_secular_small(RootArgs a) {
 // instruction occupies the pipe for the whole warp however few lanes are active.
 // Same steps and stopping rules as secular_root; all 32 lanes must call it.
 // `co` supplies the cooperative sweeps: sweep32(src, org, jl, tau, inv) and
-// sweep64(src, dorg, tau, jl) sum the root of lane src.
-template <class Coop, class Copies>
+// sweep64(src, dorg, tau, jl) sum the root of lane src.  G < 32: the sweeps are
+// summed by groups of G lanes instead of the whole warp; a pass then takes G
+// rounds, in round i every group sums the root of its i-th lane, and the roots'
+// scalar work still runs once for all 32 roots.
+template <int G, class Coop, class Copies>
 __device__ int secular_root_coop(const double* D, const double* Z, int K, int j, double rho,
                                  double rhoinv, double zsq, bool valid, const Copies& cp, Coop& co,
                                  int* org_out, double* tau_out, bool* ok, int* n32) {
+  static_assert(G == 32 || (G >= 2 && G <= 16 && (G & (G - 1)) == 0), "lanes per sweep");
   constexpr unsigned kFull = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  const int first = lane & ~(G - 1);
+  const unsigned gm = (G == 32) ? kFull : (((1u << (G & 31)) - 1u) << first);
   *ok = true;
   *n32 = 0;
   const bool act = valid && K > 1;
@@ -1788,13 +1794,27 @@ __device__ int secular_root_coop(const double* D, const double* Z, int K, int j,
   st.inv = 1.0f;
   // cooperative single-precision sweeps of the flagged lanes at (org, jl, tf, st.inv)
   auto sweep32_all = [&](bool flag, int org, int jl, float tf, Sec32& out) {
-    unsigned m = __ballot_sync(kFull, flag);
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1;
-      const Sec32 s = co.sweep32(src, __shfl_sync(kFull, org, src), __shfl_sync(kFull, jl, src),
-                                 __shfl_sync(kFull, tf, src), __shfl_sync(kFull, st.inv, src));
-      if (lane == src) out = s;
+    if constexpr (G == 32) {
+      unsigned m = __ballot_sync(kFull, flag);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const Sec32 s = co.sweep32(src, __shfl_sync(kFull, org, src), __shfl_sync(kFull, jl, src),
+                                   __shfl_sync(kFull, tf, src), __shfl_sync(kFull, st.inv, src));
+        if (lane == src) out = s;
+      }
+    } else {
+#pragma unroll 1
+      for (int i = 0; i < G; ++i) {
+        const int src = first + i;
+        const bool f = __shfl_sync(kFull, flag, src);  // uniform within each group
+        if (!__any_sync(kFull, f)) continue;
+        if (f) {
+          const Sec32 s = co.sweep32(src, __shfl_sync(gm, org, src), __shfl_sync(gm, jl, src),
+                                     __shfl_sync(gm, tf, src), __shfl_sync(gm, st.inv, src));
+          if (lane == src) out = s;
+        }
+      }
     }
   };
   const bool in32 = act && s32_begin(D, K, j, rho, rhoinv, zsq, cp, st);
@@ -1824,13 +1844,27 @@ __device__ int secular_root_coop(const double* D, const double* Z, int K, int j,
   if (act && !handed) sec_init_point(D, K, j, rho, rhoinv, zsq, q);
   // cooperative FP64 sweeps of the flagged lanes at (q.dorg, q.tau, q.jl)
   auto sweep64_all = [&](bool flag) {
-    unsigned m = __ballot_sync(kFull, flag);
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1;
-      const SecSums s = co.sweep64(src, __shfl_sync(kFull, q.dorg, src), __shfl_sync(kFull, q.tau, src),
-                                   __shfl_sync(kFull, q.jl, src));
-      if (lane == src) q.s = s;
+    if constexpr (G == 32) {
+      unsigned m = __ballot_sync(kFull, flag);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const SecSums s = co.sweep64(src, __shfl_sync(kFull, q.dorg, src), __shfl_sync(kFull, q.tau, src),
+                                     __shfl_sync(kFull, q.jl, src));
+        if (lane == src) q.s = s;
+      }
+    } else {
+#pragma unroll 1
+      for (int i = 0; i < G; ++i) {
+        const int src = first + i;
+        const bool f = __shfl_sync(kFull, flag, src);
+        if (!__any_sync(kFull, f)) continue;
+        if (f) {
+          const SecSums s = co.sweep64(src, __shfl_sync(gm, q.dorg, src), __shfl_sync(gm, q.tau, src),
+                                       __shfl_sync(gm, q.jl, src));
+          if (lane == src) q.s = s;
+        }
+      }
     }
   };
   sweep64_all(act);
@@ -1950,8 +1984,8 @@ __global__ void __launch_bounds__(128, 3) k_secular_warp(RootArgs a) {
     int org = 0, n32 = 0;
     double tau = 0.0;
     bool ok = true;
-    const int sweeps = secular_root_coop(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.rhoinv, ms.zsq, valid,
-                                         cp, co, &org, &tau, &ok, &n32);
+    const int sweeps = secular_root_coop<32>(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.rhoinv, ms.zsq,
+                                             valid, cp, co, &org, &tau, &ok, &n32);
     if (valid) {
       secular_store(a, lo, j, org, tau, sweeps, K, ok, true);
       sweeps64 += unsigned(sweeps);
@@ -1978,6 +2012,73 @@ __global__ void __launch_bounds__(128, 3) k_secular_warp(RootArgs a) {
     atomicAdd(&a.st->work[kWorkSecular32Sweeps], (unsigned long long)sweeps32);
     atomicAdd(&a.st->work[kWorkRoots], (unsigned long long)roots);
   }
+  claim_finish_block(a.st);
+}
+
+// Cooperative sweeps by groups of G lanes (small merges: plain sums over all K
+// poles, no block expansion): the root of lane src, in src's group, lives in the
+// merge at row lo of order K, broadcast within the group.
+template <int G>
+struct GroupCoop {
+  const RootArgs* a;
+  int gl, lo, K;
+  unsigned gm;
+  __device__ __forceinline__ Sec32 sweep32(int src, int org, int jl, float tau, float inv) const {
+    const int slo = __shfl_sync(gm, lo, src), sK = __shfl_sync(gm, K, src);
+    const GroupSweep32<G> sw{{a->AD32 + slo, a->AZ32 + slo, sK}, gl, gm};
+    return sw(org, jl, tau, inv);
+  }
+  __device__ __forceinline__ SecSums sweep64(int src, double dorg, double tau, int jl) const {
+    const int slo = __shfl_sync(gm, lo, src), sK = __shfl_sync(gm, K, src);
+    const GroupSweep<G> sw{a->AD + slo, a->AZ + slo, sK, gl, gm};
+    return sw(dorg, tau, jl);
+  }
+};
+
+// The small-K list in tiles, one root per lane: warps claim tiles of T consecutive
+// entries, every sweep is summed by a group of G lanes (G rounds per pass, see
+// secular_root_coop), and the roots' scalar work (model steps, convergence tests,
+// stage hand-over) runs lane-parallel for the whole tile instead of on every lane
+// of a root's group.  Entry k of a tile sits in group k mod (32 / G), so a tile of
+// 32 / G entries fills every group's first round; T is 32 where the list gives each
+// warp four such tiles, else 16, else 32 / G.  Same steps and sums as
+// k_secular_group<G> and k_secular_small<G>, so the same roots bit for bit.  Used
+// for forests, whose lists are long and sorted by K (a tile's roots have nearly
+// equal K); a single matrix's shorter lists keep k_secular_group.
+template <int G>
+__global__ void __launch_bounds__(128) k_secular_lanes(RootArgs a) {
+  const uint32_t total = *a.count;
+  if (total < a.small_list_min) {  // the warp kernel takes a short list
+    claim_finish_block(a.st);
+    return;
+  }
+  constexpr uint32_t kGroups = 32 / G;
+  const uint32_t per_warp = total / (4 * ((gridDim.x * blockDim.x) >> 5));
+  const uint32_t T = per_warp >= 32 ? 32u : per_warp >= 16 ? 16u : kGroups;
+  const uint32_t tiles = (total + T - 1) / T;
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+  const unsigned gm = ((1u << G) - 1u) << (lane & ~(G - 1));
+  const uint32_t k = uint32_t(gl) * kGroups + uint32_t(lane / G);  // this lane's tile entry
+  SecTally tally;
+  for (uint32_t t = claim_next_item(a.st); t < tiles; t = claim_next_item(a.st)) {
+    const uint32_t r = t * T + k;
+    const bool valid = k < T && r < total;
+    const int g = valid ? a.ROOTMAP[r] : 0;
+    const MState ms = valid ? a.ms[g] : MState{};
+    const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
+    GroupCoop<G> co{&a, gl, lo, K, gm};
+    const Copies32 cp{a.AD32 + lo, a.AZ32 + lo, K};
+    int org = 0, n32 = 0;
+    double tau = 0.0;
+    bool ok = true;
+    const int sweeps = secular_root_coop<G>(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.rhoinv, ms.zsq,
+                                            valid, cp, co, &org, &tau, &ok, &n32);
+    if (valid) {
+      secular_store(a, lo, j, org, tau, sweeps, K, ok, true);
+      tally.add(sweeps, n32, K);
+    }
+  }
+  tally.flush(a.st);
   claim_finish_block(a.st);
 }
 
@@ -2913,26 +3014,25 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
       ++launches;
     }
   }
-  // The small-K list.  A forest (several matrices: many small merges whose roots'
-  // sweep counts vary) takes the refill kernel, where a group of G lanes claims the
-  // next root as soon as its root is done (4096 Lanczos-style tridiagonals: 212 ->
-  // 206 ms per solve); a single matrix keeps the warp-synchronous rounds, which were
-  // as fast there (n = 65536, four families: 19.68 against 19.74 ms).  Both give the
-  // same roots bit for bit.
+  // The small-K list.  A forest (several matrices, many small merges) sorts it by K
+  // (k_order_assign) and takes it in tiles of one root per lane with four-lane
+  // sweeps, whose scalar steps run once per root instead of on all four lanes of
+  // its group (4096 Lanczos-style tridiagonals: 192 -> 168.5 ms per solve); its
+  // thread-per-root steps keep the refill kernel.  A single matrix keeps the
+  // warp-synchronous rounds: its lists are too short for full tiles, and sorting
+  // them cost more launch time than it saved (n = 65536, four families: 36.02
+  // against 36.23 ms over the solver's stages).  All of them give the same roots
+  // bit for bit.
   if (plan.batch > 1) {
-    switch (G) {  // four blocks of 128 threads per SM (128 registers)
-      case 1: k_secular_small<1><<<148 * 4, 128, 0, s>>>(ra); break;
-      case 4: k_secular_small<4><<<148 * 4, 128, 0, s>>>(ra); break;
-      case 8: k_secular_small<8><<<148 * 4, 128, 0, s>>>(ra); break;
-      default: k_secular_small<16><<<148 * 4, 128, 0, s>>>(ra); break;
-    }
+    if (G == 1)
+      k_secular_small<1><<<148 * 4, 128, 0, s>>>(ra);  // four blocks of 128 threads per SM
+    else
+      k_secular_lanes<4><<<148 * 4, 128, 0, s>>>(ra);
   } else {
-    switch (G) {
-      case 1: k_secular_thread<<<tgrid, 128, 0, s>>>(ra); break;
-      case 4: k_secular_group<4><<<ggrid, 128, 0, s>>>(ra); break;
-      case 8: k_secular_group<8><<<ggrid, 128, 0, s>>>(ra); break;
-      default: k_secular_group<16><<<ggrid, 128, 0, s>>>(ra); break;
-    }
+    if (G == 1)
+      k_secular_thread<<<tgrid, 128, 0, s>>>(ra);
+    else
+      k_secular_group<4><<<ggrid, 128, 0, s>>>(ra);
   }
   // three resident blocks per SM (168 registers per thread); each warp claims tiles
   k_secular_warp<<<148 * 3, 128, 0, s>>>(ra);

@@ -71,15 +71,16 @@ def test_batched_equals_single_matrix_solves(tde):
         assert np.max(np.abs(single - lam[a:b])) <= gate
 
 
-def test_forest_refill_roots_equal_warp_synchronous_rounds(tde):
-    """A forest takes the small-K secular kernel with refill (a group of lanes claims
-    the next root as soon as its root is done); a single matrix takes the
-    warp-synchronous rounds.  Both run each root through the same operations, so
+def test_forest_tile_roots_equal_warp_synchronous_rounds(tde):
+    """A forest sorts its small-K list by K and takes it in tiles, one root per lane
+    with four-lane sweeps; a single matrix takes the warp-synchronous rounds of
+    four-lane groups.  Both run each root through the same operations and sums, so
     with every root on the small-K path (warp_min_k above every K, no hand-over of
     short lists) a matrix's eigenvalues must agree bit for bit between the two.
     Matrices of one order below 1024 rows keep every other kernel the same: the
     per-merge deflation kernels depend only on the merge order, and the lanes per
-    root only on the step's largest merge order."""
+    root only on the step's largest merge order.  These short lists give the tiles
+    of eight roots, one per group."""
     import torch
 
     n = 1000
@@ -101,6 +102,54 @@ def test_forest_refill_roots_equal_warp_synchronous_rounds(tde):
     finally:
         tde.set_tuning()
     check_each(d, e, off, forest)
+
+
+def test_forest_long_lists_tiles_equal_single_solves(tde):
+    """320 matrices of order 1000 (six families): the forest's small-K lists are long
+    enough for tiles of 16 and 32 roots per warp, whose rounds sweep the roots of
+    several lanes per group in turn.  Every matrix's eigenvalues equal its single
+    solve bit for bit, and one matrix of each family matches the oracle.  (Below
+    1024 rows the forest and the single solves deflate with the same kernels; above,
+    a single matrix's top merges take the cluster kernel, whose run sums round
+    differently.)"""
+    import torch
+
+    n = 1000
+    rng = np.random.default_rng(5)
+    mats = []
+    for k in range(320):
+        f = k % 6
+        if f == 0:
+            mats.append(inputs.uniform11(n, 100 + k))
+        elif f == 1:
+            mats.append(inputs.normal_absnormal(n, 200 + k))
+        elif f == 2:
+            mats.append(inputs.lanczos_like(n, rng))
+        elif f == 3:
+            mats.append(inputs.toeplitz(n))
+        elif f == 4:
+            mats.append(inputs.wilkinson_plus(n))
+        else:
+            mats.append(inputs.glued_wilkinson(n))
+    d = np.concatenate([m[0] for m in mats])
+    e = np.concatenate([np.append(m[1][: n - 1], 0.0) for m in mats])
+    off = np.arange(len(mats) + 1, dtype=np.int64) * n
+    tde.set_tuning(1 << 20, 1)
+    try:
+        forest = solve_batched(tde, d, e, off, 8)
+        for k, (dk, ek) in enumerate(mats):
+            single = tde.eigvals(torch.from_numpy(np.ascontiguousarray(dk)).cuda(),
+                                 torch.from_numpy(np.ascontiguousarray(ek[: n - 1])).cuda(),
+                                 leaf=8).cpu().numpy()
+            assert np.array_equal(single.view(np.int64), forest[k * n:(k + 1) * n].view(np.int64)), k
+    finally:
+        tde.set_tuning()
+    pick = [0, 1, 2, 4, 5, 9]  # one matrix of each family
+    sub_off = np.arange(len(pick) + 1, dtype=np.int64) * n
+    sub_d = np.concatenate([mats[k][0] for k in pick])
+    sub_e = np.concatenate([np.append(mats[k][1][: n - 1], 0.0) for k in pick])
+    sub_lam = np.concatenate([forest[k * n:(k + 1) * n] for k in pick])
+    check_each(sub_d, sub_e, sub_off, sub_lam, sample=256)
 
 
 def test_batched_edge_packings(tde):
