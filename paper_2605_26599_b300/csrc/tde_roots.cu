@@ -1541,43 +1541,11 @@ __global__ void k_secular_thread(RootArgs a) {
   tally.flush(a.st);
 }
 
-// small-K list, G lanes per root (the host picks G from the step's merge order);
-// a warp takes 32 / G consecutive roots per round, in step for secular_root_sync.
-template <int G>
-__global__ void __launch_bounds__(128) k_secular_group(RootArgs a) {
-  const uint32_t total = *a.count;
-  if (total < a.small_list_min) return;  // the warp kernel takes a short list
-  const int lane = threadIdx.x & 31, gl = lane & (G - 1);
-  const unsigned mask = ((G == 32) ? 0xffffffffu : ((1u << G) - 1u)) << (lane & ~(G - 1));
-  const uint32_t per = 32 / G;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  SecTally tally;
-  for (uint32_t base = gw * per; base < total; base += nw * per) {
-    const uint32_t r = base + uint32_t(lane) / G;
-    const bool valid = r < total;
-    const int g = valid ? a.ROOTMAP[r] : 0;
-    const MState ms = valid ? a.ms[g] : MState{};
-    const int j = int(r) - ms.base, lo = valid ? a.M[g].lo : 0, K = valid ? ms.K : 0;
-    GroupSweep<G> sw{a.AD + lo, a.AZ + lo, K, gl, mask};
-    GroupSweep32<G> sw32{{a.AD32 + lo, a.AZ32 + lo, K}, gl, mask};
-    int org = 0, n32 = 0;
-    double tau = 0.0;
-    bool ok = true;
-    const int sweeps = secular_root_sync(a.AD + lo, a.AZ + lo, K, j, ms.rho, ms.rhoinv, ms.zsq, valid, sw,
-                                         sw32, &org, &tau, &ok, &n32);
-    if (valid) {
-      secular_store(a, lo, j, org, tau, sweeps, K, ok, gl == 0);
-      tally.add(sweeps, n32, K);
-    }
-  }
-  if (gl == 0) tally.flush(a.st);
-}
-
 // ---------------------------------------------------------------------------
-// Small-K roots with refill.  secular_root_sync keeps the roots of a warp in step,
-// so a warp pays for as many sweeps of each kind as its slowest root needs, and the
-// FP64 units take a warp instruction's full time however few lanes it carries.
+// Small-K roots with refill (a forest's thread-per-root steps).  Warp-synchronous
+// rounds (secular_root_sync) keep the roots of a warp in step, so a warp pays for as
+// many sweeps of each kind as its slowest root needs, and the FP64 units take a warp
+// instruction's full time however few lanes it carries.
 // Here each group of G lanes runs its root through the same steps as a state
 // machine and claims the next root of the list as soon as its root is done.  A pass
 // of the loop gives every group that needs one a single-precision sweep; FP64
@@ -2041,10 +2009,10 @@ struct GroupCoop {
 // stage hand-over) runs lane-parallel for the whole tile instead of on every lane
 // of a root's group.  Entry k of a tile sits in group k mod (32 / G), so a tile of
 // 32 / G entries fills every group's first round; T is 32 where the list gives each
-// warp four such tiles, else 16, else 32 / G.  Same steps and sums as
-// k_secular_group<G> and k_secular_small<G>, so the same roots bit for bit.  Used
-// for forests, whose lists are long and sorted by K (a tile's roots have nearly
-// equal K); a single matrix's shorter lists keep k_secular_group.
+// warp at least two tiles of 32 / G, else 16, else 32 / G.  Same steps and sums as
+// the warp-synchronous rounds of four-lane groups and as k_secular_small<G>, so the
+// same roots bit for bit.  A forest sorts its list by K first, so a tile's roots have
+// nearly equal K.
 template <int G>
 __global__ void __launch_bounds__(128) k_secular_lanes(RootArgs a) {
   const uint32_t total = *a.count;
@@ -2054,7 +2022,7 @@ __global__ void __launch_bounds__(128) k_secular_lanes(RootArgs a) {
   }
   constexpr uint32_t kGroups = 32 / G;
   const uint32_t per_warp = total / (4 * ((gridDim.x * blockDim.x) >> 5));
-  const uint32_t T = per_warp >= 32 ? 32u : per_warp >= 16 ? 16u : kGroups;
+  const uint32_t T = per_warp >= 8 ? 32u : per_warp >= 4 ? 16u : kGroups;
   const uint32_t tiles = (total + T - 1) / T;
   const int lane = threadIdx.x & 31, gl = lane & (G - 1);
   const unsigned gm = ((1u << G) - 1u) << (lane & ~(G - 1));
@@ -2997,7 +2965,6 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
   // lanes per root for the small-K list, from the largest merge order of the step
   const int64_t k0 = plan.step_maxsize[step];
   const int G = k0 <= 24 ? 1 : 4;
-  const int ggrid = int(std::min<int64_t>((nrows * G + 127) / 128, 148 * 16));
   int launches = 2;
   prof_begin(kKSecular, s);
   if (roots) {
@@ -3014,26 +2981,20 @@ int launch_roots(const Plan& plan, const Workspace& ws, int step, const Merge* M
       ++launches;
     }
   }
-  // The small-K list.  A forest (several matrices, many small merges) sorts it by K
-  // (k_order_assign) and takes it in tiles of one root per lane with four-lane
-  // sweeps, whose scalar steps run once per root instead of on all four lanes of
-  // its group (4096 Lanczos-style tridiagonals: 192 -> 168.5 ms per solve); its
-  // thread-per-root steps keep the refill kernel.  A single matrix keeps the
-  // warp-synchronous rounds: its lists are too short for full tiles, and sorting
-  // them cost more launch time than it saved (n = 65536, four families: 36.02
-  // against 36.23 ms over the solver's stages).  All of them give the same roots
-  // bit for bit.
-  if (plan.batch > 1) {
-    if (G == 1)
-      k_secular_small<1><<<148 * 4, 128, 0, s>>>(ra);  // four blocks of 128 threads per SM
-    else
-      k_secular_lanes<4><<<148 * 4, 128, 0, s>>>(ra);
-  } else {
-    if (G == 1)
-      k_secular_thread<<<tgrid, 128, 0, s>>>(ra);
-    else
-      k_secular_group<4><<<ggrid, 128, 0, s>>>(ra);
-  }
+  // The small-K list: four-lane roots in tiles of one root per lane with four-lane
+  // sweeps, whose scalar steps run once per root instead of on all four lanes of its
+  // group (4096 Lanczos-style tridiagonals: 192 -> 168.5 ms per solve, where the list
+  // is also sorted by K; n = 65536, four families: 35.98 -> 35.80 ms over the
+  // solver's stages, unsorted, since the two ordering launches per step cost a
+  // single matrix more than they gain).  Steps of merges of at most 24 rows take one
+  // thread per root: the refill kernel in a forest, warp-synchronous rounds in a
+  // single matrix.  All of them give the same roots bit for bit.
+  if (G == 4)
+    k_secular_lanes<4><<<148 * 4, 128, 0, s>>>(ra);  // four blocks of 128 threads per SM
+  else if (plan.batch > 1)
+    k_secular_small<1><<<148 * 4, 128, 0, s>>>(ra);
+  else
+    k_secular_thread<<<tgrid, 128, 0, s>>>(ra);
   // three resident blocks per SM (168 registers per thread); each warp claims tiles
   k_secular_warp<<<148 * 3, 128, 0, s>>>(ra);
   }

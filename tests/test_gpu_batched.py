@@ -71,16 +71,15 @@ def test_batched_equals_single_matrix_solves(tde):
         assert np.max(np.abs(single - lam[a:b])) <= gate
 
 
-def test_forest_tile_roots_equal_warp_synchronous_rounds(tde):
-    """A forest sorts its small-K list by K and takes it in tiles, one root per lane
-    with four-lane sweeps; a single matrix takes the warp-synchronous rounds of
-    four-lane groups.  Both run each root through the same operations and sums, so
-    with every root on the small-K path (warp_min_k above every K, no hand-over of
-    short lists) a matrix's eigenvalues must agree bit for bit between the two.
-    Matrices of one order below 1024 rows keep every other kernel the same: the
-    per-merge deflation kernels depend only on the merge order, and the lanes per
-    root only on the step's largest merge order.  These short lists give the tiles
-    of eight roots, one per group."""
+def test_forest_roots_equal_single_solves(tde):
+    """A forest sorts its small-K list by K; a single matrix keeps the deflation
+    kernels' order.  Both take the list in tiles of one root per lane with four-lane
+    sweeps, and a root's operations and sums do not depend on where it sits in the
+    list or in its tile, so with every root on the small-K path (warp_min_k above
+    every K, no hand-over of short lists) a matrix's eigenvalues must agree bit for
+    bit between the two.  Matrices of one order below 1024 rows keep every other
+    kernel the same: the per-merge deflation kernels depend only on the merge order,
+    and the lanes per root only on the step's largest merge order."""
     import torch
 
     n = 1000
