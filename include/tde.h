@@ -183,8 +183,9 @@ int tde_measure_fp64_peak(double* fma_per_s);
 
 /* Launch-shape tuning for subsequent calls on this thread (0 restores a default):
  *   warp_min_k      merges whose active rank reaches this solve one warp per root
- *                   (default 256); smaller ones give four lanes of a warp to each
- *                   root, or one thread below order 24;
+ *                   (default 256); smaller ones sum each root's sweeps over four
+ *                   lanes of a warp (one root per lane for its other steps), or
+ *                   take one thread per root below order 24;
  *   small_list_min  a step with fewer small-merge roots than this hands them to the
  *                   warp-per-root kernels too (default 18944 = 148 SMs x 4 warps x 32).
  * They change the time, and the eigenvalues only at the level of rounding (the
