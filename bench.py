@@ -454,6 +454,10 @@ def run_ours(args, rank: int, world: int, dist) -> None:
             ops = stage_ops(k, work)
             kernel_rates[k] = {"ms_per_step": ktimes[k], "tops": ops / (ktimes[k] * 1e-3) / 1e12,
                                "frac_of_peak": ops / (ktimes[k] * 1e-3) / 1e12 / peak_tops}
+            ex = load_executed_rate(k)
+            if ex is not None:  # instruction-level rate of the stage's top launch (ncu)
+                ex["frac_of_measured"] = ex["executed_tflops"] / (2.0 * peak_tops)
+                kernel_rates[k]["executed_fp64_ncu"] = ex
 
     cpu = cpu_baseline(n, fams) if (world == 1 and not args.no_cpu_baseline) else None
     accuracy = None
