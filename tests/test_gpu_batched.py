@@ -151,6 +151,44 @@ def test_forest_long_lists_tiles_equal_single_solves(tde):
     check_each(sub_d, sub_e, sub_off, sub_lam, sample=256)
 
 
+def test_forest_packing_order_changes_no_root(tde):
+    """The forest's small-K list is sorted by K and taken in tiles, so permuting the
+    matrices of a packing reorders the list and regroups the tiles; each matrix's
+    eigenvalues must not change by a bit (orders below 1024 rows, so the deflation
+    kernels do not depend on the packing either)."""
+    rng = np.random.default_rng(21)
+    mats = []
+    for k in range(96):
+        n = int(rng.integers(40, 1000))
+        f = k % 4
+        if f == 0:
+            mats.append(inputs.uniform11(n, 300 + k))
+        elif f == 1:
+            mats.append(inputs.lanczos_like(n, rng))
+        elif f == 2:
+            mats.append(inputs.glued_wilkinson(n))
+        else:
+            mats.append(inputs.normal_absnormal(n, 400 + k))
+
+    def pack(order):
+        d = np.concatenate([mats[k][0] for k in order])
+        e = np.concatenate([np.append(mats[k][1][: len(mats[k][0]) - 1], 0.0) for k in order])
+        off = np.concatenate([[0], np.cumsum([len(mats[k][0]) for k in order])]).astype(np.int64)
+        return d, e, off
+
+    fwd = list(range(len(mats)))
+    rev = fwd[::-1]
+    da, ea, oa = pack(fwd)
+    db, eb, ob = pack(rev)
+    la = solve_batched(tde, da, ea, oa, 8)
+    lb = solve_batched(tde, db, eb, ob, 8)
+    for pos_b, k in enumerate(rev):
+        a0, a1 = int(oa[k]), int(oa[k + 1])
+        b0, b1 = int(ob[pos_b]), int(ob[pos_b + 1])
+        assert np.array_equal(la[a0:a1].view(np.int64), lb[b0:b1].view(np.int64)), k
+    check_each(da, ea, oa, la, sample=64)
+
+
 def test_batched_edge_packings(tde):
     # empty matrices, order 1 and 2, a leaf-sized one and a larger one, mixed families
     parts = [inputs.uniform11(0), inputs.uniform11(1, seed=1), inputs.toeplitz(2), inputs.uniform11(0),
