@@ -189,6 +189,25 @@ def test_forest_packing_order_changes_no_root(tde):
     check_each(da, ea, oa, la, sample=64)
 
 
+def test_forest_one_large_matrix_among_many_small(tde):
+    """A forest holding one matrix of order 40000 among 200 of orders 16 to 300: the
+    large matrix's top merges take the warp kernel with the block expansion while the
+    small merges of every level go through the K-sorted list and its tiles, in the
+    same launches.  Every matrix against the oracle (sampled indices for the large
+    one, all eigenvalues for the small ones)."""
+    rng = np.random.default_rng(33)
+    parts = [inputs.uniform11(40000, 7)]
+    for k in range(200):
+        n = int(rng.integers(16, 301))
+        parts.append(inputs.lanczos_like(n, rng) if k % 2 else inputs.glued_wilkinson(n))
+    sizes = [len(p[0]) for p in parts]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    d = np.concatenate([p[0] for p in parts])
+    e = np.concatenate([np.append(p[1][: len(p[0]) - 1], 0.0) for p in parts])
+    lam = solve_batched(tde, d, e, off, 8)
+    check_each(d, e, off, lam, sample=128)
+
+
 def test_batched_edge_packings(tde):
     # empty matrices, order 1 and 2, a leaf-sized one and a larger one, mixed families
     parts = [inputs.uniform11(0), inputs.uniform11(1, seed=1), inputs.toeplitz(2), inputs.uniform11(0),
